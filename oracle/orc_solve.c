@@ -1,0 +1,290 @@
+/*
+ * CPU oracle, part 3: cycles (Section 3, V- and W-cycle with Gauss-Seidel),
+ * smooth-error estimate (Alg. 2), and the adaptive drivers (Alg. 5, Alg. 6).
+ * TEST INFRASTRUCTURE ONLY (see oracle.h).
+ */
+#include "orc_internal.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+static double vsum(int32_t n, const double* x) {
+    double s = 0.0;
+    for (int32_t i = 0; i < n; ++i) s += x[i];
+    return s;
+}
+
+static double vdot(int32_t n, const double* x, const double* y) {
+    double s = 0.0;
+    for (int32_t i = 0; i < n; ++i) s += x[i] * y[i];
+    return s;
+}
+
+static double vnorm(int32_t n, const double* x) { return sqrt(vdot(n, x, x)); }
+
+static void remove_mean(int32_t n, double* x) {
+    double m = vsum(n, x) / (double)n;
+    for (int32_t i = 0; i < n; ++i) x[i] -= m;
+}
+
+void orc_coarse_solve(const orc_hier* h, const double* r, double* x) {
+    int32_t m = h->nL;
+    for (int32_t i = 0; i < m; ++i) {
+        double s = 0.0;
+        for (int32_t j = 0; j < m; ++j) s += h->Xinv[(size_t)i * m + j] * r[j];
+        x[i] = s;
+    }
+}
+
+/* One multigrid cycle on level l for A_l x = b (x holds the start value):
+ * nu_pre forward colour-ordered Gauss-Seidel sweeps, residual, restriction by
+ * P_l^T, gamma coarse cycles from zero, prolongation x += P_l x_c, nu_post
+ * backward sweeps. The coarsest level is solved directly. */
+static void cycle(const orc_hier* h, int32_t l, const double* b, double* x, int32_t gamma) {
+    if (l == h->nlev - 1) { orc_coarse_solve(h, b, x); return; }
+    const orc_level* L = &h->lev[l];
+    for (int32_t s = 0; s < h->nu_pre; ++s)
+        orc_mcgs_sweep(L->n, L->rowptr, L->col, L->val, L->colour, L->ncolour, b, x, 1);
+    double* r = (double*)orc_xmalloc(sizeof(double) * (size_t)L->n);
+    double* bc = (double*)orc_xmalloc(sizeof(double) * (size_t)L->nc);
+    double* xc = (double*)calloc((size_t)L->nc, sizeof(double));
+    orc_residual(L->n, L->rowptr, L->col, L->val, x, b, r);
+    for (int32_t I = 0; I < L->nc; ++I) {
+        double s = 0.0;
+        for (int32_t t = L->agg_ptr[I]; t < L->agg_ptr[I + 1]; ++t) {
+            int32_t u = L->agg_mem[t];
+            s += L->pval ? L->pval[u] * r[u] : r[u];
+        }
+        bc[I] = s;
+    }
+    for (int32_t g = 0; g < gamma; ++g) cycle(h, l + 1, bc, xc, gamma);
+    for (int32_t u = 0; u < L->n; ++u)
+        x[u] += L->pval ? L->pval[u] * xc[L->agg[u]] : xc[L->agg[u]];
+    for (int32_t s = 0; s < h->nu_post; ++s)
+        orc_mcgs_sweep(L->n, L->rowptr, L->col, L->val, L->colour, L->ncolour, b, x, 0);
+    free(r); free(bc); free(xc);
+}
+
+void orc_vcycle(const orc_hier* h, const double* r, double* c) {
+    memset(c, 0, sizeof(double) * (size_t)h->lev[0].n);
+    cycle(h, 0, r, c, 1);
+}
+
+void orc_wcycle(const orc_hier* h, const double* r, double* c) {
+    memset(c, 0, sizeof(double) * (size_t)h->lev[0].n);
+    cycle(h, 0, r, c, 2);
+}
+
+int32_t orc_start_vector(int32_t n, const int32_t* rowptr, const int32_t* col,
+                         const double* val, const orc_params* p, double* e) {
+    orc_uniform_pm1(p->seed, n, e);
+    int32_t* colour = (int32_t*)orc_xmalloc(sizeof(int32_t) * (size_t)n);
+    double* zero = (double*)calloc((size_t)n, sizeof(double));
+    if (!colour || !zero) { free(colour); free(zero); return ORC_ERR_OOM; }
+    int32_t nc = orc_colour(n, rowptr, col, p->seed, colour, NULL);
+    for (int32_t s = 0; s < p->relax_sweeps; ++s)
+        orc_mcgs_sweep(n, rowptr, col, val, colour, nc, zero, e, 1);
+    remove_mean(n, e);
+    double nr = vnorm(n, e);
+    if (nr > 0.0) for (int32_t i = 0; i < n; ++i) e[i] /= nr;
+    free(colour); free(zero);
+    return ORC_OK;
+}
+
+/* Preconditioner of Alg. 2: a W-cycle on the newest hierarchy while
+ * re <= numW, else the symmetric composite product over all hierarchies
+ * built so far, applied as z += B_j (r - A z) for j = 1..re, re..1. */
+static void precond(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                    orc_hier* const* hist, int32_t re, const orc_params* p,
+                    const double* r, double* z, double* t1, double* t2) {
+    if (re <= p->numW) { orc_wcycle(hist[re - 1], r, z); return; }
+    memset(z, 0, sizeof(double) * (size_t)n);
+    for (int32_t s = 0; s < 2 * re; ++s) {
+        int32_t j = (s < re) ? s : 2 * re - 1 - s;
+        orc_residual(n, rowptr, col, val, z, r, t1);
+        orc_vcycle(hist[j], t1, t2);
+        for (int32_t i = 0; i < n; ++i) z[i] += t2[i];
+    }
+}
+
+/* Alg. 2: flexible (Polak-Ribiere) PCG on A e = r from e = 0. */
+int32_t orc_smooth_error(int32_t n, const int32_t* rowptr, const int32_t* col,
+                         const double* val, const double* rhs, orc_hier* const* hist,
+                         int32_t re, const orc_params* p, double* e) {
+    int32_t iters = (re <= p->numW) ? p->iterW : p->iterV;
+    double *r = (double*)orc_xmalloc(sizeof(double) * (size_t)n),
+           *rold = (double*)orc_xmalloc(sizeof(double) * (size_t)n),
+           *z = (double*)orc_xmalloc(sizeof(double) * (size_t)n),
+           *pp = (double*)orc_xmalloc(sizeof(double) * (size_t)n),
+           *q = (double*)orc_xmalloc(sizeof(double) * (size_t)n),
+           *t1 = (double*)orc_xmalloc(sizeof(double) * (size_t)n),
+           *t2 = (double*)orc_xmalloc(sizeof(double) * (size_t)n),
+           *zero = (double*)calloc((size_t)n, sizeof(double));
+    if (!r || !rold || !z || !pp || !q || !t1 || !t2 || !zero) {
+        free(r); free(rold); free(z); free(pp); free(q); free(t1); free(t2); free(zero);
+        return ORC_ERR_OOM;
+    }
+    memset(e, 0, sizeof(double) * (size_t)n);
+    memcpy(r, rhs, sizeof(double) * (size_t)n);
+    precond(n, rowptr, col, val, hist, re, p, r, z, t1, t2);
+    memcpy(pp, z, sizeof(double) * (size_t)n);
+    double rz = vdot(n, r, z);
+    for (int32_t it = 1; it <= iters; ++it) {
+        /* q = A p */
+        orc_residual(n, rowptr, col, val, pp, zero, q);
+        for (int32_t i = 0; i < n; ++i) q[i] = -q[i];
+        double pq = vdot(n, pp, q);
+        if (!(pq > 0.0) || !(rz > 0.0)) break;
+        double alpha = rz / pq;
+        for (int32_t i = 0; i < n; ++i) e[i] += alpha * pp[i];
+        memcpy(rold, r, sizeof(double) * (size_t)n);
+        for (int32_t i = 0; i < n; ++i) r[i] -= alpha * q[i];
+        if (it == iters) break;
+        precond(n, rowptr, col, val, hist, re, p, r, z, t1, t2);
+        double num = 0.0;
+        for (int32_t i = 0; i < n; ++i) num += z[i] * (r[i] - rold[i]);
+        double beta = num / rz;
+        rz = vdot(n, r, z);
+        for (int32_t i = 0; i < n; ++i) pp[i] = z[i] + beta * pp[i];
+    }
+    free(r); free(rold); free(z); free(pp); free(q); free(t1); free(t2); free(zero);
+    return ORC_OK;
+}
+
+#define ORC_MAX_HIST 4096
+
+int32_t orc_solve(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                  const double* b, double* x, const orc_params* p, const double* e0,
+                  orc_stats* stt, double* res_hist, int32_t cap) {
+    orc_stats st;
+    memset(&st, 0, sizeof(st));
+    for (int32_t i = 0; i < n; ++i) if (!isfinite(b[i]) || !isfinite(x[i])) return ORC_ERR_INVALID;
+    double bn = vnorm(n, b);
+    if (!(bn > 0.0)) return ORC_ERR_INVALID;
+    orc_hier** hist = (orc_hier**)calloc(ORC_MAX_HIST, sizeof(orc_hier*));
+    double *r = (double*)orc_xmalloc(sizeof(double) * (size_t)n),
+           *c = (double*)orc_xmalloc(sizeof(double) * (size_t)n),
+           *e = (double*)orc_xmalloc(sizeof(double) * (size_t)n);
+    int32_t status = ORC_OK, re = 0;
+    double oc_sum = 0.0;
+    if (!hist || !r || !c || !e) { status = ORC_ERR_OOM; goto out; }
+    remove_mean(n, x);
+    orc_residual(n, rowptr, col, val, x, b, r);
+    double res = vnorm(n, r);
+    if (e0) memcpy(e, e0, sizeof(double) * (size_t)n);
+    else if ((status = orc_start_vector(n, rowptr, col, val, p, e))) goto out;
+    hist[0] = orc_build(n, rowptr, col, val, e, p, &status);
+    if (!hist[0]) goto out;
+    re = 1;
+    oc_sum += orc_hier_oc(hist[0]);
+    int32_t k = 0;
+    double wsum = 0.0;
+    int32_t wcnt = 0;
+    if (res_hist && cap > 0) res_hist[0] = res / bn;
+    while (k < p->max_iter && res / bn > p->tol) {
+        /* x_{k+1} = V-cycle on the current hierarchy, then orthogonal to 1 */
+        orc_vcycle(hist[re - 1], r, c);
+        for (int32_t i = 0; i < n; ++i) x[i] += c[i];
+        remove_mean(n, x);
+        orc_residual(n, rowptr, col, val, x, b, r);
+        double nres = vnorm(n, r);
+        if (!isfinite(nres)) { status = ORC_ERR_DIVERGED; break; }
+        wsum += nres / res; ++wcnt;
+        res = nres;
+        ++k;
+        if (res_hist && k < cap) res_hist[k] = res / bn;
+        if (res / bn <= p->tol) break;
+        if (wsum / (double)wcnt > p->threshold && re < ORC_MAX_HIST) {
+            /* re-setup: Alg. 2 smooth error, Alg. 4 hierarchy, then x += e */
+            if ((status = orc_smooth_error(n, rowptr, col, val, r, hist, re, p, e))) break;
+            double* eh = c;
+            memcpy(eh, e, sizeof(double) * (size_t)n);
+            remove_mean(n, eh);
+            double en = vnorm(n, eh);
+            if (en > 0.0) for (int32_t i = 0; i < n; ++i) eh[i] /= en;
+            hist[re] = orc_build(n, rowptr, col, val, eh, p, &status);
+            if (!hist[re]) break;
+            oc_sum += orc_hier_oc(hist[re]);
+            ++re;
+            for (int32_t i = 0; i < n; ++i) x[i] += e[i];
+            remove_mean(n, x);
+            orc_residual(n, rowptr, col, val, x, b, r);
+            res = vnorm(n, r);
+            if (res_hist && k < cap) res_hist[k] = res / bn;
+            wsum = 0.0; wcnt = 0;
+        }
+    }
+    st.iters = k;
+    st.rel_res = res / bn;
+    if (status == ORC_OK && !(st.rel_res <= p->tol)) status = ORC_ERR_NOT_CONVERGED;
+out:
+    st.resetups = re > 0 ? re - 1 : 0;
+    st.levels = re > 0 && hist[re - 1] ? hist[re - 1]->nlev : 0;
+    st.oc_mean = re > 0 ? oc_sum / (double)re : 0.0;
+    st.status = status;
+    if (stt) *stt = st;
+    if (hist) for (int32_t j = 0; j < ORC_MAX_HIST; ++j) orc_hier_free(hist[j]);
+    free(hist); free(r); free(c); free(e);
+    return status;
+}
+
+int32_t orc_solve_zero_rhs(int32_t n, const int32_t* rowptr, const int32_t* col,
+                           const double* val, double* x, const orc_params* p,
+                           const double* e0, orc_stats* stt, double* res_hist, int32_t cap) {
+    orc_stats st;
+    memset(&st, 0, sizeof(st));
+    double *r = (double*)orc_xmalloc(sizeof(double) * (size_t)n),
+           *c = (double*)orc_xmalloc(sizeof(double) * (size_t)n),
+           *zero = (double*)calloc((size_t)n, sizeof(double)),
+           *e = (double*)orc_xmalloc(sizeof(double) * (size_t)n);
+    orc_hier* h = NULL;
+    int32_t status = ORC_OK, builds = 0;
+    double oc_sum = 0.0;
+    if (!r || !c || !zero || !e) { status = ORC_ERR_OOM; goto out; }
+    remove_mean(n, x);
+    orc_residual(n, rowptr, col, val, x, zero, r);
+    double r0 = vnorm(n, r), res = r0;
+    if (!(r0 > 0.0)) { status = ORC_OK; goto out; }
+    if (e0) memcpy(e, e0, sizeof(double) * (size_t)n);
+    else if ((status = orc_start_vector(n, rowptr, col, val, p, e))) goto out;
+    h = orc_build(n, rowptr, col, val, e, p, &status);
+    if (!h) goto out;
+    builds = 1; oc_sum += orc_hier_oc(h);
+    int32_t k = 0;
+    if (res_hist && cap > 0) res_hist[0] = 1.0;
+    while (k < p->max_iter && res / r0 > p->tol) {
+        orc_vcycle(h, r, c);
+        for (int32_t i = 0; i < n; ++i) x[i] += c[i];
+        remove_mean(n, x);
+        orc_residual(n, rowptr, col, val, x, zero, r);
+        double nres = vnorm(n, r);
+        if (!isfinite(nres)) { status = ORC_ERR_DIVERGED; break; }
+        double conv = nres / res;
+        res = nres;
+        ++k;
+        if (res_hist && k < cap) res_hist[k] = res / r0;
+        if (res / r0 <= p->tol) break;
+        if (conv > p->threshold) {
+            /* the exact error is the iterate itself: e = x / ||x|| */
+            double xn = vnorm(n, x);
+            for (int32_t i = 0; i < n; ++i) e[i] = x[i] / xn;
+            orc_hier_free(h);
+            h = orc_build(n, rowptr, col, val, e, p, &status);
+            if (!h) break;
+            ++builds; oc_sum += orc_hier_oc(h);
+        }
+    }
+    st.iters = k;
+    st.rel_res = res / r0;
+    if (status == ORC_OK && !(st.rel_res <= p->tol)) status = ORC_ERR_NOT_CONVERGED;
+out:
+    st.resetups = builds > 0 ? builds - 1 : 0;
+    st.levels = h ? h->nlev : 0;
+    st.oc_mean = builds > 0 ? oc_sum / (double)builds : 0.0;
+    st.status = status;
+    if (stt) *stt = st;
+    orc_hier_free(h);
+    free(r); free(c); free(zero); free(e);
+    return status;
+}

@@ -1,0 +1,87 @@
+"""Pins for the oracle's level operators: residual, colouring, smoother."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import oracle as O
+from paper_1806_07028_gb300 import inputs as I
+from tests.helpers import random_graph
+
+GRAPHS = [
+    lambda: I.workload("C1"),
+    lambda: I.grid3d(7, 6, 5, "checkerboard", block=2, xscale=100.0),
+    lambda: random_graph(60, 0.08, 3),
+    lambda: I.ring(50, 4),
+]
+
+
+@pytest.mark.parametrize("mk", GRAPHS)
+def test_residual_matches_scipy(mk):
+    g = mk()
+    rng = np.random.default_rng(0)
+    x, b = rng.standard_normal(g.n), rng.standard_normal(g.n)
+    r = O.residual(g, x, b)
+    ref = b - g.to_scipy() @ x
+    assert np.allclose(r, ref, rtol=0, atol=1e-12 * (np.abs(g.val).max() * np.abs(x).max() * 8 + 1))
+
+
+def test_laplacian_rows_sum_to_zero():
+    # Section 2.2: A 1 = 0, off-diagonals <= 0, symmetric
+    for mk in GRAPHS:
+        A = mk().to_scipy()
+        assert abs(A @ np.ones(A.shape[0])).max() < 1e-12 * abs(A).max() * 8
+        off = A - sp.diags(A.diagonal())
+        assert off.data.max() <= 0
+        assert abs(A - A.T).max() == 0
+
+
+def _greedy_colour_by_priority(g, seed):
+    """Sequential greedy colouring visiting vertices in decreasing (priority, id)."""
+    pri = [(O.splitmix64(seed ^ i), i) for i in range(g.n)]
+    order = sorted(range(g.n), key=lambda i: pri[i], reverse=True)
+    col = np.full(g.n, -1)
+    for v in order:
+        used = {col[u] for u in g.col[g.rowptr[v]:g.rowptr[v + 1]] if u != v and col[u] >= 0}
+        c = 0
+        while c in used:
+            c += 1
+        col[v] = c
+    return col
+
+
+@pytest.mark.parametrize("mk", GRAPHS)
+def test_colour_equals_priority_greedy(mk):
+    # Jones-Plassmann rounds colour a vertex exactly when every higher-priority
+    # neighbour is coloured, so the result equals the sequential greedy colouring
+    # in decreasing priority order.
+    g = mk()
+    col, nc, rounds = O.colour(g, seed=77)
+    assert np.array_equal(col, _greedy_colour_by_priority(g, 77))
+    assert nc == col.max() + 1
+    A = g.to_scipy().tocoo()
+    m = A.row != A.col
+    assert np.all(col[A.row[m]] != col[A.col[m]])
+
+
+@pytest.mark.parametrize("mk", GRAPHS)
+@pytest.mark.parametrize("forward", [True, False])
+def test_mcgs_equals_triangular_solve_in_colour_order(mk, forward):
+    # A forward GS sweep in a row order pi solves (D + L_pi) x_new = b - U_pi x_old
+    # for the matrix permuted by pi; rows of one colour are independent so any
+    # order inside a colour gives the same result.
+    g = mk()
+    col, nc, _ = O.colour(g, seed=5)
+    rng = np.random.default_rng(1)
+    b, x0 = rng.standard_normal(g.n), rng.standard_normal(g.n)
+    x = O.mcgs_sweep(g, col, nc, b, x0, forward=forward)
+    key = col if forward else (nc - 1 - col)
+    perm = np.lexsort((np.arange(g.n), key))
+    A = g.to_scipy()[perm][:, perm].tocsr()
+    lower = sp.tril(A, format="csr")
+    upper = sp.triu(A, k=1, format="csr")
+    xp = spla.spsolve_triangular(lower, b[perm] - upper @ x0[perm], lower=True)
+    ref = np.empty(g.n); ref[perm] = xp
+    assert np.allclose(x, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+    # and it is the same as a plain GS sweep in that order
+    assert np.allclose(O.gs_perm_sweep(g, perm, b, x0), x, rtol=0, atol=0)
