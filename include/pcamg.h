@@ -1,0 +1,216 @@
+/*
+ * pcamg.h -- C ABI of the GB300 (sm_103a) PC-alphaAMG library.
+ *
+ * PC-alphaAMG is the path-cover adaptive unsmoothed-aggregation algebraic
+ * multigrid method of Hu, Lin and Zikatanov, "An Adaptive Multigrid Method
+ * Based on Path Cover" (arXiv 1806.07028), for weighted graph Laplacians.
+ * Every step runs as a CUDA kernel of this library on one GPU.
+ *
+ * General rules
+ *  - Matrices are graph Laplacians (Section 2.2): CSR with int32 row pointers
+ *    and column indices (columns ascending in each row, diagonal stored) and
+ *    float64 values; symmetric, off-diagonals <= 0, zero row sums (up to
+ *    rounding), positive diagonal, connected graph.
+ *  - Pointers named d_* are device pointers, h_* host pointers. Inputs are
+ *    borrowed for the duration of the call only: the library copies what it
+ *    keeps. Outputs are caller-owned buffers the library writes.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). All device work
+ *    of a handle is enqueued on the stream given at setup. Calls synchronise
+ *    the stream where they must read sizes or scalars back, and before they
+ *    return results in host memory.
+ *  - Every call returns a pcamg_status; nothing is thrown across the ABI and the
+ *    library never exits or traps. pcamg_last_error(h) gives a message.
+ *  - A handle is not thread safe: use one handle from one host thread at a time.
+ */
+#ifndef PCAMG_H
+#define PCAMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define PCAMG_API __attribute__((visibility("default")))
+#else
+#define PCAMG_API
+#endif
+
+typedef struct pcamg_ctx* pcamg_handle;
+
+typedef enum {
+    PCAMG_OK = 0,
+    PCAMG_ERR_INVALID = 1,        /* bad argument or malformed CSR / vector */
+    PCAMG_ERR_NOT_LAPLACIAN = 2,  /* asymmetric, positive off-diagonal, row sum, ... */
+    PCAMG_ERR_OOM = 3,            /* device allocation failed */
+    PCAMG_ERR_CUDA = 4,           /* a CUDA runtime call or launch failed */
+    PCAMG_ERR_ROUND_CAP = 5,      /* an iterative setup round hit its cap */
+    PCAMG_ERR_SINGULAR = 6,       /* coarsest factorisation broke down */
+    PCAMG_ERR_NOT_CONVERGED = 7,  /* max_iter reached before tol (stats are filled) */
+    PCAMG_ERR_DIVERGED = 8,       /* NaN/Inf residual */
+    PCAMG_ERR_COARSE_TOO_BIG = 9, /* coarsening stalled above dense_max */
+    PCAMG_ERR_UNSUPPORTED = 10    /* feature not available in this build */
+} pcamg_status;
+
+enum { PCAMG_FP64 = 0, PCAMG_FP32_IR = 1 };                 /* precision */
+enum { PCAMG_START_RANDOM = 0, PCAMG_START_USER = 1 };      /* start vector */
+enum { PCAMG_P1_E_SCALED = 0, PCAMG_P1_BOOLEAN = 1 };       /* level-1 prolongation */
+
+/* Parameters. Defaults (pcamg_default_params) follow Section 4 of the paper:
+ * threshold 0.4 (Alg. 5(2)), numW 2, iterW 7, iterV 4, Gauss-Seidel smoothing,
+ * V-cycle, tol 1e-8. */
+typedef struct {
+    double tol;            /* stop when ||b - A x||_2 / ||b||_2 <= tol */
+    int32_t max_iter;      /* cap on V-cycle iterations */
+    double threshold;      /* re-setup when the mean convergence factor since the
+                              last setup exceeds it (Alg. 5) */
+    int32_t numW;          /* re-setups whose smooth error uses W-cycle PCG (Alg. 2) */
+    int32_t iterW;         /* PCG iterations with the W-cycle */
+    int32_t iterV;         /* PCG iterations with the composite V-cycle */
+    int32_t nu_pre;        /* forward multicolour Gauss-Seidel sweeps per level */
+    int32_t nu_post;       /* backward sweeps per level */
+    int32_t relax_sweeps;  /* sweeps on A u = 0 that smooth the random start */
+    uint64_t seed;         /* start vector and colouring priorities */
+    int32_t n_min;         /* stop coarsening at or below this many unknowns */
+    int32_t max_levels;    /* at most this many levels (<= 32) */
+    int32_t round_cap;     /* leftover rounds before the sequential tail (Alg. 3) */
+    int32_t p1_mode;       /* PCAMG_P1_*: level-1 prolongation carries e or is boolean */
+    int32_t precision;     /* PCAMG_FP64 or PCAMG_FP32_IR */
+    int32_t start;         /* PCAMG_START_RANDOM or PCAMG_START_USER (d_e0 given) */
+    int32_t dense_max;     /* largest coarsest level factorised densely (<= 4096) */
+    int32_t use_graphs;    /* capture each cycle in a CUDA graph and replay it */
+    int32_t keep_setup;    /* keep covers and reweighted graphs for export */
+    int32_t profile;       /* time the fine-level residual kernel with CUDA events */
+} pcamg_params;
+
+typedef struct {
+    int32_t iters;         /* V-cycle iterations done */
+    int32_t resetups;      /* hierarchies built inside the solve (initial one excluded) */
+    int32_t levels;        /* levels of the current hierarchy */
+    int32_t status;        /* pcamg_status of the solve */
+    double rel_res;        /* final ||b - A x|| / ||b|| (FP64, on the device) */
+    double oc_mean;        /* operator complexity averaged over all hierarchies */
+    double t_setup_ms;     /* host wall time inside re-setups (Alg. 2 + Alg. 4) */
+    double t_solve_ms;     /* host wall time of the whole call */
+    double* res_hist;      /* optional host buffer: ||r_k||/||b||, k = 0..iters */
+    int32_t res_hist_cap;  /* its capacity (0 = none) */
+    int32_t res_hist_len;  /* entries written */
+    /* fine-level residual kernel timing (params.profile != 0) */
+    int64_t prof_launches;
+    double prof_ms;        /* summed CUDA-event time of those launches */
+    double prof_bytes;     /* their algorithmic bytes: 12 nnz + 28 n each */
+} pcamg_stats;
+
+/* Fill p with the defaults above. */
+PCAMG_API pcamg_status pcamg_default_params(pcamg_params* p);
+
+/* Create a handle for A and build the first hierarchy (Alg. 5 setup, with the
+ * initial hierarchy built by Alg. 4 from a start vector instead of MWM).
+ * n >= 2, nnz = d_rowptr[n]. d_e0: start vector (device, length n) when
+ * p->start == PCAMG_START_USER, else NULL: the relaxed random start is used
+ * (uniform Philox4x64-10 numbers, relax_sweeps forward Gauss-Seidel sweeps on
+ * A u = 0, mean removed, unit 2-norm). The CSR is validated first; on error no
+ * handle is returned (*out = NULL). */
+PCAMG_API pcamg_status pcamg_setup(pcamg_handle* out, const pcamg_params* p, int32_t n,
+                                   int64_t nnz, const int32_t* d_rowptr, const int32_t* d_col,
+                                   const double* d_val, const double* d_e0, void* stream);
+
+/* PathCoverAMG_setup (Alg. 4) from the smooth error d_e (device, length n; it is
+ * copied, made orthogonal to 1 and normalised): reweighting on the A^2 pattern,
+ * path cover (Alg. 1), path-cover aggregation (Alg. 3) and Galerkin products on
+ * every level. The new hierarchy becomes the current one and joins the history
+ * used by the composite preconditioner (Alg. 2). */
+PCAMG_API pcamg_status pcamg_adapt(pcamg_handle h, const double* d_e);
+
+/* AdaptiveAMG for general b (Alg. 5): V-cycles on the current hierarchy, x kept
+ * orthogonal to 1, re-setup through Alg. 2 + Alg. 4 when the mean convergence
+ * factor since the last setup exceeds threshold. d_b (length n, sum zero) and
+ * d_x (initial guess in, solution out) are device pointers. st may be NULL. */
+PCAMG_API pcamg_status pcamg_solve(pcamg_handle h, const double* d_b, double* d_x,
+                                   pcamg_stats* st);
+
+/* AdaptiveAMG for b = 0 (Alg. 6): the iterate itself is the smooth error;
+ * rebuild when one step's convergence factor exceeds threshold. d_x holds the
+ * initial guess and receives the last iterate. The stopping test is relative
+ * to the first residual. */
+PCAMG_API pcamg_status pcamg_solve_zero_rhs(pcamg_handle h, double* d_x, pcamg_stats* st);
+
+/* End-to-end call on HOST buffers: copies A, b, x to the device, runs
+ * pcamg_setup + pcamg_solve, copies x back, frees everything. */
+PCAMG_API pcamg_status pcamg_solve_host(const pcamg_params* p, int32_t n, int64_t nnz,
+                                        const int32_t* h_rowptr, const int32_t* h_col,
+                                        const double* h_val, const double* h_b, double* h_x,
+                                        pcamg_stats* st, void* stream);
+
+/* One multigrid cycle (gamma = 1: V-cycle, 2: W-cycle) of hierarchy `hist`
+ * (0 = first built) as a correction: d_c = B d_r from a zero start, in the
+ * handle's precision (FP32_IR: r is scaled by ||r||_2 and cast to float, the
+ * correction is scaled back). Section 4: Gauss-Seidel pre- (forward colour
+ * order) and post- (backward) smoothing, restriction by P^T, prolongation by P,
+ * pinned dense solve on the coarsest level. */
+PCAMG_API pcamg_status pcamg_cycle(pcamg_handle h, int32_t hist, int32_t gamma,
+                                   const double* d_r, double* d_c);
+
+/* ApproximateSmoothError (Alg. 2) for residual d_r with the handle's current
+ * history: flexible PCG on A e = r from e = 0, preconditioned by a W-cycle on the
+ * newest hierarchy while the history holds <= numW hierarchies, else by the
+ * symmetric composite of V-cycles over all of them. Writes the raw PCG iterate. */
+PCAMG_API pcamg_status pcamg_smooth_error(pcamg_handle h, const double* d_r, double* d_e);
+
+/* The relaxed random start vector of this handle's parameters (device out). */
+PCAMG_API pcamg_status pcamg_start_vector(pcamg_handle h, double* d_e);
+
+/* Inspection. hist: 0-based hierarchy index; lev: 0-based level (0 = A).
+ * sizes[0]=n, [1]=nnz, [2]=nc (0 at the coarsest), [3]=colours, [4]=cover
+ * rounds (level 0), [5]=leftover rounds, [6]=pinned unknowns (coarsest),
+ * [7]=reweighted-graph nnz of this level (needs keep_setup). */
+PCAMG_API int32_t pcamg_num_hierarchies(pcamg_handle h);
+PCAMG_API int32_t pcamg_num_levels(pcamg_handle h, int32_t hist);
+PCAMG_API pcamg_status pcamg_level_sizes(pcamg_handle h, int32_t hist, int32_t lev,
+                                         int64_t sizes[8]);
+/* Copy one level to HOST buffers (any may be NULL): agg[n] coarse aggregate of
+ * each unknown (absent at the coarsest), nbr0/nbr1[n] its path-cover neighbours
+ * (smaller id first, -1 = none; needs keep_setup), the level matrix CSR,
+ * pval[n] the level-1 prolongation values (e-scaled mode, level 0 only),
+ * colour[n] smoother colours. */
+PCAMG_API pcamg_status pcamg_export_level(pcamg_handle h, int32_t hist, int32_t lev,
+                                          int32_t* agg, int32_t* nbr0, int32_t* nbr1,
+                                          int32_t* rowptr, int32_t* col, double* val,
+                                          double* pval, int32_t* colour);
+/* The reweighted graph of one level (level 0: the A^2 pattern with weights
+ * 1/max(|e_i - e_j|, 2^-52 max|e|), Alg. 4 step 2) as host CSR; needs keep_setup. */
+PCAMG_API pcamg_status pcamg_export_reweighted(pcamg_handle h, int32_t hist, int32_t lev,
+                                               int32_t* ptr, int32_t* col, double* w);
+
+PCAMG_API const char* pcamg_last_error(pcamg_handle h);
+PCAMG_API const char* pcamg_status_string(pcamg_status s);
+PCAMG_API void pcamg_destroy(pcamg_handle h);
+
+/* ---- single kernels, for measurement and parity tests -------------------- */
+/* r = b - A x (FP64), optionally ||r||_2^2 into *d_norm2 (device scalar, may be
+ * NULL). The fine-level residual of Alg. 5. Allocates a small device buffer of
+ * per-block partial sums when d_norm2 is given. */
+PCAMG_API pcamg_status pcamg_residual(int32_t n, const int32_t* d_rowptr, const int32_t* d_col,
+                                      const double* d_val, const double* d_x, const double* d_b,
+                                      double* d_r, double* d_norm2, void* stream);
+/* Same in FP32 (values, x, b, r float). */
+PCAMG_API pcamg_status pcamg_residual_f32(int32_t n, const int32_t* d_rowptr,
+                                          const int32_t* d_col, const float* d_val,
+                                          const float* d_x, const float* d_b, float* d_r,
+                                          void* stream);
+/* d_out[i] = (w_i >> 11) 2^-52 - 1, w_i = word i%4 of Philox4x64-10 with counter
+ * (i/4, 0, 0, 0) and key (seed, 0). */
+PCAMG_API pcamg_status pcamg_uniform(uint64_t seed, int64_t n, double* d_out, void* stream);
+/* Jones-Plassmann colouring of the pattern (rowptr, col): priority
+ * (splitmix64(seed ^ i), i), a round winner takes the smallest colour unused by
+ * its coloured neighbours. Writes d_colour[n]; *ncolour on the host. */
+PCAMG_API pcamg_status pcamg_colour(int32_t n, const int32_t* d_rowptr, const int32_t* d_col,
+                                    uint64_t seed, int32_t* d_colour, int32_t* ncolour,
+                                    void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

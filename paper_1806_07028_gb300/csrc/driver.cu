@@ -1,0 +1,441 @@
+// Cycles and the adaptive drivers:
+//  * the multigrid cycle of Section 4 (Gauss-Seidel pre/post smoothing in
+//    colour order, restriction by P^T, prolongation by P, dense coarsest solve),
+//    run in FP64 or in FP32 inside FP64 iterative refinement, optionally
+//    captured once per hierarchy in a CUDA graph;
+//  * ApproximateSmoothError (Alg. 2): flexible PCG with a W-cycle or the
+//    symmetric composite of V-cycles over all hierarchies;
+//  * AdaptiveAMG for general b (Alg. 5) and for b = 0 (Alg. 6).
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "pcamg_internal.cuh"
+
+namespace pc {
+
+// ---------------------------------------------------------------- basics
+void fail(pcamg_status s, const std::string& msg) { throw Error{s, msg}; }
+
+void check_cuda(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return;
+    cudaGetLastError();
+    pcamg_status s = (e == cudaErrorMemoryAllocation) ? PCAMG_ERR_OOM : PCAMG_ERR_CUDA;
+    throw Error{s, std::string(what) + ": " + cudaGetErrorString(e)};
+}
+
+void* Mem::alloc(size_t bytes) {
+    void* p = nullptr;
+    cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error{PCAMG_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed"};
+    }
+    live += bytes;
+    if (live > peak) peak = live;
+    return p;
+}
+
+void Mem::release(void* p, size_t bytes) {
+    cudaFreeAsync(p, stream);
+    live -= bytes;
+}
+
+Ctx::~Ctx() {
+    for (Hier* h : hist) delete h;
+    hist.clear();
+    if (h_red) cudaFreeHost(h_red);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+}
+
+void sync(Ctx& c) { PC_CUDA(cudaStreamSynchronize(c.stream)); }
+
+template <class T>
+void d2h(Ctx& c, T* host, const T* dev, size_t count) {
+    if (count == 0) return;
+    PC_CUDA(cudaMemcpyAsync(host, dev, sizeof(T) * count, cudaMemcpyDeviceToHost, c.stream));
+    sync(c);
+}
+template void d2h<int32_t>(Ctx&, int32_t*, const int32_t*, size_t);
+template void d2h<int64_t>(Ctx&, int64_t*, const int64_t*, size_t);
+template void d2h<double>(Ctx&, double*, const double*, size_t);
+
+int64_t read_i64(Ctx& c, const int64_t* dev) {
+    int64_t v = 0;
+    d2h(c, &v, dev, 1);
+    return v;
+}
+int32_t read_i32(Ctx& c, const int32_t* dev) {
+    int32_t v = 0;
+    d2h(c, &v, dev, 1);
+    return v;
+}
+double read_f64(Ctx& c, const double* dev) {
+    double v = 0;
+    d2h(c, &v, dev, 1);
+    return v;
+}
+
+// scalar slots after the reduction partials
+constexpr int kPartials = 4096;
+enum Slot { S_T0 = 0, S_T1, S_T2, S_NORM2, S_RZ, S_PQ, S_ALPHA, S_NUM, S_BETA, S_SCALE, S_INV, S_SUM, S_NSLOTS };
+static double* slot(Ctx& c, int k) { return c.red.p + kPartials + k; }
+static double* partials(Ctx& c) { return c.red.p; }
+
+void normalise_orth(Ctx& c, const double* e, double* out) {
+    cudaStream_t s = c.stream;
+    if (out != e) copy(s, c.n, e, out);
+    sum(s, c.n, out, partials(c), slot(c, S_SUM));
+    sub_mean(s, c.n, out, slot(c, S_SUM));
+    dot(s, c.n, out, out, partials(c), slot(c, S_T0));
+    scalar_ops(s, SOP_SQRT, slot(c, 0), S_T0, 0, S_T1);
+    scale_dev(s, c.n, out, nullptr, slot(c, S_T1));  // out *= 1 / ||out||
+}
+
+// ---------------------------------------------------------------- cycle
+template <class T>
+struct LV;
+template <>
+struct LV<double> {
+    static double* x(Level& L) { return L.x64.p; }
+    static double* b(Level& L) { return L.b64.p; }
+    static double* r(Level& L) { return L.r64.p; }
+    static const double* pv(Level& L) { return L.pval.p; }
+};
+template <>
+struct LV<float> {
+    static float* x(Level& L) { return L.x32.p; }
+    static float* b(Level& L) { return L.b32.p; }
+    static float* r(Level& L) { return L.r32.p; }
+    static const float* pv(Level& L) { return L.pval32.p; }
+};
+
+template <class T>
+static void smooth(Ctx& c, Level& L, const T* b, T* x, bool forward) {
+    for (int32_t t = 0; t < L.ncolour; ++t) {
+        int32_t k = forward ? t : L.ncolour - 1 - t;
+        int32_t beg = L.h_colour_ptr[k], end = L.h_colour_ptr[k + 1];
+        gs_colour<T>(c.stream, L.A, L.colour_rows_v + beg, end - beg, b, x);
+    }
+}
+
+template <class T>
+static void cycle_level(Ctx& c, Hier& h, int32_t l, int gamma) {
+    cudaStream_t s = c.stream;
+    Level& L = h.lev[l];
+    if (l == h.nlev - 1) {
+        coarse_apply<T>(s, L.n, h.Xinv.p, LV<T>::b(L), LV<T>::x(L));
+        return;
+    }
+    T* x = LV<T>::x(L);
+    T* b = LV<T>::b(L);
+    T* r = LV<T>::r(L);
+    for (int32_t k = 0; k < c.p.nu_pre; ++k) smooth<T>(c, L, b, x, true);
+    if constexpr (sizeof(T) == 8) residual64(s, L.A, x, b, r, nullptr, nullptr);
+    else residual32(s, L.A, x, b, r);
+    Level& C = h.lev[l + 1];
+    restrict_agg<T>(s, L.nc, L.agg_ptr.p, L.agg_mem.p, l == 0 ? LV<T>::pv(L) : nullptr, r, LV<T>::b(C));
+    PC_CUDA(cudaMemsetAsync(LV<T>::x(C), 0, sizeof(T) * C.n, s));
+    for (int g = 0; g < gamma; ++g) cycle_level<T>(c, h, l + 1, gamma);
+    prolong_add<T>(s, L.n, L.agg.p, l == 0 ? LV<T>::pv(L) : nullptr, LV<T>::x(C), x);
+    for (int32_t k = 0; k < c.p.nu_post; ++k) smooth<T>(c, L, b, x, false);
+}
+
+template <class T>
+static void cycle_body(Ctx& c, Hier& h, int gamma) {
+    Level& L0 = h.lev[0];
+    PC_CUDA(cudaMemsetAsync(LV<T>::x(L0), 0, sizeof(T) * L0.n, c.stream));
+    cycle_level<T>(c, h, 0, gamma);
+}
+
+static void run_body(Ctx& c, Hier& h, int gamma) {
+    bool f32 = c.p.precision == PCAMG_FP32_IR;
+    if (!c.p.use_graphs) {
+        if (f32) cycle_body<float>(c, h, gamma); else cycle_body<double>(c, h, gamma);
+        return;
+    }
+    cudaGraphExec_t& ge = h.graph[gamma - 1];
+    if (!ge) {
+        cudaGraph_t g = nullptr;
+        PC_CUDA(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
+        try {
+            if (f32) cycle_body<float>(c, h, gamma); else cycle_body<double>(c, h, gamma);
+        } catch (...) {
+            cudaStreamEndCapture(c.stream, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        PC_CUDA(cudaStreamEndCapture(c.stream, &g));
+        cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        PC_CUDA(e);
+    }
+    PC_CUDA(cudaGraphLaunch(ge, c.stream));
+}
+
+// out = B r, the correction of one cycle from a zero start
+void cycle(Ctx& c, Hier& h, int gamma, const double* r, double* out) {
+    cudaStream_t s = c.stream;
+    Level& L0 = h.lev[0];
+    if (c.p.precision == PCAMG_FP32_IR) {
+        // scale by ||r||_2 so the float cycle sees O(1) data, then scale back
+        dot(s, c.n, r, r, partials(c), slot(c, S_T0));
+        scalar_ops(s, SOP_SQRT, slot(c, 0), S_T0, 0, S_SCALE);
+        scalar_ops(s, SOP_INV, slot(c, 0), S_SCALE, 0, S_INV);
+        cast_scaled_f32(s, c.n, r, slot(c, S_INV), L0.b32.p);
+        run_body(c, h, gamma);
+        fill(s, c.n, 0.0, out);
+        add_scaled_f32(s, c.n, L0.x32.p, slot(c, S_SCALE), out);
+    } else {
+        copy(s, c.n, r, L0.b64.p);
+        run_body(c, h, gamma);
+        copy(s, c.n, L0.x64.p, out);
+    }
+}
+
+// ---------------------------------------------------------------- residual with profiling
+static void fine_residual(Ctx& c, const double* x, const double* b, double* r, double* norm2) {
+    Csr A;
+    A.n = c.n; A.nnz = c.nnz; A.rowptr = c.rowptr.p; A.col = c.col.p; A.val = c.val.p;
+    A.lpr = lanes_per_row(c.n, c.nnz);
+    if (c.p.profile) PC_CUDA(cudaEventRecord(c.ev0, c.stream));
+    residual64(c.stream, A, x, b, r, partials(c), norm2);
+    if (c.p.profile) {
+        PC_CUDA(cudaEventRecord(c.ev1, c.stream));
+        PC_CUDA(cudaEventSynchronize(c.ev1));
+        float ms = 0.f;
+        PC_CUDA(cudaEventElapsedTime(&ms, c.ev0, c.ev1));
+        c.prof_ms += ms;
+        c.prof_launches += 1;
+    }
+}
+
+static void spmv_A(Ctx& c, const double* x, double* y) {
+    Csr A;
+    A.n = c.n; A.nnz = c.nnz; A.rowptr = c.rowptr.p; A.col = c.col.p; A.val = c.val.p;
+    A.lpr = lanes_per_row(c.n, c.nnz);
+    spmv64(c.stream, A, x, y);
+}
+
+static void remove_mean(Ctx& c, double* x) {
+    sum(c.stream, c.n, x, partials(c), slot(c, S_SUM));
+    sub_mean(c.stream, c.n, x, slot(c, S_SUM));
+}
+
+// ---------------------------------------------------------------- Alg. 2
+static void precond(Ctx& c, const double* r, double* z) {
+    cudaStream_t s = c.stream;
+    int32_t re = (int32_t)c.hist.size();
+    if (re <= c.p.numW) {
+        cycle(c, *c.hist[re - 1], 2, r, z);
+        return;
+    }
+    fill(s, c.n, 0.0, z);
+    for (int32_t k = 0; k < 2 * re; ++k) {
+        int32_t j = (k < re) ? k : 2 * re - 1 - k;
+        Csr A;
+        A.n = c.n; A.nnz = c.nnz; A.rowptr = c.rowptr.p; A.col = c.col.p; A.val = c.val.p;
+        A.lpr = lanes_per_row(c.n, c.nnz);
+        residual64(s, A, z, r, c.w_t1.p, nullptr, nullptr);
+        cycle(c, *c.hist[j], 1, c.w_t1.p, c.w_t2.p);
+        axpy(s, c.n, 1.0, c.w_t2.p, z);
+    }
+}
+
+void smooth_error(Ctx& c, const double* rhs, double* e) {
+    cudaStream_t s = c.stream;
+    int32_t re = (int32_t)c.hist.size();
+    if (re < 1) fail(PCAMG_ERR_INVALID, "no hierarchy built");
+    int32_t iters = (re <= c.p.numW) ? c.p.iterW : c.p.iterV;
+    double* r = c.w_ein.p;  // running residual
+    double* rold = c.w_rold.p;
+    double* z = c.w_z.p;
+    double* pp = c.w_p.p;
+    double* q = c.w_q.p;
+    fill(s, c.n, 0.0, e);
+    copy(s, c.n, rhs, r);
+    precond(c, r, z);
+    copy(s, c.n, z, pp);
+    dot(s, c.n, r, z, partials(c), slot(c, S_RZ));
+    for (int32_t it = 1; it <= iters; ++it) {
+        spmv_A(c, pp, q);
+        dot(s, c.n, pp, q, partials(c), slot(c, S_PQ));
+        scalar_ops(s, SOP_PCG_ALPHA, slot(c, 0), S_RZ, S_PQ, S_ALPHA);  // alpha = rz/pq (0 on breakdown)
+        axpy_dev(s, c.n, slot(c, S_ALPHA), 1.0, pp, e);
+        copy(s, c.n, r, rold);
+        axpy_dev(s, c.n, slot(c, S_ALPHA), -1.0, q, r);
+        if (it == iters) break;
+        precond(c, r, z);
+        // beta = z^T (r - r_old) / (z_old^T r_old)   (Polak-Ribiere)
+        copy(s, c.n, r, c.w_t1.p);
+        axpy(s, c.n, -1.0, rold, c.w_t1.p);
+        dot(s, c.n, z, c.w_t1.p, partials(c), slot(c, S_NUM));
+        scalar_ops(s, SOP_DIV, slot(c, 0), S_NUM, S_RZ, S_BETA);
+        dot(s, c.n, r, z, partials(c), slot(c, S_RZ));
+        xpby_dev(s, c.n, z, slot(c, S_BETA), pp);
+    }
+}
+
+void start_vector(Ctx& c, double* e) {
+    cudaStream_t s = c.stream;
+    philox_uniform(s, c.p.seed, c.n, e);
+    fill(s, c.n, 0.0, c.w_t1.p);
+    Csr A;
+    A.n = c.n; A.nnz = c.nnz; A.rowptr = c.rowptr.p; A.col = c.col.p; A.val = c.val.p;
+    A.lpr = lanes_per_row(c.n, c.nnz);
+    for (int32_t k = 0; k < c.p.relax_sweeps; ++k) {
+        for (int32_t t = 0; t < c.ncolour0; ++t) {
+            int32_t beg = c.h_colour_ptr0[t], end = c.h_colour_ptr0[t + 1];
+            gs_colour<double>(s, A, c.colour_rows0.p + beg, end - beg, c.w_t1.p, e);
+        }
+    }
+    normalise_orth(c, e, e);
+}
+
+// ---------------------------------------------------------------- Alg. 5 / Alg. 6
+static double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+static double read_norm(Ctx& c) {
+    PC_CUDA(cudaMemcpyAsync(c.h_red, slot(c, S_NORM2), sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    sync(c);
+    return std::sqrt(c.h_red[0]);
+}
+
+static void rebuild(Ctx& c, double* e_raw_out) {
+    smooth_error(c, c.w_r.p, e_raw_out);
+    normalise_orth(c, e_raw_out, c.w_eh.p);
+    Hier* h = build_hierarchy(c, c.w_eh.p);
+    c.hist.push_back(h);
+}
+
+pcamg_status solve(Ctx& c, const double* b, double* x, pcamg_stats* st) {
+    cudaStream_t s = c.stream;
+    double t0 = now_ms(), t_setup = 0.0;
+    c.prof_ms = 0.0;
+    c.prof_launches = 0;
+    int32_t re0 = (int32_t)c.hist.size();
+    dot(s, c.n, b, b, partials(c), slot(c, S_NORM2));
+    double bn = read_norm(c);
+    if (!std::isfinite(bn) || !(bn > 0.0)) fail(PCAMG_ERR_INVALID, "right-hand side is zero or not finite");
+    remove_mean(c, x);
+    fine_residual(c, x, b, c.w_r.p, slot(c, S_NORM2));
+    double res = read_norm(c);
+    if (!std::isfinite(res)) fail(PCAMG_ERR_INVALID, "initial guess is not finite");
+    int32_t k = 0, hl = 0;
+    double wsum = 0.0;
+    int32_t wcnt = 0;
+    pcamg_status status = PCAMG_OK;
+    auto hist_put = [&](int32_t idx, double v) {
+        if (st && st->res_hist && idx < st->res_hist_cap) { st->res_hist[idx] = v; if (idx + 1 > hl) hl = idx + 1; }
+    };
+    hist_put(0, res / bn);
+    while (k < c.p.max_iter && res / bn > c.p.tol) {
+        Hier& h = *c.hist.back();
+        cycle(c, h, 1, c.w_r.p, c.w_c.p);
+        axpy(s, c.n, 1.0, c.w_c.p, x);
+        remove_mean(c, x);
+        fine_residual(c, x, b, c.w_r.p, slot(c, S_NORM2));
+        double nres = read_norm(c);
+        if (!std::isfinite(nres)) { status = PCAMG_ERR_DIVERGED; res = nres; break; }
+        wsum += nres / res;
+        ++wcnt;
+        res = nres;
+        ++k;
+        hist_put(k, res / bn);
+        if (res / bn <= c.p.tol) break;
+        if (wsum / (double)wcnt > c.p.threshold) {
+            double ts = now_ms();
+            rebuild(c, c.w_e.p);
+            axpy(s, c.n, 1.0, c.w_e.p, x);
+            remove_mean(c, x);
+            fine_residual(c, x, b, c.w_r.p, slot(c, S_NORM2));
+            res = read_norm(c);
+            hist_put(k, res / bn);
+            wsum = 0.0;
+            wcnt = 0;
+            t_setup += now_ms() - ts;
+        }
+    }
+    if (status == PCAMG_OK && !(res / bn <= c.p.tol)) status = PCAMG_ERR_NOT_CONVERGED;
+    sync(c);
+    if (st) {
+        st->iters = k;
+        st->resetups = (int32_t)c.hist.size() - re0;
+        st->levels = c.hist.back()->nlev;
+        st->status = status;
+        st->rel_res = res / bn;
+        double oc = 0.0;
+        for (Hier* h : c.hist) oc += h->oc;
+        st->oc_mean = oc / (double)c.hist.size();
+        st->t_setup_ms = t_setup;
+        st->t_solve_ms = now_ms() - t0;
+        st->res_hist_len = hl;
+        st->prof_launches = c.prof_launches;
+        st->prof_ms = c.prof_ms;
+        st->prof_bytes = (double)c.prof_launches * (12.0 * (double)c.nnz + 28.0 * (double)c.n);
+    }
+    return status;
+}
+
+pcamg_status solve_zero_rhs(Ctx& c, double* x, pcamg_stats* st) {
+    cudaStream_t s = c.stream;
+    double t0 = now_ms(), t_setup = 0.0;
+    int32_t re0 = (int32_t)c.hist.size();
+    double* zero = c.w_t2.p;
+    fill(s, c.n, 0.0, zero);
+    remove_mean(c, x);
+    fine_residual(c, x, zero, c.w_r.p, slot(c, S_NORM2));
+    double r0 = read_norm(c), res = r0;
+    int32_t k = 0, hl = 0;
+    pcamg_status status = PCAMG_OK;
+    auto hist_put = [&](int32_t idx, double v) {
+        if (st && st->res_hist && idx < st->res_hist_cap) { st->res_hist[idx] = v; if (idx + 1 > hl) hl = idx + 1; }
+    };
+    if (r0 > 0.0) {
+        hist_put(0, 1.0);
+        while (k < c.p.max_iter && res / r0 > c.p.tol) {
+            cycle(c, *c.hist.back(), 1, c.w_r.p, c.w_c.p);
+            axpy(s, c.n, 1.0, c.w_c.p, x);
+            remove_mean(c, x);
+            fine_residual(c, x, zero, c.w_r.p, slot(c, S_NORM2));
+            double nres = read_norm(c);
+            if (!std::isfinite(nres)) { status = PCAMG_ERR_DIVERGED; res = nres; break; }
+            double conv = nres / res;
+            res = nres;
+            ++k;
+            hist_put(k, res / r0);
+            if (res / r0 <= c.p.tol) break;
+            if (conv > c.p.threshold) {
+                double ts = now_ms();
+                // the exact error is the iterate itself: e = x / ||x||
+                normalise_orth(c, x, c.w_eh.p);
+                Hier* h = build_hierarchy(c, c.w_eh.p);
+                c.hist.push_back(h);
+                t_setup += now_ms() - ts;
+            }
+        }
+        if (status == PCAMG_OK && !(res / r0 <= c.p.tol)) status = PCAMG_ERR_NOT_CONVERGED;
+    }
+    sync(c);
+    if (st) {
+        st->iters = k;
+        st->resetups = (int32_t)c.hist.size() - re0;
+        st->levels = c.hist.back()->nlev;
+        st->status = status;
+        st->rel_res = r0 > 0.0 ? res / r0 : 0.0;
+        double oc = 0.0;
+        for (Hier* h : c.hist) oc += h->oc;
+        st->oc_mean = oc / (double)c.hist.size();
+        st->t_setup_ms = t_setup;
+        st->t_solve_ms = now_ms() - t0;
+        st->res_hist_len = hl;
+    }
+    return status;
+}
+
+}  // namespace pc

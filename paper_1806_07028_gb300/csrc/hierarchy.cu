@@ -1,0 +1,142 @@
+// PathCoverAMG_setup (Alg. 4) orchestration: reweighting on the A^2 pattern,
+// path cover, then per level path-cover aggregation (Alg. 3), prolongation
+// (level 1 carries e, Section 3.3), Galerkin products of A and of the reweighted
+// graph, path shortening, smoother colouring, and the coarsest factorisation.
+#include <memory>
+#include <utility>
+
+#include "pcamg_internal.cuh"
+
+namespace pc {
+
+Hier::~Hier() {
+    for (auto& g : graph)
+        if (g) cudaGraphExecDestroy(g);
+}
+
+static Csr make_csr(const Level& L, int32_t n, int64_t nnz, const int32_t* rp, const int32_t* ci,
+                    const double* v, const float* v32) {
+    (void)L;
+    Csr A;
+    A.n = n;
+    A.nnz = nnz;
+    A.rowptr = rp;
+    A.col = ci;
+    A.val = v;
+    A.val32 = v32;
+    A.lpr = lanes_per_row(n, nnz);
+    return A;
+}
+
+Hier* build_hierarchy(Ctx& c, const double* e) {
+    const pcamg_params& p = c.p;
+    std::unique_ptr<Hier> h(new Hier());
+    const bool f32 = p.precision == PCAMG_FP32_IR;
+    Level& L0 = h->lev[0];
+    L0.n = c.n;
+    L0.nnz = c.nnz;
+    L0.A = make_csr(L0, c.n, c.nnz, c.rowptr.p, c.col.p, c.val.p, f32 ? c.val32.p : nullptr);
+    L0.ncolour = c.ncolour0;
+    L0.colour_v = c.colour0.p;
+    L0.colour_rows_v = c.colour_rows0.p;
+    L0.h_colour_ptr = c.h_colour_ptr0;
+
+    // Alg. 4 steps 2-3: reweighted A^2 pattern and its path cover
+    Reweighted t;
+    build_candidates(c, e, t);
+    DBuf<int32_t> nbr0, nbr1;
+    nbr0.alloc(c.mem, c.n);
+    nbr1.alloc(c.mem, c.n);
+    L0.cover_rounds = path_cover(c, c.n, t, nbr0.p, nbr1.p);
+
+    int32_t nlev = 1;
+    for (int32_t l = 0;; ++l) {
+        Level& L = h->lev[l];
+        if (L.n <= p.n_min || l == p.max_levels - 1 || l == kMaxLevels - 1) break;
+        DBuf<int32_t> agg, cn0, cn1;
+        int32_t rounds = 0;
+        int32_t nc = aggregate_level(c, L.n, nbr0.p, nbr1.p, t, agg, cn0, cn1, &rounds);
+        L.leftover_rounds = rounds;
+        if ((double)nc > 0.9 * (double)L.n) break;   // coarsening stalled: L is the coarsest
+        L.nc = nc;
+        L.agg = std::move(agg);
+        build_members(c, L.n, nc, L.agg.p, L.agg_ptr, L.agg_mem);
+        if (l == 0 && p.p1_mode == PCAMG_P1_E_SCALED) {
+            build_pval(c, L.n, nc, L.agg_ptr.p, L.agg_mem.p, e, L.pval);
+            if (f32) {
+                L.pval32.alloc(c.mem, L.n);
+                cast_f32(c.stream, L.n, L.pval.p, L.pval32.p);
+            }
+        }
+        Level& C = h->lev[l + 1];
+        C.n = nc;
+        C.nnz = galerkin(c, L.n, L.A.rowptr, L.A.col, L.A.val, nc, L.agg.p, L.agg_ptr.p,
+                         L.agg_mem.p, L.pval.p, false, C.rowptr, C.col, C.val);
+        Reweighted tc;
+        tc.nnz = galerkin(c, L.n, t.ptr.p, t.col.p, t.w.p, nc, L.agg.p, L.agg_ptr.p, L.agg_mem.p,
+                          nullptr, true, tc.ptr, tc.col, tc.w);
+        if (f32) {
+            C.val32.alloc(c.mem, C.nnz);
+            cast_f32(c.stream, C.nnz, C.val.p, C.val32.p);
+        }
+        C.A = make_csr(C, C.n, C.nnz, C.rowptr.p, C.col.p, C.val.p, f32 ? C.val32.p : nullptr);
+        if (p.keep_setup) {
+            L.nbr0 = std::move(nbr0);
+            L.nbr1 = std::move(nbr1);
+            L.tptr = std::move(t.ptr);
+            L.tcol = std::move(t.col);
+            L.tw = std::move(t.w);
+            L.tnnz = t.nnz;
+        }
+        t = Reweighted();
+        t.ptr = std::move(tc.ptr);
+        t.col = std::move(tc.col);
+        t.w = std::move(tc.w);
+        t.nnz = tc.nnz;
+        nbr0 = std::move(cn0);
+        nbr1 = std::move(cn1);
+        nlev = l + 2;
+    }
+    h->nlev = nlev;
+    if (p.keep_setup) {
+        Level& Lc = h->lev[nlev - 1];
+        Lc.nbr0 = std::move(nbr0);
+        Lc.nbr1 = std::move(nbr1);
+        Lc.tptr = std::move(t.ptr);
+        Lc.tcol = std::move(t.col);
+        Lc.tw = std::move(t.w);
+        Lc.tnnz = t.nnz;
+    }
+    // smoother colouring of every level but the coarsest (level 0 is shared)
+    for (int32_t l = 1; l + 1 < nlev; ++l) {
+        Level& L = h->lev[l];
+        L.colour.alloc(c.mem, L.n);
+        L.ncolour = colour_graph(c, L.n, L.A.rowptr, L.A.col, p.seed, L.colour.p);
+        colour_lists(c, L.n, L.colour.p, L.ncolour, L.colour_rows, L.h_colour_ptr);
+        L.colour_v = L.colour.p;
+        L.colour_rows_v = L.colour_rows.p;
+    }
+    // coarsest level
+    Level& LC = h->lev[nlev - 1];
+    if (LC.n > p.dense_max) fail(PCAMG_ERR_COARSE_TOO_BIG, "coarsening stalled above dense_max");
+    bool boolean_chain = (p.p1_mode == PCAMG_P1_BOOLEAN) || nlev == 1;
+    coarse_factor(c, LC.n, LC.A.rowptr, LC.A.col, LC.A.val, boolean_chain, h->Xinv, &h->npinned);
+    h->nL = LC.n;
+    // work vectors
+    double nnz_sum = 0.0;
+    for (int32_t l = 0; l < nlev; ++l) {
+        Level& L = h->lev[l];
+        nnz_sum += (double)L.nnz;
+        if (f32) {
+            L.x32.alloc(c.mem, L.n); L.b32.alloc(c.mem, L.n); L.r32.alloc(c.mem, L.n);
+            if (l == nlev - 1) { L.x64.alloc(c.mem, L.n); L.b64.alloc(c.mem, L.n); }
+        } else {
+            L.x64.alloc(c.mem, L.n); L.b64.alloc(c.mem, L.n); L.r64.alloc(c.mem, L.n);
+        }
+    }
+    h->oc = nnz_sum / (double)c.nnz;
+    sync(c);
+    return h.release();
+}
+
+}  // namespace pc

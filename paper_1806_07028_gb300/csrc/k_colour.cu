@@ -1,0 +1,132 @@
+// Smoother colouring: Jones-Plassmann rounds with priorities
+// (splitmix64(seed ^ i), i). In a round every uncoloured vertex whose priority
+// beats all its uncoloured neighbours takes the smallest colour not used by its
+// already coloured neighbours; such winners are never adjacent, so a round's
+// assignments are independent. The colour classes are independent sets, which
+// makes a multicolour Gauss-Seidel sweep deterministic and parallel.
+#include <vector>
+
+#include "pcamg_internal.cuh"
+
+namespace pc {
+
+namespace {
+
+#define FOR_EACH(i, n) for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+inline int gridc(int64_t n) {
+    int64_t g = (n + kBlock - 1) / kBlock;
+    if (g < 1) g = 1;
+    if (g > (int64_t)kNumSMs * 32) g = kNumSMs * 32;
+    return (int)g;
+}
+
+// SplitMix64 output function (Steele, Lea, Flood 2014).
+__device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_colour_round(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                               uint64_t seed, const int* __restrict__ cin, int* __restrict__ cout,
+                               int* __restrict__ left, int* __restrict__ maxc) {
+    FOR_EACH(v64, n) {
+        int v = (int)v64;
+        int cv = cin[v];
+        if (cv >= 0) { cout[v] = cv; continue; }
+        uint64_t hv = splitmix64(seed ^ (uint64_t)(int64_t)v);
+        int beg = rowptr[v], end = rowptr[v + 1];
+        bool win = true;
+        for (int k = beg; k < end && win; ++k) {
+            int u = col[k];
+            if (u == v || cin[u] >= 0) continue;
+            uint64_t hu = splitmix64(seed ^ (uint64_t)(int64_t)u);
+            if (hu > hv || (hu == hv && u > v)) win = false;
+        }
+        if (!win) { cout[v] = -1; atomicAdd(left, 1); continue; }
+        uint64_t mask = 0;
+        for (int k = beg; k < end; ++k) {
+            int u = col[k];
+            int cu = cin[u];
+            if (u != v && cu >= 0 && cu < 64) mask |= 1ull << cu;
+        }
+        int c;
+        if (~mask != 0ull) {
+            c = __ffsll((long long)~mask) - 1;
+        } else {
+            c = 64;
+            for (;;) {  // rare: 64 or more colours around v
+                bool used = false;
+                for (int k = beg; k < end; ++k) {
+                    int u = col[k];
+                    if (u != v && cin[u] == c) { used = true; break; }
+                }
+                if (!used) break;
+                ++c;
+            }
+        }
+        cout[v] = c;
+        atomicMax(maxc, c);
+    }
+}
+
+__global__ void k_colour_flags(int n, const int* __restrict__ colour, int c, int* __restrict__ flag) {
+    FOR_EACH(v, n) flag[v] = (colour[v] == c) ? 1 : 0;
+}
+
+__global__ void k_colour_place(int n, const int* __restrict__ colour, int c,
+                               const int* __restrict__ pos, int base, int* __restrict__ rows) {
+    FOR_EACH(v, n) if (colour[v] == c) rows[base + pos[v]] = (int)v;
+}
+
+}  // namespace
+
+int32_t colour_graph(Ctx& c, int32_t n, const int32_t* rowptr, const int32_t* col, uint64_t seed,
+                     int32_t* colour) {
+    cudaStream_t s = c.stream;
+    DBuf<int32_t> tmp, left, maxc;
+    tmp.alloc(c.mem, n);
+    left.alloc(c.mem, 1);
+    maxc.alloc(c.mem, 1);
+    fill_i32(s, n, -1, colour);
+    PC_CUDA(cudaMemsetAsync(maxc.p, 0, sizeof(int32_t), s));
+    int32_t* a = colour;
+    int32_t* b = tmp.p;
+    for (int round = 0;; ++round) {
+        PC_CUDA(cudaMemsetAsync(left.p, 0, sizeof(int32_t), s));
+        k_colour_round<<<gridc(n), kBlock, 0, s>>>(n, rowptr, col, seed, a, b, left.p, maxc.p);
+        PC_LAUNCH("colour_round");
+        int32_t* t = a; a = b; b = t;
+        if (read_i32(c, left.p) == 0) break;
+        if (round > n) fail(PCAMG_ERR_ROUND_CAP, "colouring rounds exceeded n");
+    }
+    if (a != colour) PC_CUDA(cudaMemcpyAsync(colour, a, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+    int32_t nc = read_i32(c, maxc.p) + 1;
+    return nc;
+}
+
+// Rows grouped by colour, ascending inside each colour.
+void colour_lists(Ctx& c, int32_t n, const int32_t* colour, int32_t ncolour,
+                  DBuf<int32_t>& rows, std::vector<int32_t>& h_ptr) {
+    cudaStream_t s = c.stream;
+    rows.alloc(c.mem, n);
+    DBuf<int32_t> flag, pos;
+    flag.alloc(c.mem, n);
+    pos.alloc(c.mem, (size_t)n + 1);
+    h_ptr.assign((size_t)ncolour + 1, 0);
+    int64_t base = 0;
+    for (int32_t k = 0; k < ncolour; ++k) {
+        k_colour_flags<<<gridc(n), kBlock, 0, s>>>(n, colour, k, flag.p);
+        int64_t cnt = scan_i32(c, flag.p, pos.p, n);
+        k_colour_place<<<gridc(n), kBlock, 0, s>>>(n, colour, k, pos.p, (int)base, rows.p);
+        PC_LAUNCH("colour_lists");
+        h_ptr[k] = (int32_t)base;
+        base += cnt;
+    }
+    h_ptr[ncolour] = (int32_t)base;
+    sync(c);
+}
+
+}  // namespace pc

@@ -1,0 +1,999 @@
+// Setup kernels of PathCoverAMG_setup (Alg. 4):
+//  * row products: the A^2 pattern (Alg. 4 step 2) and the Galerkin products
+//    P^T A P and B^T A~ B (Alg. 4 steps 7 and 9) share one engine that, for each
+//    output row, enumerates contributions in a fixed order, merges equal column
+//    keys by summing in that order, and writes the row sorted by column;
+//  * the path cover (Alg. 1) as locally-dominant rounds over paths;
+//  * list ranking of the paths, matching along them and leftover handling
+//    (Alg. 3), aggregate numbering, members, P values and path shortening.
+// Every integer result is deterministic and independent of thread scheduling.
+#include <algorithm>
+#include <cstring>
+
+#include "pcamg_internal.cuh"
+
+namespace pc {
+
+namespace {
+
+constexpr int kThreadCap = 32;        // unique keys a thread-per-row product keeps
+constexpr int kBlockCap = 2048;       // contributions a block-per-row product stages in smem
+constexpr uint32_t kSkip = 0xffffffffu;
+
+inline int grid1(int64_t n, int block = kBlock) {
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > (int64_t)kNumSMs * 32) g = kNumSMs * 32;
+    return (int)g;
+}
+
+#define FOR_EACH(i, n) for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+// ---------------------------------------------------------------- row products
+// Row u of the A^2 pattern: for j in row u of A (A holds its diagonal), for v in
+// row j: key v, skipping v == u.
+struct CandSrc {
+    const int* __restrict__ rowptr;
+    const int* __restrict__ col;
+    __device__ int nmem(int r) const { return rowptr[r + 1] - rowptr[r]; }
+    __device__ int mem_row(int r, int t) const { return col[rowptr[r] + t]; }
+    __device__ int in_beg(int j) const { return rowptr[j]; }
+    __device__ int in_end(int j) const { return rowptr[j + 1]; }
+    __device__ void kv(int r, int, int k, uint32_t& key, double& v) const {
+        int c = col[k];
+        key = (c == r) ? kSkip : (uint32_t)c;
+        v = 0.0;
+    }
+};
+
+// Row I of P^T A P: members u of aggregate I ascending, then row u of A in
+// order; key agg(v), value (p_u a_uv) p_v (p = 1 when pval is null).
+struct GalSrc {
+    const int* __restrict__ agg_ptr;
+    const int* __restrict__ mem;
+    const int* __restrict__ rowptr;
+    const int* __restrict__ col;
+    const double* __restrict__ val;
+    const double* __restrict__ pval;
+    const int* __restrict__ agg;
+    int drop_diag;
+    __device__ int nmem(int r) const { return agg_ptr[r + 1] - agg_ptr[r]; }
+    __device__ int mem_row(int r, int t) const { return mem[agg_ptr[r] + t]; }
+    __device__ int in_beg(int u) const { return rowptr[u]; }
+    __device__ int in_end(int u) const { return rowptr[u + 1]; }
+    __device__ void kv(int r, int u, int k, uint32_t& key, double& v) const {
+        int c = col[k];
+        int J = agg[c];
+        key = (drop_diag && J == r) ? kSkip : (uint32_t)J;
+        v = pval ? __dmul_rn(__dmul_rn(pval[u], val[k]), pval[c]) : val[k];
+    }
+};
+
+// Thread per row: insertion into a sorted local list. Rows whose unique keys
+// exceed kThreadCap are flagged and listed for the block kernels.
+template <class Src, bool FILL>
+__global__ void k_rowprod_thread(int nrows, Src src, int* __restrict__ cnt,
+                                 unsigned char* __restrict__ is_long, int* __restrict__ long_list,
+                                 int* __restrict__ long_count, const int* __restrict__ optr,
+                                 int* __restrict__ ocol, double* __restrict__ oval) {
+    FOR_EACH(r64, nrows) {
+        int r = (int)r64;
+        if (FILL && is_long[r]) continue;
+        uint32_t keys[kThreadCap];
+        double vals[kThreadCap];
+        int m = 0;
+        bool over = false;
+        int nm = src.nmem(r);
+        for (int t = 0; t < nm && !over; ++t) {
+            int j = src.mem_row(r, t);
+            int e = src.in_end(j);
+            for (int k = src.in_beg(j); k < e; ++k) {
+                uint32_t key;
+                double v;
+                src.kv(r, j, k, key, v);
+                if (key == kSkip) continue;
+                int p = m;
+                while (p > 0 && keys[p - 1] > key) --p;
+                if (p > 0 && keys[p - 1] == key) {
+                    vals[p - 1] = __dadd_rn(vals[p - 1], v);
+                } else {
+                    if (m == kThreadCap) { over = true; break; }
+                    for (int q = m; q > p; --q) { keys[q] = keys[q - 1]; vals[q] = vals[q - 1]; }
+                    keys[p] = key;
+                    vals[p] = v;
+                    ++m;
+                }
+            }
+        }
+        if (!FILL) {
+            is_long[r] = over ? 1 : 0;
+            cnt[r] = over ? 0 : m;
+            if (over) long_list[atomicAdd(long_count, 1)] = r;
+        } else {
+            int o = optr[r];
+            for (int q = 0; q < m; ++q) {
+                ocol[o + q] = (int)keys[q];
+                if (oval) oval[o + q] = vals[q];
+            }
+        }
+    }
+}
+
+template <class Src>
+__global__ void k_rowprod_ub(int nlong, const int* __restrict__ rows, Src src, int64_t* __restrict__ ub) {
+    FOR_EACH(i, nlong) {
+        int r = rows[i];
+        int64_t s = 0;
+        int nm = src.nmem(r);
+        for (int t = 0; t < nm; ++t) {
+            int j = src.mem_row(r, t);
+            s += src.in_end(j) - src.in_beg(j);
+        }
+        ub[i] = s;
+    }
+}
+
+__device__ __forceinline__ int64_t next_pow2(int64_t x) {
+    int64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+// Ascending bitonic sort of P (power of two) 64-bit keys by one block.
+__device__ void block_bitonic_u64(uint64_t* keys, int64_t P) {
+    for (int64_t k = 2; k <= P; k <<= 1) {
+        for (int64_t j = k >> 1; j > 0; j >>= 1) {
+            for (int64_t i = threadIdx.x; i < P; i += blockDim.x) {
+                int64_t ixj = i ^ j;
+                if (ixj > i) {
+                    uint64_t a = keys[i], b = keys[ixj];
+                    bool up = (i & k) == 0;
+                    if ((a > b) == up) { keys[i] = b; keys[ixj] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Block-wide exclusive scan of 0/1 flags given per thread in chunks; returns
+// the prefix for this thread's item and the chunk total.
+__device__ int block_excl_scan(int flag, int* total) {
+    __shared__ int ws[32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int inc = flag;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) ws[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        int nw = blockDim.x >> 5;
+        int w = lane < nw ? ws[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < nw) ws[lane] = wi - w;
+        if (lane == nw - 1) ws[31] = wi;
+    }
+    __syncthreads();
+    int res = ws[wid] + inc - flag;
+    *total = ws[31];
+    __syncthreads();
+    return res;
+}
+
+// Block per long row: stage (key << 32 | seq) and values by sequence number,
+// sort, then each run of equal keys is summed in sequence order.
+template <class Src, bool FILL, bool GLOBAL>
+__global__ void k_rowprod_block(const int* __restrict__ rows, Src src, int* __restrict__ cnt,
+                                const int* __restrict__ optr, int* __restrict__ ocol,
+                                double* __restrict__ oval, uint64_t* __restrict__ gkeys,
+                                double* __restrict__ gvals, const int64_t* __restrict__ goff) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int r = rows[blockIdx.x];
+    uint64_t* keys;
+    double* vals;
+    if (GLOBAL) {
+        keys = gkeys + goff[blockIdx.x];
+        vals = gvals + goff[blockIdx.x];
+    } else {
+        keys = reinterpret_cast<uint64_t*>(smem_raw);
+        vals = reinterpret_cast<double*>(smem_raw + sizeof(uint64_t) * kBlockCap);
+    }
+    int64_t base = 0;
+    int nm = src.nmem(r);
+    for (int t = 0; t < nm; ++t) {
+        int j = src.mem_row(r, t);
+        int b = src.in_beg(j), e = src.in_end(j);
+        for (int k = b + threadIdx.x; k < e; k += blockDim.x) {
+            uint32_t key;
+            double v;
+            src.kv(r, j, k, key, v);
+            int64_t seq = base + (k - b);
+            keys[seq] = (key == kSkip) ? ~0ull : (((uint64_t)key << 32) | (uint64_t)seq);
+            vals[seq] = v;
+        }
+        base += e - b;
+    }
+    int64_t P = next_pow2(base);
+    for (int64_t i = base + threadIdx.x; i < P; i += blockDim.x) keys[i] = ~0ull;
+    __syncthreads();
+    block_bitonic_u64(keys, P);
+    // run starts
+    int carry = 0;
+    for (int64_t c0 = 0; c0 < base; c0 += blockDim.x) {
+        int64_t p = c0 + threadIdx.x;
+        int flag = 0;
+        if (p < base) {
+            uint64_t kp = keys[p];
+            flag = (kp != ~0ull) && (p == 0 || (keys[p - 1] >> 32) != (kp >> 32));
+        }
+        int tot;
+        int pre = block_excl_scan(flag, &tot);
+        if (FILL && flag) {
+            uint64_t kp = keys[p];
+            uint32_t kk = (uint32_t)(kp >> 32);
+            double s = vals[(uint32_t)kp];
+            for (int64_t q = p + 1; q < base; ++q) {
+                uint64_t kq = keys[q];
+                if ((uint32_t)(kq >> 32) != kk || kq == ~0ull) break;
+                s = __dadd_rn(s, vals[(uint32_t)kq]);
+            }
+            int o = optr[r] + carry + pre;
+            ocol[o] = (int)kk;
+            if (oval) oval[o] = s;
+        }
+        carry += tot;
+    }
+    if (!FILL && threadIdx.x == 0) cnt[r] = carry;
+}
+
+// ---------------------------------------------------------------- weights
+__global__ void k_maxabs(int64_t n, const double* __restrict__ x, double* __restrict__ out) {
+    __shared__ double ws[32];
+    double m = 0.0;
+    FOR_EACH(i, n) m = fmax(m, fabs(x[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+        if (threadIdx.x == 0) out[blockIdx.x] = v;
+    }
+}
+
+__global__ void k_delta(int nb, const double* __restrict__ part, double* __restrict__ delta) {
+    double m = 0.0;
+    for (int i = 0; i < nb; ++i) m = fmax(m, part[i]);
+    double d = ldexp(m, -52);
+    *delta = (d == 0.0) ? 1.0 : d;
+}
+
+// w_uv = 1 / max(|e_u - e_v|, delta)  (Alg. 4 step 2 with the tie cap)
+__global__ void k_weights(int n, const int* __restrict__ ptr, const int* __restrict__ col,
+                          const double* __restrict__ e, const double* __restrict__ delta,
+                          double* __restrict__ w) {
+    double dl = *delta;
+    FOR_EACH(u64, n) {
+        int u = (int)u64;
+        double eu = e[u];
+        for (int k = ptr[u]; k < ptr[u + 1]; ++k) {
+            double d = fabs(__dsub_rn(eu, e[col[k]]));
+            if (d < dl) d = dl;
+            w[k] = __ddiv_rn(1.0, d);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- edge order
+// Edge (a,b,w) before (c,d,x): heavier first, then smaller min id, then smaller max id.
+__device__ __forceinline__ bool edge_before(double w1, int a1, int b1, double w2, int a2, int b2) {
+    if (w1 != w2) return w1 > w2;
+    int lo1 = min(a1, b1), lo2 = min(a2, b2);
+    if (lo1 != lo2) return lo1 < lo2;
+    return max(a1, b1) < max(a2, b2);
+}
+
+// Each row re-ordered by (w desc, column asc): the order in which a vertex
+// proposes its edges. Thread per row for short rows.
+__global__ void k_order_rows_thread(int n, const int* __restrict__ ptr, const int* __restrict__ col,
+                                    const double* __restrict__ w, int* __restrict__ scol,
+                                    double* __restrict__ sw, unsigned char* __restrict__ is_long,
+                                    int* __restrict__ long_list, int* __restrict__ long_count) {
+    FOR_EACH(u64, n) {
+        int u = (int)u64;
+        int b = ptr[u], len = ptr[u + 1] - b;
+        if (len > kThreadCap) {
+            is_long[u] = 1;
+            long_list[atomicAdd(long_count, 1)] = u;
+            continue;
+        }
+        is_long[u] = 0;
+        int c[kThreadCap];
+        double x[kThreadCap];
+        int m = 0;
+        for (int k = 0; k < len; ++k) {
+            int cv = col[b + k];
+            double wv = w[b + k];
+            int p = m;
+            while (p > 0 && (x[p - 1] < wv || (x[p - 1] == wv && c[p - 1] > cv))) --p;
+            for (int q = m; q > p; --q) { c[q] = c[q - 1]; x[q] = x[q - 1]; }
+            c[p] = cv;
+            x[p] = wv;
+            ++m;
+        }
+        for (int k = 0; k < len; ++k) { scol[b + k] = c[k]; sw[b + k] = x[k]; }
+    }
+}
+
+// Long rows: bitonic sort of (~bits(w), col) packed as two keys via an index sort.
+__global__ void k_order_rows_block(const int* __restrict__ rows, const int* __restrict__ ptr,
+                                   const int* __restrict__ col, const double* __restrict__ w,
+                                   int* __restrict__ scol, double* __restrict__ sw,
+                                   uint32_t* __restrict__ gidx, const int64_t* __restrict__ goff) {
+    int u = rows[blockIdx.x];
+    int b = ptr[u], len = ptr[u + 1] - b;
+    uint32_t* idx = gidx + goff[blockIdx.x];
+    int64_t P = next_pow2(len);
+    for (int64_t i = threadIdx.x; i < P; i += blockDim.x) idx[i] = (i < len) ? (uint32_t)i : 0xffffffffu;
+    __syncthreads();
+    for (int64_t k = 2; k <= P; k <<= 1) {
+        for (int64_t j = k >> 1; j > 0; j >>= 1) {
+            for (int64_t i = threadIdx.x; i < P; i += blockDim.x) {
+                int64_t ixj = i ^ j;
+                if (ixj > i) {
+                    uint32_t a = idx[i], c2 = idx[ixj];
+                    // "a after c2" in the (w desc, col asc) order; sentinels last
+                    bool a_gt;
+                    if (a == 0xffffffffu) a_gt = (c2 != 0xffffffffu);
+                    else if (c2 == 0xffffffffu) a_gt = false;
+                    else {
+                        double wa = w[b + a], wc = w[b + c2];
+                        a_gt = (wa < wc) || (wa == wc && col[b + a] > col[b + c2]);
+                    }
+                    bool up = (i & k) == 0;
+                    if (a_gt == up) { idx[i] = c2; idx[ixj] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        scol[b + i] = col[b + idx[i]];
+        sw[b + i] = w[b + idx[i]];
+    }
+}
+
+// ---------------------------------------------------------------- path cover rounds
+__global__ void k_cover_init(int n, const int* __restrict__ ptr, int* deg, int* oe, int* cptr,
+                             int* nbr0, int* nbr1) {
+    FOR_EACH(u, n) {
+        deg[u] = 0; oe[u] = (int)u; cptr[u] = ptr[u]; nbr0[u] = -1; nbr1[u] = -1;
+    }
+}
+
+// 1. each endpoint advances to its best eligible edge (ineligible edges stay so)
+__global__ void k_cover_best(int n, const int* __restrict__ ptr, const int* __restrict__ scol,
+                             const int* __restrict__ deg, const int* __restrict__ oe,
+                             int* __restrict__ cptr, int* __restrict__ bv) {
+    FOR_EACH(u64, n) {
+        int u = (int)u64;
+        if (deg[u] >= 2) continue;
+        int p = cptr[u], e = ptr[u + 1], o = oe[u];
+        while (p < e) {
+            int v = scol[p];
+            if (deg[v] >= 2 || o == v) ++p; else break;
+        }
+        cptr[u] = p;
+        bv[u] = (p < e) ? scol[p] : -1;
+    }
+}
+
+// 2. each path keeps the better proposal of its two endpoints
+__global__ void k_cover_choose(int n, const int* __restrict__ deg, const int* __restrict__ oe,
+                               const int* __restrict__ cptr, const int* __restrict__ bv,
+                               const double* __restrict__ sw, int* __restrict__ cf,
+                               int* __restrict__ ct) {
+    FOR_EACH(u64, n) {
+        int u = (int)u64;
+        if (deg[u] >= 2) continue;
+        int o = oe[u];
+        if (u > o) continue;
+        int x = -1, y = -1;
+        double wx = 0.0;
+        if (bv[u] >= 0) { x = u; y = bv[u]; wx = sw[cptr[u]]; }
+        if (o != u && bv[o] >= 0) {
+            double wo = sw[cptr[o]];
+            if (x < 0 || edge_before(wo, o, bv[o], wx, x, y)) { x = o; y = bv[o]; }
+        }
+        cf[u] = x; ct[u] = y; cf[o] = x; ct[o] = y;
+    }
+}
+
+// 3. an edge chosen by both of its paths joins them
+__global__ void k_cover_accept(int n, int* __restrict__ deg, int* __restrict__ oe,
+                               const int* __restrict__ cf, const int* __restrict__ ct,
+                               int* __restrict__ nbr0, int* __restrict__ nbr1,
+                               int* __restrict__ counter) {
+    FOR_EACH(u64, n) {
+        int u = (int)u64;
+        if (cf[u] != u) continue;
+        int y = ct[u];
+        if (y < 0 || y < u) continue;
+        if (deg[u] >= 2) continue;
+        if (cf[y] != y || ct[y] != u) continue;
+        int a = oe[u], b = oe[y];
+        oe[a] = b;
+        oe[b] = a;
+        if (nbr0[u] < 0) nbr0[u] = y; else nbr1[u] = y;
+        if (nbr0[y] < 0) nbr0[y] = u; else nbr1[y] = u;
+        deg[u] += 1;
+        deg[y] += 1;
+        atomicAdd(counter, 1);
+    }
+}
+
+__global__ void k_canonical(int n, int* __restrict__ nbr0, int* __restrict__ nbr1) {
+    FOR_EACH(u, n) {
+        int a = nbr0[u], b = nbr1[u];
+        if (a >= 0 && b >= 0 && b < a) { nbr0[u] = b; nbr1[u] = a; }
+        else if (a < 0 && b >= 0) { nbr0[u] = b; nbr1[u] = -1; }
+    }
+}
+
+// ---------------------------------------------------------------- list ranking
+// Half-edge h = 2u+k points from u to nbr_k(u). Its successor continues away
+// from u at the head. Pointer jumping gives each half-edge the path end it
+// reaches and the number of edges to it.
+__global__ void k_rank_init(int n, const int* __restrict__ nbr0, const int* __restrict__ nbr1,
+                            int* __restrict__ jmp, int* __restrict__ dist, int* __restrict__ endv) {
+    FOR_EACH(u64, n) {
+        int u = (int)u64;
+        for (int k = 0; k < 2; ++k) {
+            int h = 2 * u + k;
+            int v = k ? nbr1[u] : nbr0[u];
+            if (v < 0) { jmp[h] = -1; dist[h] = 0; endv[h] = -1; continue; }
+            int w0 = nbr0[v], w1 = nbr1[v];
+            int w = (w0 >= 0 && w0 != u) ? w0 : ((w1 >= 0 && w1 != u) ? w1 : -1);
+            jmp[h] = (w < 0) ? -1 : (2 * v + (w0 == w ? 0 : 1));
+            dist[h] = 1;
+            endv[h] = v;
+        }
+    }
+}
+
+__global__ void k_rank_jump(int nh, const int* __restrict__ jmp, const int* __restrict__ dist,
+                            const int* __restrict__ endv, int* __restrict__ jmp2,
+                            int* __restrict__ dist2, int* __restrict__ endv2,
+                            int* __restrict__ active) {
+    FOR_EACH(h, nh) {
+        int j = jmp[h];
+        if (j >= 0) {
+            dist2[h] = dist[h] + dist[j];
+            endv2[h] = endv[j];
+            int jj = jmp[j];
+            jmp2[h] = jj;
+            if (jj >= 0) *active = 1;
+        } else {
+            dist2[h] = dist[h];
+            endv2[h] = endv[h];
+            jmp2[h] = j;
+        }
+    }
+}
+
+// Positions from the canonical end (the endpoint with the smaller id), then the
+// matching along the path: positions (0,1), (2,3), ... form aggregates named
+// by their first vertex; links to the previous and next matched pair of the
+// same path are kept for path shortening.
+__global__ void k_pair(int n, const int* __restrict__ nbr0, const int* __restrict__ nbr1,
+                       const int* __restrict__ dist, const int* __restrict__ endv,
+                       int* __restrict__ lab, int* __restrict__ size, int* __restrict__ sprev,
+                       int* __restrict__ snext, unsigned char* __restrict__ ishead) {
+    FOR_EACH(u64, n) {
+        int u = (int)u64;
+        int a = nbr0[u], b = nbr1[u];
+        int deg = (a >= 0) + (b >= 0);
+        ishead[u] = 0;
+        sprev[u] = -1;
+        snext[u] = -1;
+        if (deg == 0) continue;
+        int L, pos, toward = -1, away = -1;
+        if (deg == 1) {
+            int E = endv[2 * u], d = dist[2 * u];
+            L = d + 1;
+            if (u < E) { pos = 0; away = a; }
+            else { pos = d; toward = a; }
+        } else {
+            int E0 = endv[2 * u], d0 = dist[2 * u], E1 = endv[2 * u + 1], d1 = dist[2 * u + 1];
+            L = d0 + d1 + 1;
+            if (E0 < E1) { pos = d0; toward = a; away = b; }
+            else { pos = d1; toward = b; away = a; }
+        }
+        if ((pos & 1) || pos + 1 >= L) continue;
+        // u heads the pair (u, away)
+        int q = away;
+        lab[u] = u;
+        lab[q] = u;
+        size[u] = 2;
+        ishead[u] = 1;
+        if (pos + 3 < L) {
+            int q0 = nbr0[q], q1 = nbr1[q];
+            snext[u] = (q0 != u) ? q0 : q1;
+        }
+        if (pos >= 2) {
+            int t0 = nbr0[toward], t1 = nbr1[toward];
+            sprev[u] = (t0 != u) ? t0 : t1;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- leftovers
+// best(u): heaviest reweighted edge at u, ties to the smaller neighbour id
+__global__ void k_best(int n, const int* __restrict__ ptr, const int* __restrict__ col,
+                       const double* __restrict__ w, int* __restrict__ best,
+                       int* __restrict__ lab, int* __restrict__ size) {
+    FOR_EACH(u64, n) {
+        int u = (int)u64;
+        int bb = -1;
+        double bw = 0.0;
+        for (int k = ptr[u]; k < ptr[u + 1]; ++k) {
+            double x = w[k];
+            int c = col[k];
+            if (bb < 0 || x > bw || (x == bw && c < bb)) { bb = c; bw = x; }
+        }
+        best[u] = bb;
+        if (bb < 0 && lab[u] < 0) { lab[u] = u; size[u] = 1; }
+    }
+}
+
+// state at the start of a round: 0 aggregated, 1 waiting (best unaggregated),
+// 2 joiner of aggregate jg[u] (best aggregated)
+__global__ void k_left_classify(int n, const int* __restrict__ lab, const int* __restrict__ best,
+                                int* __restrict__ st, int* __restrict__ jg, int* __restrict__ gcnt,
+                                int* __restrict__ nleft) {
+    FOR_EACH(u64, n) {
+        int u = (int)u64;
+        if (lab[u] >= 0) { st[u] = 0; continue; }
+        atomicAdd(nleft, 1);
+        int v = best[u];
+        int g = lab[v];
+        if (g >= 0) { st[u] = 2; jg[u] = g; atomicAdd(gcnt + g, 1); }
+        else st[u] = 1;
+    }
+}
+
+// case 1: mutual best pairs among the waiting vertices
+__global__ void k_left_case1(int n, const int* __restrict__ st, const int* __restrict__ best,
+                             int* __restrict__ lab, int* __restrict__ size) {
+    FOR_EACH(u64, n) {
+        int u = (int)u64;
+        if (st[u] != 1) continue;
+        int v = best[u];
+        if (v > u && st[v] == 1 && best[v] == u) {
+            lab[u] = u;
+            lab[v] = u;
+            size[u] = 2;
+        }
+    }
+}
+
+__global__ void k_left_fill(int n, const int* __restrict__ st, const int* __restrict__ jg,
+                            const int* __restrict__ goff, int* __restrict__ gfill,
+                            int* __restrict__ list) {
+    FOR_EACH(u64, n) {
+        int u = (int)u64;
+        if (st[u] != 2) continue;
+        int g = jg[u];
+        list[goff[g] + atomicAdd(gfill + g, 1)] = u;
+    }
+}
+
+// cases 2/3: the joiners of one aggregate, in ascending order, one at a time
+__device__ __forceinline__ void left_apply(int u, int v, int* lab, int* size) {
+    int h = lab[v];
+    if (h < 0) {
+        lab[u] = u; lab[v] = u; size[u] = 2;
+    } else if (size[h] == 2) {
+        lab[u] = h; size[h] = 3;
+    } else {
+        lab[v] = u; size[h] -= 1; lab[u] = u; size[u] = 2;
+    }
+}
+
+__global__ void k_left_join(int n, const int* __restrict__ goff, int* __restrict__ list,
+                            const int* __restrict__ best, int* __restrict__ lab,
+                            int* __restrict__ size) {
+    FOR_EACH(g64, n) {
+        int g = (int)g64;
+        int b = goff[g], e = goff[g + 1];
+        if (b == e) continue;
+        for (int i = b + 1; i < e; ++i) {  // insertion sort (few joiners)
+            int x = list[i], j = i;
+            while (j > b && list[j - 1] > x) { list[j] = list[j - 1]; --j; }
+            list[j] = x;
+        }
+        for (int i = b; i < e; ++i) {
+            int u = list[i];
+            left_apply(u, best[u], lab, size);
+        }
+    }
+}
+
+// after the round cap: the paper's sequential loop, ascending order
+__global__ void k_left_tail(int n, const int* __restrict__ best, int* __restrict__ lab,
+                            int* __restrict__ size) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (int u = 0; u < n; ++u)
+        if (lab[u] < 0) left_apply(u, best[u], lab, size);
+}
+
+// ---------------------------------------------------------------- numbering
+__global__ void k_minmem(int n, const int* __restrict__ lab, int* __restrict__ minmem) {
+    FOR_EACH(u, n) atomicMin(minmem + lab[u], (int)u);
+}
+
+__global__ void k_isfirst(int n, const int* __restrict__ lab, const int* __restrict__ minmem,
+                          int* __restrict__ flag) {
+    FOR_EACH(u, n) flag[u] = (minmem[lab[u]] == (int)u) ? 1 : 0;
+}
+
+__global__ void k_agg_ids(int n, const int* __restrict__ lab, const int* __restrict__ minmem,
+                          const int* __restrict__ cidat, int* __restrict__ agg) {
+    FOR_EACH(u, n) agg[u] = cidat[minmem[lab[u]]];
+}
+
+// coarse cover: matched pair k of a path is joined to pairs k-1 and k+1
+__global__ void k_shorten(int n, const unsigned char* __restrict__ ishead,
+                          const int* __restrict__ sprev, const int* __restrict__ snext,
+                          const int* __restrict__ minmem, const int* __restrict__ cidat,
+                          int* __restrict__ cn0, int* __restrict__ cn1) {
+    FOR_EACH(u64, n) {
+        int h = (int)u64;
+        if (!ishead[h]) continue;
+        int I = cidat[minmem[h]];
+        int a = sprev[h] >= 0 ? cidat[minmem[sprev[h]]] : -1;
+        int b = snext[h] >= 0 ? cidat[minmem[snext[h]]] : -1;
+        if (a >= 0 && b >= 0) { cn0[I] = min(a, b); cn1[I] = max(a, b); }
+        else if (a >= 0) { cn0[I] = a; cn1[I] = -1; }
+        else if (b >= 0) { cn0[I] = b; cn1[I] = -1; }
+    }
+}
+
+__global__ void k_count_agg(int n, const int* __restrict__ agg, int* __restrict__ cnt) {
+    FOR_EACH(u, n) atomicAdd(cnt + agg[u], 1);
+}
+
+__global__ void k_fill_members(int n, const int* __restrict__ agg, const int* __restrict__ aptr,
+                               int* __restrict__ fillc, int* __restrict__ mem) {
+    FOR_EACH(u, n) {
+        int I = agg[u];
+        mem[aptr[I] + atomicAdd(fillc + I, 1)] = (int)u;
+    }
+}
+
+__global__ void k_sort_members(int nc, const int* __restrict__ aptr, int* __restrict__ mem) {
+    FOR_EACH(I, nc) {
+        int b = aptr[I], e = aptr[I + 1];
+        for (int i = b + 1; i < e; ++i) {
+            int x = mem[i], j = i;
+            while (j > b && mem[j - 1] > x) { mem[j] = mem[j - 1]; --j; }
+            mem[j] = x;
+        }
+    }
+}
+
+// P_1 carries e: (P_1)_uI = e_u; an aggregate where e vanishes uses 1
+__global__ void k_pval(int nc, const int* __restrict__ aptr, const int* __restrict__ mem,
+                       const double* __restrict__ e, double* __restrict__ pval) {
+    FOR_EACH(I, nc) {
+        int b = aptr[I], en = aptr[I + 1];
+        bool zero = true;
+        for (int t = b; t < en; ++t) if (e[mem[t]] != 0.0) zero = false;
+        for (int t = b; t < en; ++t) pval[mem[t]] = zero ? 1.0 : e[mem[t]];
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+template <class Src>
+static void row_product(Ctx& c, int32_t nrows, const Src& src, DBuf<int32_t>& optr,
+                        DBuf<int32_t>& ocol, DBuf<double>* oval, int64_t* nnz_out) {
+    cudaStream_t s = c.stream;
+    DBuf<int32_t> cnt, long_list, long_count;
+    DBuf<unsigned char> is_long;
+    cnt.alloc(c.mem, nrows);
+    long_list.alloc(c.mem, nrows);
+    long_count.alloc(c.mem, 1);
+    is_long.alloc(c.mem, nrows);
+    PC_CUDA(cudaMemsetAsync(long_count.p, 0, sizeof(int32_t), s));
+    k_rowprod_thread<Src, false><<<grid1(nrows), kBlock, 0, s>>>(
+        nrows, src, cnt.p, is_long.p, long_list.p, long_count.p, nullptr, nullptr, nullptr);
+    PC_LAUNCH("rowprod_thread(count)");
+    int32_t nlong = read_i32(c, long_count.p);
+    std::vector<int32_t> rowsB, rowsC;
+    std::vector<int64_t> ubC;
+    DBuf<int32_t> dB, dC;
+    DBuf<int64_t> offC;
+    DBuf<uint64_t> gkeys;
+    DBuf<double> gvals;
+    if (nlong > 0) {
+        std::vector<int32_t> rows(nlong);
+        d2h(c, rows.data(), long_list.p, nlong);
+        std::sort(rows.begin(), rows.end());   // deterministic order of the block launches
+        DBuf<int32_t> drows;
+        DBuf<int64_t> ub;
+        drows.alloc(c.mem, nlong);
+        ub.alloc(c.mem, nlong);
+        PC_CUDA(cudaMemcpyAsync(drows.p, rows.data(), sizeof(int32_t) * nlong, cudaMemcpyHostToDevice, s));
+        k_rowprod_ub<Src><<<grid1(nlong), kBlock, 0, s>>>(nlong, drows.p, src, ub.p);
+        PC_LAUNCH("rowprod_ub");
+        std::vector<int64_t> hub(nlong);
+        d2h(c, hub.data(), ub.p, nlong);
+        int64_t totC = 0;
+        std::vector<int64_t> hoff;
+        for (int32_t i = 0; i < nlong; ++i) {
+            if (hub[i] >= (int64_t)1 << 31) fail(PCAMG_ERR_INVALID, "row product: a row has 2^31 or more contributions");
+            if (hub[i] <= kBlockCap) rowsB.push_back(rows[i]);
+            else {
+                rowsC.push_back(rows[i]);
+                hoff.push_back(totC);
+                int64_t P = 1;
+                while (P < hub[i]) P <<= 1;
+                totC += P;
+            }
+        }
+        if (!rowsB.empty()) {
+            dB.alloc(c.mem, rowsB.size());
+            PC_CUDA(cudaMemcpyAsync(dB.p, rowsB.data(), sizeof(int32_t) * rowsB.size(), cudaMemcpyHostToDevice, s));
+            size_t smem = kBlockCap * (sizeof(uint64_t) + sizeof(double));
+            k_rowprod_block<Src, false, false><<<(unsigned)rowsB.size(), kBlock, smem, s>>>(
+                dB.p, src, cnt.p, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+            PC_LAUNCH("rowprod_block(count)");
+        }
+        if (!rowsC.empty()) {
+            dC.alloc(c.mem, rowsC.size());
+            offC.alloc(c.mem, rowsC.size());
+            gkeys.alloc(c.mem, totC);
+            gvals.alloc(c.mem, totC);
+            PC_CUDA(cudaMemcpyAsync(dC.p, rowsC.data(), sizeof(int32_t) * rowsC.size(), cudaMemcpyHostToDevice, s));
+            PC_CUDA(cudaMemcpyAsync(offC.p, hoff.data(), sizeof(int64_t) * hoff.size(), cudaMemcpyHostToDevice, s));
+            k_rowprod_block<Src, false, true><<<(unsigned)rowsC.size(), kBlock, 0, s>>>(
+                dC.p, src, cnt.p, nullptr, nullptr, nullptr, gkeys.p, gvals.p, offC.p);
+            PC_LAUNCH("rowprod_global(count)");
+        }
+        sync(c);
+    }
+    optr.alloc(c.mem, (size_t)nrows + 1);
+    int64_t total = scan_i32(c, cnt.p, optr.p, nrows);
+    if (total >= ((int64_t)1 << 31)) fail(PCAMG_ERR_INVALID, "row product: result has 2^31 or more entries");
+    ocol.alloc(c.mem, total);
+    double* ov = nullptr;
+    if (oval) { oval->alloc(c.mem, total); ov = oval->p; }
+    k_rowprod_thread<Src, true><<<grid1(nrows), kBlock, 0, s>>>(
+        nrows, src, nullptr, is_long.p, nullptr, nullptr, optr.p, ocol.p, ov);
+    PC_LAUNCH("rowprod_thread(fill)");
+    if (!rowsB.empty()) {
+        size_t smem = kBlockCap * (sizeof(uint64_t) + sizeof(double));
+        k_rowprod_block<Src, true, false><<<(unsigned)rowsB.size(), kBlock, smem, s>>>(
+            dB.p, src, nullptr, optr.p, ocol.p, ov, nullptr, nullptr, nullptr);
+        PC_LAUNCH("rowprod_block(fill)");
+    }
+    if (!rowsC.empty()) {
+        k_rowprod_block<Src, true, true><<<(unsigned)rowsC.size(), kBlock, 0, s>>>(
+            dC.p, src, nullptr, optr.p, ocol.p, ov, gkeys.p, gvals.p, offC.p);
+        PC_LAUNCH("rowprod_global(fill)");
+    }
+    *nnz_out = total;
+    sync(c);
+}
+
+void build_candidates(Ctx& c, const double* e, Reweighted& out) {
+    CandSrc src{c.rowptr.p, c.col.p};
+    row_product(c, c.n, src, out.ptr, out.col, nullptr, &out.nnz);
+    out.w.alloc(c.mem, out.nnz);
+    int nb = 256;
+    DBuf<double> part;
+    part.alloc(c.mem, nb + 1);
+    k_maxabs<<<nb, kBlock, 0, c.stream>>>(c.n, e, part.p);
+    k_delta<<<1, 1, 0, c.stream>>>(nb, part.p, part.p + nb);
+    k_weights<<<grid1(c.n), kBlock, 0, c.stream>>>(c.n, out.ptr.p, out.col.p, e, part.p + nb, out.w.p);
+    PC_LAUNCH("weights");
+    sync(c);
+}
+
+int32_t path_cover(Ctx& c, int32_t n, const Reweighted& t, int32_t* nbr0, int32_t* nbr1) {
+    cudaStream_t s = c.stream;
+    // rows in proposal order
+    DBuf<int32_t> scol, long_list, long_count;
+    DBuf<double> sw;
+    DBuf<unsigned char> is_long;
+    scol.alloc(c.mem, t.nnz);
+    sw.alloc(c.mem, t.nnz);
+    long_list.alloc(c.mem, n);
+    long_count.alloc(c.mem, 1);
+    is_long.alloc(c.mem, n);
+    PC_CUDA(cudaMemsetAsync(long_count.p, 0, sizeof(int32_t), s));
+    k_order_rows_thread<<<grid1(n), kBlock, 0, s>>>(n, t.ptr.p, t.col.p, t.w.p, scol.p, sw.p,
+                                                     is_long.p, long_list.p, long_count.p);
+    PC_LAUNCH("order_rows");
+    int32_t nlong = read_i32(c, long_count.p);
+    if (nlong > 0) {
+        std::vector<int32_t> rows(nlong);
+        d2h(c, rows.data(), long_list.p, nlong);
+        std::sort(rows.begin(), rows.end());
+        std::vector<int32_t> hptr((size_t)n + 1);
+        d2h(c, hptr.data(), t.ptr.p, (size_t)n + 1);
+        std::vector<int64_t> off(nlong);
+        int64_t tot = 0;
+        for (int32_t i = 0; i < nlong; ++i) {
+            off[i] = tot;
+            int64_t len = hptr[rows[i] + 1] - hptr[rows[i]], P = 1;
+            while (P < len) P <<= 1;
+            tot += P;
+        }
+        DBuf<int32_t> drows;
+        DBuf<int64_t> doff;
+        DBuf<uint32_t> gidx;
+        drows.alloc(c.mem, nlong);
+        doff.alloc(c.mem, nlong);
+        gidx.alloc(c.mem, tot);
+        PC_CUDA(cudaMemcpyAsync(drows.p, rows.data(), sizeof(int32_t) * nlong, cudaMemcpyHostToDevice, s));
+        PC_CUDA(cudaMemcpyAsync(doff.p, off.data(), sizeof(int64_t) * nlong, cudaMemcpyHostToDevice, s));
+        k_order_rows_block<<<nlong, kBlock, 0, s>>>(drows.p, t.ptr.p, t.col.p, t.w.p, scol.p, sw.p, gidx.p, doff.p);
+        PC_LAUNCH("order_rows_block");
+        sync(c);
+    }
+    DBuf<int32_t> deg, oe, cptr, bv, cf, ct, counters;
+    deg.alloc(c.mem, n); oe.alloc(c.mem, n); cptr.alloc(c.mem, n); bv.alloc(c.mem, n);
+    cf.alloc(c.mem, n); ct.alloc(c.mem, n);
+    const int kBatchMax = 64;
+    counters.alloc(c.mem, kBatchMax);
+    k_cover_init<<<grid1(n), kBlock, 0, s>>>(n, t.ptr.p, deg.p, oe.p, cptr.p, nbr0, nbr1);
+    fill_i32(s, n, -1, cf.p);
+    int32_t rounds = 0, batch = 4;
+    std::vector<int32_t> hc(kBatchMax);
+    for (;;) {
+        PC_CUDA(cudaMemsetAsync(counters.p, 0, sizeof(int32_t) * batch, s));
+        for (int r = 0; r < batch; ++r) {
+            k_cover_best<<<grid1(n), kBlock, 0, s>>>(n, t.ptr.p, scol.p, deg.p, oe.p, cptr.p, bv.p);
+            k_cover_choose<<<grid1(n), kBlock, 0, s>>>(n, deg.p, oe.p, cptr.p, bv.p, sw.p, cf.p, ct.p);
+            k_cover_accept<<<grid1(n), kBlock, 0, s>>>(n, deg.p, oe.p, cf.p, ct.p, nbr0, nbr1, counters.p + r);
+        }
+        PC_LAUNCH("cover rounds");
+        d2h(c, hc.data(), counters.p, batch);
+        bool done = false;
+        for (int r = 0; r < batch; ++r) {
+            ++rounds;
+            if (hc[r] == 0) { done = true; break; }
+        }
+        if (done) break;
+        if (rounds > n + 1) fail(PCAMG_ERR_ROUND_CAP, "path cover rounds exceeded n");
+        batch = std::min(batch * 2, kBatchMax);
+    }
+    k_canonical<<<grid1(n), kBlock, 0, s>>>(n, nbr0, nbr1);
+    PC_LAUNCH("canonical");
+    sync(c);
+    return rounds;
+}
+
+int32_t aggregate_level(Ctx& c, int32_t n, const int32_t* nbr0, const int32_t* nbr1,
+                        const Reweighted& t, DBuf<int32_t>& agg, DBuf<int32_t>& cnbr0,
+                        DBuf<int32_t>& cnbr1, int32_t* rounds_out) {
+    cudaStream_t s = c.stream;
+    int64_t nh = 2 * (int64_t)n;
+    DBuf<int32_t> jmp[2], dist[2], endv[2], active;
+    for (int k = 0; k < 2; ++k) { jmp[k].alloc(c.mem, nh); dist[k].alloc(c.mem, nh); endv[k].alloc(c.mem, nh); }
+    active.alloc(c.mem, 1);
+    k_rank_init<<<grid1(n), kBlock, 0, s>>>(n, nbr0, nbr1, jmp[0].p, dist[0].p, endv[0].p);
+    PC_LAUNCH("rank_init");
+    int cur = 0;
+    for (int it = 0; it < 40; ++it) {
+        PC_CUDA(cudaMemsetAsync(active.p, 0, sizeof(int32_t), s));
+        k_rank_jump<<<grid1(nh), kBlock, 0, s>>>((int)nh, jmp[cur].p, dist[cur].p, endv[cur].p,
+                                                 jmp[1 - cur].p, dist[1 - cur].p, endv[1 - cur].p, active.p);
+        PC_LAUNCH("rank_jump");
+        cur = 1 - cur;
+        if (read_i32(c, active.p) == 0) break;
+        if (it == 39) fail(PCAMG_ERR_ROUND_CAP, "list ranking did not finish");
+    }
+    DBuf<int32_t> lab, size, sprev, snext, best, st, jg, gcnt, goff, gfill, list, nleft;
+    DBuf<unsigned char> ishead;
+    lab.alloc(c.mem, n); size.alloc(c.mem, n); sprev.alloc(c.mem, n); snext.alloc(c.mem, n);
+    best.alloc(c.mem, n); st.alloc(c.mem, n); jg.alloc(c.mem, n); gcnt.alloc(c.mem, n);
+    goff.alloc(c.mem, (size_t)n + 1); gfill.alloc(c.mem, n); list.alloc(c.mem, n); nleft.alloc(c.mem, 1);
+    ishead.alloc(c.mem, n);
+    fill_i32(s, n, -1, lab.p);
+    fill_i32(s, n, 0, size.p);
+    k_pair<<<grid1(n), kBlock, 0, s>>>(n, nbr0, nbr1, dist[cur].p, endv[cur].p, lab.p, size.p,
+                                       sprev.p, snext.p, ishead.p);
+    k_best<<<grid1(n), kBlock, 0, s>>>(n, t.ptr.p, t.col.p, t.w.p, best.p, lab.p, size.p);
+    PC_LAUNCH("pair/best");
+    int32_t rounds = 0;
+    for (;;) {
+        PC_CUDA(cudaMemsetAsync(gcnt.p, 0, sizeof(int32_t) * n, s));
+        PC_CUDA(cudaMemsetAsync(nleft.p, 0, sizeof(int32_t), s));
+        k_left_classify<<<grid1(n), kBlock, 0, s>>>(n, lab.p, best.p, st.p, jg.p, gcnt.p, nleft.p);
+        PC_LAUNCH("left_classify");
+        if (read_i32(c, nleft.p) == 0) break;
+        if (rounds >= c.p.round_cap) {
+            k_left_tail<<<1, 1, 0, s>>>(n, best.p, lab.p, size.p);
+            PC_LAUNCH("left_tail");
+            ++rounds;
+            break;
+        }
+        k_left_case1<<<grid1(n), kBlock, 0, s>>>(n, st.p, best.p, lab.p, size.p);
+        scan_i32(c, gcnt.p, goff.p, n);
+        PC_CUDA(cudaMemsetAsync(gfill.p, 0, sizeof(int32_t) * n, s));
+        k_left_fill<<<grid1(n), kBlock, 0, s>>>(n, st.p, jg.p, goff.p, gfill.p, list.p);
+        k_left_join<<<grid1(n), kBlock, 0, s>>>(n, goff.p, list.p, best.p, lab.p, size.p);
+        PC_LAUNCH("left_round");
+        ++rounds;
+    }
+    // numbering by smallest member
+    DBuf<int32_t> minmem, flag, cidat;
+    minmem.alloc(c.mem, n); flag.alloc(c.mem, n); cidat.alloc(c.mem, (size_t)n + 1);
+    fill_i32(s, n, 0x7fffffff, minmem.p);
+    k_minmem<<<grid1(n), kBlock, 0, s>>>(n, lab.p, minmem.p);
+    k_isfirst<<<grid1(n), kBlock, 0, s>>>(n, lab.p, minmem.p, flag.p);
+    PC_LAUNCH("numbering");
+    int32_t nc = (int32_t)scan_i32(c, flag.p, cidat.p, n);
+    agg.alloc(c.mem, n);
+    k_agg_ids<<<grid1(n), kBlock, 0, s>>>(n, lab.p, minmem.p, cidat.p, agg.p);
+    cnbr0.alloc(c.mem, nc);
+    cnbr1.alloc(c.mem, nc);
+    fill_i32(s, nc, -1, cnbr0.p);
+    fill_i32(s, nc, -1, cnbr1.p);
+    k_shorten<<<grid1(n), kBlock, 0, s>>>(n, ishead.p, sprev.p, snext.p, minmem.p, cidat.p, cnbr0.p, cnbr1.p);
+    PC_LAUNCH("agg/shorten");
+    sync(c);
+    if (rounds_out) *rounds_out = rounds;
+    return nc;
+}
+
+void build_members(Ctx& c, int32_t n, int32_t nc, const int32_t* agg, DBuf<int32_t>& agg_ptr,
+                   DBuf<int32_t>& agg_mem) {
+    cudaStream_t s = c.stream;
+    DBuf<int32_t> cnt, fillc;
+    cnt.alloc(c.mem, nc);
+    fillc.alloc(c.mem, nc);
+    PC_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * nc, s));
+    PC_CUDA(cudaMemsetAsync(fillc.p, 0, sizeof(int32_t) * nc, s));
+    k_count_agg<<<grid1(n), kBlock, 0, s>>>(n, agg, cnt.p);
+    agg_ptr.alloc(c.mem, (size_t)nc + 1);
+    scan_i32(c, cnt.p, agg_ptr.p, nc);
+    agg_mem.alloc(c.mem, n);
+    k_fill_members<<<grid1(n), kBlock, 0, s>>>(n, agg, agg_ptr.p, fillc.p, agg_mem.p);
+    k_sort_members<<<grid1(nc), kBlock, 0, s>>>(nc, agg_ptr.p, agg_mem.p);
+    PC_LAUNCH("members");
+}
+
+void build_pval(Ctx& c, int32_t n, int32_t nc, const int32_t* agg_ptr, const int32_t* agg_mem,
+                const double* e, DBuf<double>& pval) {
+    pval.alloc(c.mem, n);
+    k_pval<<<grid1(nc), kBlock, 0, c.stream>>>(nc, agg_ptr, agg_mem, e, pval.p);
+    PC_LAUNCH("pval");
+}
+
+int64_t galerkin(Ctx& c, int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                 int32_t nc, const int32_t* agg, const int32_t* agg_ptr, const int32_t* agg_mem,
+                 const double* pval, bool drop_diag, DBuf<int32_t>& optr, DBuf<int32_t>& ocol,
+                 DBuf<double>& oval) {
+    (void)n;
+    GalSrc src{agg_ptr, agg_mem, rowptr, col, val, pval, agg, drop_diag ? 1 : 0};
+    int64_t nnz = 0;
+    row_product(c, nc, src, optr, ocol, &oval, &nnz);
+    return nnz;
+}
+
+}  // namespace pc

@@ -1,0 +1,277 @@
+// Sparse level operators of the cycle: residual r = b - A x (with the fused
+// ||r||^2 partials), one colour of a Gauss-Seidel sweep, restriction by P^T,
+// prolongation by P, and the dense coarsest solve.
+//
+// Rows are processed by groups of LPR lanes (LPR = power of two >= the mean
+// row length, so a warp reads several consecutive rows as one coalesced run of
+// column indices and values); each group reduces with warp shuffles.
+#include "pcamg_internal.cuh"
+
+namespace pc {
+
+int lanes_per_row(int32_t n, int64_t nnz) {
+    double avg = n > 0 ? (double)nnz / (double)n : 1.0;
+    int l = 2;
+    while (l < 32 && l < avg) l <<= 1;
+    return l;
+}
+
+namespace {
+
+template <int LPR, class T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+    for (int o = LPR / 2; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o, LPR);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+inline int sparse_grid(int64_t rows, int lpr, int block = kBlock) {
+    int64_t threads = rows * lpr;
+    int64_t g = (threads + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > (int64_t)kNumSMs * 8) g = kNumSMs * 8;
+    return (int)g;
+}
+
+// r = b - A x; when partial != null, block b writes sum of r_i^2 of its rows.
+template <class T, int LPR>
+__global__ void __launch_bounds__(kBlock) k_residual(int n, const int* __restrict__ rowptr,
+                                                     const int* __restrict__ col,
+                                                     const T* __restrict__ val,
+                                                     const T* __restrict__ x,
+                                                     const T* __restrict__ b, T* __restrict__ r,
+                                                     double* __restrict__ partial) {
+    constexpr int RPW = 32 / LPR;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane % LPR, grp = lane / LPR;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double acc2 = 0.0;
+    for (int64_t row0 = warp * RPW; row0 < n; row0 += nwarps * RPW) {
+        int64_t row = row0 + grp;
+        T s = 0;
+        if (row < n) {
+            int beg = __ldg(rowptr + row), end = __ldg(rowptr + row + 1);
+            for (int k = beg + sub; k < end; k += LPR) s += __ldg(val + k) * __ldg(x + __ldg(col + k));
+        }
+        s = group_sum<LPR>(s);
+        if (sub == 0 && row < n) {
+            T rr = __ldg(b + row) - s;
+            r[row] = rr;
+            acc2 += (double)rr * (double)rr;
+        }
+    }
+    if (partial) {
+        __shared__ double ws[kBlock / 32];
+        acc2 = warp_sum_d(acc2);
+        if (lane == 0) ws[threadIdx.x >> 5] = acc2;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double v = threadIdx.x < kBlock / 32 ? ws[threadIdx.x] : 0.0;
+            v = warp_sum_d(v);
+            if (threadIdx.x == 0) partial[blockIdx.x] = v;
+        }
+    }
+}
+
+__global__ void k_finish(int nb, const double* __restrict__ partial, double* __restrict__ out) {
+    __shared__ double ws[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += partial[i];
+    s = warp_sum_d(s);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.0;
+        v = warp_sum_d(v);
+        if (threadIdx.x == 0) *out = v;
+    }
+}
+
+// y = A x
+template <int LPR>
+__global__ void __launch_bounds__(kBlock) k_spmv(int n, const int* __restrict__ rowptr,
+                                                 const int* __restrict__ col,
+                                                 const double* __restrict__ val,
+                                                 const double* __restrict__ x,
+                                                 double* __restrict__ y) {
+    constexpr int RPW = 32 / LPR;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane % LPR, grp = lane / LPR;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t row0 = warp * RPW; row0 < n; row0 += nwarps * RPW) {
+        int64_t row = row0 + grp;
+        double s = 0;
+        if (row < n) {
+            int beg = __ldg(rowptr + row), end = __ldg(rowptr + row + 1);
+            for (int k = beg + sub; k < end; k += LPR) s += __ldg(val + k) * __ldg(x + __ldg(col + k));
+        }
+        s = group_sum<LPR>(s);
+        if (sub == 0 && row < n) y[row] = s;
+    }
+}
+
+// One colour of Gauss-Seidel: x_i = (b_i - sum_{j != i} a_ij x_j) / a_ii for the
+// listed rows. Rows of one colour share no edge, so they update independently.
+template <class T, int LPR>
+__global__ void __launch_bounds__(kBlock) k_gs(int nrows, const int* __restrict__ rows,
+                                               const int* __restrict__ rowptr,
+                                               const int* __restrict__ col,
+                                               const T* __restrict__ val,
+                                               const T* __restrict__ b, T* __restrict__ x) {
+    constexpr int RPW = 32 / LPR;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane % LPR, grp = lane / LPR;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t t0 = warp * RPW; t0 < nrows; t0 += nwarps * RPW) {
+        int64_t t = t0 + grp;
+        T s = 0, d = 0;
+        int row = -1;
+        if (t < nrows) {
+            row = __ldg(rows + t);
+            int beg = __ldg(rowptr + row), end = __ldg(rowptr + row + 1);
+            for (int k = beg + sub; k < end; k += LPR) {
+                int j = __ldg(col + k);
+                T a = __ldg(val + k);
+                if (j == row) d = a;
+                else s += a * x[j];
+            }
+        }
+        s = group_sum<LPR>(s);
+        d = group_sum<LPR>(d);
+        if (sub == 0 && t < nrows) x[row] = (__ldg(b + row) - s) / d;
+    }
+}
+
+template <class T>
+__global__ void k_restrict(int nc, const int* __restrict__ agg_ptr, const int* __restrict__ mem,
+                           const T* __restrict__ pval, const T* __restrict__ r, T* __restrict__ bc) {
+    for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
+        T s = 0;
+        int beg = __ldg(agg_ptr + I), end = __ldg(agg_ptr + I + 1);
+        for (int t = beg; t < end; ++t) {
+            int u = __ldg(mem + t);
+            s += pval ? __ldg(pval + u) * __ldg(r + u) : __ldg(r + u);
+        }
+        bc[I] = s;
+    }
+}
+
+template <class T>
+__global__ void k_prolong(int n, const int* __restrict__ agg, const T* __restrict__ pval,
+                          const T* __restrict__ xc, T* __restrict__ x) {
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
+        T c = __ldg(xc + __ldg(agg + u));
+        x[u] += pval ? __ldg(pval + u) * c : c;
+    }
+}
+
+// x = Xinv b, one warp per row (Xinv row-major, FP64)
+template <class T>
+__global__ void k_coarse_apply(int m, const double* __restrict__ X, const T* __restrict__ b,
+                               T* __restrict__ x) {
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int i = warp; i < m; i += nw) {
+        double s = 0.0;
+        for (int j = lane; j < m; j += 32) s += X[(size_t)i * m + j] * (double)b[j];
+        s = warp_sum_d(s);
+        if (lane == 0) x[i] = (T)s;
+    }
+}
+
+inline int simple_grid(int64_t n) {
+    int64_t g = (n + kBlock - 1) / kBlock;
+    if (g < 1) g = 1;
+    if (g > (int64_t)kNumSMs * 16) g = kNumSMs * 16;
+    return (int)g;
+}
+
+}  // namespace
+
+#define PC_LPR_DISPATCH(LPRV, CALL) \
+    switch (LPRV) {                  \
+        case 2: CALL(2); break;      \
+        case 4: CALL(4); break;      \
+        case 8: CALL(8); break;      \
+        case 16: CALL(16); break;    \
+        default: CALL(32); break;    \
+    }
+
+void residual64(cudaStream_t s, const Csr& A, const double* x, const double* b, double* r,
+                double* partial, double* norm2) {
+    int g = sparse_grid(A.n, A.lpr);
+#define CALL(L) k_residual<double, L><<<g, kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, b, r, norm2 ? partial : nullptr)
+    PC_LPR_DISPATCH(A.lpr, CALL)
+#undef CALL
+    if (norm2) k_finish<<<1, 1024, 0, s>>>(g, partial, norm2);
+    PC_LAUNCH("residual64");
+}
+
+void residual32(cudaStream_t s, const Csr& A, const float* x, const float* b, float* r) {
+    int g = sparse_grid(A.n, A.lpr);
+#define CALL(L) k_residual<float, L><<<g, kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val32, x, b, r, nullptr)
+    PC_LPR_DISPATCH(A.lpr, CALL)
+#undef CALL
+    PC_LAUNCH("residual32");
+}
+
+void spmv64(cudaStream_t s, const Csr& A, const double* x, double* y) {
+    int g = sparse_grid(A.n, A.lpr);
+#define CALL(L) k_spmv<L><<<g, kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, y)
+    PC_LPR_DISPATCH(A.lpr, CALL)
+#undef CALL
+    PC_LAUNCH("spmv64");
+}
+
+template <class T>
+void gs_colour(cudaStream_t s, const Csr& A, const int32_t* rows, int32_t nrows, const T* b, T* x) {
+    if (nrows <= 0) return;
+    int g = sparse_grid(nrows, A.lpr);
+    const T* val;
+    if constexpr (sizeof(T) == 8) val = A.val; else val = A.val32;
+#define CALL(L) k_gs<T, L><<<g, kBlock, 0, s>>>(nrows, rows, A.rowptr, A.col, val, b, x)
+    PC_LPR_DISPATCH(A.lpr, CALL)
+#undef CALL
+    PC_LAUNCH("gs_colour");
+}
+
+template <class T>
+void restrict_agg(cudaStream_t s, int32_t nc, const int32_t* agg_ptr, const int32_t* agg_mem,
+                  const T* pval, const T* r, T* bc) {
+    k_restrict<T><<<simple_grid(nc), kBlock, 0, s>>>(nc, agg_ptr, agg_mem, pval, r, bc);
+    PC_LAUNCH("restrict");
+}
+
+template <class T>
+void prolong_add(cudaStream_t s, int32_t n, const int32_t* agg, const T* pval, const T* xc, T* x) {
+    k_prolong<T><<<simple_grid(n), kBlock, 0, s>>>(n, agg, pval, xc, x);
+    PC_LAUNCH("prolong");
+}
+
+template <class T>
+void coarse_apply(cudaStream_t s, int32_t m, const double* Xinv, const T* b, T* x) {
+    int g = (m * 32 + kBlock - 1) / kBlock;
+    if (g > kNumSMs * 4) g = kNumSMs * 4;
+    k_coarse_apply<T><<<g, kBlock, 0, s>>>(m, Xinv, b, x);
+    PC_LAUNCH("coarse_apply");
+}
+
+template void gs_colour<double>(cudaStream_t, const Csr&, const int32_t*, int32_t, const double*, double*);
+template void gs_colour<float>(cudaStream_t, const Csr&, const int32_t*, int32_t, const float*, float*);
+template void restrict_agg<double>(cudaStream_t, int32_t, const int32_t*, const int32_t*, const double*, const double*, double*);
+template void restrict_agg<float>(cudaStream_t, int32_t, const int32_t*, const int32_t*, const float*, const float*, float*);
+template void prolong_add<double>(cudaStream_t, int32_t, const int32_t*, const double*, const double*, double*);
+template void prolong_add<float>(cudaStream_t, int32_t, const int32_t*, const float*, const float*, float*);
+template void coarse_apply<double>(cudaStream_t, int32_t, const double*, const double*, double*);
+template void coarse_apply<float>(cudaStream_t, int32_t, const double*, const float*, float*);
+
+}  // namespace pc

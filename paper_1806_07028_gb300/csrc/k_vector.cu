@@ -1,0 +1,340 @@
+// Vector kernels: deterministic reductions, axpy-type updates, precision casts,
+// scans and the Philox4x64-10 generator (Salmon et al., SC'11).
+#include "pcamg_internal.cuh"
+
+namespace pc {
+
+namespace {
+
+constexpr int kRedBlock = 256;
+constexpr int kRedMaxBlocks = 1024;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block sum in a fixed tree: warp shuffles, then warp 0 over the warp sums.
+__device__ double block_sum(double v) {
+    __shared__ double ws[32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) ws[wid] = v;
+    __syncthreads();
+    int nw = (blockDim.x + 31) >> 5;
+    v = (threadIdx.x < nw) ? ws[threadIdx.x] : 0.0;
+    if (wid == 0) v = warp_sum(v);
+    __syncthreads();
+    return v;  // valid in thread 0
+}
+
+__global__ void k_dot_partial(int64_t n, const double* __restrict__ x, const double* __restrict__ y,
+                              double* __restrict__ partial) {
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += x[i] * (y ? y[i] : 1.0);
+    s = block_sum(s);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void k_finish_sum(int nb, const double* __restrict__ partial, double* __restrict__ out) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += partial[i];
+    s = block_sum(s);
+    if (threadIdx.x == 0) *out = s;
+}
+
+__global__ void k_axpy(int64_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] += a * x[i];
+}
+
+__global__ void k_axpy_dev(int64_t n, const double* __restrict__ a, double sign, const double* __restrict__ x,
+                           double* __restrict__ y) {
+    double aa = sign * (*a);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] += aa * x[i];
+}
+
+__global__ void k_xpby_dev(int64_t n, const double* __restrict__ x, const double* __restrict__ beta,
+                           double* __restrict__ y) {
+    double b = *beta;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = x[i] + b * y[i];
+}
+
+__global__ void k_sub_mean(int64_t n, double* __restrict__ x, const double* __restrict__ total) {
+    double m = (*total) / (double)n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] -= m;
+}
+
+__global__ void k_scale_dev(int64_t n, double* __restrict__ x, const double* __restrict__ num,
+                            const double* __restrict__ den) {
+    double f = (num ? *num : 1.0) / (*den);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] *= f;
+}
+
+__global__ void k_copy(int64_t n, const double* __restrict__ x, double* __restrict__ y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = x[i];
+}
+
+__global__ void k_fill(int64_t n, double v, double* __restrict__ y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = v;
+}
+
+__global__ void k_fill_i32(int64_t n, int32_t v, int32_t* __restrict__ y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = v;
+}
+
+__global__ void k_cast_scaled_f32(int64_t n, const double* __restrict__ x, const double* __restrict__ inv,
+                                  float* __restrict__ y) {
+    double f = inv ? *inv : 1.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (float)(x[i] * f);
+}
+
+__global__ void k_add_scaled_f32(int64_t n, const float* __restrict__ c, const double* __restrict__ sc,
+                                 double* __restrict__ x) {
+    double f = *sc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += f * (double)c[i];
+}
+
+__global__ void k_cast_f64(int64_t n, const float* __restrict__ x, double* __restrict__ y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (double)x[i];
+}
+
+// Philox4x64-10 from its published definition: per round, words 0 and 2 are
+// multiplied by two odd 64-bit constants; the high halves are xored with words
+// 1 and 3 and the round key; the key advances by two Weyl increments.
+__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += W0; k1 += W1; }
+        uint64_t lo0 = M0 * c[0], hi0 = __umul64hi(M0, c[0]);
+        uint64_t lo1 = M1 * c[2], hi1 = __umul64hi(M1, c[2]);
+        uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    }
+}
+
+__global__ void k_philox_uniform(uint64_t seed, int64_t n, double* __restrict__ out) {
+    // one thread per block of four outputs
+    int64_t nb = (n + 3) >> 2;
+    for (int64_t blk = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; blk < nb; blk += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t c[4] = {(uint64_t)blk, 0, 0, 0};
+        philox4x64_10(c, seed, 0);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            int64_t i = blk * 4 + w;
+            if (i < n) out[i] = __dsub_rn(ldexp((double)(c[w] >> 11), -52), 1.0);
+        }
+    }
+}
+
+// Small scalar algebra on device slots so that Krylov steps need no host trip.
+__global__ void k_scalar(int op, double* s, int a, int b, int c) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    switch (op) {
+        case SOP_DIV: s[c] = (s[b] != 0.0) ? s[a] / s[b] : 0.0; break;
+        case SOP_SQRT: s[c] = sqrt(s[a]); break;
+        case SOP_INV_SQRT: s[c] = (s[a] > 0.0) ? 1.0 / sqrt(s[a]) : 0.0; break;
+        case SOP_PCG_ALPHA: s[c] = (s[a] > 0.0 && s[b] > 0.0) ? s[a] / s[b] : 0.0; break;
+        case SOP_NEG_DIV: s[c] = (s[b] != 0.0) ? -s[a] / s[b] : 0.0; break;
+        case SOP_INV: s[c] = (s[a] != 0.0) ? 1.0 / s[a] : 0.0; break;
+        default: break;
+    }
+}
+
+// ---- scan: tile of 1024 per block (256 threads x 4) ------------------------
+template <class TI, class TO>
+__global__ void k_scan_tiles(int64_t n, const TI* __restrict__ in, TO* __restrict__ out,
+                             int64_t* __restrict__ tile_sum) {
+    __shared__ int64_t ws[32];
+    int64_t base = (int64_t)blockIdx.x * 1024 + threadIdx.x * 4;
+    int64_t v[4];
+    int64_t t = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        int64_t i = base + k;
+        v[k] = (i < n) ? (int64_t)in[i] : 0;
+        t += v[k];
+    }
+    // inclusive warp scan of t
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t inc = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) ws[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t w = (lane < (int)(blockDim.x >> 5)) ? ws[lane] : 0;
+        int64_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < (int)(blockDim.x >> 5)) ws[lane] = wi - w;  // exclusive warp offsets
+    }
+    __syncthreads();
+    int64_t run = ws[wid] + inc - t;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        int64_t i = base + k;
+        if (i < n) out[i] = (TO)run;
+        run += v[k];
+    }
+    if (threadIdx.x == blockDim.x - 1) tile_sum[blockIdx.x] = ws[wid] + inc;
+}
+
+template <class TO>
+__global__ void k_scan_add(int64_t n, TO* __restrict__ out, const int64_t* __restrict__ tile_off) {
+    int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+    int64_t add = tile_off[blockIdx.x];
+    for (int k = 0; k < 4; ++k, i += 256)
+        if (i < n) out[i] = (TO)((int64_t)out[i] + add);
+}
+
+__global__ void k_set_last(int64_t n, int64_t* __restrict__ tile_sum_total, const int64_t* __restrict__ tile_off,
+                           const int64_t* __restrict__ tile_sum, int64_t ntiles) {
+    *tile_sum_total = tile_off[ntiles - 1] + tile_sum[ntiles - 1];
+}
+
+template <class TO>
+__global__ void k_store_total(TO* __restrict__ out, int64_t n, const int64_t* __restrict__ total) {
+    out[n] = (TO)(*total);
+}
+
+inline int grid_for(int64_t n, int per_block = kBlock) {
+    int64_t g = (n + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > (int64_t)kNumSMs * 16) g = kNumSMs * 16;
+    return (int)g;
+}
+
+}  // namespace
+
+int reduce_blocks(int64_t n) {
+    int64_t g = (n + 4 * kRedBlock - 1) / (4 * kRedBlock);
+    if (g < 1) g = 1;
+    if (g > kRedMaxBlocks) g = kRedMaxBlocks;
+    return (int)g;
+}
+
+void dot(cudaStream_t s, int64_t n, const double* x, const double* y, double* partial, double* out) {
+    int nb = reduce_blocks(n);
+    k_dot_partial<<<nb, kRedBlock, 0, s>>>(n, x, y, partial);
+    k_finish_sum<<<1, 1024, 0, s>>>(nb, partial, out);
+    PC_LAUNCH("dot");
+}
+
+void sum(cudaStream_t s, int64_t n, const double* x, double* partial, double* out) {
+    dot(s, n, x, nullptr, partial, out);
+}
+
+void axpy(cudaStream_t s, int64_t n, double a, const double* x, double* y) {
+    k_axpy<<<grid_for(n), kBlock, 0, s>>>(n, a, x, y);
+    PC_LAUNCH("axpy");
+}
+void axpy_dev(cudaStream_t s, int64_t n, const double* a, double sign, const double* x, double* y) {
+    k_axpy_dev<<<grid_for(n), kBlock, 0, s>>>(n, a, sign, x, y);
+    PC_LAUNCH("axpy_dev");
+}
+void xpby_dev(cudaStream_t s, int64_t n, const double* x, const double* beta, double* y) {
+    k_xpby_dev<<<grid_for(n), kBlock, 0, s>>>(n, x, beta, y);
+    PC_LAUNCH("xpby_dev");
+}
+void sub_mean(cudaStream_t s, int64_t n, double* x, const double* total) {
+    k_sub_mean<<<grid_for(n), kBlock, 0, s>>>(n, x, total);
+    PC_LAUNCH("sub_mean");
+}
+void scale_dev(cudaStream_t s, int64_t n, double* x, const double* num, const double* den) {
+    k_scale_dev<<<grid_for(n), kBlock, 0, s>>>(n, x, num, den);
+    PC_LAUNCH("scale_dev");
+}
+void copy(cudaStream_t s, int64_t n, const double* x, double* y) {
+    k_copy<<<grid_for(n), kBlock, 0, s>>>(n, x, y);
+    PC_LAUNCH("copy");
+}
+void fill(cudaStream_t s, int64_t n, double v, double* y) {
+    k_fill<<<grid_for(n), kBlock, 0, s>>>(n, v, y);
+    PC_LAUNCH("fill");
+}
+void fill_i32(cudaStream_t s, int64_t n, int32_t v, int32_t* y) {
+    k_fill_i32<<<grid_for(n), kBlock, 0, s>>>(n, v, y);
+    PC_LAUNCH("fill_i32");
+}
+void cast_scaled_f32(cudaStream_t s, int64_t n, const double* x, const double* inv, float* y) {
+    k_cast_scaled_f32<<<grid_for(n), kBlock, 0, s>>>(n, x, inv, y);
+    PC_LAUNCH("cast_scaled_f32");
+}
+void cast_f32(cudaStream_t s, int64_t n, const double* x, float* y) { cast_scaled_f32(s, n, x, nullptr, y); }
+void add_scaled_f32(cudaStream_t s, int64_t n, const float* c, const double* scale, double* x) {
+    k_add_scaled_f32<<<grid_for(n), kBlock, 0, s>>>(n, c, scale, x);
+    PC_LAUNCH("add_scaled_f32");
+}
+void cast_f64(cudaStream_t s, int64_t n, const float* x, double* y) {
+    k_cast_f64<<<grid_for(n), kBlock, 0, s>>>(n, x, y);
+    PC_LAUNCH("cast_f64");
+}
+void philox_uniform(cudaStream_t s, uint64_t seed, int64_t n, double* out) {
+    k_philox_uniform<<<grid_for((n + 3) / 4), kBlock, 0, s>>>(seed, n, out);
+    PC_LAUNCH("philox_uniform");
+}
+void scalar_ops(cudaStream_t s, int op, double* slots, int a, int b, int c) {
+    k_scalar<<<1, 32, 0, s>>>(op, slots, a, b, c);
+    PC_LAUNCH("scalar_ops");
+}
+
+// Exclusive scan; out[n] receives the total. Scratch comes from the context.
+template <class TI, class TO>
+static int64_t scan_impl(Ctx& c, const TI* in, TO* out, int64_t n) {
+    int64_t ntiles = (n + 1023) / 1024;
+    if (ntiles == 0) {
+        TO z = 0;
+        PC_CUDA(cudaMemcpyAsync(out, &z, sizeof(TO), cudaMemcpyHostToDevice, c.stream));
+        sync(c);
+        return 0;
+    }
+    DBuf<int64_t> tsum, toff;
+    tsum.alloc(c.mem, ntiles + 1);
+    toff.alloc(c.mem, ntiles + 1);
+    k_scan_tiles<TI, TO><<<(unsigned)ntiles, 256, 0, c.stream>>>(n, in, out, tsum.p);
+    PC_LAUNCH("scan_tiles");
+    if (ntiles > 1) {
+        scan_impl<int64_t, int64_t>(c, tsum.p, toff.p, ntiles);
+        k_scan_add<TO><<<(unsigned)ntiles, 256, 0, c.stream>>>(n, out, toff.p);
+        PC_LAUNCH("scan_add");
+    } else {
+        int64_t z = 0;
+        PC_CUDA(cudaMemcpyAsync(toff.p, &z, sizeof(int64_t), cudaMemcpyHostToDevice, c.stream));
+        PC_CUDA(cudaMemcpyAsync(toff.p + 1, tsum.p, sizeof(int64_t), cudaMemcpyDeviceToDevice, c.stream));
+    }
+    // total = toff[ntiles-1] + tsum[ntiles-1]
+    k_set_last<<<1, 1, 0, c.stream>>>(n, tsum.p + ntiles, toff.p, tsum.p, ntiles);
+    k_store_total<TO><<<1, 1, 0, c.stream>>>(out, n, tsum.p + ntiles);
+    PC_LAUNCH("scan_total");
+    return read_i64(c, tsum.p + ntiles);
+}
+
+int64_t scan_i32(Ctx& c, const int32_t* in, int32_t* out, int64_t n) {
+    return scan_impl<int32_t, int32_t>(c, in, out, n);
+}
+int64_t scan_i64(Ctx& c, const int64_t* in, int64_t* out, int64_t n) {
+    return scan_impl<int64_t, int64_t>(c, in, out, n);
+}
+
+}  // namespace pc

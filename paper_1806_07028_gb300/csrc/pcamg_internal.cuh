@@ -1,0 +1,245 @@
+// Internal declarations of the PC-alphaAMG CUDA library (sm_103a).
+// Host code throws pc::Error inside the library; the C ABI layer catches it.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "pcamg.h"
+
+namespace pc {
+
+struct Error {
+    pcamg_status status;
+    std::string msg;
+};
+
+[[noreturn]] void fail(pcamg_status s, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what);
+#define PC_CUDA(call) ::pc::check_cuda((call), #call)
+#define PC_LAUNCH(what) ::pc::check_cuda(cudaGetLastError(), what)
+
+constexpr int kMaxLevels = 32;
+constexpr int kBlock = 256;
+constexpr int kNumSMs = 152;
+
+// ---------------------------------------------------------------- memory
+// Device allocations are stream ordered (cudaMallocAsync on the handle stream).
+struct Mem {
+    cudaStream_t stream = nullptr;
+    size_t live = 0, peak = 0;
+    void* alloc(size_t bytes);
+    void release(void* p, size_t bytes);
+};
+
+template <class T>
+struct DBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    Mem* m = nullptr;
+    DBuf() = default;
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    DBuf(DBuf&& o) noexcept { *this = static_cast<DBuf&&>(o); }
+    DBuf& operator=(DBuf&& o) noexcept {
+        if (this != &o) { free(); p = o.p; n = o.n; m = o.m; o.p = nullptr; o.n = 0; }
+        return *this;
+    }
+    ~DBuf() { free(); }
+    void alloc(Mem& mem, size_t count) {
+        free();
+        m = &mem;
+        n = count;
+        p = static_cast<T*>(mem.alloc(sizeof(T) * (count ? count : 1)));
+    }
+    void free() {
+        if (p && m) m->release(p, sizeof(T) * (n ? n : 1));
+        p = nullptr;
+        n = 0;
+    }
+    T* get() const { return p; }
+};
+
+struct Csr {
+    int32_t n = 0;
+    int64_t nnz = 0;
+    const int32_t* rowptr = nullptr;  // views (owned elsewhere)
+    const int32_t* col = nullptr;
+    const double* val = nullptr;
+    const float* val32 = nullptr;
+    int lpr = 8;  // lanes per row in the sparse kernels (power of two, 2..32)
+};
+int lanes_per_row(int32_t n, int64_t nnz);
+
+// One level of a hierarchy. Level 0 borrows A (and its FP32 copy and colouring)
+// from the context.
+struct Level {
+    int32_t n = 0;
+    int64_t nnz = 0;
+    DBuf<int32_t> rowptr, col;
+    DBuf<double> val;
+    DBuf<float> val32;
+    Csr A;  // view used by the kernels
+    // smoother colouring: rows grouped by colour
+    int32_t ncolour = 0;
+    DBuf<int32_t> colour, colour_rows;
+    std::vector<int32_t> h_colour_ptr;  // ncolour + 1 offsets (host)
+    const int32_t* colour_rows_v = nullptr;
+    const int32_t* colour_v = nullptr;
+    // transfer to the next level
+    int32_t nc = 0;
+    DBuf<int32_t> agg, agg_ptr, agg_mem;
+    DBuf<double> pval;
+    DBuf<float> pval32;
+    // kept for export when params.keep_setup
+    DBuf<int32_t> nbr0, nbr1, tptr, tcol;
+    DBuf<double> tw;
+    int64_t tnnz = 0;
+    int32_t cover_rounds = 0, leftover_rounds = 0;
+    // cycle work vectors (sized n)
+    DBuf<double> x64, b64, r64;
+    DBuf<float> x32, b32, r32;
+};
+
+struct Hier {
+    int32_t nlev = 0;
+    Level lev[kMaxLevels];
+    int32_t nL = 0;
+    DBuf<double> Xinv;   // nL x nL pinned pseudo-inverse of the coarsest matrix
+    int32_t npinned = 0;
+    double oc = 0.0;
+    // CUDA graphs of the correction cycle (index: gamma-1)
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    ~Hier();
+};
+
+// A stream owned by the context; declared before every buffer so that it is
+// destroyed after them (their frees are enqueued on it).
+struct OwnedStream {
+    cudaStream_t s = nullptr;
+    ~OwnedStream() {
+        if (s) {
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+    }
+};
+
+struct Ctx {
+    pcamg_params p{};
+    OwnedStream own;
+    cudaStream_t user = nullptr;    // the caller's stream
+    cudaStream_t stream = nullptr;  // where this context's work runs
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    Mem mem;
+    int32_t n = 0;
+    int64_t nnz = 0;
+    DBuf<int32_t> rowptr, col;
+    DBuf<double> val;
+    DBuf<float> val32;
+    // level-0 colouring (A is the same in every hierarchy)
+    int32_t ncolour0 = 0;
+    DBuf<int32_t> colour0, colour_rows0;
+    std::vector<int32_t> h_colour_ptr0;
+    std::vector<Hier*> hist;
+    // driver work vectors (length n)
+    DBuf<double> w_r, w_c, w_e, w_t1, w_t2, w_z, w_p, w_q, w_rold, w_eh, w_ein, w_cin;
+    DBuf<double> red;     // reduction partials + scalar slots
+    double* h_red = nullptr;  // pinned host mirror of the scalar slots
+    std::string last_error;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int64_t prof_launches = 0;
+    double prof_ms = 0.0;
+    ~Ctx();
+};
+
+// ---------------------------------------------------------------- kernels (launch wrappers)
+// vector ops (k_vector.cu)
+int reduce_blocks(int64_t n);
+// partial[0..nb) then a second pass writes out[0]; deterministic for fixed n
+void dot(cudaStream_t s, int64_t n, const double* x, const double* y, double* partial, double* out);
+void sum(cudaStream_t s, int64_t n, const double* x, double* partial, double* out);
+void axpy(cudaStream_t s, int64_t n, double a, const double* x, double* y);           // y += a x
+void axpy_dev(cudaStream_t s, int64_t n, const double* a, double sign, const double* x, double* y);  // y += sign*(*a) x
+void xpby_dev(cudaStream_t s, int64_t n, const double* x, const double* beta, double* y);          // y = x + (*beta) y
+void sub_mean(cudaStream_t s, int64_t n, double* x, const double* total);  // x -= total/n
+void scale_dev(cudaStream_t s, int64_t n, double* x, const double* num, const double* den);  // x *= num/den
+void copy(cudaStream_t s, int64_t n, const double* x, double* y);
+void fill(cudaStream_t s, int64_t n, double v, double* y);
+void fill_i32(cudaStream_t s, int64_t n, int32_t v, int32_t* y);
+void cast_scaled_f32(cudaStream_t s, int64_t n, const double* x, const double* inv_scale, float* y);
+void add_scaled_f32(cudaStream_t s, int64_t n, const float* c, const double* scale, double* x);  // x += scale*c
+void cast_f32(cudaStream_t s, int64_t n, const double* x, float* y);
+void cast_f64(cudaStream_t s, int64_t n, const float* x, double* y);
+void philox_uniform(cudaStream_t s, uint64_t seed, int64_t n, double* out);
+void scalar_ops(cudaStream_t s, int op, double* slots, int a, int b, int c);  // small device scalar algebra
+// scalar_ops ops
+enum { SOP_DIV = 0, SOP_SQRT = 1, SOP_INV_SQRT = 2, SOP_PCG_ALPHA = 3, SOP_NEG_DIV = 4, SOP_INV = 5 };
+
+// sparse level operators (k_spmv.cu)
+void residual64(cudaStream_t s, const Csr& A, const double* x, const double* b, double* r,
+                double* partial, double* norm2);
+void residual32(cudaStream_t s, const Csr& A, const float* x, const float* b, float* r);
+void spmv64(cudaStream_t s, const Csr& A, const double* x, double* y);  // y = A x
+template <class T>
+void gs_colour(cudaStream_t s, const Csr& A, const int32_t* rows, int32_t nrows, const T* b, T* x);
+template <class T>
+void restrict_agg(cudaStream_t s, int32_t nc, const int32_t* agg_ptr, const int32_t* agg_mem,
+                  const T* pval, const T* r, T* bc);
+template <class T>
+void prolong_add(cudaStream_t s, int32_t n, const int32_t* agg, const T* pval, const T* xc, T* x);
+template <class T>
+void coarse_apply(cudaStream_t s, int32_t m, const double* Xinv, const T* b, T* x);
+
+// setup (k_setup.cu, k_colour.cu, k_dense.cu)
+struct Reweighted {  // reweighted graph of one level, rows in column order
+    DBuf<int32_t> ptr, col;
+    DBuf<double> w;
+    int64_t nnz = 0;
+};
+void build_candidates(Ctx& c, const double* e, Reweighted& out);
+int32_t path_cover(Ctx& c, int32_t n, const Reweighted& t, int32_t* nbr0, int32_t* nbr1);
+// Alg. 3 on one level: returns nc; fills agg (n), cover of the next level (nc)
+int32_t aggregate_level(Ctx& c, int32_t n, const int32_t* nbr0, const int32_t* nbr1,
+                        const Reweighted& t, DBuf<int32_t>& agg, DBuf<int32_t>& cnbr0,
+                        DBuf<int32_t>& cnbr1, int32_t* rounds);
+void build_members(Ctx& c, int32_t n, int32_t nc, const int32_t* agg, DBuf<int32_t>& agg_ptr,
+                   DBuf<int32_t>& agg_mem);
+void build_pval(Ctx& c, int32_t n, int32_t nc, const int32_t* agg_ptr, const int32_t* agg_mem,
+                const double* e, DBuf<double>& pval);
+// Galerkin: (I,J) sums of (p_u a_uv) p_v over members of I ascending then row order
+int64_t galerkin(Ctx& c, int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                 int32_t nc, const int32_t* agg, const int32_t* agg_ptr, const int32_t* agg_mem,
+                 const double* pval, bool drop_diag, DBuf<int32_t>& optr, DBuf<int32_t>& ocol,
+                 DBuf<double>& oval);
+int32_t colour_graph(Ctx& c, int32_t n, const int32_t* rowptr, const int32_t* col, uint64_t seed,
+                     int32_t* colour);
+void colour_lists(Ctx& c, int32_t n, const int32_t* colour, int32_t ncolour,
+                  DBuf<int32_t>& rows, std::vector<int32_t>& h_ptr);
+void coarse_factor(Ctx& c, int32_t m, const int32_t* rowptr, const int32_t* col, const double* val,
+                   bool force_last, DBuf<double>& Xinv, int32_t* npinned);
+
+// hierarchy + driver (hierarchy.cu, driver.cu)
+Hier* build_hierarchy(Ctx& c, const double* e_normalised);
+void cycle(Ctx& c, Hier& h, int gamma, const double* r, double* out);
+void smooth_error(Ctx& c, const double* r, double* e);
+void start_vector(Ctx& c, double* e);
+pcamg_status solve(Ctx& c, const double* b, double* x, pcamg_stats* st);
+pcamg_status solve_zero_rhs(Ctx& c, double* x, pcamg_stats* st);
+void normalise_orth(Ctx& c, const double* e, double* out);  // (e - mean)/||e - mean||
+
+// small helpers
+template <class T>
+void d2h(Ctx& c, T* host, const T* dev, size_t count);
+void sync(Ctx& c);
+int64_t read_i64(Ctx& c, const int64_t* dev);
+int32_t read_i32(Ctx& c, const int32_t* dev);
+double read_f64(Ctx& c, const double* dev);
+// exclusive scan of int32 counts into int32 offsets (out has n+1 entries); returns total
+int64_t scan_i32(Ctx& c, const int32_t* in, int32_t* out, int64_t n);
+int64_t scan_i64(Ctx& c, const int64_t* in, int64_t* out, int64_t n);
+
+}  // namespace pc

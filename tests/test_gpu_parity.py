@@ -1,0 +1,222 @@
+"""GPU path vs the CPU oracle, through the C ABI.
+
+Integer and setup results (random numbers, colours, reweighted graph, path
+cover, aggregates, coarse patterns and FP64 Galerkin values, P values) must
+match bit for bit when both sides get the same smooth error. Floating-point
+cycle results are compared with tolerances derived from the summation orders.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1806_07028_gb300 import inputs as I
+from tests.helpers import random_graph
+
+pytestmark = pytest.mark.gpu
+EPS = np.finfo(np.float64).eps
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1806_07028_gb300.build import build
+    build()
+    import paper_1806_07028_gb300 as pkg
+    return pkg
+
+
+def _graphs():
+    return {
+        "C1": I.workload("C1"),
+        "C2-small": I.workload("C2-small"),
+        "C5-small": I.workload("C5-small"),
+        "er": random_graph(3000, 0.002, 7),
+        "ring": I.ring(2000, 4),
+        "C4-small": I.workload("C4-small"),
+    }
+
+
+GRAPHS = _graphs()
+NAMES = list(GRAPHS)
+
+
+def _t(a, P, dtype=None):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), device="cuda:0", dtype=dtype)
+
+
+def test_uniform_bit_exact(P):
+    for seed, n in ((0, 1), (7, 1001), (2**40 + 3, 123457)):
+        g = P.uniform(seed, n).cpu().numpy()
+        assert np.array_equal(g.view(np.uint64), O.uniform_pm1(seed, n).view(np.uint64))
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_colour_bit_exact(P, name):
+    import torch
+    g = GRAPHS[name]
+    col, nc = P.colour(_t(g.rowptr, P, torch.int32), _t(g.col, P, torch.int32), 99)
+    ref, ncr, _ = O.colour(g, seed=99)
+    assert nc == ncr and np.array_equal(col.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_residual_and_norm(P, name):
+    import torch
+    g = GRAPHS[name]
+    rng = np.random.default_rng(3)
+    x, b = rng.standard_normal(g.n), rng.standard_normal(g.n)
+    r, nrm = P.residual(_t(g.rowptr, P, torch.int32), _t(g.col, P, torch.int32),
+                        _t(g.val, P), _t(x, P), _t(b, P))
+    ref = O.residual(g, x, b)
+    rowabs = np.abs(g.to_scipy()) @ np.abs(x) + np.abs(b)
+    assert np.all(np.abs(r.cpu().numpy() - ref) <= 32 * EPS * rowabs)
+    assert abs(nrm.item() - ref @ ref) <= 1e-12 * (ref @ ref)
+    # FP32 variant against the FP64 oracle: float rounding only
+    r32 = P.residual_f32(_t(g.rowptr, P, torch.int32), _t(g.col, P, torch.int32),
+                         _t(g.val, P, torch.float32), _t(x, P, torch.float32), _t(b, P, torch.float32))
+    assert np.all(np.abs(r32.cpu().numpy() - ref) <= 64 * 2.0**-24 * rowabs)
+
+
+def _compare_hierarchy(P, g, e, mode, precision=0):
+    params = P.default_params(keep_setup=1, p1_mode=mode, precision=precision, n_min=64)
+    s = P.Solver(g, params=params, e0=e)
+    h = O.Hierarchy(g, e, O.default_params(p1_mode=mode, n_min=64))
+    assert s.num_levels(0) == h.nlevels
+    cp, cc, cw = s.reweighted(0, 0)
+    rp, rc, rw = h.candidates()
+    assert np.array_equal(cp, rp) and np.array_equal(cc, rc)
+    assert np.array_equal(cw.view(np.uint64), rw.view(np.uint64))
+    for lev in range(h.nlevels):
+        G, R = s.level(0, lev, cover=True), h.level(lev)
+        for k in ("n", "nnz", "nc", "ncolour", "leftover_rounds"):
+            assert G[k] == R[k], (lev, k)
+        if lev == 0:
+            assert G["cover_rounds"] == R["cover_rounds"]
+        assert np.array_equal(G["nbr0"], R["nbr0"]) and np.array_equal(G["nbr1"], R["nbr1"]), lev
+        assert np.array_equal(G["rowptr"], R["rowptr"]) and np.array_equal(G["col"], R["col"]), lev
+        assert np.array_equal(G["val"].view(np.uint64), R["val"].view(np.uint64)), lev
+        if R["agg"] is not None:
+            assert np.array_equal(G["agg"], R["agg"]), lev
+        if R["pval"] is not None:
+            assert np.array_equal(G["pval"].view(np.uint64), R["pval"].view(np.uint64))
+        if lev + 1 < h.nlevels:
+            assert np.array_equal(G["colour"], R["colour"]), lev
+    assert s.sizes(0, 0)["pinned"] == h.sizes(0)["pinned"]
+    return s, h
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("mode", [0, 1])
+def test_setup_bit_exact_given_same_error(P, name, mode):
+    g = GRAPHS[name]
+    e = O.start_vector(g)          # same smooth error fed to both sides
+    s, h = _compare_hierarchy(P, g, e, mode)
+    s.close()
+
+
+def test_setup_bit_exact_with_ties(P):
+    # quantised error: many equal |e_i - e_j|, decided by the id tie-break
+    g = I.grid2d(96, 80)
+    e = np.round(np.random.default_rng(1).standard_normal(g.n), 1)
+    _compare_hierarchy(P, g, e, 0)[0].close()
+    _compare_hierarchy(P, g, np.zeros(g.n), 1)[0].close()
+
+
+@pytest.mark.parametrize("name", ["C1", "C2-small", "er"])
+@pytest.mark.parametrize("gamma", [1, 2])
+def test_cycle_matches_oracle(P, name, gamma):
+    g = GRAPHS[name]
+    e = O.start_vector(g)
+    s, h = _compare_hierarchy(P, g, e, 0)
+    r = I.rhs_normal(g.n, 5)
+    c = s.cycle(r, hist=0, gamma=gamma).cpu().numpy()
+    ref = h.vcycle(r) if gamma == 1 else h.wcycle(r)
+    assert np.linalg.norm(c - ref) <= 1e-9 * np.linalg.norm(ref)
+    s.close()
+    # FP32 cycle inside FP64 refinement: same hierarchy, float arithmetic
+    s32, _ = _compare_hierarchy(P, g, e, 0, precision=1)
+    c32 = s32.cycle(r, hist=0, gamma=gamma).cpu().numpy()
+    assert np.linalg.norm(c32 - ref) <= 2e-4 * np.linalg.norm(ref)
+    s32.close()
+
+
+def test_start_vector_and_smooth_error_match_oracle(P):
+    g = GRAPHS["C2-small"]
+    s = P.Solver(g)
+    e_gpu = s.start_vector().cpu().numpy()
+    e_orc = O.start_vector(g)
+    assert np.linalg.norm(e_gpu - e_orc) <= 1e-10
+    # Alg. 2 on the same hierarchies (W-cycle branch, then composite branch)
+    e0 = e_orc
+    s = P.Solver(g, e0=e0)
+    hs = [O.Hierarchy(g, e0)]
+    r = I.rhs_normal(g.n, 2)
+    for k in range(3):
+        eg = s.smooth_error(r).cpu().numpy()
+        eo = O.smooth_error(g, r, hs)
+        assert np.linalg.norm(eg - eo) <= 1e-7 * np.linalg.norm(eo), k
+        ek = O.start_vector(g, O.default_params(seed=100 + k))
+        s.adapt(ek)
+        hs.append(O.Hierarchy(g, ek))
+
+
+@pytest.mark.parametrize("name", NAMES + ["C3-small"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_reaches_tolerance(P, name, precision):
+    g = GRAPHS.get(name) or I.workload(name)
+    b = I.rhs_normal(g.n, 11)
+    s = P.Solver(g, params=P.default_params(precision=precision))
+    x, st = s.solve(b)
+    x = x.cpu().numpy()
+    rel = np.linalg.norm(b - g.to_scipy() @ x) / np.linalg.norm(b)
+    assert st["status"] == "OK" and rel <= 1e-8, (st, rel)
+    xo, so, _ = O.solve(g, b)
+    assert so["status"] == "OK"
+    # both meet the residual bound; their difference is bounded by the
+    # conditioning, stated here as a loose relative check
+    assert np.linalg.norm(x - xo) <= 1e-3 * np.linalg.norm(xo)
+    s.close()
+
+
+def test_solve_zero_rhs_alg6(P):
+    g = I.grid2d(64, 64)
+    x0 = np.random.default_rng(4).standard_normal(g.n)
+    s = P.Solver(g, params=P.default_params(threshold=0.5))
+    x, st = s.solve_zero_rhs(x0)
+    assert st["status"] == "OK"
+    xo, so, _ = O.solve_zero_rhs(g, x0)
+    assert so["status"] == "OK"
+
+
+def test_solve_host_e2e(P):
+    g = GRAPHS["C1"]
+    b = I.rhs_normal(g.n, 1)
+    x, st = P.solve_host(g, b)
+    assert st["status"] == "OK"
+    assert np.linalg.norm(b - g.to_scipy() @ x) <= 1e-8 * np.linalg.norm(b)
+
+
+def test_invalid_inputs_return_status(P):
+    from paper_1806_07028_gb300 import native as N
+    g = I.grid2d(8, 8)
+    bad = I.Graph(g.rowptr, g.col, g.val.copy())
+    bad.val[1] = +1.0                       # positive off-diagonal (also asymmetric)
+    with pytest.raises(N.PCAMGError) as ei:
+        P.Solver(bad)
+    assert ei.value.status == N.ERR_NOT_LAPLACIAN
+    bad = I.Graph(g.rowptr, g.col[::-1].copy(), g.val)   # unsorted columns
+    with pytest.raises(N.PCAMGError) as ei:
+        P.Solver(bad)
+    assert ei.value.status == N.ERR_INVALID
+    s = P.Solver(g)
+    b = np.ones(g.n); b[3] = np.nan
+    with pytest.raises(N.PCAMGError) as ei:
+        s.solve(b)
+    assert ei.value.status == N.ERR_INVALID
+    # max_iter hit: NOT_CONVERGED with stats filled
+    s2 = P.Solver(g, params=P.default_params(max_iter=1, threshold=10.0))
+    x, st = s2.solve(I.rhs_normal(g.n, 0))
+    assert st["status"] == "NOT_CONVERGED" and st["iters"] == 1
