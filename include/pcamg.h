@@ -14,10 +14,12 @@
  *  - Pointers named d_* are device pointers, h_* host pointers. Inputs are
  *    borrowed for the duration of the call only: the library copies what it
  *    keeps. Outputs are caller-owned buffers the library writes.
- *  - `stream` is a cudaStream_t (NULL = legacy default stream). All device work
- *    of a handle is enqueued on the stream given at setup. Calls synchronise
- *    the stream where they must read sizes or scalars back, and before they
- *    return results in host memory.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream). A handle runs
+ *    its device work on a private non-blocking stream that each call orders
+ *    after the caller's prior work on `stream` and before the caller's later
+ *    work on it (event record/wait), so results are ready for `stream` when a
+ *    call returns. Calls synchronise where they must read sizes or scalars
+ *    back, and before they return results in host memory.
  *  - Every call returns a pcamg_status; nothing is thrown across the ABI and the
  *    library never exits or traps. pcamg_last_error(h) gives a message.
  *  - A handle is not thread safe: use one handle from one host thread at a time.
@@ -94,6 +96,9 @@ typedef struct {
     double oc_mean;        /* operator complexity averaged over all hierarchies */
     double t_setup_ms;     /* host wall time inside re-setups (Alg. 2 + Alg. 4) */
     double t_solve_ms;     /* host wall time of the whole call */
+    double t_alg2_ms;      /* of t_setup_ms: smooth-error PCG (Alg. 2) */
+    double t_alg4_ms;      /* of t_setup_ms: hierarchy builds (Alg. 4) */
+    int64_t cycles;        /* multigrid cycles applied (V and W, all hierarchies) */
     double* res_hist;      /* optional host buffer: ||r_k||/||b||, k = 0..iters */
     int32_t res_hist_cap;  /* its capacity (0 = none) */
     int32_t res_hist_len;  /* entries written */
@@ -117,8 +122,9 @@ PCAMG_API pcamg_status pcamg_setup(pcamg_handle* out, const pcamg_params* p, int
                                    int64_t nnz, const int32_t* d_rowptr, const int32_t* d_col,
                                    const double* d_val, const double* d_e0, void* stream);
 
-/* PathCoverAMG_setup (Alg. 4) from the smooth error d_e (device, length n; it is
- * copied, made orthogonal to 1 and normalised): reweighting on the A^2 pattern,
+/* PathCoverAMG_setup (Alg. 4) from the smooth error d_e (device, length n, used
+ * as given; the solver itself passes the Alg. 2 output made orthogonal to 1 and
+ * normalised, and P_1 carries e): reweighting on the A^2 pattern,
  * path cover (Alg. 1), path-cover aggregation (Alg. 3) and Galerkin products on
  * every level. The new hierarchy becomes the current one and joins the history
  * used by the composite preconditioner (Alg. 2). */
@@ -183,6 +189,10 @@ PCAMG_API pcamg_status pcamg_export_level(pcamg_handle h, int32_t hist, int32_t 
  * 1/max(|e_i - e_j|, 2^-52 max|e|), Alg. 4 step 2) as host CSR; needs keep_setup. */
 PCAMG_API pcamg_status pcamg_export_reweighted(pcamg_handle h, int32_t hist, int32_t lev,
                                                int32_t* ptr, int32_t* col, double* w);
+
+/* Number of CUDA kernels this library has launched in this process so far (a
+ * replayed cycle graph counts the kernels it holds). */
+PCAMG_API int64_t pcamg_kernel_launches(void);
 
 PCAMG_API const char* pcamg_last_error(pcamg_handle h);
 PCAMG_API const char* pcamg_status_string(pcamg_status s);

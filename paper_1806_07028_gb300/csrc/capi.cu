@@ -101,7 +101,7 @@ void check_finite(Ctx& c, const double* x, int64_t n, const char* what) {
     PC_CUDA(cudaMemsetAsync(f.p, 0, sizeof(int32_t), c.stream));
     int g = (int)std::min<int64_t>((n + 255) / 256, 4096);
     if (g < 1) g = 1;
-    k_check_finite<<<g, 256, 0, c.stream>>>(n, x, f.p);
+    k_check_finite<<<g, 256, 0, c.stream>>>(n, x, f.p); ::pc::count_launches(1);
     PC_LAUNCH("check_finite");
     if (read_i32(c, f.p)) fail(PCAMG_ERR_INVALID, std::string(what) + " has a NaN or Inf entry");
 }
@@ -116,7 +116,7 @@ void validate_csr(Ctx& c) {
     f.alloc(c.mem, 1);
     PC_CUDA(cudaMemsetAsync(f.p, 0, sizeof(int32_t), c.stream));
     int g = std::min((c.n + 255) / 256, 4096);
-    k_validate<<<g, 256, 0, c.stream>>>(c.n, c.nnz, c.rowptr.p, c.col.p, c.val.p, f.p);
+    k_validate<<<g, 256, 0, c.stream>>>(c.n, c.nnz, c.rowptr.p, c.col.p, c.val.p, f.p); ::pc::count_launches(1);
     PC_LAUNCH("validate");
     int fl = read_i32(c, f.p);
     if (fl & (V_BAD_PTR | V_BAD_COL | V_UNSORTED | V_NONFINITE))
@@ -411,6 +411,8 @@ PCAMG_API pcamg_status pcamg_export_reweighted(pcamg_handle h, int32_t hist, int
         return PCAMG_OK;
     });
 }
+
+PCAMG_API int64_t pcamg_kernel_launches(void) { return launch_count(); }
 
 PCAMG_API const char* pcamg_last_error(pcamg_handle h) {
     return h ? h->last_error.c_str() : g_last_error.c_str();

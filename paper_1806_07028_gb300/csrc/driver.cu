@@ -6,6 +6,7 @@
 //  * ApproximateSmoothError (Alg. 2): flexible PCG with a W-cycle or the
 //    symmetric composite of V-cycles over all hierarchies;
 //  * AdaptiveAMG for general b (Alg. 5) and for b = 0 (Alg. 6).
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -16,6 +17,15 @@ namespace pc {
 
 // ---------------------------------------------------------------- basics
 void fail(pcamg_status s, const std::string& msg) { throw Error{s, msg}; }
+
+static std::atomic<int64_t> g_launches{0};
+static thread_local int64_t* t_capture_acc = nullptr;
+void count_launches(int64_t k) {
+    if (t_capture_acc) *t_capture_acc += k;   // recorded into a graph, not run yet
+    else g_launches.fetch_add(k, std::memory_order_relaxed);
+}
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+bool capturing() { return t_capture_acc != nullptr; }
 
 void check_cuda(cudaError_t e, const char* what) {
     if (e == cudaSuccess) return;
@@ -160,25 +170,31 @@ static void run_body(Ctx& c, Hier& h, int gamma) {
     cudaGraphExec_t& ge = h.graph[gamma - 1];
     if (!ge) {
         cudaGraph_t g = nullptr;
+        h.graph_kernels[gamma - 1] = 0;
         PC_CUDA(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
+        t_capture_acc = &h.graph_kernels[gamma - 1];
         try {
             if (f32) cycle_body<float>(c, h, gamma); else cycle_body<double>(c, h, gamma);
         } catch (...) {
+            t_capture_acc = nullptr;
             cudaStreamEndCapture(c.stream, &g);
             if (g) cudaGraphDestroy(g);
             throw;
         }
+        t_capture_acc = nullptr;
         PC_CUDA(cudaStreamEndCapture(c.stream, &g));
         cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
         cudaGraphDestroy(g);
         PC_CUDA(e);
     }
     PC_CUDA(cudaGraphLaunch(ge, c.stream));
+    count_launches(h.graph_kernels[gamma - 1]);
 }
 
 // out = B r, the correction of one cycle from a zero start
 void cycle(Ctx& c, Hier& h, int gamma, const double* r, double* out) {
     cudaStream_t s = c.stream;
+    c.ncycles += 1;
     Level& L0 = h.lev[0];
     if (c.p.precision == PCAMG_FP32_IR) {
         // scale by ||r||_2 so the float cycle sees O(1) data, then scale back
@@ -307,10 +323,15 @@ static double read_norm(Ctx& c) {
 }
 
 static void rebuild(Ctx& c, double* e_raw_out) {
+    double t0 = now_ms();
     smooth_error(c, c.w_r.p, e_raw_out);
     normalise_orth(c, e_raw_out, c.w_eh.p);
+    sync(c);
+    double t1 = now_ms();
     Hier* h = build_hierarchy(c, c.w_eh.p);
     c.hist.push_back(h);
+    c.t_alg2 += t1 - t0;
+    c.t_alg4 += now_ms() - t1;
 }
 
 pcamg_status solve(Ctx& c, const double* b, double* x, pcamg_stats* st) {
@@ -318,6 +339,8 @@ pcamg_status solve(Ctx& c, const double* b, double* x, pcamg_stats* st) {
     double t0 = now_ms(), t_setup = 0.0;
     c.prof_ms = 0.0;
     c.prof_launches = 0;
+    c.ncycles = 0;
+    c.t_alg2 = c.t_alg4 = 0.0;
     int32_t re0 = (int32_t)c.hist.size();
     dot(s, c.n, b, b, partials(c), slot(c, S_NORM2));
     double bn = read_norm(c);
@@ -375,6 +398,9 @@ pcamg_status solve(Ctx& c, const double* b, double* x, pcamg_stats* st) {
         st->t_setup_ms = t_setup;
         st->t_solve_ms = now_ms() - t0;
         st->res_hist_len = hl;
+        st->t_alg2_ms = c.t_alg2;
+        st->t_alg4_ms = c.t_alg4;
+        st->cycles = c.ncycles;
         st->prof_launches = c.prof_launches;
         st->prof_ms = c.prof_ms;
         st->prof_bytes = (double)c.prof_launches * (12.0 * (double)c.nnz + 28.0 * (double)c.n);

@@ -96,7 +96,7 @@ int32_t colour_graph(Ctx& c, int32_t n, const int32_t* rowptr, const int32_t* co
     int32_t* b = tmp.p;
     for (int round = 0;; ++round) {
         PC_CUDA(cudaMemsetAsync(left.p, 0, sizeof(int32_t), s));
-        k_colour_round<<<gridc(n), kBlock, 0, s>>>(n, rowptr, col, seed, a, b, left.p, maxc.p);
+        k_colour_round<<<gridc(n), kBlock, 0, s>>>(n, rowptr, col, seed, a, b, left.p, maxc.p); ::pc::count_launches(1);
         PC_LAUNCH("colour_round");
         int32_t* t = a; a = b; b = t;
         if (read_i32(c, left.p) == 0) break;
@@ -118,9 +118,9 @@ void colour_lists(Ctx& c, int32_t n, const int32_t* colour, int32_t ncolour,
     h_ptr.assign((size_t)ncolour + 1, 0);
     int64_t base = 0;
     for (int32_t k = 0; k < ncolour; ++k) {
-        k_colour_flags<<<gridc(n), kBlock, 0, s>>>(n, colour, k, flag.p);
+        k_colour_flags<<<gridc(n), kBlock, 0, s>>>(n, colour, k, flag.p); ::pc::count_launches(1);
         int64_t cnt = scan_i32(c, flag.p, pos.p, n);
-        k_colour_place<<<gridc(n), kBlock, 0, s>>>(n, colour, k, pos.p, (int)base, rows.p);
+        k_colour_place<<<gridc(n), kBlock, 0, s>>>(n, colour, k, pos.p, (int)base, rows.p); ::pc::count_launches(1);
         PC_LAUNCH("colour_lists");
         h_ptr[k] = (int32_t)base;
         base += cnt;

@@ -91,9 +91,9 @@ void coarse_factor(Ctx& c, int32_t m, const int32_t* rowptr, const int32_t* col,
     np.alloc(c.mem, 1);
     Xinv.alloc(c.mem, (size_t)m * m);
     int g = (m + kBlock - 1) / kBlock;
-    k_dense_assemble<<<g, kBlock, 0, s>>>(m, rowptr, col, val, D.p);
-    k_chol_pinned<<<1, 1024, 0, s>>>(m, D.p, force_last ? 1 : 0, 1e-12, L.p, pin.p, np.p);
-    k_chol_inverse<<<g, kBlock, 0, s>>>(m, L.p, pin.p, Xinv.p);
+    k_dense_assemble<<<g, kBlock, 0, s>>>(m, rowptr, col, val, D.p); ::pc::count_launches(1);
+    k_chol_pinned<<<1, 1024, 0, s>>>(m, D.p, force_last ? 1 : 0, 1e-12, L.p, pin.p, np.p); ::pc::count_launches(1);
+    k_chol_inverse<<<g, kBlock, 0, s>>>(m, L.p, pin.p, Xinv.p); ::pc::count_launches(1);
     PC_LAUNCH("coarse_factor");
     *npinned = read_i32(c, np.p);
 }

@@ -718,7 +718,7 @@ static void row_product(Ctx& c, int32_t nrows, const Src& src, DBuf<int32_t>& op
     is_long.alloc(c.mem, nrows);
     PC_CUDA(cudaMemsetAsync(long_count.p, 0, sizeof(int32_t), s));
     k_rowprod_thread<Src, false><<<grid1(nrows), kBlock, 0, s>>>(
-        nrows, src, cnt.p, is_long.p, long_list.p, long_count.p, nullptr, nullptr, nullptr);
+        nrows, src, cnt.p, is_long.p, long_list.p, long_count.p, nullptr, nullptr, nullptr); ::pc::count_launches(1);
     PC_LAUNCH("rowprod_thread(count)");
     int32_t nlong = read_i32(c, long_count.p);
     std::vector<int32_t> rowsB, rowsC;
@@ -736,7 +736,7 @@ static void row_product(Ctx& c, int32_t nrows, const Src& src, DBuf<int32_t>& op
         drows.alloc(c.mem, nlong);
         ub.alloc(c.mem, nlong);
         PC_CUDA(cudaMemcpyAsync(drows.p, rows.data(), sizeof(int32_t) * nlong, cudaMemcpyHostToDevice, s));
-        k_rowprod_ub<Src><<<grid1(nlong), kBlock, 0, s>>>(nlong, drows.p, src, ub.p);
+        k_rowprod_ub<Src><<<grid1(nlong), kBlock, 0, s>>>(nlong, drows.p, src, ub.p); ::pc::count_launches(1);
         PC_LAUNCH("rowprod_ub");
         std::vector<int64_t> hub(nlong);
         d2h(c, hub.data(), ub.p, nlong);
@@ -758,7 +758,7 @@ static void row_product(Ctx& c, int32_t nrows, const Src& src, DBuf<int32_t>& op
             PC_CUDA(cudaMemcpyAsync(dB.p, rowsB.data(), sizeof(int32_t) * rowsB.size(), cudaMemcpyHostToDevice, s));
             size_t smem = kBlockCap * (sizeof(uint64_t) + sizeof(double));
             k_rowprod_block<Src, false, false><<<(unsigned)rowsB.size(), kBlock, smem, s>>>(
-                dB.p, src, cnt.p, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+                dB.p, src, cnt.p, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr); ::pc::count_launches(1);
             PC_LAUNCH("rowprod_block(count)");
         }
         if (!rowsC.empty()) {
@@ -769,7 +769,7 @@ static void row_product(Ctx& c, int32_t nrows, const Src& src, DBuf<int32_t>& op
             PC_CUDA(cudaMemcpyAsync(dC.p, rowsC.data(), sizeof(int32_t) * rowsC.size(), cudaMemcpyHostToDevice, s));
             PC_CUDA(cudaMemcpyAsync(offC.p, hoff.data(), sizeof(int64_t) * hoff.size(), cudaMemcpyHostToDevice, s));
             k_rowprod_block<Src, false, true><<<(unsigned)rowsC.size(), kBlock, 0, s>>>(
-                dC.p, src, cnt.p, nullptr, nullptr, nullptr, gkeys.p, gvals.p, offC.p);
+                dC.p, src, cnt.p, nullptr, nullptr, nullptr, gkeys.p, gvals.p, offC.p); ::pc::count_launches(1);
             PC_LAUNCH("rowprod_global(count)");
         }
         sync(c);
@@ -781,17 +781,17 @@ static void row_product(Ctx& c, int32_t nrows, const Src& src, DBuf<int32_t>& op
     double* ov = nullptr;
     if (oval) { oval->alloc(c.mem, total); ov = oval->p; }
     k_rowprod_thread<Src, true><<<grid1(nrows), kBlock, 0, s>>>(
-        nrows, src, nullptr, is_long.p, nullptr, nullptr, optr.p, ocol.p, ov);
+        nrows, src, nullptr, is_long.p, nullptr, nullptr, optr.p, ocol.p, ov); ::pc::count_launches(1);
     PC_LAUNCH("rowprod_thread(fill)");
     if (!rowsB.empty()) {
         size_t smem = kBlockCap * (sizeof(uint64_t) + sizeof(double));
         k_rowprod_block<Src, true, false><<<(unsigned)rowsB.size(), kBlock, smem, s>>>(
-            dB.p, src, nullptr, optr.p, ocol.p, ov, nullptr, nullptr, nullptr);
+            dB.p, src, nullptr, optr.p, ocol.p, ov, nullptr, nullptr, nullptr); ::pc::count_launches(1);
         PC_LAUNCH("rowprod_block(fill)");
     }
     if (!rowsC.empty()) {
         k_rowprod_block<Src, true, true><<<(unsigned)rowsC.size(), kBlock, 0, s>>>(
-            dC.p, src, nullptr, optr.p, ocol.p, ov, gkeys.p, gvals.p, offC.p);
+            dC.p, src, nullptr, optr.p, ocol.p, ov, gkeys.p, gvals.p, offC.p); ::pc::count_launches(1);
         PC_LAUNCH("rowprod_global(fill)");
     }
     *nnz_out = total;
@@ -805,9 +805,9 @@ void build_candidates(Ctx& c, const double* e, Reweighted& out) {
     int nb = 256;
     DBuf<double> part;
     part.alloc(c.mem, nb + 1);
-    k_maxabs<<<nb, kBlock, 0, c.stream>>>(c.n, e, part.p);
-    k_delta<<<1, 1, 0, c.stream>>>(nb, part.p, part.p + nb);
-    k_weights<<<grid1(c.n), kBlock, 0, c.stream>>>(c.n, out.ptr.p, out.col.p, e, part.p + nb, out.w.p);
+    k_maxabs<<<nb, kBlock, 0, c.stream>>>(c.n, e, part.p); ::pc::count_launches(1);
+    k_delta<<<1, 1, 0, c.stream>>>(nb, part.p, part.p + nb); ::pc::count_launches(1);
+    k_weights<<<grid1(c.n), kBlock, 0, c.stream>>>(c.n, out.ptr.p, out.col.p, e, part.p + nb, out.w.p); ::pc::count_launches(1);
     PC_LAUNCH("weights");
     sync(c);
 }
@@ -825,7 +825,7 @@ int32_t path_cover(Ctx& c, int32_t n, const Reweighted& t, int32_t* nbr0, int32_
     is_long.alloc(c.mem, n);
     PC_CUDA(cudaMemsetAsync(long_count.p, 0, sizeof(int32_t), s));
     k_order_rows_thread<<<grid1(n), kBlock, 0, s>>>(n, t.ptr.p, t.col.p, t.w.p, scol.p, sw.p,
-                                                     is_long.p, long_list.p, long_count.p);
+                                                     is_long.p, long_list.p, long_count.p); ::pc::count_launches(1);
     PC_LAUNCH("order_rows");
     int32_t nlong = read_i32(c, long_count.p);
     if (nlong > 0) {
@@ -850,7 +850,7 @@ int32_t path_cover(Ctx& c, int32_t n, const Reweighted& t, int32_t* nbr0, int32_
         gidx.alloc(c.mem, tot);
         PC_CUDA(cudaMemcpyAsync(drows.p, rows.data(), sizeof(int32_t) * nlong, cudaMemcpyHostToDevice, s));
         PC_CUDA(cudaMemcpyAsync(doff.p, off.data(), sizeof(int64_t) * nlong, cudaMemcpyHostToDevice, s));
-        k_order_rows_block<<<nlong, kBlock, 0, s>>>(drows.p, t.ptr.p, t.col.p, t.w.p, scol.p, sw.p, gidx.p, doff.p);
+        k_order_rows_block<<<nlong, kBlock, 0, s>>>(drows.p, t.ptr.p, t.col.p, t.w.p, scol.p, sw.p, gidx.p, doff.p); ::pc::count_launches(1);
         PC_LAUNCH("order_rows_block");
         sync(c);
     }
@@ -859,16 +859,16 @@ int32_t path_cover(Ctx& c, int32_t n, const Reweighted& t, int32_t* nbr0, int32_
     cf.alloc(c.mem, n); ct.alloc(c.mem, n);
     const int kBatchMax = 64;
     counters.alloc(c.mem, kBatchMax);
-    k_cover_init<<<grid1(n), kBlock, 0, s>>>(n, t.ptr.p, deg.p, oe.p, cptr.p, nbr0, nbr1);
+    k_cover_init<<<grid1(n), kBlock, 0, s>>>(n, t.ptr.p, deg.p, oe.p, cptr.p, nbr0, nbr1); ::pc::count_launches(1);
     fill_i32(s, n, -1, cf.p);
     int32_t rounds = 0, batch = 4;
     std::vector<int32_t> hc(kBatchMax);
     for (;;) {
         PC_CUDA(cudaMemsetAsync(counters.p, 0, sizeof(int32_t) * batch, s));
         for (int r = 0; r < batch; ++r) {
-            k_cover_best<<<grid1(n), kBlock, 0, s>>>(n, t.ptr.p, scol.p, deg.p, oe.p, cptr.p, bv.p);
-            k_cover_choose<<<grid1(n), kBlock, 0, s>>>(n, deg.p, oe.p, cptr.p, bv.p, sw.p, cf.p, ct.p);
-            k_cover_accept<<<grid1(n), kBlock, 0, s>>>(n, deg.p, oe.p, cf.p, ct.p, nbr0, nbr1, counters.p + r);
+            k_cover_best<<<grid1(n), kBlock, 0, s>>>(n, t.ptr.p, scol.p, deg.p, oe.p, cptr.p, bv.p); ::pc::count_launches(1);
+            k_cover_choose<<<grid1(n), kBlock, 0, s>>>(n, deg.p, oe.p, cptr.p, bv.p, sw.p, cf.p, ct.p); ::pc::count_launches(1);
+            k_cover_accept<<<grid1(n), kBlock, 0, s>>>(n, deg.p, oe.p, cf.p, ct.p, nbr0, nbr1, counters.p + r); ::pc::count_launches(1);
         }
         PC_LAUNCH("cover rounds");
         d2h(c, hc.data(), counters.p, batch);
@@ -881,7 +881,7 @@ int32_t path_cover(Ctx& c, int32_t n, const Reweighted& t, int32_t* nbr0, int32_
         if (rounds > n + 1) fail(PCAMG_ERR_ROUND_CAP, "path cover rounds exceeded n");
         batch = std::min(batch * 2, kBatchMax);
     }
-    k_canonical<<<grid1(n), kBlock, 0, s>>>(n, nbr0, nbr1);
+    k_canonical<<<grid1(n), kBlock, 0, s>>>(n, nbr0, nbr1); ::pc::count_launches(1);
     PC_LAUNCH("canonical");
     sync(c);
     return rounds;
@@ -895,13 +895,13 @@ int32_t aggregate_level(Ctx& c, int32_t n, const int32_t* nbr0, const int32_t* n
     DBuf<int32_t> jmp[2], dist[2], endv[2], active;
     for (int k = 0; k < 2; ++k) { jmp[k].alloc(c.mem, nh); dist[k].alloc(c.mem, nh); endv[k].alloc(c.mem, nh); }
     active.alloc(c.mem, 1);
-    k_rank_init<<<grid1(n), kBlock, 0, s>>>(n, nbr0, nbr1, jmp[0].p, dist[0].p, endv[0].p);
+    k_rank_init<<<grid1(n), kBlock, 0, s>>>(n, nbr0, nbr1, jmp[0].p, dist[0].p, endv[0].p); ::pc::count_launches(1);
     PC_LAUNCH("rank_init");
     int cur = 0;
     for (int it = 0; it < 40; ++it) {
         PC_CUDA(cudaMemsetAsync(active.p, 0, sizeof(int32_t), s));
         k_rank_jump<<<grid1(nh), kBlock, 0, s>>>((int)nh, jmp[cur].p, dist[cur].p, endv[cur].p,
-                                                 jmp[1 - cur].p, dist[1 - cur].p, endv[1 - cur].p, active.p);
+                                                 jmp[1 - cur].p, dist[1 - cur].p, endv[1 - cur].p, active.p); ::pc::count_launches(1);
         PC_LAUNCH("rank_jump");
         cur = 1 - cur;
         if (read_i32(c, active.p) == 0) break;
@@ -916,27 +916,27 @@ int32_t aggregate_level(Ctx& c, int32_t n, const int32_t* nbr0, const int32_t* n
     fill_i32(s, n, -1, lab.p);
     fill_i32(s, n, 0, size.p);
     k_pair<<<grid1(n), kBlock, 0, s>>>(n, nbr0, nbr1, dist[cur].p, endv[cur].p, lab.p, size.p,
-                                       sprev.p, snext.p, ishead.p);
-    k_best<<<grid1(n), kBlock, 0, s>>>(n, t.ptr.p, t.col.p, t.w.p, best.p, lab.p, size.p);
+                                       sprev.p, snext.p, ishead.p); ::pc::count_launches(1);
+    k_best<<<grid1(n), kBlock, 0, s>>>(n, t.ptr.p, t.col.p, t.w.p, best.p, lab.p, size.p); ::pc::count_launches(1);
     PC_LAUNCH("pair/best");
     int32_t rounds = 0;
     for (;;) {
         PC_CUDA(cudaMemsetAsync(gcnt.p, 0, sizeof(int32_t) * n, s));
         PC_CUDA(cudaMemsetAsync(nleft.p, 0, sizeof(int32_t), s));
-        k_left_classify<<<grid1(n), kBlock, 0, s>>>(n, lab.p, best.p, st.p, jg.p, gcnt.p, nleft.p);
+        k_left_classify<<<grid1(n), kBlock, 0, s>>>(n, lab.p, best.p, st.p, jg.p, gcnt.p, nleft.p); ::pc::count_launches(1);
         PC_LAUNCH("left_classify");
         if (read_i32(c, nleft.p) == 0) break;
         if (rounds >= c.p.round_cap) {
-            k_left_tail<<<1, 1, 0, s>>>(n, best.p, lab.p, size.p);
+            k_left_tail<<<1, 1, 0, s>>>(n, best.p, lab.p, size.p); ::pc::count_launches(1);
             PC_LAUNCH("left_tail");
             ++rounds;
             break;
         }
-        k_left_case1<<<grid1(n), kBlock, 0, s>>>(n, st.p, best.p, lab.p, size.p);
+        k_left_case1<<<grid1(n), kBlock, 0, s>>>(n, st.p, best.p, lab.p, size.p); ::pc::count_launches(1);
         scan_i32(c, gcnt.p, goff.p, n);
         PC_CUDA(cudaMemsetAsync(gfill.p, 0, sizeof(int32_t) * n, s));
-        k_left_fill<<<grid1(n), kBlock, 0, s>>>(n, st.p, jg.p, goff.p, gfill.p, list.p);
-        k_left_join<<<grid1(n), kBlock, 0, s>>>(n, goff.p, list.p, best.p, lab.p, size.p);
+        k_left_fill<<<grid1(n), kBlock, 0, s>>>(n, st.p, jg.p, goff.p, gfill.p, list.p); ::pc::count_launches(1);
+        k_left_join<<<grid1(n), kBlock, 0, s>>>(n, goff.p, list.p, best.p, lab.p, size.p); ::pc::count_launches(1);
         PC_LAUNCH("left_round");
         ++rounds;
     }
@@ -944,17 +944,17 @@ int32_t aggregate_level(Ctx& c, int32_t n, const int32_t* nbr0, const int32_t* n
     DBuf<int32_t> minmem, flag, cidat;
     minmem.alloc(c.mem, n); flag.alloc(c.mem, n); cidat.alloc(c.mem, (size_t)n + 1);
     fill_i32(s, n, 0x7fffffff, minmem.p);
-    k_minmem<<<grid1(n), kBlock, 0, s>>>(n, lab.p, minmem.p);
-    k_isfirst<<<grid1(n), kBlock, 0, s>>>(n, lab.p, minmem.p, flag.p);
+    k_minmem<<<grid1(n), kBlock, 0, s>>>(n, lab.p, minmem.p); ::pc::count_launches(1);
+    k_isfirst<<<grid1(n), kBlock, 0, s>>>(n, lab.p, minmem.p, flag.p); ::pc::count_launches(1);
     PC_LAUNCH("numbering");
     int32_t nc = (int32_t)scan_i32(c, flag.p, cidat.p, n);
     agg.alloc(c.mem, n);
-    k_agg_ids<<<grid1(n), kBlock, 0, s>>>(n, lab.p, minmem.p, cidat.p, agg.p);
+    k_agg_ids<<<grid1(n), kBlock, 0, s>>>(n, lab.p, minmem.p, cidat.p, agg.p); ::pc::count_launches(1);
     cnbr0.alloc(c.mem, nc);
     cnbr1.alloc(c.mem, nc);
     fill_i32(s, nc, -1, cnbr0.p);
     fill_i32(s, nc, -1, cnbr1.p);
-    k_shorten<<<grid1(n), kBlock, 0, s>>>(n, ishead.p, sprev.p, snext.p, minmem.p, cidat.p, cnbr0.p, cnbr1.p);
+    k_shorten<<<grid1(n), kBlock, 0, s>>>(n, ishead.p, sprev.p, snext.p, minmem.p, cidat.p, cnbr0.p, cnbr1.p); ::pc::count_launches(1);
     PC_LAUNCH("agg/shorten");
     sync(c);
     if (rounds_out) *rounds_out = rounds;
@@ -969,19 +969,19 @@ void build_members(Ctx& c, int32_t n, int32_t nc, const int32_t* agg, DBuf<int32
     fillc.alloc(c.mem, nc);
     PC_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * nc, s));
     PC_CUDA(cudaMemsetAsync(fillc.p, 0, sizeof(int32_t) * nc, s));
-    k_count_agg<<<grid1(n), kBlock, 0, s>>>(n, agg, cnt.p);
+    k_count_agg<<<grid1(n), kBlock, 0, s>>>(n, agg, cnt.p); ::pc::count_launches(1);
     agg_ptr.alloc(c.mem, (size_t)nc + 1);
     scan_i32(c, cnt.p, agg_ptr.p, nc);
     agg_mem.alloc(c.mem, n);
-    k_fill_members<<<grid1(n), kBlock, 0, s>>>(n, agg, agg_ptr.p, fillc.p, agg_mem.p);
-    k_sort_members<<<grid1(nc), kBlock, 0, s>>>(nc, agg_ptr.p, agg_mem.p);
+    k_fill_members<<<grid1(n), kBlock, 0, s>>>(n, agg, agg_ptr.p, fillc.p, agg_mem.p); ::pc::count_launches(1);
+    k_sort_members<<<grid1(nc), kBlock, 0, s>>>(nc, agg_ptr.p, agg_mem.p); ::pc::count_launches(1);
     PC_LAUNCH("members");
 }
 
 void build_pval(Ctx& c, int32_t n, int32_t nc, const int32_t* agg_ptr, const int32_t* agg_mem,
                 const double* e, DBuf<double>& pval) {
     pval.alloc(c.mem, n);
-    k_pval<<<grid1(nc), kBlock, 0, c.stream>>>(nc, agg_ptr, agg_mem, e, pval.p);
+    k_pval<<<grid1(nc), kBlock, 0, c.stream>>>(nc, agg_ptr, agg_mem, e, pval.p); ::pc::count_launches(1);
     PC_LAUNCH("pval");
 }
 

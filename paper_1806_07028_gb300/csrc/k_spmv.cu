@@ -212,7 +212,8 @@ void residual64(cudaStream_t s, const Csr& A, const double* x, const double* b, 
 #define CALL(L) k_residual<double, L><<<g, kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, b, r, norm2 ? partial : nullptr)
     PC_LPR_DISPATCH(A.lpr, CALL)
 #undef CALL
-    if (norm2) k_finish<<<1, 1024, 0, s>>>(g, partial, norm2);
+    count_launches(1);
+    if (norm2) { k_finish<<<1, 1024, 0, s>>>(g, partial, norm2); ::pc::count_launches(1); }
     PC_LAUNCH("residual64");
 }
 
@@ -221,6 +222,7 @@ void residual32(cudaStream_t s, const Csr& A, const float* x, const float* b, fl
 #define CALL(L) k_residual<float, L><<<g, kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val32, x, b, r, nullptr)
     PC_LPR_DISPATCH(A.lpr, CALL)
 #undef CALL
+    count_launches(1);
     PC_LAUNCH("residual32");
 }
 
@@ -229,6 +231,7 @@ void spmv64(cudaStream_t s, const Csr& A, const double* x, double* y) {
 #define CALL(L) k_spmv<L><<<g, kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, y)
     PC_LPR_DISPATCH(A.lpr, CALL)
 #undef CALL
+    count_launches(1);
     PC_LAUNCH("spmv64");
 }
 
@@ -241,19 +244,20 @@ void gs_colour(cudaStream_t s, const Csr& A, const int32_t* rows, int32_t nrows,
 #define CALL(L) k_gs<T, L><<<g, kBlock, 0, s>>>(nrows, rows, A.rowptr, A.col, val, b, x)
     PC_LPR_DISPATCH(A.lpr, CALL)
 #undef CALL
+    count_launches(1);
     PC_LAUNCH("gs_colour");
 }
 
 template <class T>
 void restrict_agg(cudaStream_t s, int32_t nc, const int32_t* agg_ptr, const int32_t* agg_mem,
                   const T* pval, const T* r, T* bc) {
-    k_restrict<T><<<simple_grid(nc), kBlock, 0, s>>>(nc, agg_ptr, agg_mem, pval, r, bc);
+    k_restrict<T><<<simple_grid(nc), kBlock, 0, s>>>(nc, agg_ptr, agg_mem, pval, r, bc); ::pc::count_launches(1);
     PC_LAUNCH("restrict");
 }
 
 template <class T>
 void prolong_add(cudaStream_t s, int32_t n, const int32_t* agg, const T* pval, const T* xc, T* x) {
-    k_prolong<T><<<simple_grid(n), kBlock, 0, s>>>(n, agg, pval, xc, x);
+    k_prolong<T><<<simple_grid(n), kBlock, 0, s>>>(n, agg, pval, xc, x); ::pc::count_launches(1);
     PC_LAUNCH("prolong");
 }
 
@@ -261,7 +265,7 @@ template <class T>
 void coarse_apply(cudaStream_t s, int32_t m, const double* Xinv, const T* b, T* x) {
     int g = (m * 32 + kBlock - 1) / kBlock;
     if (g > kNumSMs * 4) g = kNumSMs * 4;
-    k_coarse_apply<T><<<g, kBlock, 0, s>>>(m, Xinv, b, x);
+    k_coarse_apply<T><<<g, kBlock, 0, s>>>(m, Xinv, b, x); ::pc::count_launches(1);
     PC_LAUNCH("coarse_apply");
 }
 

@@ -236,8 +236,8 @@ int reduce_blocks(int64_t n) {
 
 void dot(cudaStream_t s, int64_t n, const double* x, const double* y, double* partial, double* out) {
     int nb = reduce_blocks(n);
-    k_dot_partial<<<nb, kRedBlock, 0, s>>>(n, x, y, partial);
-    k_finish_sum<<<1, 1024, 0, s>>>(nb, partial, out);
+    k_dot_partial<<<nb, kRedBlock, 0, s>>>(n, x, y, partial); ::pc::count_launches(1);
+    k_finish_sum<<<1, 1024, 0, s>>>(nb, partial, out); ::pc::count_launches(1);
     PC_LAUNCH("dot");
 }
 
@@ -246,56 +246,56 @@ void sum(cudaStream_t s, int64_t n, const double* x, double* partial, double* ou
 }
 
 void axpy(cudaStream_t s, int64_t n, double a, const double* x, double* y) {
-    k_axpy<<<grid_for(n), kBlock, 0, s>>>(n, a, x, y);
+    k_axpy<<<grid_for(n), kBlock, 0, s>>>(n, a, x, y); ::pc::count_launches(1);
     PC_LAUNCH("axpy");
 }
 void axpy_dev(cudaStream_t s, int64_t n, const double* a, double sign, const double* x, double* y) {
-    k_axpy_dev<<<grid_for(n), kBlock, 0, s>>>(n, a, sign, x, y);
+    k_axpy_dev<<<grid_for(n), kBlock, 0, s>>>(n, a, sign, x, y); ::pc::count_launches(1);
     PC_LAUNCH("axpy_dev");
 }
 void xpby_dev(cudaStream_t s, int64_t n, const double* x, const double* beta, double* y) {
-    k_xpby_dev<<<grid_for(n), kBlock, 0, s>>>(n, x, beta, y);
+    k_xpby_dev<<<grid_for(n), kBlock, 0, s>>>(n, x, beta, y); ::pc::count_launches(1);
     PC_LAUNCH("xpby_dev");
 }
 void sub_mean(cudaStream_t s, int64_t n, double* x, const double* total) {
-    k_sub_mean<<<grid_for(n), kBlock, 0, s>>>(n, x, total);
+    k_sub_mean<<<grid_for(n), kBlock, 0, s>>>(n, x, total); ::pc::count_launches(1);
     PC_LAUNCH("sub_mean");
 }
 void scale_dev(cudaStream_t s, int64_t n, double* x, const double* num, const double* den) {
-    k_scale_dev<<<grid_for(n), kBlock, 0, s>>>(n, x, num, den);
+    k_scale_dev<<<grid_for(n), kBlock, 0, s>>>(n, x, num, den); ::pc::count_launches(1);
     PC_LAUNCH("scale_dev");
 }
 void copy(cudaStream_t s, int64_t n, const double* x, double* y) {
-    k_copy<<<grid_for(n), kBlock, 0, s>>>(n, x, y);
+    k_copy<<<grid_for(n), kBlock, 0, s>>>(n, x, y); ::pc::count_launches(1);
     PC_LAUNCH("copy");
 }
 void fill(cudaStream_t s, int64_t n, double v, double* y) {
-    k_fill<<<grid_for(n), kBlock, 0, s>>>(n, v, y);
+    k_fill<<<grid_for(n), kBlock, 0, s>>>(n, v, y); ::pc::count_launches(1);
     PC_LAUNCH("fill");
 }
 void fill_i32(cudaStream_t s, int64_t n, int32_t v, int32_t* y) {
-    k_fill_i32<<<grid_for(n), kBlock, 0, s>>>(n, v, y);
+    k_fill_i32<<<grid_for(n), kBlock, 0, s>>>(n, v, y); ::pc::count_launches(1);
     PC_LAUNCH("fill_i32");
 }
 void cast_scaled_f32(cudaStream_t s, int64_t n, const double* x, const double* inv, float* y) {
-    k_cast_scaled_f32<<<grid_for(n), kBlock, 0, s>>>(n, x, inv, y);
+    k_cast_scaled_f32<<<grid_for(n), kBlock, 0, s>>>(n, x, inv, y); ::pc::count_launches(1);
     PC_LAUNCH("cast_scaled_f32");
 }
 void cast_f32(cudaStream_t s, int64_t n, const double* x, float* y) { cast_scaled_f32(s, n, x, nullptr, y); }
 void add_scaled_f32(cudaStream_t s, int64_t n, const float* c, const double* scale, double* x) {
-    k_add_scaled_f32<<<grid_for(n), kBlock, 0, s>>>(n, c, scale, x);
+    k_add_scaled_f32<<<grid_for(n), kBlock, 0, s>>>(n, c, scale, x); ::pc::count_launches(1);
     PC_LAUNCH("add_scaled_f32");
 }
 void cast_f64(cudaStream_t s, int64_t n, const float* x, double* y) {
-    k_cast_f64<<<grid_for(n), kBlock, 0, s>>>(n, x, y);
+    k_cast_f64<<<grid_for(n), kBlock, 0, s>>>(n, x, y); ::pc::count_launches(1);
     PC_LAUNCH("cast_f64");
 }
 void philox_uniform(cudaStream_t s, uint64_t seed, int64_t n, double* out) {
-    k_philox_uniform<<<grid_for((n + 3) / 4), kBlock, 0, s>>>(seed, n, out);
+    k_philox_uniform<<<grid_for((n + 3) / 4), kBlock, 0, s>>>(seed, n, out); ::pc::count_launches(1);
     PC_LAUNCH("philox_uniform");
 }
 void scalar_ops(cudaStream_t s, int op, double* slots, int a, int b, int c) {
-    k_scalar<<<1, 32, 0, s>>>(op, slots, a, b, c);
+    k_scalar<<<1, 32, 0, s>>>(op, slots, a, b, c); ::pc::count_launches(1);
     PC_LAUNCH("scalar_ops");
 }
 
@@ -312,11 +312,11 @@ static int64_t scan_impl(Ctx& c, const TI* in, TO* out, int64_t n) {
     DBuf<int64_t> tsum, toff;
     tsum.alloc(c.mem, ntiles + 1);
     toff.alloc(c.mem, ntiles + 1);
-    k_scan_tiles<TI, TO><<<(unsigned)ntiles, 256, 0, c.stream>>>(n, in, out, tsum.p);
+    k_scan_tiles<TI, TO><<<(unsigned)ntiles, 256, 0, c.stream>>>(n, in, out, tsum.p); ::pc::count_launches(1);
     PC_LAUNCH("scan_tiles");
     if (ntiles > 1) {
         scan_impl<int64_t, int64_t>(c, tsum.p, toff.p, ntiles);
-        k_scan_add<TO><<<(unsigned)ntiles, 256, 0, c.stream>>>(n, out, toff.p);
+        k_scan_add<TO><<<(unsigned)ntiles, 256, 0, c.stream>>>(n, out, toff.p); ::pc::count_launches(1);
         PC_LAUNCH("scan_add");
     } else {
         int64_t z = 0;
@@ -324,8 +324,8 @@ static int64_t scan_impl(Ctx& c, const TI* in, TO* out, int64_t n) {
         PC_CUDA(cudaMemcpyAsync(toff.p + 1, tsum.p, sizeof(int64_t), cudaMemcpyDeviceToDevice, c.stream));
     }
     // total = toff[ntiles-1] + tsum[ntiles-1]
-    k_set_last<<<1, 1, 0, c.stream>>>(n, tsum.p + ntiles, toff.p, tsum.p, ntiles);
-    k_store_total<TO><<<1, 1, 0, c.stream>>>(out, n, tsum.p + ntiles);
+    k_set_last<<<1, 1, 0, c.stream>>>(n, tsum.p + ntiles, toff.p, tsum.p, ntiles); ::pc::count_launches(1);
+    k_store_total<TO><<<1, 1, 0, c.stream>>>(out, n, tsum.p + ntiles); ::pc::count_launches(1);
     PC_LAUNCH("scan_total");
     return read_i64(c, tsum.p + ntiles);
 }

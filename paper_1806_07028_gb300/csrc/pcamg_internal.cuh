@@ -19,8 +19,14 @@ struct Error {
 
 [[noreturn]] void fail(pcamg_status s, const std::string& msg);
 void check_cuda(cudaError_t e, const char* what);
+// Process-wide count of kernels this library has launched (a graph replay adds
+// the number of kernels it holds).
+void count_launches(int64_t k);
+int64_t launch_count();
+bool capturing();
 #define PC_CUDA(call) ::pc::check_cuda((call), #call)
 #define PC_LAUNCH(what) ::pc::check_cuda(cudaGetLastError(), what)
+#define PC_LAUNCHN(what, k) do { ::pc::check_cuda(cudaGetLastError(), what); ::pc::count_launches(k); } while (0)
 
 constexpr int kMaxLevels = 32;
 constexpr int kBlock = 256;
@@ -113,6 +119,7 @@ struct Hier {
     double oc = 0.0;
     // CUDA graphs of the correction cycle (index: gamma-1)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int64_t graph_kernels[2] = {0, 0};
     ~Hier();
 };
 
@@ -153,6 +160,8 @@ struct Ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int64_t prof_launches = 0;
     double prof_ms = 0.0;
+    int64_t ncycles = 0;
+    double t_alg2 = 0.0, t_alg4 = 0.0;
     ~Ctx();
 };
 

@@ -28,6 +28,7 @@ EXPORTS = [
     "pcamg_num_hierarchies", "pcamg_num_levels", "pcamg_level_sizes", "pcamg_export_level",
     "pcamg_export_reweighted", "pcamg_last_error", "pcamg_status_string", "pcamg_destroy",
     "pcamg_residual", "pcamg_residual_f32", "pcamg_uniform", "pcamg_colour",
+    "pcamg_kernel_launches",
 ]
 
 
@@ -55,6 +56,7 @@ class Stats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("resetups", C.c_int32), ("levels", C.c_int32),
                 ("status", C.c_int32), ("rel_res", C.c_double), ("oc_mean", C.c_double),
                 ("t_setup_ms", C.c_double), ("t_solve_ms", C.c_double),
+                ("t_alg2_ms", C.c_double), ("t_alg4_ms", C.c_double), ("cycles", C.c_int64),
                 ("res_hist", C.POINTER(C.c_double)), ("res_hist_cap", C.c_int32),
                 ("res_hist_len", C.c_int32), ("prof_launches", C.c_int64),
                 ("prof_ms", C.c_double), ("prof_bytes", C.c_double)]
@@ -92,6 +94,7 @@ def lib():
                 "pcamg_residual_f32": ([i32, vp, vp, vp, vp, vp, vp, vp], i32),
                 "pcamg_uniform": ([u64, i64, vp, vp], i32),
                 "pcamg_colour": ([i32, vp, vp, u64, vp, P(i32), vp], i32),
+                "pcamg_kernel_launches": ([], i64),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)

@@ -217,6 +217,7 @@ def test_invalid_inputs_return_status(P):
         s.solve(b)
     assert ei.value.status == N.ERR_INVALID
     # max_iter hit: NOT_CONVERGED with stats filled
-    s2 = P.Solver(g, params=P.default_params(max_iter=1, threshold=10.0))
-    x, st = s2.solve(I.rhs_normal(g.n, 0))
+    g2 = I.grid2d(48, 48)
+    s2 = P.Solver(g2, params=P.default_params(max_iter=1, threshold=10.0))
+    x, st = s2.solve(I.rhs_normal(g2.n, 0))
     assert st["status"] == "NOT_CONVERGED" and st["iters"] == 1
