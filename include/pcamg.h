@@ -85,6 +85,8 @@ typedef struct {
     int32_t use_graphs;    /* capture each cycle in a CUDA graph and replay it */
     int32_t keep_setup;    /* keep covers and reweighted graphs for export */
     int32_t profile;       /* time the fine-level residual kernel with CUDA events */
+    int32_t tail_rows;     /* levels with at most this many unknowns run inside one
+                              thread block per cycle visit (0 = never) */
 } pcamg_params;
 
 typedef struct {

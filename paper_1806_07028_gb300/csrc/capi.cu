@@ -1,5 +1,6 @@
 // C ABI of the library (see include/pcamg.h): argument checks, CSR validation,
 // handle life cycle, and error translation (no exception crosses the ABI).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -91,7 +92,7 @@ void check_params(const pcamg_params& p) {
         (p.p1_mode != PCAMG_P1_E_SCALED && p.p1_mode != PCAMG_P1_BOOLEAN) ||
         (p.precision != PCAMG_FP64 && p.precision != PCAMG_FP32_IR) ||
         (p.start != PCAMG_START_RANDOM && p.start != PCAMG_START_USER) || p.dense_max < 1 ||
-        p.dense_max > 4096)
+        p.dense_max > 4096 || p.tail_rows < 0)
         fail(PCAMG_ERR_INVALID, "invalid parameters");
 }
 
@@ -131,8 +132,9 @@ void alloc_work(Ctx& c) {
     DBuf<double>* vs[] = {&c.w_r, &c.w_c, &c.w_e, &c.w_t1, &c.w_t2, &c.w_z, &c.w_p,
                           &c.w_q, &c.w_rold, &c.w_eh, &c.w_ein, &c.w_cin};
     for (auto* v : vs) v->alloc(c.mem, c.n);
-    c.red.alloc(c.mem, 4096 + 64);
-    PC_CUDA(cudaMemsetAsync(c.red.p, 0, sizeof(double) * (4096 + 64), c.stream));
+    c.npartials = std::max<int64_t>(4096, residual_partials(c.n));
+    c.red.alloc(c.mem, c.npartials + 64);
+    PC_CUDA(cudaMemsetAsync(c.red.p, 0, sizeof(double) * (c.npartials + 64), c.stream));
     PC_CUDA(cudaMallocHost(&c.h_red, sizeof(double) * 64));
     PC_CUDA(cudaEventCreate(&c.ev0));
     PC_CUDA(cudaEventCreate(&c.ev1));
@@ -191,6 +193,7 @@ PCAMG_API pcamg_status pcamg_default_params(pcamg_params* p) {
     p->use_graphs = 1;
     p->keep_setup = 0;
     p->profile = 0;
+    p->tail_rows = 8192;
     return PCAMG_OK;
 }
 
@@ -231,6 +234,15 @@ PCAMG_API pcamg_status pcamg_setup(pcamg_handle* out, const pcamg_params* p, int
         c->colour0.alloc(c->mem, n);
         c->ncolour0 = colour_graph(*c, n, c->rowptr.p, c->col.p, c->p.seed, c->colour0.p);
         colour_lists(*c, n, c->colour0.p, c->ncolour0, c->colour_rows0, c->h_colour_ptr0);
+        // rows grouped by colour, for the streaming smoother (FP64 for the start
+        // vector and the FP64 cycle; FP32 for the FP32 cycle)
+        permute_rows<double>(*c, n, c->colour_rows0.p, c->rowptr.p, c->col.p, c->val.p, c->gs_ptr0,
+                             c->gs_col0, c->gs_val0_64);
+        if (c->p.precision == PCAMG_FP32_IR) {
+            DBuf<int32_t> p2, c2;
+            permute_rows<float>(*c, n, c->colour_rows0.p, c->rowptr.p, c->col.p, c->val.p, p2, c2,
+                                c->gs_val0_32);
+        }
         if (c->p.start == PCAMG_START_USER) {
             check_finite(*c, d_e0, n, "start vector");
             copy(c->stream, n, d_e0, c->w_e.p);
@@ -458,7 +470,7 @@ PCAMG_API pcamg_status pcamg_residual(int32_t n, const int32_t* d_rowptr, const 
         A.n = n; A.nnz = nnz; A.rowptr = d_rowptr; A.col = d_col; A.val = d_val;
         A.lpr = lanes_per_row(n, nnz);
         DBuf<double> part;
-        if (d_norm2) part.alloc(tmp.mem, 4096);
+        if (d_norm2) part.alloc(tmp.mem, std::max<int64_t>(4096, residual_partials(n)));
         residual64(tmp.stream, A, d_x, d_b, d_r, part.p, d_norm2);
         sync(tmp);
         return PCAMG_OK;

@@ -90,9 +90,8 @@ double read_f64(Ctx& c, const double* dev) {
 }
 
 // scalar slots after the reduction partials
-constexpr int kPartials = 4096;
 enum Slot { S_T0 = 0, S_T1, S_T2, S_NORM2, S_RZ, S_PQ, S_ALPHA, S_NUM, S_BETA, S_SCALE, S_INV, S_SUM, S_NSLOTS };
-static double* slot(Ctx& c, int k) { return c.red.p + kPartials + k; }
+static double* slot(Ctx& c, int k) { return c.red.p + c.npartials + k; }
 static double* partials(Ctx& c) { return c.red.p; }
 
 void normalise_orth(Ctx& c, const double* e, double* out) {
@@ -125,10 +124,13 @@ struct LV<float> {
 
 template <class T>
 static void smooth(Ctx& c, Level& L, const T* b, T* x, bool forward) {
+    const T* pv;
+    if constexpr (sizeof(T) == 8) pv = L.gs_val64_v; else pv = L.gs_val32_v;
     for (int32_t t = 0; t < L.ncolour; ++t) {
         int32_t k = forward ? t : L.ncolour - 1 - t;
         int32_t beg = L.h_colour_ptr[k], end = L.h_colour_ptr[k + 1];
-        gs_colour<T>(c.stream, L.A, L.colour_rows_v + beg, end - beg, b, x);
+        if (pv) gs_colour_perm<T>(c.stream, beg, end, L.colour_rows_v, L.gs_ptr_v, L.gs_col_v, pv, b, x);
+        else gs_colour<T>(c.stream, L.A, L.colour_rows_v + beg, end - beg, b, x);
     }
 }
 
@@ -136,6 +138,11 @@ template <class T>
 static void cycle_level(Ctx& c, Hier& h, int32_t l, int gamma) {
     cudaStream_t s = c.stream;
     Level& L = h.lev[l];
+    if (l == h.lt) {
+        tail_cycle<T>(s, reinterpret_cast<const TailLevel<T>*>(h.tail.p), l, h.nlev, gamma,
+                      c.p.nu_pre, c.p.nu_post, h.Xinv.p);
+        return;
+    }
     if (l == h.nlev - 1) {
         coarse_apply<T>(s, L.n, h.Xinv.p, LV<T>::b(L), LV<T>::x(L));
         return;
@@ -305,7 +312,11 @@ void start_vector(Ctx& c, double* e) {
     for (int32_t k = 0; k < c.p.relax_sweeps; ++k) {
         for (int32_t t = 0; t < c.ncolour0; ++t) {
             int32_t beg = c.h_colour_ptr0[t], end = c.h_colour_ptr0[t + 1];
-            gs_colour<double>(s, A, c.colour_rows0.p + beg, end - beg, c.w_t1.p, e);
+            if (c.gs_val0_64.p)
+                gs_colour_perm<double>(s, beg, end, c.colour_rows0.p, c.gs_ptr0.p, c.gs_col0.p,
+                                       c.gs_val0_64.p, c.w_t1.p, e);
+            else
+                gs_colour<double>(s, A, c.colour_rows0.p + beg, end - beg, c.w_t1.p, e);
         }
     }
     normalise_orth(c, e, e);

@@ -2,7 +2,9 @@
 // path cover, then per level path-cover aggregation (Alg. 3), prolongation
 // (level 1 carries e, Section 3.3), Galerkin products of A and of the reweighted
 // graph, path shortening, smoother colouring, and the coarsest factorisation.
+#include <cstring>
 #include <memory>
+#include <vector>
 #include <utility>
 
 #include "pcamg_internal.cuh"
@@ -28,6 +30,49 @@ static Csr make_csr(const Level& L, int32_t n, int64_t nnz, const int32_t* rp, c
     return A;
 }
 
+template <class T>
+static T* vx(Level& L) { if constexpr (sizeof(T) == 8) return L.x64.p; else return L.x32.p; }
+template <class T>
+static T* vb(Level& L) { if constexpr (sizeof(T) == 8) return L.b64.p; else return L.b32.p; }
+template <class T>
+static T* vr(Level& L) { if constexpr (sizeof(T) == 8) return L.r64.p; else return L.r32.p; }
+
+template <class T>
+static void setup_tail(Ctx& c, Hier& h) {
+    std::vector<TailLevel<T>> tl(h.nlev);
+    for (int32_t l = h.lt; l < h.nlev; ++l) {
+        Level& L = h.lev[l];
+        TailLevel<T>& t = tl[l];
+        std::memset(&t, 0, sizeof(t));
+        t.n = L.n;
+        t.nc = (l + 1 < h.nlev) ? L.nc : 0;
+        t.ncolour = (l + 1 < h.nlev) ? L.ncolour : 0;
+        t.lpr = L.A.lpr;
+        t.rowptr = L.A.rowptr;
+        t.col = L.A.col;
+        if constexpr (sizeof(T) == 8) t.val = L.A.val; else t.val = L.A.val32;
+        if (l + 1 < h.nlev) {
+            L.d_cptr.alloc(c.mem, L.h_colour_ptr.size());
+            PC_CUDA(cudaMemcpyAsync(L.d_cptr.p, L.h_colour_ptr.data(), sizeof(int32_t) * L.h_colour_ptr.size(),
+                                    cudaMemcpyHostToDevice, c.stream));
+            t.cptr = L.d_cptr.p;
+            t.crows = L.colour_rows_v;
+            t.agg = L.agg.p;
+            t.agg_ptr = L.agg_ptr.p;
+            t.agg_mem = L.agg_mem.p;
+            if (l == 0) {
+                if constexpr (sizeof(T) == 8) t.pval = L.pval.p; else t.pval = L.pval32.p;
+            }
+        }
+        t.x = vx<T>(L);
+        t.b = vb<T>(L);
+        t.r = vr<T>(L);
+    }
+    h.tail.alloc(c.mem, sizeof(TailLevel<T>) * h.nlev);
+    PC_CUDA(cudaMemcpyAsync(h.tail.p, tl.data(), sizeof(TailLevel<T>) * h.nlev, cudaMemcpyHostToDevice, c.stream));
+    sync(c);
+}
+
 Hier* build_hierarchy(Ctx& c, const double* e) {
     const pcamg_params& p = c.p;
     std::unique_ptr<Hier> h(new Hier());
@@ -40,6 +85,10 @@ Hier* build_hierarchy(Ctx& c, const double* e) {
     L0.colour_v = c.colour0.p;
     L0.colour_rows_v = c.colour_rows0.p;
     L0.h_colour_ptr = c.h_colour_ptr0;
+    L0.gs_ptr_v = c.gs_ptr0.p;
+    L0.gs_col_v = c.gs_col0.p;
+    L0.gs_val64_v = f32 ? nullptr : c.gs_val0_64.p;
+    L0.gs_val32_v = f32 ? c.gs_val0_32.p : nullptr;
 
     // Alg. 4 steps 2-3: reweighted A^2 pattern and its path cover
     Reweighted t;
@@ -135,6 +184,27 @@ Hier* build_hierarchy(Ctx& c, const double* e) {
         }
     }
     h->oc = nnz_sum / (double)c.nnz;
+    // levels from lt down run inside the single-block tail kernel
+    h->lt = nlev;
+    if (p.tail_rows > 0)
+        for (int32_t l = 0; l < nlev; ++l)
+            if (h->lev[l].n <= p.tail_rows) { h->lt = l; break; }
+    if (h->lt < nlev) {
+        if (f32) setup_tail<float>(c, *h); else setup_tail<double>(c, *h);
+    }
+    // row-permuted copies for the streaming smoother on levels above the tail
+    for (int32_t l = 1; l < h->lt && l + 1 < nlev; ++l) {
+        Level& L = h->lev[l];
+        if (f32) {
+            permute_rows<float>(c, L.n, L.colour_rows_v, L.A.rowptr, L.A.col, L.A.val, L.gs_ptr, L.gs_col, L.gs_val32);
+            L.gs_val32_v = L.gs_val32.p;
+        } else {
+            permute_rows<double>(c, L.n, L.colour_rows_v, L.A.rowptr, L.A.col, L.A.val, L.gs_ptr, L.gs_col, L.gs_val64);
+            L.gs_val64_v = L.gs_val64.p;
+        }
+        L.gs_ptr_v = L.gs_ptr.p;
+        L.gs_col_v = L.gs_col.p;
+    }
     sync(c);
     return h.release();
 }

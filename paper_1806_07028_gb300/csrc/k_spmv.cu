@@ -188,6 +188,118 @@ __global__ void k_coarse_apply(int m, const double* __restrict__ X, const T* __r
     }
 }
 
+// ---- CSR-stream kernels -----------------------------------------------------
+// A block owns a tile of kStreamRows consecutive rows. It walks the tile's
+// entries in chunks of kStreamChunk: every thread computes products a_k x_col(k)
+// for entries of the chunk (coalesced loads of col and val, independent loads of
+// x, so many are in flight), stages them in shared memory, and then each thread
+// adds the products of its own row in CSR order. A row's sum is therefore taken
+// left to right, with one rounding per product and per addition.
+constexpr int kStreamRows = 256;
+constexpr int kStreamChunk = 2048;
+
+// r_i = b_i - sum_k a_k x_col(k); partial[block] = sum of r_i^2 when requested
+template <class T, bool NORM>
+__global__ void __launch_bounds__(kStreamRows) k_res_stream(int n, const int* __restrict__ rowptr,
+                                                             const int* __restrict__ col,
+                                                             const T* __restrict__ val,
+                                                             const T* __restrict__ x,
+                                                             const T* __restrict__ b,
+                                                             T* __restrict__ r,
+                                                             double* __restrict__ partial) {
+    __shared__ T prod[kStreamChunk];
+    const int r0 = blockIdx.x * kStreamRows;
+    const int row = r0 + threadIdx.x;
+    const int rlast = min(r0 + kStreamRows, n);
+    const int tb = __ldg(rowptr + r0), te = __ldg(rowptr + rlast);
+    int rb = 0, re = 0;
+    if (row < n) { rb = __ldg(rowptr + row); re = __ldg(rowptr + row + 1); }
+    T s = 0;
+    for (int c0 = tb; c0 < te; c0 += kStreamChunk) {
+        const int c1 = min(c0 + kStreamChunk, te);
+        for (int k = c0 + threadIdx.x; k < c1; k += kStreamRows)
+            prod[k - c0] = __ldg(val + k) * __ldg(x + __ldg(col + k));
+        __syncthreads();
+        const int kb = max(rb, c0), ke = min(re, c1);
+        for (int k = kb; k < ke; ++k) s += prod[k - c0];
+        __syncthreads();
+    }
+    double rr2 = 0.0;
+    if (row < n) {
+        T rr = __ldg(b + row) - s;
+        r[row] = rr;
+        rr2 = (double)rr * (double)rr;
+    }
+    if (NORM) {
+        __shared__ double ws[kStreamRows / 32];
+        rr2 = warp_sum_d(rr2);
+        if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = rr2;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double v = threadIdx.x < kStreamRows / 32 ? ws[threadIdx.x] : 0.0;
+            v = warp_sum_d(v);
+            if (threadIdx.x == 0) partial[blockIdx.x] = v;
+        }
+    }
+}
+
+// One colour of Gauss-Seidel on the row-permuted copy (rows of a colour are
+// contiguous there): x_row = (b_row - sum_{j != row} a x_j) / a_row,row.
+template <class T>
+__global__ void __launch_bounds__(kStreamRows) k_gs_stream(int beg, int end, const int* __restrict__ rows,
+                                                            const int* __restrict__ pptr,
+                                                            const int* __restrict__ pcol,
+                                                            const T* __restrict__ pval,
+                                                            const T* __restrict__ b, T* __restrict__ x) {
+    __shared__ T prod[kStreamChunk];
+    __shared__ int pc[kStreamChunk];
+    const int t0 = beg + blockIdx.x * kStreamRows;
+    const int t = t0 + threadIdx.x;
+    const int tlast = min(t0 + kStreamRows, end);
+    const int tb = __ldg(pptr + t0), te = __ldg(pptr + tlast);
+    int rb = 0, re = 0, row = -1;
+    if (t < end) { rb = __ldg(pptr + t); re = __ldg(pptr + t + 1); row = __ldg(rows + t); }
+    T s = 0, d = 0;
+    for (int c0 = tb; c0 < te; c0 += kStreamChunk) {
+        const int c1 = min(c0 + kStreamChunk, te);
+        for (int k = c0 + threadIdx.x; k < c1; k += kStreamRows) {
+            const int j = __ldg(pcol + k);
+            pc[k - c0] = j;
+            prod[k - c0] = __ldg(pval + k) * x[j];
+        }
+        __syncthreads();
+        const int kb = max(rb, c0), ke = min(re, c1);
+        for (int k = kb; k < ke; ++k) {
+            if (pc[k - c0] == row) d = __ldg(pval + k);
+            else s += prod[k - c0];
+        }
+        __syncthreads();
+    }
+    if (t < end) x[row] = (__ldg(b + row) - s) / d;
+}
+
+// Row-permuted copy: row t of the copy is row rows[t] of A.
+__global__ void k_perm_counts(int n, const int* __restrict__ rows, const int* __restrict__ rowptr,
+                              int* __restrict__ cnt) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        int r = rows[t];
+        cnt[t] = rowptr[r + 1] - rowptr[r];
+    }
+}
+
+template <class T>
+__global__ void k_perm_fill(int n, const int* __restrict__ rows, const int* __restrict__ rowptr,
+                            const int* __restrict__ col, const double* __restrict__ val,
+                            const int* __restrict__ pptr, int* __restrict__ pcol, T* __restrict__ pval) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+        int r = rows[t], o = pptr[t];
+        for (int k = rowptr[r]; k < rowptr[r + 1]; ++k, ++o) {
+            pcol[o] = col[k];
+            pval[o] = (T)val[k];
+        }
+    }
+}
+
 inline int simple_grid(int64_t n) {
     int64_t g = (n + kBlock - 1) / kBlock;
     if (g < 1) g = 1;
@@ -208,21 +320,21 @@ inline int simple_grid(int64_t n) {
 
 void residual64(cudaStream_t s, const Csr& A, const double* x, const double* b, double* r,
                 double* partial, double* norm2) {
-    int g = sparse_grid(A.n, A.lpr);
-#define CALL(L) k_residual<double, L><<<g, kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, b, r, norm2 ? partial : nullptr)
-    PC_LPR_DISPATCH(A.lpr, CALL)
-#undef CALL
-    count_launches(1);
-    if (norm2) { k_finish<<<1, 1024, 0, s>>>(g, partial, norm2); ::pc::count_launches(1); }
+    int g = (A.n + kStreamRows - 1) / kStreamRows;
+    if (norm2) {
+        k_res_stream<double, true><<<g, kStreamRows, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, b, r, partial); ::pc::count_launches(1);
+        k_finish<<<1, 1024, 0, s>>>(g, partial, norm2); ::pc::count_launches(1);
+    } else {
+        k_res_stream<double, false><<<g, kStreamRows, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, b, r, nullptr); ::pc::count_launches(1);
+    }
     PC_LAUNCH("residual64");
 }
 
+int residual_partials(int32_t n) { return (n + kStreamRows - 1) / kStreamRows; }
+
 void residual32(cudaStream_t s, const Csr& A, const float* x, const float* b, float* r) {
-    int g = sparse_grid(A.n, A.lpr);
-#define CALL(L) k_residual<float, L><<<g, kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val32, x, b, r, nullptr)
-    PC_LPR_DISPATCH(A.lpr, CALL)
-#undef CALL
-    count_launches(1);
+    int g = (A.n + kStreamRows - 1) / kStreamRows;
+    k_res_stream<float, false><<<g, kStreamRows, 0, s>>>(A.n, A.rowptr, A.col, A.val32, x, b, r, nullptr); ::pc::count_launches(1);
     PC_LAUNCH("residual32");
 }
 
@@ -249,6 +361,31 @@ void gs_colour(cudaStream_t s, const Csr& A, const int32_t* rows, int32_t nrows,
 }
 
 template <class T>
+void gs_colour_perm(cudaStream_t s, int32_t beg, int32_t end, const int32_t* rows, const int32_t* pptr,
+                    const int32_t* pcol, const T* pval, const T* b, T* x) {
+    if (end <= beg) return;
+    int g = (end - beg + kStreamRows - 1) / kStreamRows;
+    k_gs_stream<T><<<g, kStreamRows, 0, s>>>(beg, end, rows, pptr, pcol, pval, b, x); ::pc::count_launches(1);
+    PC_LAUNCH("gs_colour_perm");
+}
+
+template <class T>
+void permute_rows(Ctx& c, int32_t n, const int32_t* rows, const int32_t* rowptr, const int32_t* col,
+                  const double* val, DBuf<int32_t>& pptr, DBuf<int32_t>& pcol, DBuf<T>& pval) {
+    cudaStream_t s = c.stream;
+    int64_t nnz = 0;
+    DBuf<int32_t> cnt;
+    cnt.alloc(c.mem, n);
+    k_perm_counts<<<simple_grid(n), kBlock, 0, s>>>(n, rows, rowptr, cnt.p); ::pc::count_launches(1);
+    pptr.alloc(c.mem, (size_t)n + 1);
+    nnz = scan_i32(c, cnt.p, pptr.p, n);
+    pcol.alloc(c.mem, nnz);
+    pval.alloc(c.mem, nnz);
+    k_perm_fill<T><<<simple_grid(n), kBlock, 0, s>>>(n, rows, rowptr, col, val, pptr.p, pcol.p, pval.p); ::pc::count_launches(1);
+    PC_LAUNCH("permute_rows");
+}
+
+template <class T>
 void restrict_agg(cudaStream_t s, int32_t nc, const int32_t* agg_ptr, const int32_t* agg_mem,
                   const T* pval, const T* r, T* bc) {
     k_restrict<T><<<simple_grid(nc), kBlock, 0, s>>>(nc, agg_ptr, agg_mem, pval, r, bc); ::pc::count_launches(1);
@@ -270,6 +407,10 @@ void coarse_apply(cudaStream_t s, int32_t m, const double* Xinv, const T* b, T* 
 }
 
 template void gs_colour<double>(cudaStream_t, const Csr&, const int32_t*, int32_t, const double*, double*);
+template void gs_colour_perm<double>(cudaStream_t, int32_t, int32_t, const int32_t*, const int32_t*, const int32_t*, const double*, const double*, double*);
+template void gs_colour_perm<float>(cudaStream_t, int32_t, int32_t, const int32_t*, const int32_t*, const int32_t*, const float*, const float*, float*);
+template void permute_rows<double>(Ctx&, int32_t, const int32_t*, const int32_t*, const int32_t*, const double*, DBuf<int32_t>&, DBuf<int32_t>&, DBuf<double>&);
+template void permute_rows<float>(Ctx&, int32_t, const int32_t*, const int32_t*, const int32_t*, const double*, DBuf<int32_t>&, DBuf<int32_t>&, DBuf<float>&);
 template void gs_colour<float>(cudaStream_t, const Csr&, const int32_t*, int32_t, const float*, float*);
 template void restrict_agg<double>(cudaStream_t, int32_t, const int32_t*, const int32_t*, const double*, const double*, double*);
 template void restrict_agg<float>(cudaStream_t, int32_t, const int32_t*, const int32_t*, const float*, const float*, float*);

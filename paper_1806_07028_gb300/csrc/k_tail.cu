@@ -1,0 +1,164 @@
+// Coarse tail of the multigrid cycle in one thread block.
+//
+// Below a few thousand unknowns a level's work is far smaller than the cost of
+// launching its kernels, and a W-cycle visits level l 2^l times. All levels
+// from `l0` down to the coarsest therefore run inside one 1024-thread block:
+// the same steps as the per-level kernels (colour-ordered Gauss-Seidel, the
+// residual, restriction by P^T, the gamma child visits, prolongation by P, the
+// backward sweep, and the dense coarsest solve), with __syncthreads() between
+// dependent steps. The recursion is an explicit state machine that every
+// thread follows identically. Vectors written inside the kernel are read with
+// ordinary (coherent) loads; only the read-only level data use __ldg.
+#include "pcamg_internal.cuh"
+
+namespace pc {
+
+namespace {
+
+constexpr int kTailThreads = 1024;
+constexpr int kTailWarps = kTailThreads / 32;
+
+template <class T>
+__device__ __forceinline__ T gsum(T v, int lpr) {
+    for (int o = lpr >> 1; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o, lpr);
+    return v;
+}
+
+template <class T>
+__device__ void tail_gs(const TailLevel<T>& L, int k) {
+    const int beg = __ldg(L.cptr + k), end = __ldg(L.cptr + k + 1);
+    const int lpr = L.lpr, rpw = 32 / lpr;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, sub = lane % lpr, grp = lane / lpr;
+    T* x = L.x;
+    const T* b = L.b;
+    for (int t0 = beg + warp * rpw; t0 < end; t0 += kTailWarps * rpw) {
+        int t = t0 + grp, row = -1;
+        T s = 0, d = 0;
+        if (t < end) {
+            row = __ldg(L.crows + t);
+            int e = __ldg(L.rowptr + row + 1);
+            for (int q = __ldg(L.rowptr + row) + sub; q < e; q += lpr) {
+                int j = __ldg(L.col + q);
+                T a = __ldg(L.val + q);
+                if (j == row) d = a;
+                else s += a * x[j];
+            }
+        }
+        s = gsum(s, lpr);
+        d = gsum(d, lpr);
+        if (sub == 0 && t < end) x[row] = (b[row] - s) / d;
+    }
+    __syncthreads();
+}
+
+template <class T>
+__device__ void tail_residual(const TailLevel<T>& L) {
+    const int lpr = L.lpr, rpw = 32 / lpr;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, sub = lane % lpr, grp = lane / lpr;
+    const T* x = L.x;
+    const T* b = L.b;
+    T* r = L.r;
+    for (int r0 = warp * rpw; r0 < L.n; r0 += kTailWarps * rpw) {
+        int row = r0 + grp;
+        T s = 0;
+        if (row < L.n) {
+            int e = __ldg(L.rowptr + row + 1);
+            for (int q = __ldg(L.rowptr + row) + sub; q < e; q += lpr) s += __ldg(L.val + q) * x[__ldg(L.col + q)];
+        }
+        s = gsum(s, lpr);
+        if (sub == 0 && row < L.n) r[row] = b[row] - s;
+    }
+    __syncthreads();
+}
+
+template <class T>
+__device__ void tail_restrict_zero(const TailLevel<T>& L, const TailLevel<T>& C) {
+    T* bc = C.b;
+    T* xc = C.x;
+    const T* r = L.r;
+    for (int I = threadIdx.x; I < L.nc; I += kTailThreads) {
+        T s = 0;
+        int e = __ldg(L.agg_ptr + I + 1);
+        for (int t = __ldg(L.agg_ptr + I); t < e; ++t) {
+            int u = __ldg(L.agg_mem + t);
+            s += L.pval ? __ldg(L.pval + u) * r[u] : r[u];
+        }
+        bc[I] = s;
+        xc[I] = 0;
+    }
+    __syncthreads();
+}
+
+template <class T>
+__device__ void tail_prolong(const TailLevel<T>& L, const TailLevel<T>& C) {
+    T* x = L.x;
+    const T* xc = C.x;
+    for (int u = threadIdx.x; u < L.n; u += kTailThreads) {
+        T c = xc[__ldg(L.agg + u)];
+        x[u] += L.pval ? __ldg(L.pval + u) * c : c;
+    }
+    __syncthreads();
+}
+
+template <class T>
+__device__ void tail_coarse(const TailLevel<T>& L, const double* __restrict__ X) {
+    const int m = L.n, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const T* b = L.b;
+    T* x = L.x;
+    for (int i = warp; i < m; i += kTailWarps) {
+        double s = 0.0;
+        for (int j = lane; j < m; j += 32) s += __ldg(X + (size_t)i * m + j) * (double)b[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) x[i] = (T)s;
+    }
+    __syncthreads();
+}
+
+template <class T>
+__global__ void __launch_bounds__(kTailThreads) k_tail(const TailLevel<T>* __restrict__ lv, int l0, int L,
+                                                       int gamma, int nu_pre, int nu_post,
+                                                       const double* __restrict__ Xinv) {
+    int cnt[kMaxLevels];
+    int l = l0;
+    bool down = true;
+    for (;;) {
+        if (down) {
+            if (l == L - 1) {
+                tail_coarse(lv[l], Xinv);
+                down = false;
+                if (--l < l0) break;
+                continue;
+            }
+            const TailLevel<T>& V = lv[l];
+            for (int s = 0; s < nu_pre; ++s)
+                for (int k = 0; k < V.ncolour; ++k) tail_gs(V, k);
+            tail_residual(V);
+            tail_restrict_zero(V, lv[l + 1]);
+            cnt[l] = gamma;
+            ++l;
+        } else {
+            if (--cnt[l] > 0) { ++l; down = true; continue; }
+            const TailLevel<T>& V = lv[l];
+            tail_prolong(V, lv[l + 1]);
+            for (int s = 0; s < nu_post; ++s)
+                for (int k = V.ncolour - 1; k >= 0; --k) tail_gs(V, k);
+            if (l == l0) break;
+            --l;
+        }
+    }
+}
+
+}  // namespace
+
+template <class T>
+void tail_cycle(cudaStream_t s, const TailLevel<T>* lv, int l0, int L, int gamma, int nu_pre,
+                int nu_post, const double* Xinv) {
+    k_tail<T><<<1, kTailThreads, 0, s>>>(lv, l0, L, gamma, nu_pre, nu_post, Xinv); ::pc::count_launches(1);
+    PC_LAUNCH("tail_cycle");
+}
+
+template void tail_cycle<double>(cudaStream_t, const TailLevel<double>*, int, int, int, int, int, const double*);
+template void tail_cycle<float>(cudaStream_t, const TailLevel<float>*, int, int, int, int, int, const double*);
+
+}  // namespace pc

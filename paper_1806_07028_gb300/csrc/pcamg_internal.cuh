@@ -108,7 +108,30 @@ struct Level {
     // cycle work vectors (sized n)
     DBuf<double> x64, b64, r64;
     DBuf<float> x32, b32, r32;
+    DBuf<int32_t> d_cptr;  // colour offsets on the device (levels run by the tail kernel)
+    // row-permuted copy (rows grouped by colour) for the streaming smoother
+    DBuf<int32_t> gs_ptr, gs_col;
+    DBuf<double> gs_val64;
+    DBuf<float> gs_val32;
+    const int32_t *gs_ptr_v = nullptr, *gs_col_v = nullptr;
+    const double* gs_val64_v = nullptr;
+    const float* gs_val32_v = nullptr;
 };
+
+// Level view used by the single-block coarse tail (k_tail.cu).
+template <class T>
+struct TailLevel {
+    int n, nc, ncolour, lpr;
+    const int *rowptr, *col;
+    const T* val;
+    const int *cptr, *crows;
+    const int *agg, *agg_ptr, *agg_mem;
+    const T* pval;
+    T *x, *b, *r;
+};
+template <class T>
+void tail_cycle(cudaStream_t s, const TailLevel<T>* lv, int l0, int L, int gamma, int nu_pre,
+                int nu_post, const double* Xinv);
 
 struct Hier {
     int32_t nlev = 0;
@@ -117,6 +140,8 @@ struct Hier {
     DBuf<double> Xinv;   // nL x nL pinned pseudo-inverse of the coarsest matrix
     int32_t npinned = 0;
     double oc = 0.0;
+    int32_t lt = -1;                 // first level run by the coarse tail kernel
+    DBuf<unsigned char> tail;        // TailLevel<T>[nlev] on the device
     // CUDA graphs of the correction cycle (index: gamma-1)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t graph_kernels[2] = {0, 0};
@@ -151,10 +176,14 @@ struct Ctx {
     int32_t ncolour0 = 0;
     DBuf<int32_t> colour0, colour_rows0;
     std::vector<int32_t> h_colour_ptr0;
+    DBuf<int32_t> gs_ptr0, gs_col0;   // row-permuted copy of A by colour
+    DBuf<double> gs_val0_64;
+    DBuf<float> gs_val0_32;
     std::vector<Hier*> hist;
     // driver work vectors (length n)
     DBuf<double> w_r, w_c, w_e, w_t1, w_t2, w_z, w_p, w_q, w_rold, w_eh, w_ein, w_cin;
     DBuf<double> red;     // reduction partials + scalar slots
+    int64_t npartials = 4096;
     double* h_red = nullptr;  // pinned host mirror of the scalar slots
     std::string last_error;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -195,6 +224,13 @@ void residual32(cudaStream_t s, const Csr& A, const float* x, const float* b, fl
 void spmv64(cudaStream_t s, const Csr& A, const double* x, double* y);  // y = A x
 template <class T>
 void gs_colour(cudaStream_t s, const Csr& A, const int32_t* rows, int32_t nrows, const T* b, T* x);
+template <class T>
+void gs_colour_perm(cudaStream_t s, int32_t beg, int32_t end, const int32_t* rows, const int32_t* pptr,
+                    const int32_t* pcol, const T* pval, const T* b, T* x);
+template <class T>
+void permute_rows(Ctx& c, int32_t n, const int32_t* rows, const int32_t* rowptr, const int32_t* col,
+                  const double* val, DBuf<int32_t>& pptr, DBuf<int32_t>& pcol, DBuf<T>& pval);
+int residual_partials(int32_t n);
 template <class T>
 void restrict_agg(cudaStream_t s, int32_t nc, const int32_t* agg_ptr, const int32_t* agg_mem,
                   const T* pval, const T* r, T* bc);

@@ -221,3 +221,22 @@ def test_invalid_inputs_return_status(P):
     s2 = P.Solver(g2, params=P.default_params(max_iter=1, threshold=10.0))
     x, st = s2.solve(I.rhs_normal(g2.n, 0))
     assert st["status"] == "NOT_CONVERGED" and st["iters"] == 1
+
+
+@pytest.mark.parametrize("name", ["C1", "C2-small", "C4-small"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_coarse_tail_block_matches_per_level_kernels(P, name, precision):
+    # the single-block coarse tail runs the same steps as the per-level kernels:
+    # no tail, a partial tail and an all-levels tail give the same correction
+    g = GRAPHS[name]
+    e = O.start_vector(g)
+    h = O.Hierarchy(g, e)
+    r = I.rhs_normal(g.n, 8)
+    tol = 1e-9 if precision == 0 else 2e-4
+    for gamma in (1, 2):
+        ref = h.vcycle(r) if gamma == 1 else h.wcycle(r)
+        for tail in (0, 2000, 10**9):
+            s = P.Solver(g, params=P.default_params(precision=precision, tail_rows=tail), e0=e)
+            c = s.cycle(r, hist=0, gamma=gamma).cpu().numpy()
+            assert np.linalg.norm(c - ref) <= tol * np.linalg.norm(ref), (tail, gamma)
+            s.close()
