@@ -87,6 +87,9 @@ typedef struct {
     int32_t profile;       /* time the fine-level residual kernel with CUDA events */
     int32_t tail_rows;     /* levels with at most this many unknowns run inside one
                               thread block per cycle visit (0 = never) */
+    int32_t l1jac_rows;    /* coarse levels (not the finest) with at most this many
+                              unknowns are smoothed by l1-Jacobi, x += (b - A x)/d with
+                              d_i = sum_j |a_ij|, instead of multicolour Gauss-Seidel */
 } pcamg_params;
 
 typedef struct {

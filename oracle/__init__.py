@@ -54,7 +54,7 @@ class Params(C.Structure):
                 ("nu_pre", C.c_int32), ("nu_post", C.c_int32), ("relax_sweeps", C.c_int32),
                 ("seed", C.c_uint64), ("n_min", C.c_int32), ("max_levels", C.c_int32),
                 ("round_cap", C.c_int32), ("p1_mode", C.c_int32), ("leftover_mode", C.c_int32),
-                ("cover_mode", C.c_int32), ("dense_max", C.c_int32)]
+                ("cover_mode", C.c_int32), ("dense_max", C.c_int32), ("l1jac_rows", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -86,6 +86,7 @@ def lib():
             L.orc_colour.restype = C.c_int32
             L.orc_mcgs_sweep.argtypes = [C.c_int32, _i32p, _i32p, _f64p, _i32p, C.c_int32,
                                          _f64p, _f64p, C.c_int32]
+            L.orc_l1jac_sweep.argtypes = [C.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p]
             L.orc_gs_perm_sweep.argtypes = [C.c_int32, _i32p, _i32p, _f64p, _i32p, _f64p, _f64p]
             L.orc_candidates.argtypes = [C.c_int32, _i32p, _i32p, _f64p, C.POINTER(_PI),
                                          C.POINTER(_PI), C.POINTER(_PD)]
@@ -200,6 +201,13 @@ def mcgs_sweep(g, colours, ncolour, b, x, forward=True):
     rp, ci, v = _csr(g)
     x = _f64(x).copy()
     lib().orc_mcgs_sweep(g.n, rp, ci, v, _i32(colours), ncolour, _f64(b), x, 1 if forward else 0)
+    return x
+
+
+def l1jac_sweep(g, b, x):
+    rp, ci, v = _csr(g)
+    x = _f64(x).copy()
+    lib().orc_l1jac_sweep(g.n, rp, ci, v, _f64(b), x)
     return x
 
 

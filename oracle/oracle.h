@@ -53,6 +53,8 @@ typedef struct {
     int32_t leftover_mode;/* ORC_LEFT_* */
     int32_t cover_mode;   /* ORC_COVER_* */
     int32_t dense_max;    /* largest coarsest level solved densely */
+    int32_t l1jac_rows;   /* levels >= 1 with at most this many unknowns are smoothed
+                             by l1-Jacobi instead of multicolour Gauss-Seidel */
 } orc_params;
 
 typedef struct {
@@ -89,6 +91,9 @@ int32_t orc_colour(int32_t n, const int32_t* rowptr, const int32_t* col, uint64_
 void orc_mcgs_sweep(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
                     const int32_t* colour, int32_t ncolour, const double* b, double* x,
                     int32_t forward);
+/* One l1-Jacobi sweep: x += (b - A x) / d, d_i = sum_j |a_ij| (row order). */
+void orc_l1jac_sweep(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                     const double* b, double* x);
 /* One Gauss-Seidel sweep visiting rows in the order perm[0..n-1]. */
 void orc_gs_perm_sweep(int32_t n, const int32_t* rowptr, const int32_t* col,
                        const double* val, const int32_t* perm, const double* b, double* x);

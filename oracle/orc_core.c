@@ -35,6 +35,7 @@ void orc_default_params(orc_params* p) {
     p->leftover_mode = ORC_LEFT_ROUNDS;
     p->cover_mode = ORC_COVER_LD;
     p->dense_max = 4096;
+    p->l1jac_rows = 16384;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -159,6 +160,18 @@ void orc_mcgs_sweep(int32_t n, const int32_t* rowptr, const int32_t* col, const 
         for (int32_t i = 0; i < n; ++i)
             if (colour[i] == c) gs_row(rowptr, col, val, b, x, i);
     }
+}
+
+void orc_l1jac_sweep(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                     const double* b, double* x) {
+    double* r = (double*)orc_xmalloc(sizeof(double) * (size_t)n);
+    orc_residual(n, rowptr, col, val, x, b, r);
+    for (int32_t i = 0; i < n; ++i) {
+        double d = 0.0;
+        for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) d += fabs(val[k]);
+        x[i] += r[i] / d;
+    }
+    free(r);
 }
 
 void orc_gs_perm_sweep(int32_t n, const int32_t* rowptr, const int32_t* col,

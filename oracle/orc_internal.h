@@ -13,6 +13,7 @@ typedef struct {
     double* val;
     int32_t ncolour;
     int32_t* colour;
+    int32_t jac;             /* smoothed by l1-Jacobi (no colouring) */
     /* reweighted graph of this level (level 0: candidates on the A^2 pattern) */
     int32_t *tptr, *tcol;
     double* tw;

@@ -526,9 +526,12 @@ orc_hier* orc_build(int32_t n, const int32_t* rowptr, const int32_t* col, const 
         C->nbr0 = cn0; C->nbr1 = cn1;
         h->nlev = l + 2;
     }
-    /* smoother colouring on every level but the coarsest */
+    /* smoother colouring on every level but the coarsest; small coarse levels
+     * are smoothed by l1-Jacobi and need none */
     for (int32_t l = 0; l + 1 < h->nlev; ++l) {
         orc_level* L = &h->lev[l];
+        L->jac = (l >= 1 && L->n <= p->l1jac_rows);
+        if (L->jac) continue;
         L->colour = (int32_t*)orc_xmalloc(sizeof(int32_t) * (size_t)L->n);
         if (!L->colour) { st = ORC_ERR_OOM; goto fail; }
         L->ncolour = orc_colour(L->n, L->rowptr, L->col, p->seed, L->colour, NULL);

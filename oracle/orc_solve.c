@@ -44,8 +44,10 @@ void orc_coarse_solve(const orc_hier* h, const double* r, double* x) {
 static void cycle(const orc_hier* h, int32_t l, const double* b, double* x, int32_t gamma) {
     if (l == h->nlev - 1) { orc_coarse_solve(h, b, x); return; }
     const orc_level* L = &h->lev[l];
-    for (int32_t s = 0; s < h->nu_pre; ++s)
-        orc_mcgs_sweep(L->n, L->rowptr, L->col, L->val, L->colour, L->ncolour, b, x, 1);
+    for (int32_t s = 0; s < h->nu_pre; ++s) {
+        if (L->jac) orc_l1jac_sweep(L->n, L->rowptr, L->col, L->val, b, x);
+        else orc_mcgs_sweep(L->n, L->rowptr, L->col, L->val, L->colour, L->ncolour, b, x, 1);
+    }
     double* r = (double*)orc_xmalloc(sizeof(double) * (size_t)L->n);
     double* bc = (double*)orc_xmalloc(sizeof(double) * (size_t)L->nc);
     double* xc = (double*)calloc((size_t)L->nc, sizeof(double));
@@ -61,8 +63,10 @@ static void cycle(const orc_hier* h, int32_t l, const double* b, double* x, int3
     for (int32_t g = 0; g < gamma; ++g) cycle(h, l + 1, bc, xc, gamma);
     for (int32_t u = 0; u < L->n; ++u)
         x[u] += L->pval ? L->pval[u] * xc[L->agg[u]] : xc[L->agg[u]];
-    for (int32_t s = 0; s < h->nu_post; ++s)
-        orc_mcgs_sweep(L->n, L->rowptr, L->col, L->val, L->colour, L->ncolour, b, x, 0);
+    for (int32_t s = 0; s < h->nu_post; ++s) {
+        if (L->jac) orc_l1jac_sweep(L->n, L->rowptr, L->col, L->val, b, x);
+        else orc_mcgs_sweep(L->n, L->rowptr, L->col, L->val, L->colour, L->ncolour, b, x, 0);
+    }
     free(r); free(bc); free(xc);
 }
 

@@ -124,6 +124,15 @@ struct LV<float> {
 
 template <class T>
 static void smooth(Ctx& c, Level& L, const T* b, T* x, bool forward) {
+    if (L.jac) {   // l1-Jacobi: x += (b - A x) / d
+        T* r;
+        const T* d;
+        if constexpr (sizeof(T) == 8) { r = L.r64.p; d = L.dl1_64.p; } else { r = L.r32.p; d = L.dl1_32.p; }
+        if constexpr (sizeof(T) == 8) residual64(c.stream, L.A, x, b, r, nullptr, nullptr);
+        else residual32(c.stream, L.A, x, b, r);
+        jacobi_update<T>(c.stream, L.n, r, d, x);
+        return;
+    }
     const T* pv;
     if constexpr (sizeof(T) == 8) pv = L.gs_val64_v; else pv = L.gs_val32_v;
     for (int32_t t = 0; t < L.ncolour; ++t) {

@@ -47,15 +47,19 @@ static void setup_tail(Ctx& c, Hier& h) {
         t.n = L.n;
         t.nc = (l + 1 < h.nlev) ? L.nc : 0;
         t.ncolour = (l + 1 < h.nlev) ? L.ncolour : 0;
+        t.jac = L.jac;
+        if constexpr (sizeof(T) == 8) t.dl1 = L.dl1_64.p; else t.dl1 = L.dl1_32.p;
         t.lpr = L.A.lpr;
         t.rowptr = L.A.rowptr;
         t.col = L.A.col;
         if constexpr (sizeof(T) == 8) t.val = L.A.val; else t.val = L.A.val32;
         if (l + 1 < h.nlev) {
-            L.d_cptr.alloc(c.mem, L.h_colour_ptr.size());
-            PC_CUDA(cudaMemcpyAsync(L.d_cptr.p, L.h_colour_ptr.data(), sizeof(int32_t) * L.h_colour_ptr.size(),
-                                    cudaMemcpyHostToDevice, c.stream));
-            t.cptr = L.d_cptr.p;
+            if (!L.jac) {
+                L.d_cptr.alloc(c.mem, L.h_colour_ptr.size());
+                PC_CUDA(cudaMemcpyAsync(L.d_cptr.p, L.h_colour_ptr.data(), sizeof(int32_t) * L.h_colour_ptr.size(),
+                                        cudaMemcpyHostToDevice, c.stream));
+                t.cptr = L.d_cptr.p;
+            }
             t.crows = L.colour_rows_v;
             t.agg = L.agg.p;
             t.agg_ptr = L.agg_ptr.p;
@@ -156,9 +160,21 @@ Hier* build_hierarchy(Ctx& c, const double* e) {
         Lc.tw = std::move(t.w);
         Lc.tnnz = t.nnz;
     }
-    // smoother colouring of every level but the coarsest (level 0 is shared)
+    // smoother of every level but the coarsest: small coarse levels use
+    // l1-Jacobi (diagonal of row l1 norms), the others multicolour Gauss-Seidel
+    // (level 0's colouring is shared)
     for (int32_t l = 1; l + 1 < nlev; ++l) {
         Level& L = h->lev[l];
+        if (L.n <= p.l1jac_rows) {
+            L.jac = 1;
+            L.dl1_64.alloc(c.mem, L.n);
+            l1_diagonal(c.stream, L.n, L.A.rowptr, L.A.val, L.dl1_64.p);
+            if (f32) {
+                L.dl1_32.alloc(c.mem, L.n);
+                cast_f32(c.stream, L.n, L.dl1_64.p, L.dl1_32.p);
+            }
+            continue;
+        }
         L.colour.alloc(c.mem, L.n);
         L.ncolour = colour_graph(c, L.n, L.A.rowptr, L.A.col, p.seed, L.colour.p);
         colour_lists(c, L.n, L.colour.p, L.ncolour, L.colour_rows, L.h_colour_ptr);
@@ -195,6 +211,7 @@ Hier* build_hierarchy(Ctx& c, const double* e) {
     // row-permuted copies for the streaming smoother on levels above the tail
     for (int32_t l = 1; l < h->lt && l + 1 < nlev; ++l) {
         Level& L = h->lev[l];
+        if (L.jac) continue;
         if (f32) {
             permute_rows<float>(c, L.n, L.colour_rows_v, L.A.rowptr, L.A.col, L.A.val, L.gs_ptr, L.gs_col, L.gs_val32);
             L.gs_val32_v = L.gs_val32.p;

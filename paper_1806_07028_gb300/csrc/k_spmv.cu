@@ -278,6 +278,22 @@ __global__ void __launch_bounds__(kStreamRows) k_gs_stream(int beg, int end, con
     if (t < end) x[row] = (__ldg(b + row) - s) / d;
 }
 
+template <class T>
+__global__ void k_jacobi_update(int n, const T* __restrict__ r, const T* __restrict__ d, T* __restrict__ x) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        x[i] += r[i] / d[i];
+}
+
+// d_i = sum_j |a_ij|, left to right in CSR order
+__global__ void k_l1_diagonal(int n, const int* __restrict__ rowptr, const double* __restrict__ val,
+                              double* __restrict__ d) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) s += fabs(val[k]);
+        d[i] = s;
+    }
+}
+
 // Row-permuted copy: row t of the copy is row rows[t] of A.
 __global__ void k_perm_counts(int n, const int* __restrict__ rows, const int* __restrict__ rowptr,
                               int* __restrict__ cnt) {
@@ -331,6 +347,19 @@ void residual64(cudaStream_t s, const Csr& A, const double* x, const double* b, 
 }
 
 int residual_partials(int32_t n) { return (n + kStreamRows - 1) / kStreamRows; }
+
+template <class T>
+void jacobi_update(cudaStream_t s, int32_t n, const T* r, const T* d, T* x) {
+    k_jacobi_update<T><<<simple_grid(n), kBlock, 0, s>>>(n, r, d, x); ::pc::count_launches(1);
+    PC_LAUNCH("jacobi_update");
+}
+template void jacobi_update<double>(cudaStream_t, int32_t, const double*, const double*, double*);
+template void jacobi_update<float>(cudaStream_t, int32_t, const float*, const float*, float*);
+
+void l1_diagonal(cudaStream_t s, int32_t n, const int32_t* rowptr, const double* val, double* d) {
+    k_l1_diagonal<<<simple_grid(n), kBlock, 0, s>>>(n, rowptr, val, d); ::pc::count_launches(1);
+    PC_LAUNCH("l1_diagonal");
+}
 
 void residual32(cudaStream_t s, const Csr& A, const float* x, const float* b, float* r) {
     int g = (A.n + kStreamRows - 1) / kStreamRows;

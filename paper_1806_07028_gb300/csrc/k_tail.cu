@@ -8,7 +8,9 @@
 // backward sweep, and the dense coarsest solve), with __syncthreads() between
 // dependent steps. The recursion is an explicit state machine that every
 // thread follows identically. Vectors written inside the kernel are read with
-// ordinary (coherent) loads; only the read-only level data use __ldg.
+// ordinary (coherent) loads; only the read-only level data use __ldg. Small
+// coarse levels are smoothed by l1-Jacobi (two block-wide phases per sweep),
+// others by colour-ordered Gauss-Seidel (one phase per colour).
 #include "pcamg_internal.cuh"
 
 namespace pc {
@@ -51,23 +53,44 @@ __device__ void tail_gs(const TailLevel<T>& L, int k) {
     __syncthreads();
 }
 
+// r = b - A x, rows in tiles of one per thread; the tile's products a x are
+// staged in shared memory in chunks (many independent loads in flight), then
+// each thread adds its row's products in CSR order.
+constexpr int kTailChunk = 4096;
+
 template <class T>
-__device__ void tail_residual(const TailLevel<T>& L) {
-    const int lpr = L.lpr, rpw = 32 / lpr;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, sub = lane % lpr, grp = lane / lpr;
+__device__ void tail_residual(const TailLevel<T>& L, T* prod) {
     const T* x = L.x;
     const T* b = L.b;
     T* r = L.r;
-    for (int r0 = warp * rpw; r0 < L.n; r0 += kTailWarps * rpw) {
-        int row = r0 + grp;
+    for (int r0 = 0; r0 < L.n; r0 += kTailThreads) {
+        const int row = r0 + threadIdx.x;
+        const int rlast = min(r0 + kTailThreads, L.n);
+        const int tb = __ldg(L.rowptr + r0), te = __ldg(L.rowptr + rlast);
+        int rb = 0, re = 0;
+        if (row < L.n) { rb = __ldg(L.rowptr + row); re = __ldg(L.rowptr + row + 1); }
         T s = 0;
-        if (row < L.n) {
-            int e = __ldg(L.rowptr + row + 1);
-            for (int q = __ldg(L.rowptr + row) + sub; q < e; q += lpr) s += __ldg(L.val + q) * x[__ldg(L.col + q)];
+        for (int c0 = tb; c0 < te; c0 += kTailChunk) {
+            const int c1 = min(c0 + kTailChunk, te);
+            for (int k = c0 + threadIdx.x; k < c1; k += kTailThreads)
+                prod[k - c0] = __ldg(L.val + k) * x[__ldg(L.col + k)];
+            __syncthreads();
+            const int kb = max(rb, c0), ke = min(re, c1);
+            for (int k = kb; k < ke; ++k) s += prod[k - c0];
+            __syncthreads();
         }
-        s = gsum(s, lpr);
-        if (sub == 0 && row < L.n) r[row] = b[row] - s;
+        if (row < L.n) r[row] = b[row] - s;
     }
+    __syncthreads();
+}
+
+// l1-Jacobi sweep: x += (b - A x) / d
+template <class T>
+__device__ void tail_jacobi(const TailLevel<T>& L, T* prod) {
+    tail_residual(L, prod);
+    T* x = L.x;
+    const T* r = L.r;
+    for (int i = threadIdx.x; i < L.n; i += kTailThreads) x[i] += r[i] / __ldg(L.dl1 + i);
     __syncthreads();
 }
 
@@ -119,6 +142,8 @@ template <class T>
 __global__ void __launch_bounds__(kTailThreads) k_tail(const TailLevel<T>* __restrict__ lv, int l0, int L,
                                                        int gamma, int nu_pre, int nu_post,
                                                        const double* __restrict__ Xinv) {
+    __shared__ __align__(16) unsigned char smem[kTailChunk * sizeof(T)];
+    T* prod = reinterpret_cast<T*>(smem);
     int cnt[kMaxLevels];
     int l = l0;
     bool down = true;
@@ -131,9 +156,11 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const TailLevel<T>* __res
                 continue;
             }
             const TailLevel<T>& V = lv[l];
-            for (int s = 0; s < nu_pre; ++s)
-                for (int k = 0; k < V.ncolour; ++k) tail_gs(V, k);
-            tail_residual(V);
+            for (int s = 0; s < nu_pre; ++s) {
+                if (V.jac) tail_jacobi(V, prod);
+                else for (int k = 0; k < V.ncolour; ++k) tail_gs(V, k);
+            }
+            tail_residual(V, prod);
             tail_restrict_zero(V, lv[l + 1]);
             cnt[l] = gamma;
             ++l;
@@ -141,8 +168,10 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const TailLevel<T>* __res
             if (--cnt[l] > 0) { ++l; down = true; continue; }
             const TailLevel<T>& V = lv[l];
             tail_prolong(V, lv[l + 1]);
-            for (int s = 0; s < nu_post; ++s)
-                for (int k = V.ncolour - 1; k >= 0; --k) tail_gs(V, k);
+            for (int s = 0; s < nu_post; ++s) {
+                if (V.jac) tail_jacobi(V, prod);
+                else for (int k = V.ncolour - 1; k >= 0; --k) tail_gs(V, k);
+            }
             if (l == l0) break;
             --l;
         }

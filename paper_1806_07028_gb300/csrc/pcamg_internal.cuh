@@ -116,12 +116,17 @@ struct Level {
     const int32_t *gs_ptr_v = nullptr, *gs_col_v = nullptr;
     const double* gs_val64_v = nullptr;
     const float* gs_val32_v = nullptr;
+    // l1-Jacobi smoothing (small coarse levels): d_i = sum_j |a_ij|
+    int32_t jac = 0;
+    DBuf<double> dl1_64;
+    DBuf<float> dl1_32;
 };
 
 // Level view used by the single-block coarse tail (k_tail.cu).
 template <class T>
 struct TailLevel {
-    int n, nc, ncolour, lpr;
+    int n, nc, ncolour, lpr, jac;
+    const T* dl1;
     const int *rowptr, *col;
     const T* val;
     const int *cptr, *crows;
@@ -231,6 +236,9 @@ template <class T>
 void permute_rows(Ctx& c, int32_t n, const int32_t* rows, const int32_t* rowptr, const int32_t* col,
                   const double* val, DBuf<int32_t>& pptr, DBuf<int32_t>& pcol, DBuf<T>& pval);
 int residual_partials(int32_t n);
+template <class T>
+void jacobi_update(cudaStream_t s, int32_t n, const T* r, const T* d, T* x);   // x += r / d
+void l1_diagonal(cudaStream_t s, int32_t n, const int32_t* rowptr, const double* val, double* d);
 template <class T>
 void restrict_agg(cudaStream_t s, int32_t nc, const int32_t* agg_ptr, const int32_t* agg_mem,
                   const T* pval, const T* r, T* bc);

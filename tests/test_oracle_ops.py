@@ -85,3 +85,21 @@ def test_mcgs_equals_triangular_solve_in_colour_order(mk, forward):
     assert np.allclose(x, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
     # and it is the same as a plain GS sweep in that order
     assert np.allclose(O.gs_perm_sweep(g, perm, b, x0), x, rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("mk", GRAPHS)
+def test_l1_jacobi_sweep(mk):
+    # x_new = x + D^{-1} (b - A x) with D the diagonal of row l1 norms; the
+    # l1 smoother never increases the energy norm of the error for SPD A
+    # (2D - A is positive definite)
+    g = mk()
+    A = g.to_scipy()
+    rng = np.random.default_rng(2)
+    xs = rng.standard_normal(g.n); xs -= xs.mean()
+    b = A @ xs
+    x0 = rng.standard_normal(g.n)
+    x1 = O.l1jac_sweep(g, b, x0)
+    d = np.asarray(abs(A).sum(axis=1)).ravel()
+    assert np.allclose(x1, x0 + (b - A @ x0) / d, rtol=1e-13, atol=1e-13 * np.abs(x1).max())
+    e0, e1 = xs - x0, xs - x1
+    assert e1 @ (A @ e1) < e0 @ (A @ e0)
