@@ -42,7 +42,7 @@ def _args():
     ap.add_argument("--workload", default="C2")
     ap.add_argument("--form", default="fp32ir", choices=["fp32ir", "fp64"])
     ap.add_argument("--no-extras", action="store_true", help="skip fp64 form, e2e and oracle legs")
-    ap.add_argument("--only-kernel", default=None, choices=["residual64"],
+    ap.add_argument("--only-kernel", default=None, choices=["residual64", "vcycle", "wcycle"],
                     help="time one kernel alone on the workload (used for ncu captures)")
     ap.add_argument("--reps", type=int, default=20)
     return ap.parse_args()
@@ -353,9 +353,31 @@ def run_reference(a):
 
 
 def run_kernel(a):
-    """One kernel alone on the workload's fine matrix, timed with CUDA events."""
+    """One kernel (or one multigrid cycle) alone on the workload, timed with
+    CUDA events on the launching stream."""
     import numpy as np
     import torch
+
+    if a.only_kernel in ("vcycle", "wcycle"):
+        from paper_1806_07028_gb300 import Solver, default_params, inputs as I
+        g = I.workload(a.workload)
+        prec = 1 if a.form == "fp32ir" else 0
+        dev = torch.device("cuda", 0)
+        s = Solver(_device_graph(g, dev), params=default_params(precision=prec), device=dev)
+        r = torch.as_tensor(I.rhs_normal(g.n, 3), device=dev)
+        gamma = 1 if a.only_kernel == "vcycle" else 2
+        for _ in range(2):
+            s.cycle(r, 0, gamma)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(a.reps):
+            s.cycle(r, 0, gamma)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3 / a.reps
+        print(json.dumps({"cycle": a.only_kernel, "workload": a.workload, "form": a.form, "ms": ms,
+                          "levels": s.num_levels(0)}), flush=True)
+        s.close()
+        return
 
     from paper_1806_07028_gb300 import inputs as I, residual
     g = I.workload(a.workload)

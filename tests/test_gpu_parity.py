@@ -102,7 +102,7 @@ def _compare_hierarchy(P, g, e, mode, precision=0):
             assert np.array_equal(G["agg"], R["agg"]), lev
         if R["pval"] is not None:
             assert np.array_equal(G["pval"].view(np.uint64), R["pval"].view(np.uint64))
-        if lev + 1 < h.nlevels:
+        if lev + 1 < h.nlevels and R["ncolour"] > 0:
             assert np.array_equal(G["colour"], R["colour"]), lev
     assert s.sizes(0, 0)["pinned"] == h.sizes(0)["pinned"]
     return s, h
