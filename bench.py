@@ -42,7 +42,7 @@ def _args():
     ap.add_argument("--workload", default="C2")
     ap.add_argument("--form", default="fp32ir", choices=["fp32ir", "fp64"])
     ap.add_argument("--no-extras", action="store_true", help="skip fp64 form, e2e and oracle legs")
-    ap.add_argument("--only-kernel", default=None, choices=["residual64", "vcycle", "wcycle"],
+    ap.add_argument("--only-kernel", default=None, choices=["residual64", "vcycle", "wcycle", "adapt"],
                     help="time one kernel alone on the workload (used for ncu captures)")
     ap.add_argument("--reps", type=int, default=20)
     return ap.parse_args()
@@ -358,6 +358,24 @@ def run_kernel(a):
     import numpy as np
     import torch
 
+    if a.only_kernel == "adapt":
+        from paper_1806_07028_gb300 import Solver, default_params, inputs as I
+        g = I.workload(a.workload)
+        prec = 1 if a.form == "fp32ir" else 0
+        dev = torch.device("cuda", 0)
+        s = Solver(_device_graph(g, dev), params=default_params(precision=prec), device=dev)
+        e = s.start_vector()
+        s.adapt(e)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(a.reps):
+            s.adapt(e)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3 / a.reps
+        print(json.dumps({"adapt": a.workload, "form": a.form, "ms": ms, "levels": s.num_levels(-1)}),
+              flush=True)
+        s.close()
+        return
     if a.only_kernel in ("vcycle", "wcycle"):
         from paper_1806_07028_gb300 import Solver, default_params, inputs as I
         g = I.workload(a.workload)

@@ -193,7 +193,7 @@ PCAMG_API pcamg_status pcamg_default_params(pcamg_params* p) {
     p->use_graphs = 1;
     p->keep_setup = 0;
     p->profile = 0;
-    p->tail_rows = 4096;
+    p->tail_rows = 2048;
     p->l1jac_rows = 16384;
     return PCAMG_OK;
 }
@@ -236,13 +236,16 @@ PCAMG_API pcamg_status pcamg_setup(pcamg_handle* out, const pcamg_params* p, int
         c->ncolour0 = colour_graph(*c, n, c->rowptr.p, c->col.p, c->p.seed, c->colour0.p);
         colour_lists(*c, n, c->colour0.p, c->ncolour0, c->colour_rows0, c->h_colour_ptr0);
         // rows grouped by colour, for the streaming smoother (FP64 for the start
-        // vector and the FP64 cycle; FP32 for the FP32 cycle)
-        permute_rows<double>(*c, n, c->colour_rows0.p, c->rowptr.p, c->col.p, c->val.p, c->gs_ptr0,
-                             c->gs_col0, c->gs_val0_64);
-        if (c->p.precision == PCAMG_FP32_IR) {
-            DBuf<int32_t> p2, c2;
-            permute_rows<float>(*c, n, c->colour_rows0.p, c->rowptr.p, c->col.p, c->val.p, p2, c2,
-                                c->gs_val0_32);
+        // vector and the FP64 cycle; FP32 for the FP32 cycle), when its launches
+        // are large enough to pay off
+        if (use_stream(n / std::max(1, c->ncolour0), lanes_per_row(n, nnz))) {
+            permute_rows<double>(*c, n, c->colour_rows0.p, c->rowptr.p, c->col.p, c->val.p, c->gs_ptr0,
+                                 c->gs_col0, c->gs_val0_64);
+            if (c->p.precision == PCAMG_FP32_IR) {
+                DBuf<int32_t> p2, c2;
+                permute_rows<float>(*c, n, c->colour_rows0.p, c->rowptr.p, c->col.p, c->val.p, p2, c2,
+                                    c->gs_val0_32);
+            }
         }
         if (c->p.start == PCAMG_START_USER) {
             check_finite(*c, d_e0, n, "start vector");

@@ -211,7 +211,7 @@ Hier* build_hierarchy(Ctx& c, const double* e) {
     // row-permuted copies for the streaming smoother on levels above the tail
     for (int32_t l = 1; l < h->lt && l + 1 < nlev; ++l) {
         Level& L = h->lev[l];
-        if (L.jac) continue;
+        if (L.jac || L.ncolour < 1 || !use_stream(L.n / L.ncolour, L.A.lpr)) continue;
         if (f32) {
             permute_rows<float>(c, L.n, L.colour_rows_v, L.A.rowptr, L.A.col, L.A.val, L.gs_ptr, L.gs_col, L.gs_val32);
             L.gs_val32_v = L.gs_val32.p;

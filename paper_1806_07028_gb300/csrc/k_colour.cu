@@ -72,13 +72,28 @@ __global__ void k_colour_round(int n, const int* __restrict__ rowptr, const int*
     }
 }
 
-__global__ void k_colour_flags(int n, const int* __restrict__ colour, int c, int* __restrict__ flag) {
-    FOR_EACH(v, n) flag[v] = (colour[v] == c) ? 1 : 0;
+__global__ void k_colour_count(int n, const int* __restrict__ colour, int* __restrict__ cnt) {
+    FOR_EACH(v, n) atomicAdd(cnt + colour[v], 1);
 }
 
-__global__ void k_colour_place(int n, const int* __restrict__ colour, int c,
-                               const int* __restrict__ pos, int base, int* __restrict__ rows) {
-    FOR_EACH(v, n) if (colour[v] == c) rows[base + pos[v]] = (int)v;
+// Rows of each colour into its segment. Within a warp, lanes of equal colour
+// take consecutive slots with one atomic per colour, so segments fill in
+// nearly ascending row order (the order inside a colour does not change the
+// sweep: rows of one colour are independent).
+__global__ void k_colour_place(int n, const int* __restrict__ colour, const int* __restrict__ base,
+                               int* __restrict__ cursor, int* __restrict__ rows) {
+    for (int64_t v0 = blockIdx.x * (int64_t)blockDim.x; v0 < n; v0 += (int64_t)gridDim.x * blockDim.x) {
+        int64_t v = v0 + threadIdx.x;
+        int c = (v < n) ? colour[v] : -1;
+        unsigned peers = __match_any_sync(0xffffffffu, c);
+        int lane = threadIdx.x & 31;
+        int leader = __ffs(peers) - 1;
+        int rank = __popc(peers & ((1u << lane) - 1u));
+        int off = 0;
+        if (lane == leader && c >= 0) off = atomicAdd(cursor + c, __popc(peers));
+        off = __shfl_sync(0xffffffffu, off, leader);
+        if (c >= 0) rows[base[c] + off + rank] = (int)v;
+    }
 }
 
 }  // namespace
@@ -94,38 +109,49 @@ int32_t colour_graph(Ctx& c, int32_t n, const int32_t* rowptr, const int32_t* co
     PC_CUDA(cudaMemsetAsync(maxc.p, 0, sizeof(int32_t), s));
     int32_t* a = colour;
     int32_t* b = tmp.p;
-    for (int round = 0;; ++round) {
-        PC_CUDA(cudaMemsetAsync(left.p, 0, sizeof(int32_t), s));
-        k_colour_round<<<gridc(n), kBlock, 0, s>>>(n, rowptr, col, seed, a, b, left.p, maxc.p); ::pc::count_launches(1);
+    // rounds in batches; a round after the last one changes nothing
+    const int kBatch = 4;
+    DBuf<int32_t> lefts;
+    lefts.alloc(c.mem, kBatch);
+    int32_t hl[kBatch];
+    for (int round = 0;;) {
+        PC_CUDA(cudaMemsetAsync(lefts.p, 0, sizeof(int32_t) * kBatch, s));
+        for (int k = 0; k < kBatch; ++k) {
+            k_colour_round<<<gridc(n), kBlock, 0, s>>>(n, rowptr, col, seed, a, b, lefts.p + k, maxc.p); ::pc::count_launches(1);
+            int32_t* t = a; a = b; b = t;
+        }
         PC_LAUNCH("colour_round");
-        int32_t* t = a; a = b; b = t;
-        if (read_i32(c, left.p) == 0) break;
-        if (round > n) fail(PCAMG_ERR_ROUND_CAP, "colouring rounds exceeded n");
+        d2h(c, hl, lefts.p, kBatch);
+        round += kBatch;
+        if (hl[kBatch - 1] == 0) break;
+        if (round > n + kBatch) fail(PCAMG_ERR_ROUND_CAP, "colouring rounds exceeded n");
     }
+    (void)left;
     if (a != colour) PC_CUDA(cudaMemcpyAsync(colour, a, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
     int32_t nc = read_i32(c, maxc.p) + 1;
     return nc;
 }
 
-// Rows grouped by colour, ascending inside each colour.
+// Rows grouped by colour (segments in colour order).
 void colour_lists(Ctx& c, int32_t n, const int32_t* colour, int32_t ncolour,
                   DBuf<int32_t>& rows, std::vector<int32_t>& h_ptr) {
     cudaStream_t s = c.stream;
     rows.alloc(c.mem, n);
-    DBuf<int32_t> flag, pos;
-    flag.alloc(c.mem, n);
-    pos.alloc(c.mem, (size_t)n + 1);
+    DBuf<int32_t> cnt, base, cursor;
+    cnt.alloc(c.mem, ncolour);
+    base.alloc(c.mem, ncolour);
+    cursor.alloc(c.mem, ncolour);
+    PC_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * ncolour, s));
+    PC_CUDA(cudaMemsetAsync(cursor.p, 0, sizeof(int32_t) * ncolour, s));
+    k_colour_count<<<gridc(n), kBlock, 0, s>>>(n, colour, cnt.p); ::pc::count_launches(1);
+    PC_LAUNCH("colour_count");
+    std::vector<int32_t> hc(ncolour);
+    d2h(c, hc.data(), cnt.p, ncolour);
     h_ptr.assign((size_t)ncolour + 1, 0);
-    int64_t base = 0;
-    for (int32_t k = 0; k < ncolour; ++k) {
-        k_colour_flags<<<gridc(n), kBlock, 0, s>>>(n, colour, k, flag.p); ::pc::count_launches(1);
-        int64_t cnt = scan_i32(c, flag.p, pos.p, n);
-        k_colour_place<<<gridc(n), kBlock, 0, s>>>(n, colour, k, pos.p, (int)base, rows.p); ::pc::count_launches(1);
-        PC_LAUNCH("colour_lists");
-        h_ptr[k] = (int32_t)base;
-        base += cnt;
-    }
-    h_ptr[ncolour] = (int32_t)base;
+    for (int32_t k = 0; k < ncolour; ++k) h_ptr[k + 1] = h_ptr[k] + hc[k];
+    PC_CUDA(cudaMemcpyAsync(base.p, h_ptr.data(), sizeof(int32_t) * ncolour, cudaMemcpyHostToDevice, s));
+    k_colour_place<<<gridc(n), kBlock, 0, s>>>(n, colour, base.p, cursor.p, rows.p); ::pc::count_launches(1);
+    PC_LAUNCH("colour_place");
     sync(c);
 }
 

@@ -897,15 +897,19 @@ int32_t aggregate_level(Ctx& c, int32_t n, const int32_t* nbr0, const int32_t* n
     active.alloc(c.mem, 1);
     k_rank_init<<<grid1(n), kBlock, 0, s>>>(n, nbr0, nbr1, jmp[0].p, dist[0].p, endv[0].p); ::pc::count_launches(1);
     PC_LAUNCH("rank_init");
+    // pointer jumping: the active flag is read every 4 rounds (rounds after the
+    // last jump copy their input)
     int cur = 0;
-    for (int it = 0; it < 40; ++it) {
+    for (int it = 0;; it += 4) {
         PC_CUDA(cudaMemsetAsync(active.p, 0, sizeof(int32_t), s));
-        k_rank_jump<<<grid1(nh), kBlock, 0, s>>>((int)nh, jmp[cur].p, dist[cur].p, endv[cur].p,
-                                                 jmp[1 - cur].p, dist[1 - cur].p, endv[1 - cur].p, active.p); ::pc::count_launches(1);
+        for (int k = 0; k < 4; ++k) {
+            k_rank_jump<<<grid1(nh), kBlock, 0, s>>>((int)nh, jmp[cur].p, dist[cur].p, endv[cur].p,
+                                                     jmp[1 - cur].p, dist[1 - cur].p, endv[1 - cur].p, active.p); ::pc::count_launches(1);
+            cur = 1 - cur;
+        }
         PC_LAUNCH("rank_jump");
-        cur = 1 - cur;
         if (read_i32(c, active.p) == 0) break;
-        if (it == 39) fail(PCAMG_ERR_ROUND_CAP, "list ranking did not finish");
+        if (it > 40) fail(PCAMG_ERR_ROUND_CAP, "list ranking did not finish");
     }
     DBuf<int32_t> lab, size, sprev, snext, best, st, jg, gcnt, goff, gfill, list, nleft;
     DBuf<unsigned char> ishead;
@@ -933,7 +937,7 @@ int32_t aggregate_level(Ctx& c, int32_t n, const int32_t* nbr0, const int32_t* n
             break;
         }
         k_left_case1<<<grid1(n), kBlock, 0, s>>>(n, st.p, best.p, lab.p, size.p); ::pc::count_launches(1);
-        scan_i32(c, gcnt.p, goff.p, n);
+        scan_i32_device(c, gcnt.p, goff.p, n);
         PC_CUDA(cudaMemsetAsync(gfill.p, 0, sizeof(int32_t) * n, s));
         k_left_fill<<<grid1(n), kBlock, 0, s>>>(n, st.p, jg.p, goff.p, gfill.p, list.p); ::pc::count_launches(1);
         k_left_join<<<grid1(n), kBlock, 0, s>>>(n, goff.p, list.p, best.p, lab.p, size.p); ::pc::count_launches(1);

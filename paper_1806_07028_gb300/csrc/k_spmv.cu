@@ -31,11 +31,13 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
+// One pass over the rows (no grid-stride loop): every row group is its own
+// warp slot, so the whole level's loads are in flight at once.
 inline int sparse_grid(int64_t rows, int lpr, int block = kBlock) {
     int64_t threads = rows * lpr;
     int64_t g = (threads + block - 1) / block;
     if (g < 1) g = 1;
-    if (g > (int64_t)kNumSMs * 8) g = kNumSMs * 8;
+    if (g > (int64_t)1 << 30) g = (int64_t)1 << 30;
     return (int)g;
 }
 
@@ -197,6 +199,36 @@ __global__ void k_coarse_apply(int m, const double* __restrict__ X, const T* __r
 // left to right, with one rounding per product and per addition.
 constexpr int kStreamRows = 256;
 constexpr int kStreamChunk = 2048;
+// below this many rows a launch of the streaming kernels would not fill the GPU
+constexpr int kStreamMinRows = kNumSMs * kStreamRows * 2;
+
+// Products a_k x_col(k) of entries [c0, c1) into prod[k - c0]: each thread
+// first loads kUnroll column indices and values (independent, coalesced), then
+// the kUnroll gathered x, so many loads are in flight per thread. x is read
+// with ordinary loads when the caller writes it in the same kernel (GS).
+constexpr int kUnroll = kStreamChunk / kStreamRows;
+
+template <class T, bool KEEP_COL>
+__device__ __forceinline__ void stage_products(int c0, int c1, const int* __restrict__ col,
+                                               const T* __restrict__ val, const T* x, T* prod,
+                                               int* pc) {
+    int cj[kUnroll];
+    T cv[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+        const int k = c0 + threadIdx.x + u * kStreamRows;
+        cj[u] = (k < c1) ? __ldg(col + k) : 0;
+        cv[u] = (k < c1) ? __ldg(val + k) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+        const int k = c0 + threadIdx.x + u * kStreamRows;
+        if (k < c1) {
+            prod[k - c0] = cv[u] * x[cj[u]];
+            if (KEEP_COL) pc[k - c0] = cj[u];
+        }
+    }
+}
 
 // r_i = b_i - sum_k a_k x_col(k); partial[block] = sum of r_i^2 when requested
 template <class T, bool NORM>
@@ -217,8 +249,7 @@ __global__ void __launch_bounds__(kStreamRows) k_res_stream(int n, const int* __
     T s = 0;
     for (int c0 = tb; c0 < te; c0 += kStreamChunk) {
         const int c1 = min(c0 + kStreamChunk, te);
-        for (int k = c0 + threadIdx.x; k < c1; k += kStreamRows)
-            prod[k - c0] = __ldg(val + k) * __ldg(x + __ldg(col + k));
+        stage_products<T, false>(c0, c1, col, val, x, prod, nullptr);
         __syncthreads();
         const int kb = max(rb, c0), ke = min(re, c1);
         for (int k = kb; k < ke; ++k) s += prod[k - c0];
@@ -262,11 +293,7 @@ __global__ void __launch_bounds__(kStreamRows) k_gs_stream(int beg, int end, con
     T s = 0, d = 0;
     for (int c0 = tb; c0 < te; c0 += kStreamChunk) {
         const int c1 = min(c0 + kStreamChunk, te);
-        for (int k = c0 + threadIdx.x; k < c1; k += kStreamRows) {
-            const int j = __ldg(pcol + k);
-            pc[k - c0] = j;
-            prod[k - c0] = __ldg(pval + k) * x[j];
-        }
+        stage_products<T, true>(c0, c1, pcol, pval, x, prod, pc);
         __syncthreads();
         const int kb = max(rb, c0), ke = min(re, c1);
         for (int k = kb; k < ke; ++k) {
@@ -334,14 +361,24 @@ inline int simple_grid(int64_t n) {
         default: CALL(32); break;    \
     }
 
+bool use_stream(int32_t rows, int lpr) { return lpr <= 16 && rows >= kStreamMinRows; }
+
 void residual64(cudaStream_t s, const Csr& A, const double* x, const double* b, double* r,
                 double* partial, double* norm2) {
-    int g = (A.n + kStreamRows - 1) / kStreamRows;
-    if (norm2) {
-        k_res_stream<double, true><<<g, kStreamRows, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, b, r, partial); ::pc::count_launches(1);
-        k_finish<<<1, 1024, 0, s>>>(g, partial, norm2); ::pc::count_launches(1);
+    if (use_stream(A.n, A.lpr) || norm2) {
+        int g = (A.n + kStreamRows - 1) / kStreamRows;
+        if (norm2) {
+            k_res_stream<double, true><<<g, kStreamRows, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, b, r, partial); ::pc::count_launches(1);
+            k_finish<<<1, 1024, 0, s>>>(g, partial, norm2); ::pc::count_launches(1);
+        } else {
+            k_res_stream<double, false><<<g, kStreamRows, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, b, r, nullptr); ::pc::count_launches(1);
+        }
     } else {
-        k_res_stream<double, false><<<g, kStreamRows, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, b, r, nullptr); ::pc::count_launches(1);
+        int g = sparse_grid(A.n, A.lpr);
+#define CALL(L) k_residual<double, L><<<g, kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, b, r, nullptr)
+        PC_LPR_DISPATCH(A.lpr, CALL)
+#undef CALL
+        count_launches(1);
     }
     PC_LAUNCH("residual64");
 }
@@ -362,8 +399,16 @@ void l1_diagonal(cudaStream_t s, int32_t n, const int32_t* rowptr, const double*
 }
 
 void residual32(cudaStream_t s, const Csr& A, const float* x, const float* b, float* r) {
-    int g = (A.n + kStreamRows - 1) / kStreamRows;
-    k_res_stream<float, false><<<g, kStreamRows, 0, s>>>(A.n, A.rowptr, A.col, A.val32, x, b, r, nullptr); ::pc::count_launches(1);
+    if (use_stream(A.n, A.lpr)) {
+        int g = (A.n + kStreamRows - 1) / kStreamRows;
+        k_res_stream<float, false><<<g, kStreamRows, 0, s>>>(A.n, A.rowptr, A.col, A.val32, x, b, r, nullptr); ::pc::count_launches(1);
+    } else {
+        int g = sparse_grid(A.n, A.lpr);
+#define CALL(L) k_residual<float, L><<<g, kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val32, x, b, r, nullptr)
+        PC_LPR_DISPATCH(A.lpr, CALL)
+#undef CALL
+        count_launches(1);
+    }
     PC_LAUNCH("residual32");
 }
 

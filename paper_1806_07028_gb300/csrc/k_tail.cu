@@ -54,15 +54,25 @@ __device__ void tail_gs(const TailLevel<T>& L, int k) {
 }
 
 // r = b - A x, rows in tiles of one per thread; the tile's products a x are
-// staged in shared memory in chunks (many independent loads in flight), then
-// each thread adds its row's products in CSR order.
+// staged in shared memory in chunks (each thread first loads kTailUnroll
+// column indices and values, so many loads are in flight), then each thread
+// adds its row's products in CSR order. When the level is small enough, x is
+// first copied to shared memory so the products need no gathers from L2.
 constexpr int kTailChunk = 4096;
+constexpr int kTailUnroll = kTailChunk / kTailThreads;
+constexpr int kTailXs = 2048;
 
 template <class T>
-__device__ void tail_residual(const TailLevel<T>& L, T* prod) {
-    const T* x = L.x;
+__device__ void tail_residual(const TailLevel<T>& L, T* prod, T* xs) {
+    const T* xg = L.x;
     const T* b = L.b;
     T* r = L.r;
+    const bool staged = L.n <= kTailXs;
+    if (staged) {
+        for (int i = threadIdx.x; i < L.n; i += kTailThreads) xs[i] = xg[i];
+        __syncthreads();
+    }
+    const T* x = staged ? xs : xg;
     for (int r0 = 0; r0 < L.n; r0 += kTailThreads) {
         const int row = r0 + threadIdx.x;
         const int rlast = min(r0 + kTailThreads, L.n);
@@ -72,8 +82,19 @@ __device__ void tail_residual(const TailLevel<T>& L, T* prod) {
         T s = 0;
         for (int c0 = tb; c0 < te; c0 += kTailChunk) {
             const int c1 = min(c0 + kTailChunk, te);
-            for (int k = c0 + threadIdx.x; k < c1; k += kTailThreads)
-                prod[k - c0] = __ldg(L.val + k) * x[__ldg(L.col + k)];
+            int cj[kTailUnroll];
+            T cv[kTailUnroll];
+#pragma unroll
+            for (int u = 0; u < kTailUnroll; ++u) {
+                const int k = c0 + threadIdx.x + u * kTailThreads;
+                cj[u] = (k < c1) ? __ldg(L.col + k) : 0;
+                cv[u] = (k < c1) ? __ldg(L.val + k) : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < kTailUnroll; ++u) {
+                const int k = c0 + threadIdx.x + u * kTailThreads;
+                if (k < c1) prod[k - c0] = cv[u] * x[cj[u]];
+            }
             __syncthreads();
             const int kb = max(rb, c0), ke = min(re, c1);
             for (int k = kb; k < ke; ++k) s += prod[k - c0];
@@ -86,8 +107,8 @@ __device__ void tail_residual(const TailLevel<T>& L, T* prod) {
 
 // l1-Jacobi sweep: x += (b - A x) / d
 template <class T>
-__device__ void tail_jacobi(const TailLevel<T>& L, T* prod) {
-    tail_residual(L, prod);
+__device__ void tail_jacobi(const TailLevel<T>& L, T* prod, T* xs) {
+    tail_residual(L, prod, xs);
     T* x = L.x;
     const T* r = L.r;
     for (int i = threadIdx.x; i < L.n; i += kTailThreads) x[i] += r[i] / __ldg(L.dl1 + i);
@@ -142,8 +163,9 @@ template <class T>
 __global__ void __launch_bounds__(kTailThreads) k_tail(const TailLevel<T>* __restrict__ lv, int l0, int L,
                                                        int gamma, int nu_pre, int nu_post,
                                                        const double* __restrict__ Xinv) {
-    __shared__ __align__(16) unsigned char smem[kTailChunk * sizeof(T)];
+    __shared__ __align__(16) unsigned char smem[(kTailChunk + kTailXs) * sizeof(T)];
     T* prod = reinterpret_cast<T*>(smem);
+    T* xs = prod + kTailChunk;
     int cnt[kMaxLevels];
     int l = l0;
     bool down = true;
@@ -157,10 +179,10 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const TailLevel<T>* __res
             }
             const TailLevel<T>& V = lv[l];
             for (int s = 0; s < nu_pre; ++s) {
-                if (V.jac) tail_jacobi(V, prod);
+                if (V.jac) tail_jacobi(V, prod, xs);
                 else for (int k = 0; k < V.ncolour; ++k) tail_gs(V, k);
             }
-            tail_residual(V, prod);
+            tail_residual(V, prod, xs);
             tail_restrict_zero(V, lv[l + 1]);
             cnt[l] = gamma;
             ++l;
@@ -169,7 +191,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const TailLevel<T>* __res
             const TailLevel<T>& V = lv[l];
             tail_prolong(V, lv[l + 1]);
             for (int s = 0; s < nu_post; ++s) {
-                if (V.jac) tail_jacobi(V, prod);
+                if (V.jac) tail_jacobi(V, prod, xs);
                 else for (int k = V.ncolour - 1; k >= 0; --k) tail_gs(V, k);
             }
             if (l == l0) break;

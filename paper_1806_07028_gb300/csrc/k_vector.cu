@@ -301,12 +301,10 @@ void scalar_ops(cudaStream_t s, int op, double* slots, int a, int b, int c) {
 
 // Exclusive scan; out[n] receives the total. Scratch comes from the context.
 template <class TI, class TO>
-static int64_t scan_impl(Ctx& c, const TI* in, TO* out, int64_t n) {
+static int64_t scan_impl(Ctx& c, const TI* in, TO* out, int64_t n, bool read_total = true) {
     int64_t ntiles = (n + 1023) / 1024;
     if (ntiles == 0) {
-        TO z = 0;
-        PC_CUDA(cudaMemcpyAsync(out, &z, sizeof(TO), cudaMemcpyHostToDevice, c.stream));
-        sync(c);
+        PC_CUDA(cudaMemsetAsync(out, 0, sizeof(TO), c.stream));
         return 0;
     }
     DBuf<int64_t> tsum, toff;
@@ -315,23 +313,25 @@ static int64_t scan_impl(Ctx& c, const TI* in, TO* out, int64_t n) {
     k_scan_tiles<TI, TO><<<(unsigned)ntiles, 256, 0, c.stream>>>(n, in, out, tsum.p); ::pc::count_launches(1);
     PC_LAUNCH("scan_tiles");
     if (ntiles > 1) {
-        scan_impl<int64_t, int64_t>(c, tsum.p, toff.p, ntiles);
+        scan_impl<int64_t, int64_t>(c, tsum.p, toff.p, ntiles, false);
         k_scan_add<TO><<<(unsigned)ntiles, 256, 0, c.stream>>>(n, out, toff.p); ::pc::count_launches(1);
         PC_LAUNCH("scan_add");
     } else {
-        int64_t z = 0;
-        PC_CUDA(cudaMemcpyAsync(toff.p, &z, sizeof(int64_t), cudaMemcpyHostToDevice, c.stream));
+        PC_CUDA(cudaMemsetAsync(toff.p, 0, sizeof(int64_t), c.stream));
         PC_CUDA(cudaMemcpyAsync(toff.p + 1, tsum.p, sizeof(int64_t), cudaMemcpyDeviceToDevice, c.stream));
     }
     // total = toff[ntiles-1] + tsum[ntiles-1]
     k_set_last<<<1, 1, 0, c.stream>>>(n, tsum.p + ntiles, toff.p, tsum.p, ntiles); ::pc::count_launches(1);
     k_store_total<TO><<<1, 1, 0, c.stream>>>(out, n, tsum.p + ntiles); ::pc::count_launches(1);
     PC_LAUNCH("scan_total");
-    return read_i64(c, tsum.p + ntiles);
+    return read_total ? read_i64(c, tsum.p + ntiles) : -1;
 }
 
 int64_t scan_i32(Ctx& c, const int32_t* in, int32_t* out, int64_t n) {
     return scan_impl<int32_t, int32_t>(c, in, out, n);
+}
+void scan_i32_device(Ctx& c, const int32_t* in, int32_t* out, int64_t n) {
+    scan_impl<int32_t, int32_t>(c, in, out, n, false);
 }
 int64_t scan_i64(Ctx& c, const int64_t* in, int64_t* out, int64_t n) {
     return scan_impl<int64_t, int64_t>(c, in, out, n);

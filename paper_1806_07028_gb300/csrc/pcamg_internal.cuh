@@ -236,6 +236,7 @@ template <class T>
 void permute_rows(Ctx& c, int32_t n, const int32_t* rows, const int32_t* rowptr, const int32_t* col,
                   const double* val, DBuf<int32_t>& pptr, DBuf<int32_t>& pcol, DBuf<T>& pval);
 int residual_partials(int32_t n);
+bool use_stream(int32_t rows, int lpr);  // streaming kernels pay off for this launch
 template <class T>
 void jacobi_update(cudaStream_t s, int32_t n, const T* r, const T* d, T* x);   // x += r / d
 void l1_diagonal(cudaStream_t s, int32_t n, const int32_t* rowptr, const double* val, double* d);
@@ -294,5 +295,7 @@ double read_f64(Ctx& c, const double* dev);
 // exclusive scan of int32 counts into int32 offsets (out has n+1 entries); returns total
 int64_t scan_i32(Ctx& c, const int32_t* in, int32_t* out, int64_t n);
 int64_t scan_i64(Ctx& c, const int64_t* in, int64_t* out, int64_t n);
+// the same without reading the total back (no host synchronisation)
+void scan_i32_device(Ctx& c, const int32_t* in, int32_t* out, int64_t n);
 
 }  // namespace pc
