@@ -36,10 +36,16 @@ __global__ void __launch_bounds__(1024) k_chol_pinned(int m, const double* __res
     for (int k = 0; k < m; ++k) {
         if (threadIdx.x == 0) {
             double d = D[(size_t)k * m + k];
-            for (int j = 0; j < k; ++j) {
-                double l = L[(size_t)k * m + j];
-                d = __dsub_rn(d, __dmul_rn(l, l));
+            const double* Lk = L + (size_t)k * m;
+            int j = 0;
+            for (; j + 8 <= k; j += 8) {
+                double l[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) l[u] = Lk[j + u];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) d = __dsub_rn(d, __dmul_rn(l[u], l[u]));
             }
+            for (; j < k; ++j) d = __dsub_rn(d, __dmul_rn(Lk[j], Lk[j]));
             int p = (force_last && k == m - 1) || !(d > tau * s_maxd);
             s_pin = p;
             pin[k] = p;
@@ -49,9 +55,19 @@ __global__ void __launch_bounds__(1024) k_chol_pinned(int m, const double* __res
         __syncthreads();
         if (!s_pin) {
             double lkk = s_lkk;
+            const double* Lk = L + (size_t)k * m;
             for (int i = k + 1 + threadIdx.x; i < m; i += blockDim.x) {
+                const double* Li = L + (size_t)i * m;
                 double s = D[(size_t)i * m + k];
-                for (int j = 0; j < k; ++j) s = __dsub_rn(s, __dmul_rn(L[(size_t)i * m + j], L[(size_t)k * m + j]));
+                int j = 0;
+                for (; j + 8 <= k; j += 8) {
+                    double a[8], b[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) { a[u] = Li[j + u]; b[u] = Lk[j + u]; }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) s = __dsub_rn(s, __dmul_rn(a[u], b[u]));
+                }
+                for (; j < k; ++j) s = __dsub_rn(s, __dmul_rn(Li[j], Lk[j]));
                 L[(size_t)i * m + k] = __ddiv_rn(s, lkk);
             }
         }
@@ -66,13 +82,30 @@ __global__ void k_chol_inverse(int m, const double* __restrict__ L, const int* _
         for (int i = 0; i < m; ++i) {
             if (pin[i]) { X[(size_t)i * m + c] = 0.0; continue; }
             double s = (i == c) ? 1.0 : 0.0;
-            for (int j = 0; j < i; ++j) s = __dsub_rn(s, __dmul_rn(L[(size_t)i * m + j], X[(size_t)j * m + c]));
-            X[(size_t)i * m + c] = __ddiv_rn(s, L[(size_t)i * m + i]);
+            const double* Li = L + (size_t)i * m;
+            int j = 0;
+            for (; j + 8 <= i; j += 8) {
+                double a[8], b[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) { a[u] = Li[j + u]; b[u] = X[(size_t)(j + u) * m + c]; }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) s = __dsub_rn(s, __dmul_rn(a[u], b[u]));
+            }
+            for (; j < i; ++j) s = __dsub_rn(s, __dmul_rn(Li[j], X[(size_t)j * m + c]));
+            X[(size_t)i * m + c] = __ddiv_rn(s, Li[i]);
         }
         for (int i = m - 1; i >= 0; --i) {
             if (pin[i]) { X[(size_t)i * m + c] = 0.0; continue; }
             double s = X[(size_t)i * m + c];
-            for (int j = i + 1; j < m; ++j) s = __dsub_rn(s, __dmul_rn(L[(size_t)j * m + i], X[(size_t)j * m + c]));
+            int j = i + 1;
+            for (; j + 8 <= m; j += 8) {
+                double a[8], b[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) { a[u] = L[(size_t)(j + u) * m + i]; b[u] = X[(size_t)(j + u) * m + c]; }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) s = __dsub_rn(s, __dmul_rn(a[u], b[u]));
+            }
+            for (; j < m; ++j) s = __dsub_rn(s, __dmul_rn(L[(size_t)j * m + i], X[(size_t)j * m + c]));
             X[(size_t)i * m + c] = __ddiv_rn(s, L[(size_t)i * m + i]);
         }
     }

@@ -27,6 +27,13 @@ inline int grid1(int64_t n, int block = kBlock) {
     return (int)g;
 }
 
+inline int grid_warps(int64_t rows) {
+    int64_t g = (rows + 7) / 8;
+    if (g < 1) g = 1;
+    if (g > (int64_t)kNumSMs * 64) g = kNumSMs * 64;
+    return (int)g;
+}
+
 #define FOR_EACH(i, n) for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
 // ---------------------------------------------------------------- row products
@@ -116,6 +123,163 @@ __global__ void k_rowprod_thread(int nrows, Src src, int* __restrict__ cnt,
                 if (oval) oval[o + q] = vals[q];
             }
         }
+    }
+}
+
+// Warp per row. The row's contributions are numbered in their fixed order
+// (member rows one after another); lanes take 32 consecutive contributions at
+// a time. Equal keys of one chunk form a group whose leader adds the group's
+// values, lowest lane first, into a shared-memory hash table, so every key's
+// sum is formed in contribution order. The table is then sorted by key.
+// Rows with more than kWarpMembers member rows or kWarpKeys distinct keys are
+// flagged for the block kernels.
+constexpr int kWarpKeys = 128;       // hash table slots per warp
+constexpr int kWarpMaxKeys = 96;     // more distinct keys than this: long row
+constexpr int kWarpMembers = 64;
+constexpr int kWarpsPerBlock = 8;
+
+struct WarpScratch {
+    int key[kWarpKeys];
+    double val[kWarpKeys];
+    int skey[32];
+    double sval[32];
+    int mpre[kWarpMembers + 1];
+    int mrow[kWarpMembers];
+};
+
+template <class Src, bool FILL>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_rowprod_warp(
+        int nrows, Src src, int* __restrict__ cnt, unsigned char* __restrict__ is_long,
+        int* __restrict__ long_list, int* __restrict__ long_count, const int* __restrict__ optr,
+        int* __restrict__ ocol, double* __restrict__ oval) {
+    __shared__ WarpScratch ws_all[kWarpsPerBlock];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    WarpScratch& W = ws_all[wib];
+    const int64_t gw = (int64_t)blockIdx.x * kWarpsPerBlock + wib;
+    const int64_t nw = (int64_t)gridDim.x * kWarpsPerBlock;
+    for (int64_t r64 = gw; r64 < nrows; r64 += nw) {
+        const int r = (int)r64;
+        if (FILL && is_long[r]) continue;
+        const int nm = src.nmem(r);
+        bool over = nm > kWarpMembers;
+        if (!over) {
+            // member rows and the prefix of their lengths
+            int len = 0, mr = 0;
+            if (lane < nm) { mr = src.mem_row(r, lane); len = src.in_end(mr) - src.in_beg(mr); }
+            int inc = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += y;
+            }
+            int carry = __shfl_sync(0xffffffffu, inc, 31);
+            if (lane < nm) { W.mpre[lane + 1] = inc; W.mrow[lane] = mr; }
+            if (nm > 32) {
+                int len2 = 0, mr2 = 0;
+                if (lane + 32 < nm) { mr2 = src.mem_row(r, lane + 32); len2 = src.in_end(mr2) - src.in_beg(mr2); }
+                int inc2 = len2;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    int y = __shfl_up_sync(0xffffffffu, inc2, o);
+                    if (lane >= o) inc2 += y;
+                }
+                if (lane + 32 < nm) { W.mpre[lane + 33] = carry + inc2; W.mrow[lane + 32] = mr2; }
+            }
+            if (lane == 0) W.mpre[0] = 0;
+            for (int q = lane; q < kWarpKeys; q += 32) W.key[q] = -1;
+            __syncwarp();
+            const int total = W.mpre[nm];
+            int nkeys = 0;
+            for (int e0 = 0; e0 < total && !over; e0 += 32) {
+                const int e = e0 + lane;
+                int key = -1;
+                double v = 0.0;
+                if (e < total) {
+                    int lo = 0, hi = nm - 1;          // member t with mpre[t] <= e < mpre[t+1]
+                    while (lo < hi) {
+                        int mid = (lo + hi + 1) >> 1;
+                        if (W.mpre[mid] <= e) lo = mid; else hi = mid - 1;
+                    }
+                    const int j = W.mrow[lo];
+                    const int k = src.in_beg(j) + (e - W.mpre[lo]);
+                    uint32_t kk;
+                    src.kv(r, j, k, kk, v);
+                    key = (kk == kSkip) ? -1 : (int)kk;
+                }
+                W.skey[lane] = key;
+                W.sval[lane] = v;
+                unsigned peers = __match_any_sync(0xffffffffu, key);
+                const bool leader = key >= 0 && lane == __ffs(peers) - 1;
+                __syncwarp();
+                int inserted = 0, full = 0;
+                if (leader) {
+                    unsigned h = ((unsigned)key * 2654435761u) & (kWarpKeys - 1);
+                    int slot = -1;
+                    for (int probe = 0; probe < kWarpKeys; ++probe) {
+                        int prev = atomicCAS(&W.key[h], -1, key);
+                        if (prev == -1) { slot = (int)h; inserted = 1; break; }
+                        if (prev == key) { slot = (int)h; break; }
+                        h = (h + 1) & (kWarpKeys - 1);
+                    }
+                    if (slot < 0) full = 1;
+                    else {
+                        unsigned m = peers;
+                        double acc = inserted ? 0.0 : W.val[slot];
+                        bool first = inserted;
+                        while (m) {
+                            int l = __ffs(m) - 1;
+                            m &= m - 1;
+                            if (first) { acc = W.sval[l]; first = false; }
+                            else acc = __dadd_rn(acc, W.sval[l]);
+                        }
+                        W.val[slot] = acc;
+                    }
+                }
+                nkeys += __popc(__ballot_sync(0xffffffffu, inserted));
+                if (__any_sync(0xffffffffu, full) || nkeys > kWarpMaxKeys) over = true;
+                __syncwarp();
+            }
+            if (!over) {
+                // compact the table and sort it by key (bitonic over 128 slots)
+                __syncwarp();
+                for (int q = lane; q < kWarpKeys; q += 32) {
+                    int k2 = W.key[q];
+                    W.key[q] = (k2 < 0) ? 0x7fffffff : k2;
+                }
+                __syncwarp();
+                for (int kk = 2; kk <= kWarpKeys; kk <<= 1) {
+                    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+                        for (int i = lane; i < kWarpKeys; i += 32) {
+                            int ixj = i ^ jj;
+                            if (ixj > i) {
+                                int a = W.key[i], b = W.key[ixj];
+                                bool up = (i & kk) == 0;
+                                if ((a > b) == up) {
+                                    W.key[i] = b; W.key[ixj] = a;
+                                    double t = W.val[i]; W.val[i] = W.val[ixj]; W.val[ixj] = t;
+                                }
+                            }
+                        }
+                        __syncwarp();
+                    }
+                }
+                if (!FILL) {
+                    if (lane == 0) { cnt[r] = nkeys; is_long[r] = 0; }
+                } else {
+                    const int o = optr[r];
+                    for (int q = lane; q < nkeys; q += 32) {
+                        ocol[o + q] = W.key[q];
+                        if (oval) oval[o + q] = W.val[q];
+                    }
+                }
+            }
+        }
+        if (over && !FILL && lane == 0) {
+            is_long[r] = 1;
+            cnt[r] = 0;
+            long_list[atomicAdd(long_count, 1)] = r;
+        }
+        __syncwarp();
     }
 }
 
@@ -717,9 +881,9 @@ static void row_product(Ctx& c, int32_t nrows, const Src& src, DBuf<int32_t>& op
     long_count.alloc(c.mem, 1);
     is_long.alloc(c.mem, nrows);
     PC_CUDA(cudaMemsetAsync(long_count.p, 0, sizeof(int32_t), s));
-    k_rowprod_thread<Src, false><<<grid1(nrows), kBlock, 0, s>>>(
+    k_rowprod_warp<Src, false><<<grid_warps(nrows), kWarpsPerBlock * 32, 0, s>>>(
         nrows, src, cnt.p, is_long.p, long_list.p, long_count.p, nullptr, nullptr, nullptr); ::pc::count_launches(1);
-    PC_LAUNCH("rowprod_thread(count)");
+    PC_LAUNCH("rowprod_warp(count)");
     int32_t nlong = read_i32(c, long_count.p);
     std::vector<int32_t> rowsB, rowsC;
     std::vector<int64_t> ubC;
@@ -780,9 +944,9 @@ static void row_product(Ctx& c, int32_t nrows, const Src& src, DBuf<int32_t>& op
     ocol.alloc(c.mem, total);
     double* ov = nullptr;
     if (oval) { oval->alloc(c.mem, total); ov = oval->p; }
-    k_rowprod_thread<Src, true><<<grid1(nrows), kBlock, 0, s>>>(
+    k_rowprod_warp<Src, true><<<grid_warps(nrows), kWarpsPerBlock * 32, 0, s>>>(
         nrows, src, nullptr, is_long.p, nullptr, nullptr, optr.p, ocol.p, ov); ::pc::count_launches(1);
-    PC_LAUNCH("rowprod_thread(fill)");
+    PC_LAUNCH("rowprod_warp(fill)");
     if (!rowsB.empty()) {
         size_t smem = kBlockCap * (sizeof(uint64_t) + sizeof(double));
         k_rowprod_block<Src, true, false><<<(unsigned)rowsB.size(), kBlock, smem, s>>>(
