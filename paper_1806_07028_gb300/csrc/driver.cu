@@ -143,13 +143,15 @@ static void smooth(Ctx& c, Level& L, const T* b, T* x, bool forward) {
     }
 }
 
+// One visit of level l. `fresh`: x arrives as the result of one l1-Jacobi
+// sweep from zero (the parent wrote b/d), so the first pre-sweep is done.
 template <class T>
-static void cycle_level(Ctx& c, Hier& h, int32_t l, int gamma) {
+static void cycle_level(Ctx& c, Hier& h, int32_t l, int gamma, bool fresh) {
     cudaStream_t s = c.stream;
     Level& L = h.lev[l];
     if (l == h.lt) {
         tail_cycle<T>(s, reinterpret_cast<const TailLevel<T>*>(h.tail.p), l, h.nlev, gamma,
-                      c.p.nu_pre, c.p.nu_post, h.Xinv.p);
+                      c.p.nu_pre, c.p.nu_post, h.Xinv.p, fresh ? 1 : 0);
         return;
     }
     if (l == h.nlev - 1) {
@@ -158,14 +160,19 @@ static void cycle_level(Ctx& c, Hier& h, int32_t l, int gamma) {
     }
     T* x = LV<T>::x(L);
     T* b = LV<T>::b(L);
+    for (int32_t k = fresh ? 1 : 0; k < c.p.nu_pre; ++k) smooth<T>(c, L, b, x, true);
+    Level& C = h.lev[l + 1];
+    // the child starts from zero; an l1-Jacobi child's first sweep from zero is
+    // b/d, written by the restriction itself (the tail child does the same)
+    const bool child_fresh = C.jac && c.p.nu_pre >= 1 && l + 1 < h.nlev - 1;
+    const T* dc = nullptr;
+    if (child_fresh) { if constexpr (sizeof(T) == 8) dc = C.dl1_64.p; else dc = C.dl1_32.p; }
     T* r = LV<T>::r(L);
-    for (int32_t k = 0; k < c.p.nu_pre; ++k) smooth<T>(c, L, b, x, true);
     if constexpr (sizeof(T) == 8) residual64(s, L.A, x, b, r, nullptr, nullptr);
     else residual32(s, L.A, x, b, r);
-    Level& C = h.lev[l + 1];
-    restrict_agg<T>(s, L.nc, L.agg_ptr.p, L.agg_mem.p, l == 0 ? LV<T>::pv(L) : nullptr, r, LV<T>::b(C));
-    PC_CUDA(cudaMemsetAsync(LV<T>::x(C), 0, sizeof(T) * C.n, s));
-    for (int g = 0; g < gamma; ++g) cycle_level<T>(c, h, l + 1, gamma);
+    restrict_agg<T>(s, L.nc, L.agg_ptr.p, L.agg_mem.p, l == 0 ? LV<T>::pv(L) : nullptr, r,
+                    LV<T>::b(C), LV<T>::x(C), dc);
+    for (int g = 0; g < gamma; ++g) cycle_level<T>(c, h, l + 1, gamma, child_fresh && g == 0);
     prolong_add<T>(s, L.n, L.agg.p, l == 0 ? LV<T>::pv(L) : nullptr, LV<T>::x(C), x);
     for (int32_t k = 0; k < c.p.nu_post; ++k) smooth<T>(c, L, b, x, false);
 }
@@ -174,7 +181,7 @@ template <class T>
 static void cycle_body(Ctx& c, Hier& h, int gamma) {
     Level& L0 = h.lev[0];
     PC_CUDA(cudaMemsetAsync(LV<T>::x(L0), 0, sizeof(T) * L0.n, c.stream));
-    cycle_level<T>(c, h, 0, gamma);
+    cycle_level<T>(c, h, 0, gamma, false);
 }
 
 static void run_body(Ctx& c, Hier& h, int gamma) {

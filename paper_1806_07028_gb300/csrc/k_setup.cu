@@ -127,22 +127,19 @@ __global__ void k_rowprod_thread(int nrows, Src src, int* __restrict__ cnt,
 }
 
 // Warp per row. The row's contributions are numbered in their fixed order
-// (member rows one after another); lanes take 32 consecutive contributions at
-// a time. Equal keys of one chunk form a group whose leader adds the group's
-// values, lowest lane first, into a shared-memory hash table, so every key's
-// sum is formed in contribution order. The table is then sorted by key.
-// Rows with more than kWarpMembers member rows or kWarpKeys distinct keys are
-// flagged for the block kernels.
-constexpr int kWarpKeys = 128;       // hash table slots per warp
-constexpr int kWarpMaxKeys = 96;     // more distinct keys than this: long row
+// (member rows one after another); lanes stage them as 64-bit keys
+// (column << 32 | number) with their values in shared memory, the warp sorts
+// the keys (bitonic, padded to a power of two), and the first lane of each run
+// of equal columns adds the run's values in contribution order. Rows with more
+// than kWarpMembers member rows or kWarpCap contributions are flagged for the
+// block kernels.
+constexpr int kWarpCap = 128;
 constexpr int kWarpMembers = 64;
 constexpr int kWarpsPerBlock = 8;
 
 struct WarpScratch {
-    int key[kWarpKeys];
-    double val[kWarpKeys];
-    int skey[32];
-    double sval[32];
+    uint64_t key[kWarpCap];
+    double val[kWarpCap];
     int mpre[kWarpMembers + 1];
     int mrow[kWarpMembers];
 };
@@ -162,6 +159,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_rowprod_warp(
         if (FILL && is_long[r]) continue;
         const int nm = src.nmem(r);
         bool over = nm > kWarpMembers;
+        int total = 0;
         if (!over) {
             // member rows and the prefix of their lengths
             int len = 0, mr = 0;
@@ -172,7 +170,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_rowprod_warp(
                 int y = __shfl_up_sync(0xffffffffu, inc, o);
                 if (lane >= o) inc += y;
             }
-            int carry = __shfl_sync(0xffffffffu, inc, 31);
+            total = __shfl_sync(0xffffffffu, inc, 31);
             if (lane < nm) { W.mpre[lane + 1] = inc; W.mrow[lane] = mr; }
             if (nm > 32) {
                 int len2 = 0, mr2 = 0;
@@ -183,16 +181,18 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_rowprod_warp(
                     int y = __shfl_up_sync(0xffffffffu, inc2, o);
                     if (lane >= o) inc2 += y;
                 }
-                if (lane + 32 < nm) { W.mpre[lane + 33] = carry + inc2; W.mrow[lane + 32] = mr2; }
+                if (lane + 32 < nm) { W.mpre[lane + 33] = total + inc2; W.mrow[lane + 32] = mr2; }
+                total += __shfl_sync(0xffffffffu, inc2, 31);
             }
             if (lane == 0) W.mpre[0] = 0;
-            for (int q = lane; q < kWarpKeys; q += 32) W.key[q] = -1;
+            over = total > kWarpCap;
+        }
+        if (!over) {
             __syncwarp();
-            const int total = W.mpre[nm];
-            int nkeys = 0;
-            for (int e0 = 0; e0 < total && !over; e0 += 32) {
-                const int e = e0 + lane;
-                int key = -1;
+            int P = 32;
+            while (P < total) P <<= 1;
+            for (int e = lane; e < P; e += 32) {
+                uint64_t key = ~0ull;
                 double v = 0.0;
                 if (e < total) {
                     int lo = 0, hi = nm - 1;          // member t with mpre[t] <= e < mpre[t+1]
@@ -204,75 +204,48 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_rowprod_warp(
                     const int k = src.in_beg(j) + (e - W.mpre[lo]);
                     uint32_t kk;
                     src.kv(r, j, k, kk, v);
-                    key = (kk == kSkip) ? -1 : (int)kk;
+                    if (kk != kSkip) key = ((uint64_t)kk << 32) | (uint64_t)e;
                 }
-                W.skey[lane] = key;
-                W.sval[lane] = v;
-                unsigned peers = __match_any_sync(0xffffffffu, key);
-                const bool leader = key >= 0 && lane == __ffs(peers) - 1;
-                __syncwarp();
-                int inserted = 0, full = 0;
-                if (leader) {
-                    unsigned h = ((unsigned)key * 2654435761u) & (kWarpKeys - 1);
-                    int slot = -1;
-                    for (int probe = 0; probe < kWarpKeys; ++probe) {
-                        int prev = atomicCAS(&W.key[h], -1, key);
-                        if (prev == -1) { slot = (int)h; inserted = 1; break; }
-                        if (prev == key) { slot = (int)h; break; }
-                        h = (h + 1) & (kWarpKeys - 1);
-                    }
-                    if (slot < 0) full = 1;
-                    else {
-                        unsigned m = peers;
-                        double acc = inserted ? 0.0 : W.val[slot];
-                        bool first = inserted;
-                        while (m) {
-                            int l = __ffs(m) - 1;
-                            m &= m - 1;
-                            if (first) { acc = W.sval[l]; first = false; }
-                            else acc = __dadd_rn(acc, W.sval[l]);
-                        }
-                        W.val[slot] = acc;
-                    }
-                }
-                nkeys += __popc(__ballot_sync(0xffffffffu, inserted));
-                if (__any_sync(0xffffffffu, full) || nkeys > kWarpMaxKeys) over = true;
-                __syncwarp();
+                W.key[e] = key;
+                W.val[e] = v;
             }
-            if (!over) {
-                // compact the table and sort it by key (bitonic over 128 slots)
-                __syncwarp();
-                for (int q = lane; q < kWarpKeys; q += 32) {
-                    int k2 = W.key[q];
-                    W.key[q] = (k2 < 0) ? 0x7fffffff : k2;
-                }
-                __syncwarp();
-                for (int kk = 2; kk <= kWarpKeys; kk <<= 1) {
-                    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-                        for (int i = lane; i < kWarpKeys; i += 32) {
-                            int ixj = i ^ jj;
-                            if (ixj > i) {
-                                int a = W.key[i], b = W.key[ixj];
-                                bool up = (i & kk) == 0;
-                                if ((a > b) == up) {
-                                    W.key[i] = b; W.key[ixj] = a;
-                                    double t = W.val[i]; W.val[i] = W.val[ixj]; W.val[ixj] = t;
-                                }
-                            }
+            __syncwarp();
+            for (int kk = 2; kk <= P; kk <<= 1) {
+                for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+                    for (int i = lane; i < P; i += 32) {
+                        int ixj = i ^ jj;
+                        if (ixj > i) {
+                            uint64_t a = W.key[i], b = W.key[ixj];
+                            bool up = (i & kk) == 0;
+                            if ((a > b) == up) { W.key[i] = b; W.key[ixj] = a; }
                         }
-                        __syncwarp();
                     }
-                }
-                if (!FILL) {
-                    if (lane == 0) { cnt[r] = nkeys; is_long[r] = 0; }
-                } else {
-                    const int o = optr[r];
-                    for (int q = lane; q < nkeys; q += 32) {
-                        ocol[o + q] = W.key[q];
-                        if (oval) oval[o + q] = W.val[q];
-                    }
+                    __syncwarp();
                 }
             }
+            // runs of equal columns
+            int carry = 0;
+            const int o = FILL ? optr[r] : 0;
+            for (int e0 = 0; e0 < P; e0 += 32) {
+                const int e = e0 + lane;
+                const uint64_t ke = W.key[e];
+                const bool start = ke != ~0ull && (e == 0 || (W.key[e - 1] >> 32) != (ke >> 32));
+                const unsigned ball = __ballot_sync(0xffffffffu, start);
+                if (FILL && start) {
+                    const uint32_t c = (uint32_t)(ke >> 32);
+                    double sum = W.val[(uint32_t)ke];
+                    for (int q = e + 1; q < P; ++q) {
+                        const uint64_t kq = W.key[q];
+                        if (kq == ~0ull || (uint32_t)(kq >> 32) != c) break;
+                        sum = __dadd_rn(sum, W.val[(uint32_t)kq]);
+                    }
+                    const int idx = o + carry + __popc(ball & ((1u << lane) - 1u));
+                    ocol[idx] = (int)c;
+                    if (oval) oval[idx] = sum;
+                }
+                carry += __popc(ball);
+            }
+            if (!FILL && lane == 0) { cnt[r] = carry; is_long[r] = 0; }
         }
         if (over && !FILL && lane == 0) {
             is_long[r] = 1;

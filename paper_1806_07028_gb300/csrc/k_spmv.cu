@@ -153,9 +153,13 @@ __global__ void __launch_bounds__(kBlock) k_gs(int nrows, const int* __restrict_
     }
 }
 
+// bc_I = sum over members u of aggregate I (ascending) of p_u r_u, and the
+// child's start value: zero, or bc_I / d_I when the child begins with an
+// l1-Jacobi sweep from zero (x = 0 + (b - A 0) / d = b / d exactly).
 template <class T>
 __global__ void k_restrict(int nc, const int* __restrict__ agg_ptr, const int* __restrict__ mem,
-                           const T* __restrict__ pval, const T* __restrict__ r, T* __restrict__ bc) {
+                           const T* __restrict__ pval, const T* __restrict__ r, T* __restrict__ bc,
+                           T* __restrict__ xc, const T* __restrict__ dc) {
     for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
         T s = 0;
         int beg = __ldg(agg_ptr + I), end = __ldg(agg_ptr + I + 1);
@@ -164,6 +168,7 @@ __global__ void k_restrict(int nc, const int* __restrict__ agg_ptr, const int* _
             s += pval ? __ldg(pval + u) * __ldg(r + u) : __ldg(r + u);
         }
         bc[I] = s;
+        if (xc) xc[I] = dc ? s / __ldg(dc + I) : T(0);
     }
 }
 
@@ -461,8 +466,8 @@ void permute_rows(Ctx& c, int32_t n, const int32_t* rows, const int32_t* rowptr,
 
 template <class T>
 void restrict_agg(cudaStream_t s, int32_t nc, const int32_t* agg_ptr, const int32_t* agg_mem,
-                  const T* pval, const T* r, T* bc) {
-    k_restrict<T><<<simple_grid(nc), kBlock, 0, s>>>(nc, agg_ptr, agg_mem, pval, r, bc); ::pc::count_launches(1);
+                  const T* pval, const T* r, T* bc, T* xc, const T* dc) {
+    k_restrict<T><<<simple_grid(nc), kBlock, 0, s>>>(nc, agg_ptr, agg_mem, pval, r, bc, xc, dc); ::pc::count_launches(1);
     PC_LAUNCH("restrict");
 }
 
@@ -486,8 +491,8 @@ template void gs_colour_perm<float>(cudaStream_t, int32_t, int32_t, const int32_
 template void permute_rows<double>(Ctx&, int32_t, const int32_t*, const int32_t*, const int32_t*, const double*, DBuf<int32_t>&, DBuf<int32_t>&, DBuf<double>&);
 template void permute_rows<float>(Ctx&, int32_t, const int32_t*, const int32_t*, const int32_t*, const double*, DBuf<int32_t>&, DBuf<int32_t>&, DBuf<float>&);
 template void gs_colour<float>(cudaStream_t, const Csr&, const int32_t*, int32_t, const float*, float*);
-template void restrict_agg<double>(cudaStream_t, int32_t, const int32_t*, const int32_t*, const double*, const double*, double*);
-template void restrict_agg<float>(cudaStream_t, int32_t, const int32_t*, const int32_t*, const float*, const float*, float*);
+template void restrict_agg<double>(cudaStream_t, int32_t, const int32_t*, const int32_t*, const double*, const double*, double*, double*, const double*);
+template void restrict_agg<float>(cudaStream_t, int32_t, const int32_t*, const int32_t*, const float*, const float*, float*, float*, const float*);
 template void prolong_add<double>(cudaStream_t, int32_t, const int32_t*, const double*, const double*, double*);
 template void prolong_add<float>(cudaStream_t, int32_t, const int32_t*, const float*, const float*, float*);
 template void coarse_apply<double>(cudaStream_t, int32_t, const double*, const double*, double*);

@@ -149,8 +149,10 @@ __device__ void tail_jacobi(const TailLevel<T>& L, T* prod, T* xs) {
     step_sync<CL>();
 }
 
+// Restriction of the residual and the child's start value: zero, or b/d when
+// the child begins with an l1-Jacobi sweep from zero.
 template <class T, int CL>
-__device__ void tail_restrict_zero(const TailLevel<T>& L, const TailLevel<T>& C) {
+__device__ void tail_restrict(const TailLevel<T>& L, const TailLevel<T>& C, bool child_fresh) {
     int lo, hi;
     share<CL>(L.nc, lo, hi);
     T* bc = C.b;
@@ -163,7 +165,7 @@ __device__ void tail_restrict_zero(const TailLevel<T>& L, const TailLevel<T>& C)
             s += L.pval ? __ldg(L.pval + u) * ldv(L.r + u) : ldv(L.r + u);
         }
         bc[I] = s;
-        xc[I] = 0;
+        xc[I] = child_fresh ? s / __ldg(C.dl1 + I) : T(0);
     }
     step_sync<CL>();
 }
@@ -198,13 +200,14 @@ __device__ void tail_coarse(const TailLevel<T>& L, const double* __restrict__ X)
 
 template <class T, int CL>
 __device__ void tail_body(const TailLevel<T>* __restrict__ lv, int l0, int L, int gamma, int nu_pre,
-                          int nu_post, const double* __restrict__ Xinv) {
+                          int nu_post, const double* __restrict__ Xinv, int fresh0) {
     __shared__ __align__(16) unsigned char smem[(kTailChunk + kTailXs) * sizeof(T)];
     T* prod = reinterpret_cast<T*>(smem);
     T* xs = prod + kTailChunk;
     int cnt[kMaxLevels];
     int l = l0;
     bool down = true;
+    bool fresh = fresh0 != 0;   // x of level l arrives as one Jacobi sweep from zero
     for (;;) {
         if (down) {
             if (l == L - 1) {
@@ -214,16 +217,18 @@ __device__ void tail_body(const TailLevel<T>* __restrict__ lv, int l0, int L, in
                 continue;
             }
             const TailLevel<T>& V = lv[l];
-            for (int s = 0; s < nu_pre; ++s) {
+            for (int s = fresh ? 1 : 0; s < nu_pre; ++s) {
                 if (V.jac) tail_jacobi<T, CL>(V, prod, xs);
                 else for (int k = 0; k < V.ncolour; ++k) tail_gs<T, CL>(V, k);
             }
+            const bool cf = lv[l + 1].jac && nu_pre >= 1 && l + 1 < L - 1;
             tail_residual<T, CL>(V, prod, xs);
-            tail_restrict_zero<T, CL>(V, lv[l + 1]);
+            tail_restrict<T, CL>(V, lv[l + 1], cf);
             cnt[l] = gamma;
             ++l;
+            fresh = cf;
         } else {
-            if (--cnt[l] > 0) { ++l; down = true; continue; }
+            if (--cnt[l] > 0) { ++l; down = true; fresh = false; continue; }
             const TailLevel<T>& V = lv[l];
             tail_prolong<T, CL>(V, lv[l + 1]);
             for (int s = 0; s < nu_post; ++s) {
@@ -239,20 +244,20 @@ __device__ void tail_body(const TailLevel<T>* __restrict__ lv, int l0, int L, in
 template <class T>
 __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kTailThreads)
     k_tail_cluster(const TailLevel<T>* __restrict__ lv, int l0, int L, int gamma, int nu_pre,
-                   int nu_post, const double* __restrict__ Xinv) {
-    tail_body<T, kCluster>(lv, l0, L, gamma, nu_pre, nu_post, Xinv);
+                   int nu_post, const double* __restrict__ Xinv, int fresh) {
+    tail_body<T, kCluster>(lv, l0, L, gamma, nu_pre, nu_post, Xinv, fresh);
 }
 
 }  // namespace
 
 template <class T>
 void tail_cycle(cudaStream_t s, const TailLevel<T>* lv, int l0, int L, int gamma, int nu_pre,
-                int nu_post, const double* Xinv) {
-    k_tail_cluster<T><<<kCluster, kTailThreads, 0, s>>>(lv, l0, L, gamma, nu_pre, nu_post, Xinv); ::pc::count_launches(1);
+                int nu_post, const double* Xinv, int fresh) {
+    k_tail_cluster<T><<<kCluster, kTailThreads, 0, s>>>(lv, l0, L, gamma, nu_pre, nu_post, Xinv, fresh); ::pc::count_launches(1);
     PC_LAUNCH("tail_cycle");
 }
 
-template void tail_cycle<double>(cudaStream_t, const TailLevel<double>*, int, int, int, int, int, const double*);
-template void tail_cycle<float>(cudaStream_t, const TailLevel<float>*, int, int, int, int, int, const double*);
+template void tail_cycle<double>(cudaStream_t, const TailLevel<double>*, int, int, int, int, int, const double*, int);
+template void tail_cycle<float>(cudaStream_t, const TailLevel<float>*, int, int, int, int, int, const double*, int);
 
 }  // namespace pc

@@ -136,7 +136,7 @@ struct TailLevel {
 };
 template <class T>
 void tail_cycle(cudaStream_t s, const TailLevel<T>* lv, int l0, int L, int gamma, int nu_pre,
-                int nu_post, const double* Xinv);
+                int nu_post, const double* Xinv, int fresh);
 
 struct Hier {
     int32_t nlev = 0;
@@ -242,7 +242,7 @@ void jacobi_update(cudaStream_t s, int32_t n, const T* r, const T* d, T* x);   /
 void l1_diagonal(cudaStream_t s, int32_t n, const int32_t* rowptr, const double* val, double* d);
 template <class T>
 void restrict_agg(cudaStream_t s, int32_t nc, const int32_t* agg_ptr, const int32_t* agg_mem,
-                  const T* pval, const T* r, T* bc);
+                  const T* pval, const T* r, T* bc, T* xc, const T* dc);
 template <class T>
 void prolong_add(cudaStream_t s, int32_t n, const int32_t* agg, const T* pval, const T* xc, T* x);
 template <class T>
