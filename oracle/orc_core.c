@@ -35,7 +35,7 @@ void orc_default_params(orc_params* p) {
     p->leftover_mode = ORC_LEFT_ROUNDS;
     p->cover_mode = ORC_COVER_LD;
     p->dense_max = 4096;
-    p->l1jac_rows = 262144;
+    p->l1jac_rows = 2147483647;
 }
 
 /* ------------------------------------------------------------------------- */

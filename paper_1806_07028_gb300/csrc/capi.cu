@@ -194,7 +194,7 @@ PCAMG_API pcamg_status pcamg_default_params(pcamg_params* p) {
     p->keep_setup = 0;
     p->profile = 0;
     p->tail_rows = 2048;
-    p->l1jac_rows = 262144;
+    p->l1jac_rows = 2147483647;
     return PCAMG_OK;
 }
 
