@@ -210,6 +210,24 @@ PCAMG_API void pcamg_destroy(pcamg_handle h);
 PCAMG_API pcamg_status pcamg_residual(int32_t n, const int32_t* d_rowptr, const int32_t* d_col,
                                       const double* d_val, const double* d_x, const double* d_b,
                                       double* d_r, double* d_norm2, void* stream);
+/* The same residual and ||r||_2^2 WITHOUT any device allocation. The paper has
+ * no counterpart: this is for callers that cannot allocate device memory --
+ * e.g. code recording the stream into a CUDA graph, a time-critical loop that
+ * may not pay for cudaMalloc/cudaFree (they can synchronise the device), or a
+ * process whose device memory is all handed out by its own pool. The per-block
+ * partial sums live in one fixed device array of 65536 doubles (512 KB) that
+ * every GPU which loads the library holds until the process exits, so
+ * n <= 16,777,216 rows (larger n: PCAMG_ERR_INVALID). d_norm2 is required.
+ * The first call on a device looks up that array's device address (with the
+ * device current) and caches it; make that first call before any stream
+ * capture. All calls share the array: calls whose work overlaps on the GPU
+ * (other streams, other host threads) race on it and must be serialised by
+ * the caller. Each call overwrites every entry it reads, so no clearing is
+ * needed. Errors: pcamg_last_error(NULL). */
+PCAMG_API pcamg_status pcamg_residual_noalloc(int32_t n, const int32_t* d_rowptr,
+                                              const int32_t* d_col, const double* d_val,
+                                              const double* d_x, const double* d_b, double* d_r,
+                                              double* d_norm2, void* stream);
 /* Same in FP32 (values, x, b, r float). */
 PCAMG_API pcamg_status pcamg_residual_f32(int32_t n, const int32_t* d_rowptr,
                                           const int32_t* d_col, const float* d_val,

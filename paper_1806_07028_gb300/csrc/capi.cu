@@ -168,6 +168,10 @@ void copy_out(Ctx& c, T* host, const T* dev, size_t count) {
 
 }  // namespace
 
+namespace pc {
+void set_global_error(const std::string& m) { g_last_error = m; }
+}  // namespace pc
+
 extern "C" {
 
 PCAMG_API pcamg_status pcamg_default_params(pcamg_params* p) {

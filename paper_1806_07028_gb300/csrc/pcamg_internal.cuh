@@ -18,6 +18,7 @@ struct Error {
 };
 
 [[noreturn]] void fail(pcamg_status s, const std::string& msg);
+void set_global_error(const std::string& msg);   // message for pcamg_last_error(NULL)
 void check_cuda(cudaError_t e, const char* what);
 // Process-wide count of kernels this library has launched (a graph replay adds
 // the number of kernels it holds).

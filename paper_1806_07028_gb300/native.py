@@ -28,7 +28,7 @@ EXPORTS = [
     "pcamg_num_hierarchies", "pcamg_num_levels", "pcamg_level_sizes", "pcamg_export_level",
     "pcamg_export_reweighted", "pcamg_last_error", "pcamg_status_string", "pcamg_destroy",
     "pcamg_residual", "pcamg_residual_f32", "pcamg_uniform", "pcamg_colour",
-    "pcamg_kernel_launches",
+    "pcamg_kernel_launches", "pcamg_residual_noalloc",
 ]
 
 
@@ -96,6 +96,7 @@ def lib():
                 "pcamg_uniform": ([u64, i64, vp, vp], i32),
                 "pcamg_colour": ([i32, vp, vp, u64, vp, P(i32), vp], i32),
                 "pcamg_kernel_launches": ([], i64),
+                "pcamg_residual_noalloc": ([i32, vp, vp, vp, vp, vp, vp, vp, vp], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
