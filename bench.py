@@ -45,6 +45,8 @@ def _args():
     ap.add_argument("--only-kernel", default=None, choices=["residual64", "vcycle", "wcycle", "adapt"],
                     help="time one kernel alone on the workload (used for ncu captures)")
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--summarize-launches", default=None, metavar="CSV",
+                    help="reduce an ncu --csv launch list to per-kernel launches, time and share")
     return ap.parse_args()
 
 
@@ -420,9 +422,38 @@ def run_kernel(a):
                       "frac": byt / ms / 1e6 / peak, "peak_kind": kind}), flush=True)
 
 
+def summarize_launches(path):
+    """Per-kernel launches, total device time and share from an ncu launch list
+    (--metrics gpu__time_duration.sum --csv); template arguments are kept, call
+    arguments dropped."""
+    import collections
+    import csv
+    import re
+    by = collections.defaultdict(lambda: [0, 0.0])
+    with open(path) as f:
+        rows = csv.reader(line for line in f if line.startswith('"'))
+        hdr = next(rows)
+        ki, vi = hdr.index("Kernel Name"), hdr.index("Metric Value")
+        ui = hdr.index("Metric Unit")
+        for r in rows:
+            name = re.sub(r"\(.*", "", r[ki]).replace("void ", "").replace("pc::<unnamed>::", "")
+            scale = {"ns": 1e-3, "usecond": 1.0, "us": 1.0, "msecond": 1e3, "ms": 1e3, "nsecond": 1e-3}.get(r[ui], 1e-3)
+            by[name][0] += 1
+            by[name][1] += float(r[vi].replace(",", "")) * scale
+    tot = sum(t for _, t in by.values())
+    n = sum(c for c, _ in by.values())
+    lines = [f"launches: {n}   total device time: {tot / 1e3:.3f} ms (cold-cache, serialised)",
+             f"{'kernel':60s} {'launches':>9s} {'total ms':>10s} {'share':>7s}"]
+    for k, (c, t) in sorted(by.items(), key=lambda x: -x[1][1]):
+        lines.append(f"{k[:60]:60s} {c:9d} {t / 1e3:10.3f} {100 * t / tot:6.2f}%")
+    print("\n".join(lines))
+
+
 def main():
     a = _args()
-    if a.only_kernel:
+    if a.summarize_launches:
+        summarize_launches(a.summarize_launches)
+    elif a.only_kernel:
         run_kernel(a)
     elif a.impl == "reference":
         run_reference(a)
