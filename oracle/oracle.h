@@ -78,7 +78,8 @@ uint64_t orc_splitmix64(uint64_t x);
 void orc_uniform_pm1(uint64_t seed, int64_t n, double* out);
 
 /* ---- level operators -------------------------------------------------------- */
-/* r = b - A x, row sums taken left to right in CSR order. */
+/* r = b - A x, row sums taken left to right in CSR order, one fused
+ * multiply-add (single rounding) per entry. */
 void orc_residual(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
                   const double* x, const double* b, double* r);
 /* Jones-Plassmann colouring: priority (splitmix64(seed^i), i), larger wins; a

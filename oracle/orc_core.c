@@ -91,7 +91,8 @@ void orc_residual(int32_t n, const int32_t* rowptr, const int32_t* col, const do
                   const double* x, const double* b, double* r) {
     for (int32_t i = 0; i < n; ++i) {
         double s = 0.0;
-        for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) s += val[k] * x[col[k]];
+        /* one fused multiply-add per entry, left to right */
+        for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) s = fma(val[k], x[col[k]], s);
         r[i] = b[i] - s;
     }
 }
@@ -147,7 +148,7 @@ static void gs_row(const int32_t* rowptr, const int32_t* col, const double* val,
     for (int32_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
         int32_t j = col[k];
         if (j == i) d = val[k];
-        else s += val[k] * x[j];
+        else s = fma(val[k], x[j], s);
     }
     x[i] = (b[i] - s) / d;
 }

@@ -18,6 +18,10 @@ int lanes_per_row(int32_t n, int64_t nnz) {
 
 namespace {
 
+// one rounding per multiply-add, in both precisions
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
 template <int LPR, class T>
 __device__ __forceinline__ T group_sum(T v) {
 #pragma unroll
@@ -60,7 +64,7 @@ __global__ void __launch_bounds__(kBlock) k_residual(int n, const int* __restric
         T s = 0;
         if (row < n) {
             int beg = __ldg(rowptr + row), end = __ldg(rowptr + row + 1);
-            for (int k = beg + sub; k < end; k += LPR) s += __ldg(val + k) * __ldg(x + __ldg(col + k));
+            for (int k = beg + sub; k < end; k += LPR) s = fma_t(__ldg(val + k), __ldg(x + __ldg(col + k)), s);
         }
         s = group_sum<LPR>(s);
         if (sub == 0 && row < n) {
@@ -113,7 +117,7 @@ __global__ void __launch_bounds__(kBlock) k_spmv(int n, const int* __restrict__ 
         double s = 0;
         if (row < n) {
             int beg = __ldg(rowptr + row), end = __ldg(rowptr + row + 1);
-            for (int k = beg + sub; k < end; k += LPR) s += __ldg(val + k) * __ldg(x + __ldg(col + k));
+            for (int k = beg + sub; k < end; k += LPR) s = fma_t(__ldg(val + k), __ldg(x + __ldg(col + k)), s);
         }
         s = group_sum<LPR>(s);
         if (sub == 0 && row < n) y[row] = s;
@@ -144,7 +148,7 @@ __global__ void __launch_bounds__(kBlock) k_gs(int nrows, const int* __restrict_
                 int j = __ldg(col + k);
                 T a = __ldg(val + k);
                 if (j == row) d = a;
-                else s += a * x[j];
+                else s = fma_t(a, x[j], s);
             }
         }
         s = group_sum<LPR>(s);
@@ -207,16 +211,17 @@ constexpr int kStreamChunk = 2048;
 // below this many rows a launch of the streaming kernels would not fill the GPU
 constexpr int kStreamMinRows = kNumSMs * kStreamRows * 2;
 
-// Products a_k x_col(k) of entries [c0, c1) into prod[k - c0]: each thread
-// first loads kUnroll column indices and values (independent, coalesced), then
-// the kUnroll gathered x, so many loads are in flight per thread. x is read
-// with ordinary loads when the caller writes it in the same kernel (GS).
+// Entries [c0, c1) staged in shared memory: value a_k into av[k - c0] and the
+// gathered x_col(k) into xv[k - c0]. Each thread first loads kUnroll column
+// indices and values (independent, coalesced), then the kUnroll gathered x, so
+// many loads are in flight per thread. x is read with ordinary loads when the
+// caller writes it in the same kernel (GS).
 constexpr int kUnroll = kStreamChunk / kStreamRows;
 
 template <class T, bool KEEP_COL>
 __device__ __forceinline__ void stage_products(int c0, int c1, const int* __restrict__ col,
-                                               const T* __restrict__ val, const T* x, T* prod,
-                                               int* pc) {
+                                               const T* __restrict__ val, const T* x, T* av,
+                                               T* xv, int* pc) {
     int cj[kUnroll];
     T cv[kUnroll];
 #pragma unroll
@@ -229,13 +234,15 @@ __device__ __forceinline__ void stage_products(int c0, int c1, const int* __rest
     for (int u = 0; u < kUnroll; ++u) {
         const int k = c0 + threadIdx.x + u * kStreamRows;
         if (k < c1) {
-            prod[k - c0] = cv[u] * x[cj[u]];
+            av[k - c0] = cv[u];
+            xv[k - c0] = x[cj[u]];
             if (KEEP_COL) pc[k - c0] = cj[u];
         }
     }
 }
 
-// r_i = b_i - sum_k a_k x_col(k); partial[block] = sum of r_i^2 when requested
+// r_i = b_i - sum_k a_k x_col(k) (fused multiply-adds left to right);
+// partial[block] = sum of r_i^2 when requested
 template <class T, bool NORM>
 __global__ void __launch_bounds__(kStreamRows) k_res_stream(int n, const int* __restrict__ rowptr,
                                                              const int* __restrict__ col,
@@ -244,7 +251,8 @@ __global__ void __launch_bounds__(kStreamRows) k_res_stream(int n, const int* __
                                                              const T* __restrict__ b,
                                                              T* __restrict__ r,
                                                              double* __restrict__ partial) {
-    __shared__ T prod[kStreamChunk];
+    __shared__ T av[kStreamChunk];
+    __shared__ T xv[kStreamChunk];
     const int r0 = blockIdx.x * kStreamRows;
     const int row = r0 + threadIdx.x;
     const int rlast = min(r0 + kStreamRows, n);
@@ -254,10 +262,10 @@ __global__ void __launch_bounds__(kStreamRows) k_res_stream(int n, const int* __
     T s = 0;
     for (int c0 = tb; c0 < te; c0 += kStreamChunk) {
         const int c1 = min(c0 + kStreamChunk, te);
-        stage_products<T, false>(c0, c1, col, val, x, prod, nullptr);
+        stage_products<T, false>(c0, c1, col, val, x, av, xv, nullptr);
         __syncthreads();
         const int kb = max(rb, c0), ke = min(re, c1);
-        for (int k = kb; k < ke; ++k) s += prod[k - c0];
+        for (int k = kb; k < ke; ++k) s = fma_t(av[k - c0], xv[k - c0], s);
         __syncthreads();
     }
     double rr2 = 0.0;
@@ -287,7 +295,8 @@ __global__ void __launch_bounds__(kStreamRows) k_gs_stream(int beg, int end, con
                                                             const int* __restrict__ pcol,
                                                             const T* __restrict__ pval,
                                                             const T* __restrict__ b, T* __restrict__ x) {
-    __shared__ T prod[kStreamChunk];
+    __shared__ T av[kStreamChunk];
+    __shared__ T xv[kStreamChunk];
     __shared__ int pc[kStreamChunk];
     const int t0 = beg + blockIdx.x * kStreamRows;
     const int t = t0 + threadIdx.x;
@@ -298,12 +307,12 @@ __global__ void __launch_bounds__(kStreamRows) k_gs_stream(int beg, int end, con
     T s = 0, d = 0;
     for (int c0 = tb; c0 < te; c0 += kStreamChunk) {
         const int c1 = min(c0 + kStreamChunk, te);
-        stage_products<T, true>(c0, c1, pcol, pval, x, prod, pc);
+        stage_products<T, true>(c0, c1, pcol, pval, x, av, xv, pc);
         __syncthreads();
         const int kb = max(rb, c0), ke = min(re, c1);
         for (int k = kb; k < ke; ++k) {
-            if (pc[k - c0] == row) d = __ldg(pval + k);
-            else s += prod[k - c0];
+            if (pc[k - c0] == row) d = av[k - c0];
+            else s = fma_t(av[k - c0], xv[k - c0], s);
         }
         __syncthreads();
     }
