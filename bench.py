@@ -204,7 +204,7 @@ def run_ours(a):
     pms = sum(s["prof_ms"] for s in stats)
     bytes_per_launch = 12.0 * g.nnz + 28.0 * g.n
     achieved = (bytes_per_launch / (pms / pl / 1e3) / 1e9) if pl else None
-    roofline = {"bound": "hbm", "kernel": "k_residual<double,8> (fine-level r = b - A x, ||r||^2)",
+    roofline = {"bound": "hbm", "kernel": "k_res_stream<double,1> (fine-level r = b - A x with ||r||^2)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None,
                 "traffic": _traffic_per_launch(),
@@ -308,7 +308,7 @@ def oracle_sample(g, b, gpu_stats, max_seconds=40.0):
 # Iteration structure of one solve of the C2 workload (hierarchies built and
 # cycles applied), as reported by the solver's own statistics; the oracle's
 # solve follows the same trajectory on this graph (same counts).
-SOLVE_COUNTS = {"C2": {"builds": 19, "cycles": 1376, "wcycles": 14}}
+SOLVE_COUNTS = {"C2": {"builds": 21, "cycles": 1690, "wcycles": 14}}
 
 
 def run_reference(a):

@@ -211,12 +211,18 @@ constexpr int kStreamChunk = 2048;
 // below this many rows a launch of the streaming kernels would not fill the GPU
 constexpr int kStreamMinRows = kNumSMs * kStreamRows * 2;
 
-// Entries [c0, c1) staged in shared memory: value a_k into av[k - c0] and the
-// gathered x_col(k) into xv[k - c0]. Each thread first loads kUnroll column
+// Entries [c0, c1) staged in shared memory. FP64: the value a_k into av and
+// the gathered x_col(k) into xv, so the row sum can take one fused multiply-add
+// per entry (GB300's FP64 rate makes the separate multiply the bottleneck).
+// FP32: the product a_k x_col(k) into av (FP32 arithmetic is plentiful and
+// half the staging traffic is saved). Each thread first loads kUnroll column
 // indices and values (independent, coalesced), then the kUnroll gathered x, so
 // many loads are in flight per thread. x is read with ordinary loads when the
 // caller writes it in the same kernel (GS).
 constexpr int kUnroll = kStreamChunk / kStreamRows;
+
+template <class T>
+constexpr int kXv = sizeof(T) == 8 ? kStreamChunk : 1;
 
 template <class T, bool KEEP_COL>
 __device__ __forceinline__ void stage_products(int c0, int c1, const int* __restrict__ col,
@@ -234,11 +240,18 @@ __device__ __forceinline__ void stage_products(int c0, int c1, const int* __rest
     for (int u = 0; u < kUnroll; ++u) {
         const int k = c0 + threadIdx.x + u * kStreamRows;
         if (k < c1) {
-            av[k - c0] = cv[u];
-            xv[k - c0] = x[cj[u]];
+            if constexpr (sizeof(T) == 8) { av[k - c0] = cv[u]; xv[k - c0] = x[cj[u]]; }
+            else av[k - c0] = cv[u] * x[cj[u]];
             if (KEEP_COL) pc[k - c0] = cj[u];
         }
     }
+}
+
+// add entry k's contribution to s (see stage_products)
+template <class T>
+__device__ __forceinline__ T row_add(const T* av, const T* xv, int i, T s) {
+    if constexpr (sizeof(T) == 8) return fma_t(av[i], xv[i], s);
+    else return s + av[i];
 }
 
 // r_i = b_i - sum_k a_k x_col(k) (fused multiply-adds left to right);
@@ -252,7 +265,7 @@ __global__ void __launch_bounds__(kStreamRows) k_res_stream(int n, const int* __
                                                              T* __restrict__ r,
                                                              double* __restrict__ partial) {
     __shared__ T av[kStreamChunk];
-    __shared__ T xv[kStreamChunk];
+    __shared__ T xv[kXv<T>];
     const int r0 = blockIdx.x * kStreamRows;
     const int row = r0 + threadIdx.x;
     const int rlast = min(r0 + kStreamRows, n);
@@ -265,7 +278,7 @@ __global__ void __launch_bounds__(kStreamRows) k_res_stream(int n, const int* __
         stage_products<T, false>(c0, c1, col, val, x, av, xv, nullptr);
         __syncthreads();
         const int kb = max(rb, c0), ke = min(re, c1);
-        for (int k = kb; k < ke; ++k) s = fma_t(av[k - c0], xv[k - c0], s);
+        for (int k = kb; k < ke; ++k) s = row_add<T>(av, xv, k - c0, s);
         __syncthreads();
     }
     double rr2 = 0.0;
@@ -296,7 +309,7 @@ __global__ void __launch_bounds__(kStreamRows) k_gs_stream(int beg, int end, con
                                                             const T* __restrict__ pval,
                                                             const T* __restrict__ b, T* __restrict__ x) {
     __shared__ T av[kStreamChunk];
-    __shared__ T xv[kStreamChunk];
+    __shared__ T xv[kXv<T>];
     __shared__ int pc[kStreamChunk];
     const int t0 = beg + blockIdx.x * kStreamRows;
     const int t = t0 + threadIdx.x;
@@ -311,8 +324,8 @@ __global__ void __launch_bounds__(kStreamRows) k_gs_stream(int beg, int end, con
         __syncthreads();
         const int kb = max(rb, c0), ke = min(re, c1);
         for (int k = kb; k < ke; ++k) {
-            if (pc[k - c0] == row) d = av[k - c0];
-            else s = fma_t(av[k - c0], xv[k - c0], s);
+            if (pc[k - c0] == row) d = (sizeof(T) == 8) ? av[k - c0] : __ldg(pval + k);
+            else s = row_add<T>(av, xv, k - c0, s);
         }
         __syncthreads();
     }

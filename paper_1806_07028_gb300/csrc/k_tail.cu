@@ -100,8 +100,6 @@ __device__ void tail_gs(const TailLevel<T>& L, int k) {
 // first copied to shared memory so the products need no gathers from L2.
 template <class T, int CL>
 __device__ void tail_residual(const TailLevel<T>& L, T* prod, T* xs) {
-    T* av = prod;                    // values (kTailChunk / 2 per chunk)
-    T* xv = prod + kTailChunk / 2;   // gathered x
     const T* xg = L.x;
     T* r = L.r;
     const bool staged = L.n <= kTailXs;
@@ -118,29 +116,24 @@ __device__ void tail_residual(const TailLevel<T>& L, T* prod, T* xs) {
         int rb = 0, re = 0;
         if (row < hi) { rb = __ldg(L.rowptr + row); re = __ldg(L.rowptr + row + 1); }
         T s = 0;
-        constexpr int kHalf = kTailChunk / 2;
-        constexpr int kU = kHalf / kTailThreads;
-        for (int c0 = tb; c0 < te; c0 += kHalf) {
-            const int c1 = min(c0 + kHalf, te);
-            int cj[kU];
-            T cv[kU];
+        for (int c0 = tb; c0 < te; c0 += kTailChunk) {
+            const int c1 = min(c0 + kTailChunk, te);
+            int cj[kTailUnroll];
+            T cv[kTailUnroll];
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
+            for (int u = 0; u < kTailUnroll; ++u) {
                 const int k = c0 + threadIdx.x + u * kTailThreads;
                 cj[u] = (k < c1) ? __ldg(L.col + k) : 0;
                 cv[u] = (k < c1) ? __ldg(L.val + k) : T(0);
             }
 #pragma unroll
-            for (int u = 0; u < kU; ++u) {
+            for (int u = 0; u < kTailUnroll; ++u) {
                 const int k = c0 + threadIdx.x + u * kTailThreads;
-                if (k < c1) {
-                    av[k - c0] = cv[u];
-                    xv[k - c0] = staged ? xs[cj[u]] : ldv(xg + cj[u]);
-                }
+                if (k < c1) prod[k - c0] = cv[u] * (staged ? xs[cj[u]] : ldv(xg + cj[u]));
             }
             __syncthreads();
             const int kb = max(rb, c0), ke = min(re, c1);
-            for (int k = kb; k < ke; ++k) s = fma_t(av[k - c0], xv[k - c0], s);
+            for (int k = kb; k < ke; ++k) s += prod[k - c0];
             __syncthreads();
         }
         if (row < hi) r[row] = ldv(L.b + row) - s;
