@@ -92,7 +92,8 @@ void check_params(const pcamg_params& p) {
         (p.p1_mode != PCAMG_P1_E_SCALED && p.p1_mode != PCAMG_P1_BOOLEAN) ||
         (p.precision != PCAMG_FP64 && p.precision != PCAMG_FP32_IR) ||
         (p.start != PCAMG_START_RANDOM && p.start != PCAMG_START_USER) || p.dense_max < 1 ||
-        p.dense_max > 4096 || p.tail_rows < 0 || p.l1jac_rows < 0)
+        p.dense_max > 4096 || p.tail_rows < 0 || p.l1jac_rows < 0 || p.tail_dense < 0 ||
+        p.tail_dense > 3)
         fail(PCAMG_ERR_INVALID, "invalid parameters");
 }
 
@@ -199,6 +200,7 @@ PCAMG_API pcamg_status pcamg_default_params(pcamg_params* p) {
     p->profile = 0;
     p->tail_rows = 2048;
     p->l1jac_rows = 2147483647;
+    p->tail_dense = 2;
     return PCAMG_OK;
 }
 

@@ -145,10 +145,27 @@ static void smooth(Ctx& c, Level& L, const T* b, T* x, bool forward) {
 
 // One visit of level l. `fresh`: x arrives as the result of one l1-Jacobi
 // sweep from zero (the parent wrote b/d), so the first pre-sweep is done.
+// `first`: x is zero or that fresh start, i.e. this is the child's first visit.
 template <class T>
-static void cycle_level(Ctx& c, Hier& h, int32_t l, int gamma, bool fresh) {
+static void cycle_level(Ctx& c, Hier& h, int32_t l, int gamma, bool fresh, bool first) {
     cudaStream_t s = c.stream;
     Level& L = h.lev[l];
+    if (l == h.lt && h.tail_op[gamma - 1].p) {
+        // the tail levels as their dense operator N: a visit from a zero start
+        // is x = N b; a later visit continues from x, x += N (b - A x)
+        const T* Nm = reinterpret_cast<const T*>(h.tail_op[gamma - 1].p);
+        T* x = LV<T>::x(L);
+        T* b = LV<T>::b(L);
+        if (first) {
+            tail_gemv<T>(s, L.n, h.tail_ld, Nm, b, x, false);
+        } else {
+            T* r = LV<T>::r(L);
+            if constexpr (sizeof(T) == 8) residual64(s, L.A, x, b, r, nullptr, nullptr);
+            else residual32(s, L.A, x, b, r);
+            tail_gemv<T>(s, L.n, h.tail_ld, Nm, r, x, true);
+        }
+        return;
+    }
     if (l == h.lt) {
         tail_cycle<T>(s, reinterpret_cast<const TailLevel<T>*>(h.tail.p), l, h.nlev, gamma,
                       c.p.nu_pre, c.p.nu_post, h.Xinv.p, fresh ? 1 : 0);
@@ -172,7 +189,7 @@ static void cycle_level(Ctx& c, Hier& h, int32_t l, int gamma, bool fresh) {
     else residual32(s, L.A, x, b, r);
     restrict_agg<T>(s, L.nc, L.agg_ptr.p, L.agg_mem.p, l == 0 ? LV<T>::pv(L) : nullptr, r,
                     LV<T>::b(C), LV<T>::x(C), dc);
-    for (int g = 0; g < gamma; ++g) cycle_level<T>(c, h, l + 1, gamma, child_fresh && g == 0);
+    for (int g = 0; g < gamma; ++g) cycle_level<T>(c, h, l + 1, gamma, child_fresh && g == 0, g == 0);
     prolong_add<T>(s, L.n, L.agg.p, l == 0 ? LV<T>::pv(L) : nullptr, LV<T>::x(C), x);
     for (int32_t k = 0; k < c.p.nu_post; ++k) smooth<T>(c, L, b, x, false);
 }
@@ -181,11 +198,37 @@ template <class T>
 static void cycle_body(Ctx& c, Hier& h, int gamma) {
     Level& L0 = h.lev[0];
     PC_CUDA(cudaMemsetAsync(LV<T>::x(L0), 0, sizeof(T) * L0.n, c.stream));
-    cycle_level<T>(c, h, 0, gamma, false);
+    cycle_level<T>(c, h, 0, gamma, false, true);
+}
+
+// Forms the tail levels' dense operator for this cycle kind once per
+// hierarchy, when params.tail_dense selects the kind, the tail has more than
+// the coarsest level and its vectors fit one block's shared memory.
+template <class T>
+static void ensure_tail_op(Ctx& c, Hier& h, int gamma) {
+    const int k = gamma - 1;
+    if (h.tail_op_tried[k]) return;
+    h.tail_op_tried[k] = true;
+    if (!(c.p.tail_dense & (1 << k)) || h.lt >= h.nlev - 1) return;
+    int n[kMaxLevels] = {0};
+    for (int32_t l = 0; l < h.nlev; ++l) n[l] = h.lev[l].n;
+    if (!tail_operator_fits<T>(n, h.lt, h.nlev)) return;
+    const int m = n[h.lt];
+    constexpr int w = 16 / sizeof(T);
+    h.tail_ld = (m + w - 1) / w * w;
+    const size_t bytes = sizeof(T) * (size_t)m * h.tail_ld;
+    h.tail_op[k].alloc(c.mem, bytes);
+    PC_CUDA(cudaMemsetAsync(h.tail_op[k].p, 0, bytes, c.stream));
+    int dev = 0, nsm = 0;
+    PC_CUDA(cudaGetDevice(&dev));
+    PC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    tail_operator<T>(c.stream, reinterpret_cast<const TailLevel<T>*>(h.tail.p), n, h.lt, h.nlev, gamma,
+                     c.p.nu_pre, c.p.nu_post, h.Xinv.p, reinterpret_cast<T*>(h.tail_op[k].p), h.tail_ld, nsm);
 }
 
 static void run_body(Ctx& c, Hier& h, int gamma) {
     bool f32 = c.p.precision == PCAMG_FP32_IR;
+    if (f32) ensure_tail_op<float>(c, h, gamma); else ensure_tail_op<double>(c, h, gamma);
     if (!c.p.use_graphs) {
         if (f32) cycle_body<float>(c, h, gamma); else cycle_body<double>(c, h, gamma);
         return;

@@ -51,8 +51,13 @@ __device__ __forceinline__ void share(int n, int& lo, int& hi) {
     hi = (int)(((int64_t)n * (q + 1)) / CL);
 }
 
-template <class T>
-__device__ __forceinline__ T ldv(const T* p) { return __ldcg(p); }
+// vectors written inside the kernel: read from L2 when the cluster's blocks
+// share them, plainly when they live in this block's shared memory (LOC)
+template <bool LOC, class T>
+__device__ __forceinline__ T ldv(const T* p) {
+    if constexpr (LOC) return *p;
+    else return __ldcg(p);
+}
 
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
@@ -63,7 +68,7 @@ __device__ __forceinline__ T gsum(T v, int lpr) {
     return v;
 }
 
-template <class T, int CL>
+template <class T, int CL, bool LOC>
 __device__ void tail_gs(const TailLevel<T>& L, int k) {
     const int beg = __ldg(L.cptr + k), end = __ldg(L.cptr + k + 1);
     int lo, hi;
@@ -83,12 +88,12 @@ __device__ void tail_gs(const TailLevel<T>& L, int k) {
                 int j = __ldg(L.col + q);
                 T a = __ldg(L.val + q);
                 if (j == row) d = a;
-                else s = fma_t(a, ldv(x + j), s);
+                else s = fma_t(a, ldv<LOC>(x + j), s);
             }
         }
         s = gsum(s, lpr);
         d = gsum(d, lpr);
-        if (sub == 0 && t < hi) x[row] = (ldv(L.b + row) - s) / d;
+        if (sub == 0 && t < hi) x[row] = (ldv<LOC>(L.b + row) - s) / d;
     }
     step_sync<CL>();
 }
@@ -98,13 +103,13 @@ __device__ void tail_gs(const TailLevel<T>& L, int k) {
 // loads kTailUnroll column indices and values, so many loads are in flight),
 // then each thread adds its row's products in CSR order. A small level's x is
 // first copied to shared memory so the products need no gathers from L2.
-template <class T, int CL>
+template <class T, int CL, bool LOC>
 __device__ void tail_residual(const TailLevel<T>& L, T* prod, T* xs) {
     const T* xg = L.x;
     T* r = L.r;
-    const bool staged = L.n <= kTailXs;
+    const bool staged = !LOC && L.n <= kTailXs;
     if (staged) {
-        for (int i = threadIdx.x; i < L.n; i += kTailThreads) xs[i] = ldv(xg + i);
+        for (int i = threadIdx.x; i < L.n; i += kTailThreads) xs[i] = ldv<LOC>(xg + i);
         __syncthreads();
     }
     int lo, hi;
@@ -129,32 +134,32 @@ __device__ void tail_residual(const TailLevel<T>& L, T* prod, T* xs) {
 #pragma unroll
             for (int u = 0; u < kTailUnroll; ++u) {
                 const int k = c0 + threadIdx.x + u * kTailThreads;
-                if (k < c1) prod[k - c0] = cv[u] * (staged ? xs[cj[u]] : ldv(xg + cj[u]));
+                if (k < c1) prod[k - c0] = cv[u] * (staged ? xs[cj[u]] : ldv<LOC>(xg + cj[u]));
             }
             __syncthreads();
             const int kb = max(rb, c0), ke = min(re, c1);
             for (int k = kb; k < ke; ++k) s += prod[k - c0];
             __syncthreads();
         }
-        if (row < hi) r[row] = ldv(L.b + row) - s;
+        if (row < hi) r[row] = ldv<LOC>(L.b + row) - s;
     }
     step_sync<CL>();
 }
 
 // l1-Jacobi sweep: x += (b - A x) / d
-template <class T, int CL>
+template <class T, int CL, bool LOC>
 __device__ void tail_jacobi(const TailLevel<T>& L, T* prod, T* xs) {
-    tail_residual<T, CL>(L, prod, xs);
+    tail_residual<T, CL, LOC>(L, prod, xs);
     int lo, hi;
     share<CL>(L.n, lo, hi);
     T* x = L.x;
-    for (int i = lo + threadIdx.x; i < hi; i += kTailThreads) x[i] = ldv(x + i) + ldv(L.r + i) / __ldg(L.dl1 + i);
+    for (int i = lo + threadIdx.x; i < hi; i += kTailThreads) x[i] = ldv<LOC>(x + i) + ldv<LOC>(L.r + i) / __ldg(L.dl1 + i);
     step_sync<CL>();
 }
 
 // Restriction of the residual and the child's start value: zero, or b/d when
 // the child begins with an l1-Jacobi sweep from zero.
-template <class T, int CL>
+template <class T, int CL, bool LOC>
 __device__ void tail_restrict(const TailLevel<T>& L, const TailLevel<T>& C, bool child_fresh) {
     int lo, hi;
     share<CL>(L.nc, lo, hi);
@@ -165,7 +170,7 @@ __device__ void tail_restrict(const TailLevel<T>& L, const TailLevel<T>& C, bool
         int e = __ldg(L.agg_ptr + I + 1);
         for (int t = __ldg(L.agg_ptr + I); t < e; ++t) {
             int u = __ldg(L.agg_mem + t);
-            s += L.pval ? __ldg(L.pval + u) * ldv(L.r + u) : ldv(L.r + u);
+            s += L.pval ? __ldg(L.pval + u) * ldv<LOC>(L.r + u) : ldv<LOC>(L.r + u);
         }
         bc[I] = s;
         xc[I] = child_fresh ? s / __ldg(C.dl1 + I) : T(0);
@@ -173,19 +178,19 @@ __device__ void tail_restrict(const TailLevel<T>& L, const TailLevel<T>& C, bool
     step_sync<CL>();
 }
 
-template <class T, int CL>
+template <class T, int CL, bool LOC>
 __device__ void tail_prolong(const TailLevel<T>& L, const TailLevel<T>& C) {
     int lo, hi;
     share<CL>(L.n, lo, hi);
     T* x = L.x;
     for (int u = lo + threadIdx.x; u < hi; u += kTailThreads) {
-        T c = ldv(C.x + __ldg(L.agg + u));
-        x[u] = ldv(x + u) + (L.pval ? __ldg(L.pval + u) * c : c);
+        T c = ldv<LOC>(C.x + __ldg(L.agg + u));
+        x[u] = ldv<LOC>(x + u) + (L.pval ? __ldg(L.pval + u) * c : c);
     }
     step_sync<CL>();
 }
 
-template <class T, int CL>
+template <class T, int CL, bool LOC>
 __device__ void tail_coarse(const TailLevel<T>& L, const double* __restrict__ X) {
     const int m = L.n, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int lo, hi;
@@ -193,7 +198,7 @@ __device__ void tail_coarse(const TailLevel<T>& L, const double* __restrict__ X)
     T* x = L.x;
     for (int i = lo + warp; i < hi; i += kTailWarps) {
         double s = 0.0;
-        for (int j = lane; j < m; j += 32) s += __ldg(X + (size_t)i * m + j) * (double)ldv(L.b + j);
+        for (int j = lane; j < m; j += 32) s += __ldg(X + (size_t)i * m + j) * (double)ldv<LOC>(L.b + j);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
         if (lane == 0) x[i] = (T)s;
@@ -201,7 +206,7 @@ __device__ void tail_coarse(const TailLevel<T>& L, const double* __restrict__ X)
     step_sync<CL>();
 }
 
-template <class T, int CL>
+template <class T, int CL, bool LOC>
 __device__ void tail_body(const TailLevel<T>* __restrict__ lv, int l0, int L, int gamma, int nu_pre,
                           int nu_post, const double* __restrict__ Xinv, int fresh0) {
     __shared__ __align__(16) unsigned char smem[(kTailChunk + kTailXs) * sizeof(T)];
@@ -214,29 +219,29 @@ __device__ void tail_body(const TailLevel<T>* __restrict__ lv, int l0, int L, in
     for (;;) {
         if (down) {
             if (l == L - 1) {
-                tail_coarse<T, CL>(lv[l], Xinv);
+                tail_coarse<T, CL, LOC>(lv[l], Xinv);
                 down = false;
                 if (--l < l0) break;
                 continue;
             }
             const TailLevel<T>& V = lv[l];
             for (int s = fresh ? 1 : 0; s < nu_pre; ++s) {
-                if (V.jac) tail_jacobi<T, CL>(V, prod, xs);
-                else for (int k = 0; k < V.ncolour; ++k) tail_gs<T, CL>(V, k);
+                if (V.jac) tail_jacobi<T, CL, LOC>(V, prod, xs);
+                else for (int k = 0; k < V.ncolour; ++k) tail_gs<T, CL, LOC>(V, k);
             }
             const bool cf = lv[l + 1].jac && nu_pre >= 1 && l + 1 < L - 1;
-            tail_residual<T, CL>(V, prod, xs);
-            tail_restrict<T, CL>(V, lv[l + 1], cf);
+            tail_residual<T, CL, LOC>(V, prod, xs);
+            tail_restrict<T, CL, LOC>(V, lv[l + 1], cf);
             cnt[l] = gamma;
             ++l;
             fresh = cf;
         } else {
             if (--cnt[l] > 0) { ++l; down = true; fresh = false; continue; }
             const TailLevel<T>& V = lv[l];
-            tail_prolong<T, CL>(V, lv[l + 1]);
+            tail_prolong<T, CL, LOC>(V, lv[l + 1]);
             for (int s = 0; s < nu_post; ++s) {
-                if (V.jac) tail_jacobi<T, CL>(V, prod, xs);
-                else for (int k = V.ncolour - 1; k >= 0; --k) tail_gs<T, CL>(V, k);
+                if (V.jac) tail_jacobi<T, CL, LOC>(V, prod, xs);
+                else for (int k = V.ncolour - 1; k >= 0; --k) tail_gs<T, CL, LOC>(V, k);
             }
             if (l == l0) break;
             --l;
@@ -248,10 +253,126 @@ template <class T>
 __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kTailThreads)
     k_tail_cluster(const TailLevel<T>* __restrict__ lv, int l0, int L, int gamma, int nu_pre,
                    int nu_post, const double* __restrict__ Xinv, int fresh) {
-    tail_body<T, kCluster>(lv, l0, L, gamma, nu_pre, nu_post, Xinv, fresh);
+    tail_body<T, kCluster, false>(lv, l0, L, gamma, nu_pre, nu_post, Xinv, fresh);
+}
+
+// Columns of the tail's linear operator. One visit of the tail levels from a
+// zero start is a linear map b -> x of the first tail level (every step --
+// l1-Jacobi or Gauss-Seidel sweeps, restriction, the gamma child visits,
+// prolongation, the pinned pseudo-inverse -- is linear), so column j of its
+// matrix N is the visit applied to the unit vector e_j. Each block takes
+// columns j = blockIdx.x, blockIdx.x + gridDim.x, ... and runs the same state
+// machine as the cluster kernel on one block, with every level's x, b and r in
+// its shared memory; N is stored row-major with row stride ld.
+template <class T>
+__global__ void __launch_bounds__(kTailThreads, 1)
+    k_tail_columns(const TailLevel<T>* __restrict__ lvg, int l0, int L, int gamma, int nu_pre,
+                   int nu_post, const double* __restrict__ Xinv, T* __restrict__ Nout, int ld) {
+    extern __shared__ __align__(16) unsigned char dyn[];
+    __shared__ TailLevel<T> lvs[kMaxLevels];
+    if (threadIdx.x == 0) {
+        T* p = reinterpret_cast<T*>(dyn);
+        for (int l = l0; l < L; ++l) {
+            lvs[l] = lvg[l];
+            const int n = lvs[l].n;
+            lvs[l].x = p; p += n;
+            lvs[l].b = p; p += n;
+            lvs[l].r = p; p += n;
+        }
+    }
+    __syncthreads();
+    const int m = lvs[l0].n;
+    T* x = lvs[l0].x;
+    T* b = lvs[l0].b;
+    for (int j = blockIdx.x; j < m; j += gridDim.x) {
+        for (int i = threadIdx.x; i < m; i += kTailThreads) {
+            b[i] = (i == j) ? T(1) : T(0);
+            x[i] = T(0);
+        }
+        __syncthreads();
+        tail_body<T, 1, true>(lvs, l0, L, gamma, nu_pre, nu_post, Xinv, 0);
+        for (int i = threadIdx.x; i < m; i += kTailThreads) Nout[(size_t)i * ld + j] = x[i];
+        __syncthreads();
+    }
+}
+
+constexpr int kGemvWarps = 16;
+
+template <class T> struct Vec16;
+template <> struct Vec16<float> { using V = float4; };
+template <> struct Vec16<double> { using V = double2; };
+
+__device__ __forceinline__ float dot16(float4 a, float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
+__device__ __forceinline__ double dot16(double2 a, double2 b) { return a.x * b.x + a.y * b.y; }
+
+// x = N v (accum = 0) or x += N v (accum = 1); one warp per row of N, v staged
+// in shared memory with zeros up to ld, rows read as 16-byte vectors.
+template <class T>
+__global__ void __launch_bounds__(kGemvWarps * 32)
+    k_tail_gemv(int m, int ld, const T* __restrict__ Nm, const T* __restrict__ v, T* __restrict__ x,
+                int accum) {
+    using V = typename Vec16<T>::V;
+    constexpr int W = 16 / sizeof(T);
+    extern __shared__ __align__(16) unsigned char dyn[];
+    T* vs = reinterpret_cast<T*>(dyn);
+    for (int j = threadIdx.x; j < ld; j += blockDim.x) vs[j] = (j < m) ? v[j] : T(0);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = blockIdx.x * kGemvWarps + warp;
+    if (row >= m) return;
+    const V* a = reinterpret_cast<const V*>(Nm + (size_t)row * ld);
+    const V* vv = reinterpret_cast<const V*>(vs);
+    T s = 0;
+#pragma unroll 4
+    for (int q = lane; q < ld / W; q += 32) s += dot16(__ldg(a + q), vv[q]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) x[row] = accum ? x[row] + s : s;
 }
 
 }  // namespace
+
+// dynamic shared memory of k_tail_columns: x, b, r of every tail level
+template <class T>
+size_t tail_operator_smem(const int* n, int l0, int L) {
+    size_t e = 0;
+    for (int l = l0; l < L; ++l) e += 3 * (size_t)n[l];
+    return e * sizeof(T);
+}
+
+template <class T>
+bool tail_operator_fits(const int* n, int l0, int L) {
+    const size_t stat = (kTailChunk + kTailXs) * sizeof(T) + sizeof(TailLevel<T>) * kMaxLevels;
+    return tail_operator_smem<T>(n, l0, L) + stat <= 220 * 1024;
+}
+
+template <class T>
+void tail_operator(cudaStream_t s, const TailLevel<T>* lv, const int* n, int l0, int L, int gamma,
+                   int nu_pre, int nu_post, const double* Xinv, T* Nout, int ld, int nsm) {
+    const size_t dyn = tail_operator_smem<T>(n, l0, L);
+    if (!tail_operator_fits<T>(n, l0, L)) fail(PCAMG_ERR_INVALID, "tail operator: levels exceed shared memory");
+    PC_CUDA(cudaFuncSetAttribute(k_tail_columns<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    const int m = n[l0];
+    const int grid = std::max(1, std::min(m, nsm));
+    k_tail_columns<T><<<grid, kTailThreads, dyn, s>>>(lv, l0, L, gamma, nu_pre, nu_post, Xinv, Nout, ld); ::pc::count_launches(1);
+    PC_LAUNCH("tail_operator");
+}
+
+template <class T>
+void tail_gemv(cudaStream_t s, int m, int ld, const T* Nm, const T* v, T* x, bool accum) {
+    const int grid = (m + kGemvWarps - 1) / kGemvWarps;
+    k_tail_gemv<T><<<grid, kGemvWarps * 32, sizeof(T) * ld, s>>>(m, ld, Nm, v, x, accum ? 1 : 0); ::pc::count_launches(1);
+    PC_LAUNCH("tail_gemv");
+}
+
+template size_t tail_operator_smem<float>(const int*, int, int);
+template size_t tail_operator_smem<double>(const int*, int, int);
+template bool tail_operator_fits<float>(const int*, int, int);
+template bool tail_operator_fits<double>(const int*, int, int);
+template void tail_operator<float>(cudaStream_t, const TailLevel<float>*, const int*, int, int, int, int, int, const double*, float*, int, int);
+template void tail_operator<double>(cudaStream_t, const TailLevel<double>*, const int*, int, int, int, int, int, const double*, double*, int, int);
+template void tail_gemv<float>(cudaStream_t, int, int, const float*, const float*, float*, bool);
+template void tail_gemv<double>(cudaStream_t, int, int, const double*, const double*, double*, bool);
 
 template <class T>
 void tail_cycle(cudaStream_t s, const TailLevel<T>* lv, int l0, int L, int gamma, int nu_pre,

@@ -138,6 +138,16 @@ struct TailLevel {
 template <class T>
 void tail_cycle(cudaStream_t s, const TailLevel<T>* lv, int l0, int L, int gamma, int nu_pre,
                 int nu_post, const double* Xinv, int fresh);
+// The tail's operator N (x = N b for one visit from a zero start), formed
+// column by column; n[l] = unknowns of level l; N row-major, row stride ld.
+template <class T>
+bool tail_operator_fits(const int* n, int l0, int L);
+template <class T>
+void tail_operator(cudaStream_t s, const TailLevel<T>* lv, const int* n, int l0, int L, int gamma,
+                   int nu_pre, int nu_post, const double* Xinv, T* Nout, int ld, int nsm);
+// x = N v, or x += N v (accum)
+template <class T>
+void tail_gemv(cudaStream_t s, int m, int ld, const T* Nm, const T* v, T* x, bool accum);
 
 struct Hier {
     int32_t nlev = 0;
@@ -148,6 +158,11 @@ struct Hier {
     double oc = 0.0;
     int32_t lt = -1;                 // first level run by the coarse tail kernel
     DBuf<unsigned char> tail;        // TailLevel<T>[nlev] on the device
+    // dense operator of the tail levels per cycle kind (index gamma-1), when
+    // params.tail_dense selects it; row-major m x tail_ld, m = lev[lt].n
+    DBuf<unsigned char> tail_op[2];
+    bool tail_op_tried[2] = {false, false};
+    int32_t tail_ld = 0;
     // CUDA graphs of the correction cycle (index: gamma-1)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t graph_kernels[2] = {0, 0};

@@ -50,7 +50,7 @@ class Params(C.Structure):
                 ("round_cap", C.c_int32), ("p1_mode", C.c_int32), ("precision", C.c_int32),
                 ("start", C.c_int32), ("dense_max", C.c_int32), ("use_graphs", C.c_int32),
                 ("keep_setup", C.c_int32), ("profile", C.c_int32), ("tail_rows", C.c_int32),
-                ("l1jac_rows", C.c_int32)]
+                ("l1jac_rows", C.c_int32), ("tail_dense", C.c_int32)]
 
 
 class Stats(C.Structure):

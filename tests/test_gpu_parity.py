@@ -227,7 +227,9 @@ def test_invalid_inputs_return_status(P):
 @pytest.mark.parametrize("precision", [0, 1])
 def test_coarse_tail_block_matches_per_level_kernels(P, name, precision):
     # the single-block coarse tail runs the same steps as the per-level kernels:
-    # no tail, a partial tail and an all-levels tail give the same correction
+    # no tail, a partial tail and an all-levels tail give the same correction;
+    # so does the tail applied as its dense operator (one visit from zero is a
+    # linear map), for V- and W-cycles, on the first and on repeated visits
     g = GRAPHS[name]
     e = O.start_vector(g)
     h = O.Hierarchy(g, e)
@@ -236,7 +238,10 @@ def test_coarse_tail_block_matches_per_level_kernels(P, name, precision):
     for gamma in (1, 2):
         ref = h.vcycle(r) if gamma == 1 else h.wcycle(r)
         for tail in (0, 2000, 10**9):
-            s = P.Solver(g, params=P.default_params(precision=precision, tail_rows=tail), e0=e)
-            c = s.cycle(r, hist=0, gamma=gamma).cpu().numpy()
-            assert np.linalg.norm(c - ref) <= tol * np.linalg.norm(ref), (tail, gamma)
-            s.close()
+            for dense in ((0,) if tail == 0 else (0, 3)):
+                s = P.Solver(g, params=P.default_params(precision=precision, tail_rows=tail,
+                                                        tail_dense=dense), e0=e)
+                for _ in range(2):   # the second call replays the captured graph
+                    c = s.cycle(r, hist=0, gamma=gamma).cpu().numpy()
+                    assert np.linalg.norm(c - ref) <= tol * np.linalg.norm(ref), (tail, dense, gamma)
+                s.close()
