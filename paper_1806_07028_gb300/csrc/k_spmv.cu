@@ -9,10 +9,12 @@
 
 namespace pc {
 
+// Lanes cooperating on one row in the sub-warp kernels: enough that each lane
+// takes about three entries of an average row (2..32).
 int lanes_per_row(int32_t n, int64_t nnz) {
     double avg = n > 0 ? (double)nnz / (double)n : 1.0;
     int l = 2;
-    while (l < 32 && l < avg) l <<= 1;
+    while (l < 32 && 3.0 * l < avg) l <<= 1;
     return l;
 }
 
@@ -207,7 +209,9 @@ __global__ void k_coarse_apply(int m, const double* __restrict__ X, const T* __r
 // adds the products of its own row in CSR order. A row's sum is therefore taken
 // left to right, with one rounding per product and per addition.
 constexpr int kStreamRows = 256;
-constexpr int kStreamChunk = 2048;
+// entries staged per chunk: FP64 stages a value and an x per entry, FP32 one product
+template <class T>
+constexpr int kStreamChunk = sizeof(T) == 8 ? 2048 : 4096;
 // below this many rows a launch of the streaming kernels would not fill the GPU
 constexpr int kStreamMinRows = kNumSMs * kStreamRows * 2;
 
@@ -219,25 +223,26 @@ constexpr int kStreamMinRows = kNumSMs * kStreamRows * 2;
 // indices and values (independent, coalesced), then the kUnroll gathered x, so
 // many loads are in flight per thread. x is read with ordinary loads when the
 // caller writes it in the same kernel (GS).
-constexpr int kUnroll = kStreamChunk / kStreamRows;
+template <class T>
+constexpr int kUnroll = kStreamChunk<T> / kStreamRows;
 
 template <class T>
-constexpr int kXv = sizeof(T) == 8 ? kStreamChunk : 1;
+constexpr int kXv = sizeof(T) == 8 ? kStreamChunk<T> : 1;
 
 template <class T, bool KEEP_COL>
 __device__ __forceinline__ void stage_products(int c0, int c1, const int* __restrict__ col,
                                                const T* __restrict__ val, const T* x, T* av,
                                                T* xv, int* pc) {
-    int cj[kUnroll];
-    T cv[kUnroll];
+    int cj[kUnroll<T>];
+    T cv[kUnroll<T>];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
+    for (int u = 0; u < kUnroll<T>; ++u) {
         const int k = c0 + threadIdx.x + u * kStreamRows;
         cj[u] = (k < c1) ? __ldg(col + k) : 0;
         cv[u] = (k < c1) ? __ldg(val + k) : T(0);
     }
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
+    for (int u = 0; u < kUnroll<T>; ++u) {
         const int k = c0 + threadIdx.x + u * kStreamRows;
         if (k < c1) {
             if constexpr (sizeof(T) == 8) { av[k - c0] = cv[u]; xv[k - c0] = x[cj[u]]; }
@@ -264,7 +269,7 @@ __global__ void __launch_bounds__(kStreamRows) k_res_stream(int n, const int* __
                                                              const T* __restrict__ b,
                                                              T* __restrict__ r,
                                                              double* __restrict__ partial) {
-    __shared__ T av[kStreamChunk];
+    __shared__ T av[kStreamChunk<T>];
     __shared__ T xv[kXv<T>];
     const int r0 = blockIdx.x * kStreamRows;
     const int row = r0 + threadIdx.x;
@@ -273,8 +278,8 @@ __global__ void __launch_bounds__(kStreamRows) k_res_stream(int n, const int* __
     int rb = 0, re = 0;
     if (row < n) { rb = __ldg(rowptr + row); re = __ldg(rowptr + row + 1); }
     T s = 0;
-    for (int c0 = tb; c0 < te; c0 += kStreamChunk) {
-        const int c1 = min(c0 + kStreamChunk, te);
+    for (int c0 = tb; c0 < te; c0 += kStreamChunk<T>) {
+        const int c1 = min(c0 + kStreamChunk<T>, te);
         stage_products<T, false>(c0, c1, col, val, x, av, xv, nullptr);
         __syncthreads();
         const int kb = max(rb, c0), ke = min(re, c1);
@@ -308,9 +313,9 @@ __global__ void __launch_bounds__(kStreamRows) k_gs_stream(int beg, int end, con
                                                             const int* __restrict__ pcol,
                                                             const T* __restrict__ pval,
                                                             const T* __restrict__ b, T* __restrict__ x) {
-    __shared__ T av[kStreamChunk];
+    __shared__ T av[kStreamChunk<T>];
     __shared__ T xv[kXv<T>];
-    __shared__ int pc[kStreamChunk];
+    __shared__ int pc[kStreamChunk<T>];
     const int t0 = beg + blockIdx.x * kStreamRows;
     const int t = t0 + threadIdx.x;
     const int tlast = min(t0 + kStreamRows, end);
@@ -318,8 +323,8 @@ __global__ void __launch_bounds__(kStreamRows) k_gs_stream(int beg, int end, con
     int rb = 0, re = 0, row = -1;
     if (t < end) { rb = __ldg(pptr + t); re = __ldg(pptr + t + 1); row = __ldg(rows + t); }
     T s = 0, d = 0;
-    for (int c0 = tb; c0 < te; c0 += kStreamChunk) {
-        const int c1 = min(c0 + kStreamChunk, te);
+    for (int c0 = tb; c0 < te; c0 += kStreamChunk<T>) {
+        const int c1 = min(c0 + kStreamChunk<T>, te);
         stage_products<T, true>(c0, c1, pcol, pval, x, av, xv, pc);
         __syncthreads();
         const int kb = max(rb, c0), ke = min(re, c1);
@@ -388,7 +393,9 @@ inline int simple_grid(int64_t n) {
         default: CALL(32); break;    \
     }
 
-bool use_stream(int32_t rows, int lpr) { return lpr <= 16 && rows >= kStreamMinRows; }
+// streaming kernels: sparse rows (a tile of 256 rows then fits about one
+// chunk) and enough rows to fill the GPU
+bool use_stream(int32_t rows, int lpr) { return lpr <= 4 && rows >= kStreamMinRows; }
 
 void residual64(cudaStream_t s, const Csr& A, const double* x, const double* b, double* r,
                 double* partial, double* norm2) {
