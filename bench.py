@@ -439,13 +439,14 @@ def summarize_launches(path):
         ki, vi = hdr.index("Kernel Name"), hdr.index("Metric Value")
         ui = hdr.index("Metric Unit")
         for r in rows:
-            name = re.sub(r"\(.*", "", r[ki]).replace("void ", "").replace("pc::<unnamed>::", "")
+            name = re.sub(r"\(.*", "", r[ki]).replace("void ", "")
+            name = re.sub(r"^(pc::)?(<unnamed>::|unnamed>::)", "", name)
             scale = {"ns": 1e-3, "usecond": 1.0, "us": 1.0, "msecond": 1e3, "ms": 1e3, "nsecond": 1e-3}.get(r[ui], 1e-3)
             by[name][0] += 1
             by[name][1] += float(r[vi].replace(",", "")) * scale
     tot = sum(t for _, t in by.values())
     n = sum(c for c, _ in by.values())
-    lines = [f"launches: {n}   total device time: {tot / 1e3:.3f} ms (cold-cache, serialised)",
+    lines = [f"launches: {n}   total device time: {tot / 1e3:.3f} ms (one launch at a time)",
              f"{'kernel':60s} {'launches':>9s} {'total ms':>10s} {'share':>7s}"]
     for k, (c, t) in sorted(by.items(), key=lambda x: -x[1][1]):
         lines.append(f"{k[:60]:60s} {c:9d} {t / 1e3:10.3f} {100 * t / tot:6.2f}%")
