@@ -6,12 +6,16 @@ backward pass and the Adam update. The paper has no learned component (its
 first hierarchy comes from a matching, Section 4); this network is the
 project's own definition and is written out here as that definition:
 
-* input features per vertex i: ``[u_i sqrt(n), log max(deg_i, 1), log max(D_i, tiny)]``
-  with u the relaxed random start vector (unit norm, zero mean), deg_i the
+* input features per vertex i: ``u_i sqrt(n)``, ``log max(deg_i, 1)`` and
+  ``log max(D_i, tiny)``, the last two minus their means over the vertices;
+  u is the relaxed random start vector (unit norm, zero mean), deg_i the
   number of off-diagonal neighbours and D_i = sum_{j != i} |a_ij|;
-* input head ``h0 = GELU(W_in f + b_in)`` (3 -> 64);
-* four layers ``h' = GELU(W_l [h ; m] + b_l)`` with the weighted neighbour mean
-  ``m_i = sum_{j != i} |a_ij| h_j / D_i`` (128 -> 64);
+* input head ``h0 = C(GELU(W_in f + b_in))`` (3 -> 64);
+* four layers ``h' = C(GELU(W_l [h ; m] + b_l))`` with the weighted neighbour
+  mean ``m_i = sum_{j != i} |a_ij| h_j / D_i`` (128 -> 64);
+* C subtracts from every channel its mean over the vertices, so activations
+  carry the variation between vertices rather than a common offset (which
+  bfloat16 activations would otherwise resolve poorly);
 * output head ``y = w_out . h + b_out`` (64 -> 1), then y minus its mean,
   divided by its 2-norm;
 * loss: for every vertex i over its candidate set C(i) (the pattern of A^2
@@ -79,20 +83,6 @@ def bf16_round(x):
     return r.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def init_params(seed=0):
-    """Seeded initial weights (uniform +-1/sqrt(fan_in), biases zero), FP32 values."""
-    rng = np.random.default_rng(seed)
-    parts = {}
-    for name, s in param_shapes():
-        if name.startswith("b"):
-            parts[name] = np.zeros(s)
-        else:
-            fan_in = s[-1] if len(s) == 2 else s[0]
-            a = 1.0 / math.sqrt(fan_in)
-            parts[name] = rng.uniform(-a, a, s)
-    return flatten(parts).astype(np.float32).astype(np.float64)
-
-
 def gelu(x):
     return 0.5 * x * (1.0 + erf(x / math.sqrt(2.0)))
 
@@ -115,9 +105,14 @@ def graph_terms(g):
 def features(g, u):
     _, D, deg = graph_terms(g)
     n = g.n
-    return np.stack([np.asarray(u, np.float64) * math.sqrt(n),
-                     np.log(np.maximum(deg, 1).astype(np.float64)),
-                     np.log(np.maximum(D, TINY))], axis=1)
+    f1 = np.log(np.maximum(deg, 1).astype(np.float64))
+    f2 = np.log(np.maximum(D, TINY))
+    return np.stack([np.asarray(u, np.float64) * math.sqrt(n), f1 - f1.mean(), f2 - f2.mean()], axis=1)
+
+
+def centre(h):
+    """Subtract every channel's mean over the vertices."""
+    return h - h.mean(axis=0)
 
 
 def neighbour_mean(g, h):
@@ -134,12 +129,12 @@ def forward(g, u, theta, keep=False):
     Dinv = 1.0 / np.maximum(D, TINY)
     F = features(g, u)
     z_in = F @ P["W_in"].T + P["b_in"]
-    h = gelu(z_in)
+    h = centre(gelu(z_in))
     hs, ms, zs = [h], [], []
     for l in range(LAYERS):
         m = (W @ h) * Dinv[:, None]
         z = np.concatenate([h, m], axis=1) @ P[f"W{l}"].T + P[f"b{l}"]
-        h = gelu(z)
+        h = centre(gelu(z))
         ms.append(m); zs.append(z); hs.append(h)
     y = h @ P["w_out"] + P["b_out"][0]
     zc = y - y.mean()
@@ -214,14 +209,14 @@ def backward(g, u, theta, ehat, cand=None):
     WT = W.T.tocsr()
     for l in reversed(range(LAYERS)):
         z, h, m = C["zs"][l], C["hs"][l], C["ms"][l]
-        dz = dh * gelu_grad(z)
+        dz = centre(dh) * gelu_grad(z)
         X = np.concatenate([h, m], axis=1)
         grads[f"W{l}"] = dz.T @ X
         grads[f"b{l}"] = dz.sum(axis=0)
         dX = dz @ P[f"W{l}"]
         dm = dX[:, HIDDEN:]
         dh = dX[:, :HIDDEN] + WT @ (dm * Dinv[:, None])
-    dz_in = dh * gelu_grad(C["z_in"])
+    dz_in = centre(dh) * gelu_grad(C["z_in"])
     grads["W_in"] = dz_in.T @ C["F"]
     grads["b_in"] = dz_in.sum(axis=0)
     return L, flatten(grads)

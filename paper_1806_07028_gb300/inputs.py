@@ -288,3 +288,19 @@ def workload(name, seed=None):
 
 WORKLOADS = ["C1", "C2", "C2-small", "C2-mid", "C3", "C3-small", "C4", "C4-small",
              "C5", "C5-small"]
+
+
+def mpnn_init_params(seed=0):
+    """Seeded initial weights of the learned start-vector network, FP32: every
+    weight matrix uniform in +-1/sqrt(fan_in), biases zero, in the flat order
+    W_in (64x3), b_in (64), [W_l (64x128), b_l (64)] x 4, w_out (64), b_out (1)."""
+    rng = np.random.default_rng(seed)
+    shapes = [((64, 3), 3), ((64,), 0)] + [((64, 128), 128), ((64,), 0)] * 4 + [((64,), 64), ((1,), 0)]
+    parts = []
+    for shape, fan_in in shapes:
+        if fan_in == 0:
+            parts.append(np.zeros(shape).ravel())
+        else:
+            a = 1.0 / np.sqrt(fan_in)
+            parts.append(rng.uniform(-a, a, shape).ravel())
+    return np.concatenate(parts).astype(np.float32)

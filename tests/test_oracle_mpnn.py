@@ -20,7 +20,7 @@ def case():
     rng = np.random.default_rng(0)
     u = _unit(rng.standard_normal(g.n))
     e = _unit(rng.standard_normal(g.n))
-    th = M.bf16_round(M.init_params(1))
+    th = M.bf16_round(I.mpnn_init_params(1).astype(np.float64))
     th[M.n_params() - 1] = 0.3           # nonzero output bias
     return g, u, e, th, M.candidate_pattern(g)
 
@@ -131,7 +131,7 @@ def test_adam_first_step_is_signed_lr():
 
 
 def test_init_and_layout():
-    th = M.init_params(3)
+    th = I.mpnn_init_params(3).astype(np.float64)
     assert th.size == M.n_params() == 33345
     assert np.array_equal(th.astype(np.float32).astype(np.float64), th)
     P = M.unflatten(th)
