@@ -57,7 +57,10 @@ typedef enum {
 } pcamg_status;
 
 enum { PCAMG_FP64 = 0, PCAMG_FP32_IR = 1 };                 /* precision */
-enum { PCAMG_START_RANDOM = 0, PCAMG_START_USER = 1 };      /* start vector */
+enum { PCAMG_START_RANDOM = 0, PCAMG_START_USER = 1, PCAMG_START_LEARNED = 2 };  /* start vector */
+
+/* A start-vector network (see the pcamg_mpnn_* calls below). */
+typedef struct pcamg_mpnn_s* pcamg_mpnn;
 enum { PCAMG_P1_E_SCALED = 0, PCAMG_P1_BOOLEAN = 1 };       /* level-1 prolongation */
 
 /* Parameters. Defaults (pcamg_default_params) follow Section 4 of the paper:
@@ -80,7 +83,9 @@ typedef struct {
     int32_t round_cap;     /* leftover rounds before the sequential tail (Alg. 3) */
     int32_t p1_mode;       /* PCAMG_P1_*: level-1 prolongation carries e or is boolean */
     int32_t precision;     /* PCAMG_FP64 or PCAMG_FP32_IR */
-    int32_t start;         /* PCAMG_START_RANDOM or PCAMG_START_USER (d_e0 given) */
+    int32_t start;         /* PCAMG_START_RANDOM, PCAMG_START_USER (d_e0 given) or
+                              PCAMG_START_LEARNED (the network `mpnn` maps the relaxed
+                              random start and the graph's degrees to the start vector) */
     int32_t dense_max;     /* largest coarsest level factorised densely (<= 4096) */
     int32_t use_graphs;    /* capture each cycle in a CUDA graph and replay it */
     int32_t keep_setup;    /* keep covers and reweighted graphs for export */
@@ -98,6 +103,11 @@ typedef struct {
                               recursing through them. Same result up to rounding; used
                               when the tail has two or more levels and its vectors fit
                               one block's shared memory, else the recursion runs. */
+    int32_t max_resetups;  /* pcamg_solve builds at most this many new hierarchies and
+                              stops (PCAMG_ERR_NOT_CONVERGED) right after the last one,
+                              or instead of one more; -1 = no limit. Used to collect
+                              the first smooth error of a run (training data). */
+    pcamg_mpnn mpnn;       /* the network for PCAMG_START_LEARNED, else NULL */
 } pcamg_params;
 
 typedef struct {
@@ -210,6 +220,51 @@ PCAMG_API int64_t pcamg_kernel_launches(void);
 PCAMG_API const char* pcamg_last_error(pcamg_handle h);
 PCAMG_API const char* pcamg_status_string(pcamg_status s);
 PCAMG_API void pcamg_destroy(pcamg_handle h);
+
+/* The normalised smooth error (zero mean, unit 2-norm) from which the newest
+ * hierarchy of h was built (the start vector after pcamg_setup, the Alg. 2
+ * output after a re-setup). d_e: device, length n. */
+PCAMG_API pcamg_status pcamg_last_smooth_error(pcamg_handle h, double* d_e);
+
+/* ---- learned start vector ------------------------------------------------
+ * The paper has no learned component; this network is the library's own. It
+ * maps per-vertex features -- the relaxed random start u (times sqrt(n)), log
+ * degree and log weighted degree D_i = sum_{j != i} |a_ij| (both minus their
+ * means over the vertices) -- through an input layer (3 -> 64), four
+ * message-passing layers h' = C(GELU(W_l [h ; m] + b_l)) with the weighted
+ * neighbour mean m_i = sum_{j != i} |a_ij| h_j / D_i (128 -> 64), C removing
+ * every channel's mean over the vertices, and a linear output (64 -> 1) to y;
+ * the start vector is (y - mean y) / ||y - mean y||. Weights are applied
+ * rounded to bfloat16, the layer products on the tensor cores with FP32
+ * accumulation. Training minimises, per vertex over its A^2 candidate pairs,
+ * the cross-entropy between the softmax of -|e_i - e_j|/tau_i of a target
+ * smooth error e and that of the prediction (tau_i: standard deviation of
+ * |e_i - e_j| over the pairs), with Adam on FP32 master weights.
+ * Parameters: a flat FP32 vector of pcamg_mpnn_num_params() entries in the
+ * order W_in (64x3 row-major), b_in, then per layer W_l (64x128 row-major,
+ * columns 0-63 act on h, 64-127 on m) and b_l, then w_out (64), b_out (1).
+ * All calls are synchronous; the network owns its device memory. */
+PCAMG_API int64_t pcamg_mpnn_num_params(void);
+/* New network with the given host parameters (Adam state zero). */
+PCAMG_API pcamg_status pcamg_mpnn_create(pcamg_mpnn* out, const float* h_params);
+PCAMG_API void pcamg_mpnn_destroy(pcamg_mpnn m);
+PCAMG_API pcamg_status pcamg_mpnn_get_params(pcamg_mpnn m, float* h_params);
+/* Replace the parameters and reset the Adam state. */
+PCAMG_API pcamg_status pcamg_mpnn_set_params(pcamg_mpnn m, const float* h_params);
+/* The gradient of the last pcamg_mpnn_loss_grad call (host, num_params). */
+PCAMG_API pcamg_status pcamg_mpnn_get_grad(pcamg_mpnn m, float* h_grad);
+/* The network's start vector on the graph of g: d_u is the relaxed random
+ * start (pcamg_start_vector), d_y receives the output (device, length n). */
+PCAMG_API pcamg_status pcamg_mpnn_forward(pcamg_mpnn m, pcamg_handle g, const double* d_u, double* d_y);
+/* Loss against the target smooth error d_target (device, zero mean, unit norm)
+ * into *h_loss, and its gradient kept in the network for pcamg_mpnn_adam_step. */
+PCAMG_API pcamg_status pcamg_mpnn_loss_grad(pcamg_mpnn m, pcamg_handle g, const double* d_u,
+                                            const double* d_target, double* h_loss);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) with learning rate lr. */
+PCAMG_API pcamg_status pcamg_mpnn_adam_step(pcamg_mpnn m, float lr);
+/* Save / load: one JSON header line, then the FP32 parameters, little-endian. */
+PCAMG_API pcamg_status pcamg_mpnn_save(pcamg_mpnn m, const char* path);
+PCAMG_API pcamg_status pcamg_mpnn_load(pcamg_mpnn* out, const char* path);
 
 /* ---- single kernels, for measurement and parity tests -------------------- */
 /* r = b - A x (FP64), optionally ||r||_2^2 into *d_norm2 (device scalar, may be

@@ -1,6 +1,7 @@
 // C ABI of the library (see include/pcamg.h): argument checks, CSR validation,
 // handle life cycle, and error translation (no exception crosses the ABI).
 #include <algorithm>
+#include <cstdio>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -91,7 +92,8 @@ void check_params(const pcamg_params& p) {
         p.max_levels < 1 || p.max_levels > kMaxLevels || p.round_cap < 0 ||
         (p.p1_mode != PCAMG_P1_E_SCALED && p.p1_mode != PCAMG_P1_BOOLEAN) ||
         (p.precision != PCAMG_FP64 && p.precision != PCAMG_FP32_IR) ||
-        (p.start != PCAMG_START_RANDOM && p.start != PCAMG_START_USER) || p.dense_max < 1 ||
+        (p.start != PCAMG_START_RANDOM && p.start != PCAMG_START_USER && p.start != PCAMG_START_LEARNED) ||
+        (p.start == PCAMG_START_LEARNED && !p.mpnn) || p.max_resetups < -1 || p.dense_max < 1 ||
         p.dense_max > 4096 || p.tail_rows < 0 || p.l1jac_rows < 0 || p.tail_dense < 0 ||
         p.tail_dense > 3)
         fail(PCAMG_ERR_INVALID, "invalid parameters");
@@ -201,6 +203,8 @@ PCAMG_API pcamg_status pcamg_default_params(pcamg_params* p) {
     p->tail_rows = 2048;
     p->l1jac_rows = 2147483647;
     p->tail_dense = 2;
+    p->max_resetups = -1;
+    p->mpnn = nullptr;
     return PCAMG_OK;
 }
 
@@ -256,10 +260,14 @@ PCAMG_API pcamg_status pcamg_setup(pcamg_handle* out, const pcamg_params* p, int
         if (c->p.start == PCAMG_START_USER) {
             check_finite(*c, d_e0, n, "start vector");
             copy(c->stream, n, d_e0, c->w_e.p);
+        } else if (c->p.start == PCAMG_START_LEARNED) {
+            start_vector(*c, c->w_t2.p);
+            mpnn_forward(*c, *reinterpret_cast<pc::Mpnn*>(c->p.mpnn), c->w_t2.p, c->w_e.p);
         } else {
             start_vector(*c, c->w_e.p);
         }
         c->hist.push_back(build_hierarchy(*c, c->w_e.p));
+        c->last_e = c->w_e.p;
         sync(*c);
         return PCAMG_OK;
     });
@@ -275,6 +283,7 @@ PCAMG_API pcamg_status pcamg_adapt(pcamg_handle h, const double* d_e) {
         check_finite(*h, d_e, h->n, "smooth error");
         copy(h->stream, h->n, d_e, h->w_eh.p);
         h->hist.push_back(build_hierarchy(*h, h->w_eh.p));
+        h->last_e = h->w_eh.p;
         return PCAMG_OK;
     });
 }
@@ -365,6 +374,137 @@ PCAMG_API pcamg_status pcamg_start_vector(pcamg_handle h, double* d_e) {
         Enter guard(*h);
         start_vector(*h, d_e);
         sync(*h);
+        return PCAMG_OK;
+    });
+}
+
+PCAMG_API pcamg_status pcamg_last_smooth_error(pcamg_handle h, double* d_e) {
+    if (!h || !d_e) return set_err(h, PCAMG_ERR_INVALID, "null argument");
+    return guarded(h, [&]() -> pcamg_status {
+        if (!h->last_e) fail(PCAMG_ERR_INVALID, "no hierarchy built");
+        Enter guard(*h);
+        copy(h->stream, h->n, h->last_e, d_e);
+        sync(*h);
+        return PCAMG_OK;
+    });
+}
+
+// ---- learned start vector
+static void check_params_finite(const float* w) {
+    for (int64_t i = 0; i < kMpnnParams; ++i)
+        if (!std::isfinite(w[i])) fail(PCAMG_ERR_INVALID, "mpnn parameters are not finite");
+}
+
+PCAMG_API int64_t pcamg_mpnn_num_params(void) { return kMpnnParams; }
+
+PCAMG_API pcamg_status pcamg_mpnn_create(pcamg_mpnn* out, const float* h_params) {
+    if (!out || !h_params) return set_err(nullptr, PCAMG_ERR_INVALID, "null argument");
+    *out = nullptr;
+    return guarded(nullptr, [&]() -> pcamg_status {
+        check_params_finite(h_params);
+        *out = reinterpret_cast<pcamg_mpnn>(mpnn_create(h_params));
+        return PCAMG_OK;
+    });
+}
+
+PCAMG_API void pcamg_mpnn_destroy(pcamg_mpnn m) { mpnn_destroy(reinterpret_cast<pc::Mpnn*>(m)); }
+
+PCAMG_API pcamg_status pcamg_mpnn_get_params(pcamg_mpnn m, float* h_params) {
+    if (!m || !h_params) return set_err(nullptr, PCAMG_ERR_INVALID, "null argument");
+    return guarded(nullptr, [&]() -> pcamg_status {
+        mpnn_get_params(*reinterpret_cast<pc::Mpnn*>(m), h_params);
+        return PCAMG_OK;
+    });
+}
+
+PCAMG_API pcamg_status pcamg_mpnn_set_params(pcamg_mpnn m, const float* h_params) {
+    if (!m || !h_params) return set_err(nullptr, PCAMG_ERR_INVALID, "null argument");
+    return guarded(nullptr, [&]() -> pcamg_status {
+        check_params_finite(h_params);
+        mpnn_set_params(*reinterpret_cast<pc::Mpnn*>(m), h_params);
+        return PCAMG_OK;
+    });
+}
+
+PCAMG_API pcamg_status pcamg_mpnn_get_grad(pcamg_mpnn m, float* h_grad) {
+    if (!m || !h_grad) return set_err(nullptr, PCAMG_ERR_INVALID, "null argument");
+    return guarded(nullptr, [&]() -> pcamg_status {
+        mpnn_get_grad(*reinterpret_cast<pc::Mpnn*>(m), h_grad);
+        return PCAMG_OK;
+    });
+}
+
+PCAMG_API pcamg_status pcamg_mpnn_forward(pcamg_mpnn m, pcamg_handle g, const double* d_u, double* d_y) {
+    if (!m || !g || !d_u || !d_y) return set_err(g, PCAMG_ERR_INVALID, "null argument");
+    return guarded(g, [&]() -> pcamg_status {
+        Enter guard(*g);
+        mpnn_forward(*g, *reinterpret_cast<pc::Mpnn*>(m), d_u, d_y);
+        return PCAMG_OK;
+    });
+}
+
+PCAMG_API pcamg_status pcamg_mpnn_loss_grad(pcamg_mpnn m, pcamg_handle g, const double* d_u,
+                                            const double* d_target, double* h_loss) {
+    if (!m || !g || !d_u || !d_target || !h_loss) return set_err(g, PCAMG_ERR_INVALID, "null argument");
+    return guarded(g, [&]() -> pcamg_status {
+        Enter guard(*g);
+        *h_loss = mpnn_loss_grad(*g, *reinterpret_cast<pc::Mpnn*>(m), d_u, d_target);
+        return PCAMG_OK;
+    });
+}
+
+PCAMG_API pcamg_status pcamg_mpnn_adam_step(pcamg_mpnn m, float lr) {
+    if (!m || !(lr > 0.0f) || !std::isfinite(lr)) return set_err(nullptr, PCAMG_ERR_INVALID, "invalid argument");
+    return guarded(nullptr, [&]() -> pcamg_status {
+        mpnn_adam(*reinterpret_cast<pc::Mpnn*>(m), lr);
+        return PCAMG_OK;
+    });
+}
+
+static const char kMpnnHead[] = "{\"format\": \"pcamg-mpnn\", \"version\": 1, \"dtype\": \"f32-le\", \"params\": ";
+
+static bool little_endian() {
+    const uint32_t one = 1;
+    unsigned char b;
+    std::memcpy(&b, &one, 1);
+    return b == 1;
+}
+
+static std::string mpnn_header() { return std::string(kMpnnHead) + std::to_string((long long)kMpnnParams) + "}\n"; }
+
+PCAMG_API pcamg_status pcamg_mpnn_save(pcamg_mpnn m, const char* path) {
+    if (!m || !path) return set_err(nullptr, PCAMG_ERR_INVALID, "null argument");
+    return guarded(nullptr, [&]() -> pcamg_status {
+        if (!little_endian()) fail(PCAMG_ERR_UNSUPPORTED, "mpnn files are little-endian");
+        std::vector<float> w(kMpnnParams);
+        mpnn_get_params(*reinterpret_cast<pc::Mpnn*>(m), w.data());
+        FILE* f = std::fopen(path, "wb");
+        if (!f) fail(PCAMG_ERR_INVALID, "cannot open file for writing");
+        const std::string head = mpnn_header();
+        bool ok = std::fwrite(head.data(), 1, head.size(), f) == head.size() &&
+                  std::fwrite(w.data(), sizeof(float), w.size(), f) == w.size();
+        ok = (std::fclose(f) == 0) && ok;
+        if (!ok) fail(PCAMG_ERR_INVALID, "write failed");
+        return PCAMG_OK;
+    });
+}
+
+PCAMG_API pcamg_status pcamg_mpnn_load(pcamg_mpnn* out, const char* path) {
+    if (!out || !path) return set_err(nullptr, PCAMG_ERR_INVALID, "null argument");
+    *out = nullptr;
+    return guarded(nullptr, [&]() -> pcamg_status {
+        if (!little_endian()) fail(PCAMG_ERR_UNSUPPORTED, "mpnn files are little-endian");
+        FILE* f = std::fopen(path, "rb");
+        if (!f) fail(PCAMG_ERR_INVALID, "cannot open file");
+        const std::string head = mpnn_header();
+        std::string got(head.size(), '\0');
+        std::vector<float> w(kMpnnParams);
+        bool ok = std::fread(&got[0], 1, got.size(), f) == got.size() && got == head &&
+                  std::fread(w.data(), sizeof(float), w.size(), f) == w.size();
+        std::fclose(f);
+        if (!ok) fail(PCAMG_ERR_INVALID, "not a pcamg-mpnn file of this layout");
+        check_params_finite(w.data());
+        *out = reinterpret_cast<pcamg_mpnn>(mpnn_create(w.data()));
         return PCAMG_OK;
     });
 }

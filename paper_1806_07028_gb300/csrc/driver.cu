@@ -94,6 +94,10 @@ enum Slot { S_T0 = 0, S_T1, S_T2, S_NORM2, S_RZ, S_PQ, S_ALPHA, S_NUM, S_BETA, S
 static double* slot(Ctx& c, int k) { return c.red.p + c.npartials + k; }
 static double* partials(Ctx& c) { return c.red.p; }
 
+double* red_partials(Ctx& c) { return partials(c); }
+double* mpnn_slots(Ctx& c) { return slot(c, 32); }
+const double* norm_slot(Ctx& c) { return slot(c, S_T1); }
+
 void normalise_orth(Ctx& c, const double* e, double* out) {
     cudaStream_t s = c.stream;
     if (out != e) copy(s, c.n, e, out);
@@ -400,6 +404,7 @@ static void rebuild(Ctx& c, double* e_raw_out) {
     double t1 = now_ms();
     Hier* h = build_hierarchy(c, c.w_eh.p);
     c.hist.push_back(h);
+    c.last_e = c.w_eh.p;
     c.t_alg2 += t1 - t0;
     c.t_alg4 += now_ms() - t1;
 }
@@ -442,6 +447,7 @@ pcamg_status solve(Ctx& c, const double* b, double* x, pcamg_stats* st) {
         hist_put(k, res / bn);
         if (res / bn <= c.p.tol) break;
         if (wsum / (double)wcnt > c.p.threshold) {
+            if (c.p.max_resetups >= 0 && (int32_t)c.hist.size() - re0 >= c.p.max_resetups) break;
             double ts = now_ms();
             rebuild(c, c.w_e.p);
             axpy(s, c.n, 1.0, c.w_e.p, x);
@@ -452,6 +458,7 @@ pcamg_status solve(Ctx& c, const double* b, double* x, pcamg_stats* st) {
             wsum = 0.0;
             wcnt = 0;
             t_setup += now_ms() - ts;
+            if (c.p.max_resetups >= 0 && (int32_t)c.hist.size() - re0 >= c.p.max_resetups) break;
         }
     }
     if (status == PCAMG_OK && !(res / bn <= c.p.tol)) status = PCAMG_ERR_NOT_CONVERGED;
@@ -512,6 +519,7 @@ pcamg_status solve_zero_rhs(Ctx& c, double* x, pcamg_stats* st) {
                 normalise_orth(c, x, c.w_eh.p);
                 Hier* h = build_hierarchy(c, c.w_eh.p);
                 c.hist.push_back(h);
+                c.last_e = c.w_eh.p;
                 t_setup += now_ms() - ts;
             }
         }

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -181,6 +182,8 @@ struct OwnedStream {
     }
 };
 
+struct Reweighted;
+
 struct Ctx {
     pcamg_params p{};
     OwnedStream own;
@@ -212,6 +215,8 @@ struct Ctx {
     double prof_ms = 0.0;
     int64_t ncycles = 0;
     double t_alg2 = 0.0, t_alg4 = 0.0;
+    const double* last_e = nullptr;          // normalised error of the newest hierarchy
+    std::unique_ptr<Reweighted> mpnn_cand;   // A^2 candidate pattern for the network's loss
     ~Ctx();
 };
 
@@ -300,6 +305,23 @@ void start_vector(Ctx& c, double* e);
 pcamg_status solve(Ctx& c, const double* b, double* x, pcamg_stats* st);
 pcamg_status solve_zero_rhs(Ctx& c, double* x, pcamg_stats* st);
 void normalise_orth(Ctx& c, const double* e, double* out);  // (e - mean)/||e - mean||
+double* red_partials(Ctx& c);        // reduction partials of the context
+double* mpnn_slots(Ctx& c);          // 8 device scalars for the network's reductions
+const double* norm_slot(Ctx& c);     // ||e - mean|| of the last normalise_orth
+
+// learned start vector (k_mpnn.cu)
+constexpr int kMpnnHidden = 64;
+constexpr int kMpnnLayers = 4;
+constexpr int kMpnnParams = 64 * 3 + 64 + 4 * (64 * 128 + 64) + 64 + 1;   // 33345
+struct Mpnn;
+Mpnn* mpnn_create(const float* h_params);
+void mpnn_destroy(Mpnn* m);
+void mpnn_set_params(Mpnn& m, const float* h_params);   // also resets the Adam state
+void mpnn_get_params(Mpnn& m, float* h_params);
+void mpnn_get_grad(Mpnn& m, float* h_grad);
+void mpnn_forward(Ctx& c, Mpnn& m, const double* u, double* yhat);
+double mpnn_loss_grad(Ctx& c, Mpnn& m, const double* u, const double* target);  // gradient kept in m
+void mpnn_adam(Mpnn& m, float lr);
 
 // small helpers
 template <class T>

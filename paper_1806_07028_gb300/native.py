@@ -18,7 +18,7 @@ _lib = None
 OK, ERR_INVALID, ERR_NOT_LAPLACIAN, ERR_OOM, ERR_CUDA, ERR_ROUND_CAP, ERR_SINGULAR, \
     ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_COARSE_TOO_BIG, ERR_UNSUPPORTED = range(11)
 FP64, FP32_IR = 0, 1
-START_RANDOM, START_USER = 0, 1
+START_RANDOM, START_USER, START_LEARNED = 0, 1, 2
 P1_E_SCALED, P1_BOOLEAN = 0, 1
 
 # every entry point of include/pcamg.h
@@ -28,7 +28,10 @@ EXPORTS = [
     "pcamg_num_hierarchies", "pcamg_num_levels", "pcamg_level_sizes", "pcamg_export_level",
     "pcamg_export_reweighted", "pcamg_last_error", "pcamg_status_string", "pcamg_destroy",
     "pcamg_residual", "pcamg_residual_f32", "pcamg_uniform", "pcamg_colour",
-    "pcamg_kernel_launches", "pcamg_residual_noalloc",
+    "pcamg_kernel_launches", "pcamg_residual_noalloc", "pcamg_last_smooth_error",
+    "pcamg_mpnn_num_params", "pcamg_mpnn_create", "pcamg_mpnn_destroy", "pcamg_mpnn_get_params",
+    "pcamg_mpnn_set_params", "pcamg_mpnn_get_grad", "pcamg_mpnn_forward", "pcamg_mpnn_loss_grad",
+    "pcamg_mpnn_adam_step", "pcamg_mpnn_save", "pcamg_mpnn_load",
 ]
 
 
@@ -50,7 +53,8 @@ class Params(C.Structure):
                 ("round_cap", C.c_int32), ("p1_mode", C.c_int32), ("precision", C.c_int32),
                 ("start", C.c_int32), ("dense_max", C.c_int32), ("use_graphs", C.c_int32),
                 ("keep_setup", C.c_int32), ("profile", C.c_int32), ("tail_rows", C.c_int32),
-                ("l1jac_rows", C.c_int32), ("tail_dense", C.c_int32)]
+                ("l1jac_rows", C.c_int32), ("tail_dense", C.c_int32), ("max_resetups", C.c_int32),
+                ("mpnn", C.c_void_p)]
 
 
 class Stats(C.Structure):
@@ -97,6 +101,18 @@ def lib():
                 "pcamg_colour": ([i32, vp, vp, u64, vp, P(i32), vp], i32),
                 "pcamg_kernel_launches": ([], i64),
                 "pcamg_residual_noalloc": ([i32, vp, vp, vp, vp, vp, vp, vp, vp], i32),
+                "pcamg_last_smooth_error": ([vp, vp], i32),
+                "pcamg_mpnn_num_params": ([], i64),
+                "pcamg_mpnn_create": ([P(vp), vp], i32),
+                "pcamg_mpnn_destroy": ([vp], None),
+                "pcamg_mpnn_get_params": ([vp, vp], i32),
+                "pcamg_mpnn_set_params": ([vp, vp], i32),
+                "pcamg_mpnn_get_grad": ([vp, vp], i32),
+                "pcamg_mpnn_forward": ([vp, vp, vp, vp], i32),
+                "pcamg_mpnn_loss_grad": ([vp, vp, vp, vp, P(dbl)], i32),
+                "pcamg_mpnn_adam_step": ([vp, C.c_float], i32),
+                "pcamg_mpnn_save": ([vp, C.c_char_p], i32),
+                "pcamg_mpnn_load": ([P(vp), C.c_char_p], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)

@@ -58,12 +58,15 @@ class Solver:
     """A handle of the library bound to one CSR Laplacian on one GPU."""
 
     def __init__(self, graph, params: N.Params | None = None, e0=None, device="cuda:0",
-                 stream=None):
+                 stream=None, mpnn=None):
         torch = _torch()
         self.device = torch.device(device)
         self.params = params if params is not None else default_params()
         if e0 is not None:
             self.params.start = N.START_USER
+        if mpnn is not None:           # learned start vector
+            self.params.start = N.START_LEARNED
+            self.params.mpnn = mpnn._h
         self.n = int(graph.n)
         self.nnz = int(graph.nnz)
         with torch.cuda.device(self.device):
@@ -160,6 +163,14 @@ class Solver:
         with torch.cuda.device(self.device):
             et = torch.empty(self.n, dtype=torch.float64, device=self.device)
             N.check(N.lib().pcamg_start_vector(self._h, _ptr(et)), self._h)
+            return et
+
+    def last_smooth_error(self):
+        """The normalised error the newest hierarchy was built from."""
+        torch = _torch()
+        with torch.cuda.device(self.device):
+            et = torch.empty(self.n, dtype=torch.float64, device=self.device)
+            N.check(N.lib().pcamg_last_smooth_error(self._h, _ptr(et)), self._h)
             return et
 
     # -- inspection -----------------------------------------------------------
@@ -263,3 +274,131 @@ def solve_host(graph, b, x0=None, params=None):
     if status not in (N.OK, N.ERR_NOT_CONVERGED):
         N.check(status)
     return x, _stats_dict(st, None)
+
+
+class Mpnn:
+    """The learned start-vector network (see include/pcamg.h): parameters live
+    on the GPU; forward, loss gradient and Adam run in the library's kernels."""
+
+    def __init__(self, params=None, seed=0, _handle=None):
+        if _handle is not None:
+            self._h = _handle
+            return
+        if params is None:
+            from .inputs import mpnn_init_params
+            params = mpnn_init_params(seed)
+        w = np.ascontiguousarray(params, dtype=np.float32)
+        if w.size != self.num_params():
+            raise ValueError(f"expected {self.num_params()} parameters, got {w.size}")
+        h = C.c_void_p()
+        N.check(N.lib().pcamg_mpnn_create(C.byref(h), w.ctypes.data_as(C.c_void_p)))
+        self._h = h
+
+    @staticmethod
+    def num_params():
+        return int(N.lib().pcamg_mpnn_num_params())
+
+    @classmethod
+    def load(cls, path):
+        h = C.c_void_p()
+        N.check(N.lib().pcamg_mpnn_load(C.byref(h), str(path).encode()))
+        return cls(_handle=h)
+
+    def save(self, path):
+        N.check(N.lib().pcamg_mpnn_save(self._h, str(path).encode()))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            N.lib().pcamg_mpnn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def params(self):
+        w = np.empty(self.num_params(), dtype=np.float32)
+        N.check(N.lib().pcamg_mpnn_get_params(self._h, w.ctypes.data_as(C.c_void_p)))
+        return w
+
+    @params.setter
+    def params(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        N.check(N.lib().pcamg_mpnn_set_params(self._h, w.ctypes.data_as(C.c_void_p)))
+
+    def grad(self):
+        g = np.empty(self.num_params(), dtype=np.float32)
+        N.check(N.lib().pcamg_mpnn_get_grad(self._h, g.ctypes.data_as(C.c_void_p)))
+        return g
+
+    def forward(self, solver, u):
+        """The network's start vector on solver's graph from the relaxed random start u."""
+        torch = _torch()
+        with torch.cuda.device(solver.device):
+            ut = _dev(u, torch.float64, solver.device)
+            yt = torch.empty(solver.n, dtype=torch.float64, device=solver.device)
+            N.check(N.lib().pcamg_mpnn_forward(self._h, solver._h, _ptr(ut), _ptr(yt)), solver._h)
+            return yt
+
+    def loss_grad(self, solver, u, target):
+        """Loss against the target smooth error; the gradient stays in the network."""
+        torch = _torch()
+        with torch.cuda.device(solver.device):
+            ut = _dev(u, torch.float64, solver.device)
+            tt = _dev(target, torch.float64, solver.device)
+            L = C.c_double(0.0)
+            N.check(N.lib().pcamg_mpnn_loss_grad(self._h, solver._h, _ptr(ut), _ptr(tt), C.byref(L)),
+                    solver._h)
+            return float(L.value)
+
+    def adam_step(self, lr=1e-3):
+        N.check(N.lib().pcamg_mpnn_adam_step(self._h, C.c_float(lr)))
+
+
+def training_example(graph, seed=0, params=None):
+    """One training example of the learned start: a solver bound to the graph
+    (kept for the loss's A^2 pattern), the relaxed random start u, and the
+    target -- the first Alg. 2 smooth error of a plain run (right-hand side
+    N(0,1) minus its mean, stopped right after the first re-setup). Returns
+    None when the plain run converged without a re-setup."""
+    from .inputs import rhs_normal
+    p = params if params is not None else default_params()
+    p.max_resetups = 1
+    s = Solver(graph, params=p)
+    _, st = s.solve(rhs_normal(graph.n, seed), raise_on_error=False)
+    if st["resetups"] < 1:
+        s.close()
+        return None
+    return s, s.start_vector(), s.last_smooth_error()
+
+
+def train(net, examples, epochs=10, lr=1e-3):
+    """Adam over the examples, one step per example per epoch; returns the mean
+    loss of every epoch."""
+    hist = []
+    for _ in range(epochs):
+        tot = 0.0
+        for s, u, t in examples:
+            tot += net.loss_grad(s, u, t)
+            net.adam_step(lr)
+        hist.append(tot / max(1, len(examples)))
+    return hist
+
+
+def first_cycles(graph, mpnn=None, e0=None, cycles=5, seed=0, params=None):
+    """Convergence factors ||r_k|| / ||r_{k-1}|| of the first V-cycles on the
+    first hierarchy (no re-setup), from the relaxed random start, the learned
+    start (mpnn) or a given start vector (e0)."""
+    from .inputs import rhs_normal
+    p = params if params is not None else default_params()
+    p.threshold = 1e30
+    p.max_iter = cycles
+    p.tol = 1e-300
+    s = Solver(graph, params=p, mpnn=mpnn, e0=e0)
+    _, st = s.solve(rhs_normal(graph.n, seed), raise_on_error=False)
+    s.close()
+    h = st["res_hist"]
+    return h[1:] / h[:-1]

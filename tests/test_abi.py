@@ -54,6 +54,6 @@ def test_struct_layout_matches_header(built):
     src = open(os.path.join(ROOT, "include", "pcamg.h")).read()
     body = re.search(r"typedef struct \{(.*?)\} pcamg_params;", src, re.S).group(1)
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
-    fields = re.findall(r"\b(?:double|int32_t|uint64_t)\s+([\w\s,]+);", body)
+    fields = re.findall(r"\b(?:double|int32_t|uint64_t|pcamg_mpnn)\s+([\w\s,]+);", body)
     names = [f.strip() for grp in fields for f in grp.split(",")]
     assert names == [f for f, _ in N.Params._fields_]
