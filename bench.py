@@ -40,7 +40,7 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="C2")
-    ap.add_argument("--form", default="fp32ir", choices=["fp32ir", "fp64"])
+    ap.add_argument("--form", default="fp32ir", choices=["fp32ir", "fp64", "fp32ir+learned"])
     ap.add_argument("--no-extras", action="store_true", help="skip fp64 form, e2e and oracle legs")
     ap.add_argument("--only-kernel", default=None, choices=["residual64", "vcycle", "wcycle", "adapt"],
                     help="time one kernel alone on the workload (used for ncu captures)")
@@ -156,10 +156,20 @@ def run_ours(a):
     b_host = I.rhs_normal(g.n, 11 + rank)
     dg = _device_graph(g, dev)
     b = torch.as_tensor(b_host, device=dev)
-    prec = 1 if a.form == "fp32ir" else 0
+    prec = 0 if a.form == "fp64" else 1
+    nets = {}
 
-    def step(form_prec, profile=0):
-        s = Solver(dg, params=default_params(precision=form_prec, profile=profile), device=dev)
+    def step(form, profile=0):
+        """One solve in a form: fp64, fp32ir, or fp32ir+learned (the shipped
+        start-vector network, its forward inside the setup)."""
+        p = default_params(precision=0 if form == "fp64" else 1, profile=profile)
+        net = None
+        if form.endswith("+learned"):
+            if "net" not in nets:
+                from paper_1806_07028_gb300 import Mpnn
+                nets["net"] = Mpnn.pretrained()
+            net = nets["net"]
+        s = Solver(dg, params=p, device=dev, mpnn=net)
         x, st = s.solve(b)
         s.close()
         return x, st
@@ -170,7 +180,7 @@ def run_ours(a):
             dist.barrier()
 
     for _ in range(a.warmup):
-        step(prec, profile=1)
+        step(a.form, profile=1)
     torch.cuda.synchronize()
     barrier()
     clocks = Clocks(local)
@@ -182,7 +192,7 @@ def run_ours(a):
     ev0.record()
     stats = []
     for _ in range(a.steps):
-        x, st = step(prec, profile=1)
+        x, st = step(a.form, profile=1)
         stats.append(st)
     ev1.record()
     torch.cuda.synchronize()
@@ -213,7 +223,8 @@ def run_ours(a):
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32 cycles in f64 refinement" if prec else "f64",
+           "vs_baseline": None, "dtype": ("f64" if not prec else "f32 cycles in f64 refinement" +
+                     (", bf16 tensor-core start network" if a.form.endswith("+learned") else "")),
            "data": "synthetic (seeded generator, same recipe as the configuration)",
            "config": {"workload": WORKLOAD, "n": g.n, "nnz": g.nnz, "form": a.form,
                       "tol": 1e-8, "parallelism": "replicas" if world > 1 else "single GPU",
@@ -226,20 +237,22 @@ def run_ours(a):
            "roofline": roofline, "clocks": clk, "gpu_launches": int(launches)}
 
     if not a.no_extras and rank == 0:
-        # the other form, same graph and b
-        other = 0 if prec else 1
-        step(other)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        _, st2 = step(other)
-        e1.record()
-        torch.cuda.synchronize()
-        ms2 = e0.elapsed_time(e1)
-        out["forms"] = {a.form: {"ms": ms, "unknowns_per_s": g.n / (ms / 1e3)},
-                        ("fp64" if other == 0 else "fp32ir"): {
-                            "ms": ms2, "unknowns_per_s": g.n / (ms2 / 1e3), "iters": st2["iters"],
-                            "resetups": st2["resetups"]}}
+        # the other forms, same graph and b (one warm-up solve, one timed)
+        out["forms"] = {a.form: {"ms": ms, "unknowns_per_s": g.n / (ms / 1e3), "iters": stats[-1]["iters"],
+                                 "resetups": stats[-1]["resetups"]}}
+        for other in ("fp64", "fp32ir", "fp32ir+learned"):
+            if other == a.form:
+                continue
+            step(other)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, st2 = step(other)
+            e1.record()
+            torch.cuda.synchronize()
+            ms2 = e0.elapsed_time(e1)
+            out["forms"][other] = {"ms": ms2, "unknowns_per_s": g.n / (ms2 / 1e3), "iters": st2["iters"],
+                                   "resetups": st2["resetups"]}
         # end to end through the public host-buffer call: pinned host inputs,
         # H2D of A, b, x and D2H of x inside the timed region
         rp = torch.as_tensor(g.rowptr).pin_memory().numpy()
@@ -251,10 +264,15 @@ def run_ours(a):
             pass
         hg = HG()
         hg.n, hg.nnz, hg.rowptr, hg.col, hg.val = g.n, g.nnz, rp, ci, va
-        solve_host(hg, bh, params=default_params(precision=prec))
+        def host_params():
+            hp = default_params(precision=prec)
+            if a.form.endswith("+learned"):
+                hp.start, hp.mpnn = N.START_LEARNED, nets["net"]._h
+            return hp
+        solve_host(hg, bh, params=host_params())
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        xe, ste = solve_host(hg, bh, params=default_params(precision=prec))
+        xe, ste = solve_host(hg, bh, params=host_params())
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
         h2d = rp.nbytes + ci.nbytes + va.nbytes + bh.nbytes + 8 * g.n
@@ -363,7 +381,7 @@ def run_kernel(a):
     if a.only_kernel == "adapt":
         from paper_1806_07028_gb300 import Solver, default_params, inputs as I
         g = I.workload(a.workload)
-        prec = 1 if a.form == "fp32ir" else 0
+        prec = 0 if a.form == "fp64" else 1
         dev = torch.device("cuda", 0)
         s = Solver(_device_graph(g, dev), params=default_params(precision=prec), device=dev)
         e = s.start_vector()
@@ -381,7 +399,7 @@ def run_kernel(a):
     if a.only_kernel in ("vcycle", "wcycle"):
         from paper_1806_07028_gb300 import Solver, default_params, inputs as I
         g = I.workload(a.workload)
-        prec = 1 if a.form == "fp32ir" else 0
+        prec = 0 if a.form == "fp64" else 1
         dev = torch.device("cuda", 0)
         s = Solver(_device_graph(g, dev), params=default_params(precision=prec), device=dev)
         r = torch.as_tensor(I.rhs_normal(g.n, 3), device=dev)

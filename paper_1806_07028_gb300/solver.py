@@ -299,6 +299,14 @@ class Mpnn:
         return int(N.lib().pcamg_mpnn_num_params())
 
     @classmethod
+    def pretrained(cls):
+        """The network shipped with the package: trained by train_mpnn on 200
+        seeded random geometric graphs (n 10k-100k), 30 epochs."""
+        import os
+        return cls.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights",
+                                     "mpnn_rgg200.mpnn"))
+
+    @classmethod
     def load(cls, path):
         h = C.c_void_p()
         N.check(N.lib().pcamg_mpnn_load(C.byref(h), str(path).encode()))

@@ -157,3 +157,19 @@ def test_training_example_and_loss_decrease(P):
     assert hist[-1] < hist[0]
     s.close()
     net.close()
+
+
+def test_trained_network_gain(P):
+    # what the shipped network (trained on 200 seeded random geometric graphs)
+    # gains over the relaxed random start on held-out graphs of the same kind:
+    # the first hierarchy's convergence factor, the re-setups and the solve time
+    from paper_1806_07028_gb300 import train_mpnn as T
+    net = P.Mpnn.pretrained()
+    rows = T.evaluate(net, T.rgg_set(3, 20_000, 40_000, seed=424242))
+    m = T.summarise(rows)
+    print("held-out means:", m)
+    for r in rows:
+        assert r["random"]["status"] == "OK" and r["learned"]["status"] == "OK"
+    assert m["learned"]["resetups"] <= m["random"]["resetups"]
+    assert m["learned"]["conv"] <= m["random"]["conv"] + 0.005
+    net.close()
