@@ -42,7 +42,7 @@ def _args():
     ap.add_argument("--workload", default="C2")
     ap.add_argument("--form", default="fp32ir", choices=["fp32ir", "fp64", "fp32ir+learned"])
     ap.add_argument("--no-extras", action="store_true", help="skip fp64 form, e2e and oracle legs")
-    ap.add_argument("--only-kernel", default=None, choices=["residual64", "vcycle", "wcycle", "adapt"],
+    ap.add_argument("--only-kernel", default=None, choices=["residual64", "vcycle", "wcycle", "adapt", "mpnn"],
                     help="time one kernel alone on the workload (used for ncu captures)")
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--summarize-launches", default=None, metavar="CSV",
@@ -387,13 +387,37 @@ def run_kernel(a):
         e = s.start_vector()
         s.adapt(e)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("adapt")
         t0 = time.perf_counter()
         for _ in range(a.reps):
             s.adapt(e)
         torch.cuda.synchronize()
         ms = (time.perf_counter() - t0) * 1e3 / a.reps
+        torch.cuda.nvtx.range_pop()
         print(json.dumps({"adapt": a.workload, "form": a.form, "ms": ms, "levels": s.num_levels(-1)}),
               flush=True)
+        s.close()
+        return
+    if a.only_kernel == "mpnn":
+        # the learned start's forward pass (shipped weights) on the workload's graph
+        from paper_1806_07028_gb300 import Mpnn, Solver, default_params, inputs as I
+        g = I.workload(a.workload)
+        dev = torch.device("cuda", 0)
+        s = Solver(_device_graph(g, dev), params=default_params(precision=1), device=dev)
+        u = s.start_vector()
+        net = Mpnn.pretrained()
+        for _ in range(2):
+            net.forward(s, u)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("mpnn")
+        t0 = time.perf_counter()
+        for _ in range(a.reps):
+            net.forward(s, u)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3 / a.reps
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"mpnn_forward": a.workload, "n": g.n, "nnz": g.nnz, "ms": ms}), flush=True)
+        net.close()
         s.close()
         return
     if a.only_kernel in ("vcycle", "wcycle"):

@@ -95,7 +95,7 @@ typedef struct {
     int32_t l1jac_rows;    /* coarse levels (not the finest) with at most this many
                               unknowns are smoothed by l1-Jacobi, x += (b - A x)/d with
                               d_i = sum_j |a_ij|, instead of multicolour Gauss-Seidel */
-    int32_t tail_dense;    /* bit 0: V-cycles, bit 1: W-cycles. For the selected cycle
+    int32_t tail_dense;    /* bit 0: V-cycles, bit 1: W-cycles (default 3: both). For the selected cycle
                               kinds the levels below tail_rows are applied as their
                               dense linear operator N (formed once per hierarchy, on
                               first use: one visit of those levels from a zero start is

@@ -202,7 +202,7 @@ PCAMG_API pcamg_status pcamg_default_params(pcamg_params* p) {
     p->profile = 0;
     p->tail_rows = 2048;
     p->l1jac_rows = 2147483647;
-    p->tail_dense = 2;
+    p->tail_dense = 3;
     p->max_resetups = -1;
     p->mpnn = nullptr;
     return PCAMG_OK;

@@ -273,8 +273,7 @@ void cycle(Ctx& c, Hier& h, int gamma, const double* r, double* out) {
         scalar_ops(s, SOP_INV, slot(c, 0), S_SCALE, 0, S_INV);
         cast_scaled_f32(s, c.n, r, slot(c, S_INV), L0.b32.p);
         run_body(c, h, gamma);
-        fill(s, c.n, 0.0, out);
-        add_scaled_f32(s, c.n, L0.x32.p, slot(c, S_SCALE), out);
+        set_scaled_f32(s, c.n, L0.x32.p, slot(c, S_SCALE), out);
     } else {
         copy(s, c.n, r, L0.b64.p);
         run_body(c, h, gamma);

@@ -245,8 +245,28 @@ __global__ void __launch_bounds__(kThr, 2)
                 const float2 g = *reinterpret_cast<const float2*>(G + (size_t)row * kH + 2 * lane);
                 h0 = g.x - mu0;
                 h1 = g.y - mu1;
+                // four neighbours per step, their rows loaded before any is used
+                // (the diagonal entry contributes with weight zero)
                 const int e = rowptr[row + 1];
-                for (int q = rowptr[row]; q < e; ++q) {
+                int q = rowptr[row];
+                for (; q + 4 <= e; q += 4) {
+                    int j[4];
+                    float w[4];
+                    float2 f[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        j[u] = col[q + u];
+                        w[u] = (j[u] == row) ? 0.f : (float)fabs(val[q + u]);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) f[u] = *reinterpret_cast<const float2*>(G + (size_t)j[u] * kH + 2 * lane);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        a0 = fmaf(w[u], f[u].x, a0);
+                        a1 = fmaf(w[u], f[u].y, a1);
+                    }
+                }
+                for (; q < e; ++q) {
                     const int j = col[q];
                     if (j == row) continue;
                     const float w = (float)fabs(val[q]);
@@ -493,7 +513,26 @@ __global__ void k_nbr_back(int n, const int* __restrict__ rowptr, const int* __r
     const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     for (int i = w0; i < n; i += nw) {
         float2 a = *reinterpret_cast<const float2*>(dHs + (size_t)i * kH + 2 * lane);
-        for (int q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+        const int e = rowptr[i + 1];
+        int q = rowptr[i];
+        for (; q + 4 <= e; q += 4) {
+            int k[4];
+            float w[4];
+            float2 m[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) k[u] = col[q + u];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                w[u] = (k[u] == i) ? 0.f : (float)fabs(val[q + u]) * invD[k[u]];
+                m[u] = *reinterpret_cast<const float2*>(dM + (size_t)k[u] * kH + 2 * lane);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a.x = fmaf(w[u], m[u].x, a.x);
+                a.y = fmaf(w[u], m[u].y, a.y);
+            }
+        }
+        for (; q < e; ++q) {
             const int k = col[q];
             if (k == i) continue;
             const float w = (float)fabs(val[q]) * invD[k];
@@ -568,12 +607,23 @@ __global__ void __launch_bounds__(kThr, 1)
     if (warp == 0) tmem_free(tmem, 64);
 }
 
-// out[k] = sum over partial rows b of part[b][k], in b order (FP64 sum)
-__global__ void k_sum_parts(int nb, int K, const float* __restrict__ part, float* __restrict__ out) {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < nb; ++b) s += (double)part[(size_t)b * K + k];
-        out[k] = (float)s;
+// out[k] = sum over the partial rows b of part[b][k]: block k, its threads
+// take b = tid, tid + 256, ... and a fixed tree combines them (FP64).
+constexpr int kSumThreads = 256;
+__global__ void __launch_bounds__(kSumThreads) k_sum_parts(int nb, int K, const float* __restrict__ part,
+                                                         float* __restrict__ out) {
+    __shared__ double ws[kSumThreads / 32];
+    const int k = blockIdx.x;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += kSumThreads) s += (double)part[(size_t)b * K + k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kSumThreads / 32; ++w) t += ws[w];
+        out[k] = (float)t;
     }
 }
 
@@ -590,12 +640,25 @@ __global__ void k_colsums(int n, int mode, const float* __restrict__ dZ, const d
     const int b = blockIdx.x;
     const int i0 = b * kSumRows, i1 = min(n, i0 + kSumRows);
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        if (mode == 0 || mode == 3) {     // plain sums: FP32 within the block, four chains
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+            const float* X = (mode == 0) ? dZ : F;
+            const int ld = (mode == 0) ? kH : 3;
+            int i = i0;
+            for (; i + 4 <= i1; i += 4) {
+                a0 += X[(size_t)i * ld + k];
+                a1 += X[(size_t)(i + 1) * ld + k];
+                a2 += X[(size_t)(i + 2) * ld + k];
+                a3 += X[(size_t)(i + 3) * ld + k];
+            }
+            for (; i < i1; ++i) a0 += X[(size_t)i * ld + k];
+            part[(size_t)b * K + k] = (a0 + a1) + (a2 + a3);
+            continue;
+        }
         double s = 0.0;
         const double mu = (mode == 1 && k < kH) ? (double)gsum[k] / (double)n : 0.0;
         for (int i = i0; i < i1; ++i) {
-            if (mode == 0) s += dZ[(size_t)i * kH + k];
-            else if (mode == 3) s += F[3 * i + k];
-            else if (mode == 1) s += (k < kH) ? dy[i] * ((double)G[(size_t)i * kH + k] - mu) : dy[i];
+            if (mode == 1) s += (k < kH) ? dy[i] * ((double)G[(size_t)i * kH + k] - mu) : dy[i];
             else if (k < 192) s += (double)dZ[(size_t)i * kH + k / 3] * F[3 * i + k % 3];
             else s += dZ[(size_t)i * kH + (k - 192)];
         }
@@ -721,7 +784,7 @@ static int sum_blocks(int n) { return (n + kSumRows - 1) / kSumRows; }
 static void colsum64(cudaStream_t s, int n, const float* X, float* part, float* out) {
     const int nb = sum_blocks(n);
     k_colsums<<<nb, 64, 0, s>>>(n, 0, X, nullptr, nullptr, nullptr, nullptr, part, kH); ::pc::count_launches(1);
-    k_sum_parts<<<1, 64, 0, s>>>(nb, kH, part, out); ::pc::count_launches(1);
+    k_sum_parts<<<kH, kSumThreads, 0, s>>>(nb, kH, part, out); ::pc::count_launches(1);
 }
 
 // forward; train = keep X_l, Z_l, every G_l, F and Z_in for the backward pass
@@ -748,7 +811,7 @@ static void forward(Ctx& c, Mpnn& P, const double* u, double* yhat, MpnnWork& w,
     ::pc::count_launches(1);
     // column sums of the features, for centring the two degree features
     k_colsums<<<nb, 64, 0, s>>>(n, 3, nullptr, nullptr, nullptr, nullptr, w.F.p, w.part.p, 3); ::pc::count_launches(1);
-    k_sum_parts<<<1, 64, 0, s>>>(nb, 3, w.part.p, w.gsum.p); ::pc::count_launches(1);
+    k_sum_parts<<<3, kSumThreads, 0, s>>>(nb, 3, w.part.p, w.gsum.p); ::pc::count_launches(1);
     k_mpnn_in<<<grid_for(n), 256, 0, s>>>(n, w.gsum.p, P.wq, w.F.p, train ? w.Zin.p : nullptr, w.G.p);
     ::pc::count_launches(1);
     auto Gl = [&](int l) { return w.G.p + (train ? (size_t)l : (size_t)(l & 1)) * nh; };
@@ -829,7 +892,7 @@ double mpnn_loss_grad(Ctx& c, Mpnn& P, const double* u, const double* target) {
     k_colsums<<<nb, 128, 0, s>>>(n, 1, nullptr, w.gz.p, w.G.p + (size_t)L * nh, w.gsum.p + L * kH, nullptr,
                                  w.part.p, 65);
     ::pc::count_launches(1);
-    k_sum_parts<<<1, 128, 0, s>>>(nb, 65, w.part.p, P.g + kOffWout); ::pc::count_launches(1);
+    k_sum_parts<<<65, kSumThreads, 0, s>>>(nb, 65, w.part.p, P.g + kOffWout); ::pc::count_launches(1);
     k_head_back<<<grid_for((int64_t)nh), 256, 0, s>>>(n, w.gz.p, P.wq, w.dH.p); ::pc::count_launches(1);
     set_smem((const void*)k_mpnn_dx, 32768);
     set_smem((const void*)k_mpnn_dw, 49152);
@@ -842,7 +905,7 @@ double mpnn_loss_grad(Ctx& c, Mpnn& P, const double* u, const double* target) {
         colsum64(s, n, w.dZ.p, w.part.p, gW + kH * 128);
         k_mpnn_dw<<<gdw, kThr, 49152, s>>>(n, w.X.p + (size_t)l * nh * 2, w.dZb.p, wpart.p, w.err.p);
         ::pc::count_launches(1);
-        k_sum_parts<<<(kH * 128 + 255) / 256, 256, 0, s>>>(gdw, kH * 128, wpart.p, gW); ::pc::count_launches(1);
+        k_sum_parts<<<kH * 128, kSumThreads, 0, s>>>(gdw, kH * 128, wpart.p, gW); ::pc::count_launches(1);
         k_mpnn_dx<<<gdx, kThr, 32768, s>>>(n, w.dZb.p, P.wl + (size_t)l * kH * 128, w.dHs.p, w.dM.p, w.err.p);
         ::pc::count_launches(1);
         k_nbr_back<<<grid_for((int64_t)n * 32), 256, 0, s>>>(n, c.rowptr.p, c.col.p, c.val.p, w.invD.p, w.dHs.p,
@@ -855,7 +918,7 @@ double mpnn_loss_grad(Ctx& c, Mpnn& P, const double* u, const double* target) {
     ::pc::count_launches(1);
     k_colsums<<<nb, 256, 0, s>>>(n, 2, w.dZ.p, nullptr, nullptr, nullptr, w.F.p, w.part.p, 256);
     ::pc::count_launches(1);
-    k_sum_parts<<<1, 256, 0, s>>>(nb, 256, w.part.p, P.g + kOffWin); ::pc::count_launches(1);
+    k_sum_parts<<<256, kSumThreads, 0, s>>>(nb, 256, w.part.p, P.g + kOffWin); ::pc::count_launches(1);
     PC_LAUNCH("mpnn_backward");
     check_err(c, w.err.p);
     double L0 = 0.0;

@@ -144,11 +144,18 @@ struct WarpScratch {
     int mrow[kWarpMembers];
 };
 
-template <class Src, bool FILL>
+// MODE 0: count the row's distinct columns (cnt) and flag long rows;
+// MODE 1: write the row at optr[r] (counts known);
+// MODE 2: both at once -- count, flag, and write the row at tptr[r] of a
+//         temporary layout sized by each row's contribution count (compacted
+//         afterwards), so the sort-reduce runs once.
+template <class Src, int MODE>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_rowprod_warp(
         int nrows, Src src, int* __restrict__ cnt, unsigned char* __restrict__ is_long,
         int* __restrict__ long_list, int* __restrict__ long_count, const int* __restrict__ optr,
-        int* __restrict__ ocol, double* __restrict__ oval) {
+        int* __restrict__ ocol, double* __restrict__ oval, const int64_t* __restrict__ tptr) {
+    constexpr bool FILL = MODE != 0;
+    constexpr bool COUNT = MODE != 1;
     __shared__ WarpScratch ws_all[kWarpsPerBlock];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     WarpScratch& W = ws_all[wib];
@@ -156,7 +163,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_rowprod_warp(
     const int64_t nw = (int64_t)gridDim.x * kWarpsPerBlock;
     for (int64_t r64 = gw; r64 < nrows; r64 += nw) {
         const int r = (int)r64;
-        if (FILL && is_long[r]) continue;
+        if (MODE == 1 && is_long[r]) continue;
         const int nm = src.nmem(r);
         bool over = nm > kWarpMembers;
         int total = 0;
@@ -225,7 +232,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_rowprod_warp(
             }
             // runs of equal columns
             int carry = 0;
-            const int o = FILL ? optr[r] : 0;
+            const int64_t o = (MODE == 1) ? (int64_t)optr[r] : (MODE == 2 ? tptr[r] : 0);
             for (int e0 = 0; e0 < P; e0 += 32) {
                 const int e = e0 + lane;
                 const uint64_t ke = W.key[e];
@@ -239,20 +246,57 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_rowprod_warp(
                         if (kq == ~0ull || (uint32_t)(kq >> 32) != c) break;
                         sum = __dadd_rn(sum, W.val[(uint32_t)kq]);
                     }
-                    const int idx = o + carry + __popc(ball & ((1u << lane) - 1u));
+                    const int64_t idx = o + carry + __popc(ball & ((1u << lane) - 1u));
                     ocol[idx] = (int)c;
                     if (oval) oval[idx] = sum;
                 }
                 carry += __popc(ball);
             }
-            if (!FILL && lane == 0) { cnt[r] = carry; is_long[r] = 0; }
+            if (COUNT && lane == 0) { cnt[r] = carry; is_long[r] = 0; }
         }
-        if (over && !FILL && lane == 0) {
+        if (over && COUNT && lane == 0) {
             is_long[r] = 1;
             cnt[r] = 0;
             long_list[atomicAdd(long_count, 1)] = r;
         }
         __syncwarp();
+    }
+}
+
+// Contribution count of every row the warp kernel takes (0 for the rows it
+// leaves to the block kernels): the temporary layout of the one-pass product.
+template <class Src>
+__global__ void k_rowprod_ubrow(int nrows, Src src, int64_t* __restrict__ ub) {
+    FOR_EACH(r64, nrows) {
+        const int r = (int)r64;
+        const int nm = src.nmem(r);
+        int64_t s = 0;
+        if (nm <= kWarpMembers)
+            for (int t = 0; t < nm; ++t) {
+                const int j = src.mem_row(r, t);
+                s += src.in_end(j) - src.in_beg(j);
+            }
+        ub[r] = (nm <= kWarpMembers && s <= kWarpCap) ? s : 0;
+    }
+}
+
+// Copy the rows written in the temporary layout to their final place (a warp per row).
+__global__ void k_rowprod_compact(int nrows, const unsigned char* __restrict__ is_long, const int* __restrict__ cnt,
+                                  const int64_t* __restrict__ tptr, const int* __restrict__ tcol,
+                                  const double* __restrict__ tval, const int* __restrict__ optr,
+                                  int* __restrict__ ocol, double* __restrict__ oval) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = w0; r < nrows; r += nw) {
+        if (is_long[r]) continue;
+        const int m = cnt[r];
+        const int64_t t = tptr[r];
+        const int o = optr[r];
+        for (int q = lane; q < m; q += 32) {
+            ocol[o + q] = tcol[t + q];
+            if (oval) oval[o + q] = tval[t + q];
+        }
     }
 }
 
@@ -854,9 +898,21 @@ static void row_product(Ctx& c, int32_t nrows, const Src& src, DBuf<int32_t>& op
     long_count.alloc(c.mem, 1);
     is_long.alloc(c.mem, nrows);
     PC_CUDA(cudaMemsetAsync(long_count.p, 0, sizeof(int32_t), s));
-    k_rowprod_warp<Src, false><<<grid_warps(nrows), kWarpsPerBlock * 32, 0, s>>>(
-        nrows, src, cnt.p, is_long.p, long_list.p, long_count.p, nullptr, nullptr, nullptr); ::pc::count_launches(1);
-    PC_LAUNCH("rowprod_warp(count)");
+    // one pass of the warp kernel into a temporary layout sized by the rows'
+    // contribution counts
+    DBuf<int64_t> ubr, tptr;
+    DBuf<int32_t> tcol;
+    DBuf<double> tval;
+    ubr.alloc(c.mem, nrows);
+    tptr.alloc(c.mem, (size_t)nrows + 1);
+    k_rowprod_ubrow<Src><<<grid1(nrows), kBlock, 0, s>>>(nrows, src, ubr.p); ::pc::count_launches(1);
+    const int64_t tot_ub = scan_i64(c, ubr.p, tptr.p, nrows);
+    tcol.alloc(c.mem, std::max<int64_t>(tot_ub, 1));
+    if (oval) tval.alloc(c.mem, std::max<int64_t>(tot_ub, 1));
+    k_rowprod_warp<Src, 2><<<grid_warps(nrows), kWarpsPerBlock * 32, 0, s>>>(
+        nrows, src, cnt.p, is_long.p, long_list.p, long_count.p, nullptr, tcol.p, oval ? tval.p : nullptr, tptr.p);
+    ::pc::count_launches(1);
+    PC_LAUNCH("rowprod_warp(once)");
     int32_t nlong = read_i32(c, long_count.p);
     std::vector<int32_t> rowsB, rowsC;
     std::vector<int64_t> ubC;
@@ -917,9 +973,10 @@ static void row_product(Ctx& c, int32_t nrows, const Src& src, DBuf<int32_t>& op
     ocol.alloc(c.mem, total);
     double* ov = nullptr;
     if (oval) { oval->alloc(c.mem, total); ov = oval->p; }
-    k_rowprod_warp<Src, true><<<grid_warps(nrows), kWarpsPerBlock * 32, 0, s>>>(
-        nrows, src, nullptr, is_long.p, nullptr, nullptr, optr.p, ocol.p, ov); ::pc::count_launches(1);
-    PC_LAUNCH("rowprod_warp(fill)");
+    k_rowprod_compact<<<grid_warps(nrows), kWarpsPerBlock * 32, 0, s>>>(nrows, is_long.p, cnt.p, tptr.p, tcol.p,
+                                                                         oval ? tval.p : nullptr, optr.p, ocol.p, ov);
+    ::pc::count_launches(1);
+    PC_LAUNCH("rowprod_compact");
     if (!rowsB.empty()) {
         size_t smem = kBlockCap * (sizeof(uint64_t) + sizeof(double));
         k_rowprod_block<Src, true, false><<<(unsigned)rowsB.size(), kBlock, smem, s>>>(

@@ -209,9 +209,9 @@ __global__ void k_coarse_apply(int m, const double* __restrict__ X, const T* __r
 // adds the products of its own row in CSR order. A row's sum is therefore taken
 // left to right, with one rounding per product and per addition.
 constexpr int kStreamRows = 256;
-// entries staged per chunk: FP64 stages a value and an x per entry, FP32 one product
+// entries staged per chunk (FP64 stages a value and an x per entry, FP32 one product)
 template <class T>
-constexpr int kStreamChunk = sizeof(T) == 8 ? 2048 : 4096;
+constexpr int kStreamChunk = 2048;
 // below this many rows a launch of the streaming kernels would not fill the GPU
 constexpr int kStreamMinRows = kNumSMs * kStreamRows * 2;
 
@@ -395,7 +395,7 @@ inline int simple_grid(int64_t n) {
 
 // streaming kernels: sparse rows (a tile of 256 rows then fits about one
 // chunk) and enough rows to fill the GPU
-bool use_stream(int32_t rows, int lpr) { return lpr <= 4 && rows >= kStreamMinRows; }
+bool use_stream(int32_t rows, int lpr) { return lpr <= 8 && rows >= kStreamMinRows; }
 
 void residual64(cudaStream_t s, const Csr& A, const double* x, const double* b, double* r,
                 double* partial, double* norm2) {

@@ -29,11 +29,28 @@ __device__ double block_sum(double v) {
     return v;  // valid in thread 0
 }
 
+// Per-block partial of sum x_i y_i (or sum x_i): four independent loads and
+// fused multiply-adds per step (GB300's FP64 rate, not HBM, bounds these
+// loops), accumulated in a fixed order.
+template <bool HAS_Y>
 __global__ void k_dot_partial(int64_t n, const double* __restrict__ x, const double* __restrict__ y,
                               double* __restrict__ partial) {
-    double s = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        s += x[i] * (y ? y[i] : 1.0);
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    const int64_t st = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (; i + 3 * st < n; i += 4 * st) {
+        const double a0 = x[i], a1 = x[i + st], a2 = x[i + 2 * st], a3 = x[i + 3 * st];
+        if constexpr (HAS_Y) {
+            s0 = fma(a0, y[i], s0);
+            s1 = fma(a1, y[i + st], s1);
+            s2 = fma(a2, y[i + 2 * st], s2);
+            s3 = fma(a3, y[i + 3 * st], s3);
+        } else {
+            s0 += a0; s1 += a1; s2 += a2; s3 += a3;
+        }
+    }
+    for (; i < n; i += st) s0 = HAS_Y ? fma(x[i], y[i], s0) : s0 + x[i];
+    double s = (s0 + s1) + (s2 + s3);
     s = block_sum(s);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
@@ -104,6 +121,13 @@ __global__ void k_add_scaled_f32(int64_t n, const float* __restrict__ c, const d
     double f = *sc;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         x[i] += f * (double)c[i];
+}
+
+__global__ void k_set_scaled_f32(int64_t n, const float* __restrict__ c, const double* __restrict__ sc,
+                                 double* __restrict__ x) {
+    double f = *sc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = f * (double)c[i];
 }
 
 __global__ void k_cast_f64(int64_t n, const float* __restrict__ x, double* __restrict__ y) {
@@ -236,7 +260,9 @@ int reduce_blocks(int64_t n) {
 
 void dot(cudaStream_t s, int64_t n, const double* x, const double* y, double* partial, double* out) {
     int nb = reduce_blocks(n);
-    k_dot_partial<<<nb, kRedBlock, 0, s>>>(n, x, y, partial); ::pc::count_launches(1);
+    if (y) k_dot_partial<true><<<nb, kRedBlock, 0, s>>>(n, x, y, partial);
+    else k_dot_partial<false><<<nb, kRedBlock, 0, s>>>(n, x, nullptr, partial);
+    ::pc::count_launches(1);
     k_finish_sum<<<1, 1024, 0, s>>>(nb, partial, out); ::pc::count_launches(1);
     PC_LAUNCH("dot");
 }
@@ -285,6 +311,10 @@ void cast_f32(cudaStream_t s, int64_t n, const double* x, float* y) { cast_scale
 void add_scaled_f32(cudaStream_t s, int64_t n, const float* c, const double* scale, double* x) {
     k_add_scaled_f32<<<grid_for(n), kBlock, 0, s>>>(n, c, scale, x); ::pc::count_launches(1);
     PC_LAUNCH("add_scaled_f32");
+}
+void set_scaled_f32(cudaStream_t s, int64_t n, const float* c, const double* scale, double* x) {
+    k_set_scaled_f32<<<grid_for(n), kBlock, 0, s>>>(n, c, scale, x); ::pc::count_launches(1);
+    PC_LAUNCH("set_scaled_f32");
 }
 void cast_f64(cudaStream_t s, int64_t n, const float* x, double* y) {
     k_cast_f64<<<grid_for(n), kBlock, 0, s>>>(n, x, y); ::pc::count_launches(1);

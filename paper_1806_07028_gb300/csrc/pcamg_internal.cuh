@@ -236,6 +236,7 @@ void fill(cudaStream_t s, int64_t n, double v, double* y);
 void fill_i32(cudaStream_t s, int64_t n, int32_t v, int32_t* y);
 void cast_scaled_f32(cudaStream_t s, int64_t n, const double* x, const double* inv_scale, float* y);
 void add_scaled_f32(cudaStream_t s, int64_t n, const float* c, const double* scale, double* x);  // x += scale*c
+void set_scaled_f32(cudaStream_t s, int64_t n, const float* c, const double* scale, double* x);  // x = scale*c
 void cast_f32(cudaStream_t s, int64_t n, const double* x, float* y);
 void cast_f64(cudaStream_t s, int64_t n, const float* x, double* y);
 void philox_uniform(cudaStream_t s, uint64_t seed, int64_t n, double* out);
