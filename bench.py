@@ -50,6 +50,29 @@ def _args():
     return ap.parse_args()
 
 
+def barrier():
+    """Barrier across the ranks of a torchrun launch (no-op for one process)."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+
+
+def max_over_ranks(ms, device=None):
+    """The slowest rank's time: the job's time for weak-scaling replicas."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(n, world, ms):
+    """Whole-job throughput: every rank solves its own n-unknown system."""
+    return n * world / (ms / 1e3)
+
+
 def _dist():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -174,11 +197,6 @@ def run_ours(a):
         s.close()
         return x, st
 
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
     for _ in range(a.warmup):
         step(a.form, profile=1)
     torch.cuda.synchronize()
@@ -199,14 +217,10 @@ def run_ours(a):
     launches = N.lib().pcamg_kernel_launches() - launches0
     ms = ev0.elapsed_time(ev1) / a.steps
     clk = clocks.stop()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, device=dev)
     x_host = x.cpu().numpy()
     rel = float(np.linalg.norm(b_host - g.to_scipy() @ x_host) / np.linalg.norm(b_host))
-    value = g.n * world / (ms / 1e3)
+    value = job_value(g.n, world, ms)
 
     # roofline of the fine-level FP64 residual kernel (events on its own stream)
     peak, peak_kind = _peaks()

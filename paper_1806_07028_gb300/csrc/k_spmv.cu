@@ -259,8 +259,12 @@ __device__ __forceinline__ T row_add(const T* av, const T* xv, int i, T s) {
     else return s + av[i];
 }
 
-// r_i = b_i - sum_k a_k x_col(k) (fused multiply-adds left to right);
-// partial[block] = sum of r_i^2 when requested
+// r_i = b_i - sum_k a_k x_col(k) (fused multiply-adds left to right). With
+// NORM a block takes kNormTiles consecutive tiles, accumulates r_i^2 of its
+// rows in registers and writes one partial (the per-row reduction is the
+// costly part at GB300's FP64 rate, so it is done once per block).
+constexpr int kNormTiles = 4;
+
 template <class T, bool NORM>
 __global__ void __launch_bounds__(kStreamRows) k_res_stream(int n, const int* __restrict__ rowptr,
                                                              const int* __restrict__ col,
@@ -271,26 +275,31 @@ __global__ void __launch_bounds__(kStreamRows) k_res_stream(int n, const int* __
                                                              double* __restrict__ partial) {
     __shared__ T av[kStreamChunk<T>];
     __shared__ T xv[kXv<T>];
-    const int r0 = blockIdx.x * kStreamRows;
-    const int row = r0 + threadIdx.x;
-    const int rlast = min(r0 + kStreamRows, n);
-    const int tb = __ldg(rowptr + r0), te = __ldg(rowptr + rlast);
-    int rb = 0, re = 0;
-    if (row < n) { rb = __ldg(rowptr + row); re = __ldg(rowptr + row + 1); }
-    T s = 0;
-    for (int c0 = tb; c0 < te; c0 += kStreamChunk<T>) {
-        const int c1 = min(c0 + kStreamChunk<T>, te);
-        stage_products<T, false>(c0, c1, col, val, x, av, xv, nullptr);
-        __syncthreads();
-        const int kb = max(rb, c0), ke = min(re, c1);
-        for (int k = kb; k < ke; ++k) s = row_add<T>(av, xv, k - c0, s);
-        __syncthreads();
-    }
+    constexpr int TPB = NORM ? kNormTiles : 1;
+    const int ntiles = (n + kStreamRows - 1) / kStreamRows;
+    const int t_end = min(ntiles, (int)(blockIdx.x + 1) * TPB);
     double rr2 = 0.0;
-    if (row < n) {
-        T rr = __ldg(b + row) - s;
-        r[row] = rr;
-        rr2 = (double)rr * (double)rr;
+    for (int t = blockIdx.x * TPB; t < t_end; ++t) {
+        const int r0 = t * kStreamRows;
+        const int row = r0 + threadIdx.x;
+        const int rlast = min(r0 + kStreamRows, n);
+        const int tb = __ldg(rowptr + r0), te = __ldg(rowptr + rlast);
+        int rb = 0, re = 0;
+        if (row < n) { rb = __ldg(rowptr + row); re = __ldg(rowptr + row + 1); }
+        T s = 0;
+        for (int c0 = tb; c0 < te; c0 += kStreamChunk<T>) {
+            const int c1 = min(c0 + kStreamChunk<T>, te);
+            stage_products<T, false>(c0, c1, col, val, x, av, xv, nullptr);
+            __syncthreads();
+            const int kb = max(rb, c0), ke = min(re, c1);
+            for (int k = kb; k < ke; ++k) s = row_add<T>(av, xv, k - c0, s);
+            __syncthreads();
+        }
+        if (row < n) {
+            T rr = __ldg(b + row) - s;
+            r[row] = rr;
+            if (NORM) rr2 = fma((double)rr, (double)rr, rr2);
+        }
     }
     if (NORM) {
         __shared__ double ws[kStreamRows / 32];
@@ -402,8 +411,9 @@ void residual64(cudaStream_t s, const Csr& A, const double* x, const double* b, 
     if (use_stream(A.n, A.lpr) || norm2) {
         int g = (A.n + kStreamRows - 1) / kStreamRows;
         if (norm2) {
-            k_res_stream<double, true><<<g, kStreamRows, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, b, r, partial); ::pc::count_launches(1);
-            k_finish<<<1, 1024, 0, s>>>(g, partial, norm2); ::pc::count_launches(1);
+            const int gn = (g + kNormTiles - 1) / kNormTiles;   // <= residual_partials(n)
+            k_res_stream<double, true><<<gn, kStreamRows, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, b, r, partial); ::pc::count_launches(1);
+            k_finish<<<1, 1024, 0, s>>>(gn, partial, norm2); ::pc::count_launches(1);
         } else {
             k_res_stream<double, false><<<g, kStreamRows, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, b, r, nullptr); ::pc::count_launches(1);
         }
