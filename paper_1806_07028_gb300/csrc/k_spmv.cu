@@ -229,76 +229,141 @@ constexpr int kUnroll = kStreamChunk<T> / kStreamRows;
 template <class T>
 constexpr int kXv = sizeof(T) == 8 ? kStreamChunk<T> : 1;
 
-template <class T, bool KEEP_COL>
-__device__ __forceinline__ void stage_products(int c0, int c1, const int* __restrict__ col,
-                                               const T* __restrict__ val, const T* x, T* av,
-                                               T* xv, int* pc) {
+// Column indices and values of one chunk, entry c0 + tid + u * kStreamRows in
+// slot u, held in registers between their (coalesced, independent) loads and
+// the staging.
+template <class T>
+struct ChunkRegs {
     int cj[kUnroll<T>];
     T cv[kUnroll<T>];
+};
+
+template <class T>
+__device__ __forceinline__ void load_chunk(int c0, int c1, const int* __restrict__ col, const T* __restrict__ val,
+                                           ChunkRegs<T>& R) {
 #pragma unroll
     for (int u = 0; u < kUnroll<T>; ++u) {
         const int k = c0 + threadIdx.x + u * kStreamRows;
-        cj[u] = (k < c1) ? __ldg(col + k) : 0;
-        cv[u] = (k < c1) ? __ldg(val + k) : T(0);
+        R.cj[u] = (k < c1) ? __ldg(col + k) : 0;
+        R.cv[u] = (k < c1) ? __ldg(val + k) : T(0);
+    }
+}
+
+// Stage entries [c0, c1) held in R: gather x_col(k) (ordinary loads: the GS
+// kernel writes x) and store value and x (FP64) or their product (FP32), and
+// the column (GS) in shared memory.
+template <class T, bool KEEP_COL>
+__device__ __forceinline__ void stage_regs(int c0, int c1, const ChunkRegs<T>& R, const T* x, T* av, T* xv,
+                                           int* pc) {
+    T xg[kUnroll<T>];
+#pragma unroll
+    for (int u = 0; u < kUnroll<T>; ++u) {
+        const int k = c0 + threadIdx.x + u * kStreamRows;
+        xg[u] = (k < c1) ? x[R.cj[u]] : T(0);
     }
 #pragma unroll
     for (int u = 0; u < kUnroll<T>; ++u) {
         const int k = c0 + threadIdx.x + u * kStreamRows;
         if (k < c1) {
-            if constexpr (sizeof(T) == 8) { av[k - c0] = cv[u]; xv[k - c0] = x[cj[u]]; }
-            else av[k - c0] = cv[u] * x[cj[u]];
-            if (KEEP_COL) pc[k - c0] = cj[u];
+            if constexpr (sizeof(T) == 8) { av[k - c0] = R.cv[u]; xv[k - c0] = xg[u]; }
+            else av[k - c0] = R.cv[u] * xg[u];
+            if (KEEP_COL) pc[k - c0] = R.cj[u];
         }
     }
 }
 
-// add entry k's contribution to s (see stage_products)
+// add entry k's contribution to s (see stage_regs)
 template <class T>
 __device__ __forceinline__ T row_add(const T* av, const T* xv, int i, T s) {
     if constexpr (sizeof(T) == 8) return fma_t(av[i], xv[i], s);
     else return s + av[i];
 }
 
-// r_i = b_i - sum_k a_k x_col(k) (fused multiply-adds left to right). With
-// NORM a block takes kNormTiles consecutive tiles, accumulates r_i^2 of its
-// rows in registers and writes one partial (the per-row reduction is the
-// costly part at GB300's FP64 rate, so it is done once per block).
-constexpr int kNormTiles = 4;
+// Where a tile's rows live: the tile's entry range [tb, te), this thread's row,
+// its entry range [rb, re) and b at that row (loaded early, ahead of use).
+template <class T>
+struct TileMeta {
+    int tb, te, rb, re, row;
+    T bv;
+};
 
-template <class T, bool NORM>
-__global__ void __launch_bounds__(kStreamRows) k_res_stream(int n, const int* __restrict__ rowptr,
-                                                             const int* __restrict__ col,
-                                                             const T* __restrict__ val,
-                                                             const T* __restrict__ x,
-                                                             const T* __restrict__ b,
-                                                             T* __restrict__ r,
-                                                             double* __restrict__ partial) {
+template <class T, bool PERM>
+__device__ __forceinline__ TileMeta<T> tile_meta(int t0, int tend, const int* __restrict__ ptr,
+                                                 const int* __restrict__ rows, const T* __restrict__ b) {
+    TileMeta<T> m;
+    const int tl = min(t0 + kStreamRows, tend);
+    const int t = t0 + threadIdx.x;
+    m.tb = __ldg(ptr + t0);
+    m.te = __ldg(ptr + tl);
+    m.rb = m.re = 0;
+    m.row = -1;
+    m.bv = T(0);
+    if (t < tend) {
+        m.rb = __ldg(ptr + t);
+        m.re = __ldg(ptr + t + 1);
+        m.row = PERM ? __ldg(rows + t) : t;
+        m.bv = __ldg(b + m.row);
+    }
+    return m;
+}
+
+// A block owns tpb consecutive tiles of kStreamRows rows. While it adds up one
+// chunk's rows from shared memory, the loads of the next chunk (of this tile or
+// the first of the next tile) and the next tile's row pointers and b are
+// already in flight, so the only exposed latency per tile is the x gather.
+// The row sums keep the CSR order of each row.
+//   PERM = false: rows t of [0, n) (residual r = b - A x, optional ||r||^2);
+//   PERM = true:  permuted rows rows[t] of [beg, end) of one colour, Gauss-Seidel
+//                 x_row = (b_row - sum_{j != row} a x_j) / a_row,row.
+template <class T, bool PERM, bool NORM>
+__device__ __forceinline__ void stream_tiles(int beg, int end, int tpb, const int* __restrict__ rows,
+                                             const int* __restrict__ ptr, const int* __restrict__ col,
+                                             const T* __restrict__ val, const T* x_in, const T* __restrict__ b,
+                                             T* out, double* __restrict__ partial) {
     __shared__ T av[kStreamChunk<T>];
     __shared__ T xv[kXv<T>];
-    constexpr int TPB = NORM ? kNormTiles : 1;
-    const int ntiles = (n + kStreamRows - 1) / kStreamRows;
-    const int t_end = min(ntiles, (int)(blockIdx.x + 1) * TPB);
+    __shared__ int pc[PERM ? kStreamChunk<T> : 1];
+    const int ntiles = (end - beg + kStreamRows - 1) / kStreamRows;
+    const int tfirst = blockIdx.x * tpb;
+    const int tstop = min(ntiles, tfirst + tpb);
     double rr2 = 0.0;
-    for (int t = blockIdx.x * TPB; t < t_end; ++t) {
-        const int r0 = t * kStreamRows;
-        const int row = r0 + threadIdx.x;
-        const int rlast = min(r0 + kStreamRows, n);
-        const int tb = __ldg(rowptr + r0), te = __ldg(rowptr + rlast);
-        int rb = 0, re = 0;
-        if (row < n) { rb = __ldg(rowptr + row); re = __ldg(rowptr + row + 1); }
-        T s = 0;
-        for (int c0 = tb; c0 < te; c0 += kStreamChunk<T>) {
-            const int c1 = min(c0 + kStreamChunk<T>, te);
-            stage_products<T, false>(c0, c1, col, val, x, av, xv, nullptr);
-            __syncthreads();
-            const int kb = max(rb, c0), ke = min(re, c1);
-            for (int k = kb; k < ke; ++k) s = row_add<T>(av, xv, k - c0, s);
-            __syncthreads();
-        }
-        if (row < n) {
-            T rr = __ldg(b + row) - s;
-            r[row] = rr;
-            if (NORM) rr2 = fma((double)rr, (double)rr, rr2);
+    if (tfirst < tstop) {
+        TileMeta<T> M = tile_meta<T, PERM>(beg + tfirst * kStreamRows, end, ptr, rows, b);
+        ChunkRegs<T> R;
+        load_chunk<T>(M.tb, min(M.tb + kStreamChunk<T>, M.te), col, val, R);
+        for (int t = tfirst; t < tstop; ++t) {
+            TileMeta<T> Mn = M;
+            T s = 0, d = 0;
+            for (int c0 = M.tb;;) {
+                const int c1 = min(c0 + kStreamChunk<T>, M.te);
+                stage_regs<T, PERM>(c0, c1, R, x_in, av, xv, pc);
+                __syncthreads();
+                // R is free again: start the loads the next round needs
+                if (c1 < M.te) {
+                    load_chunk<T>(c1, min(c1 + kStreamChunk<T>, M.te), col, val, R);
+                } else if (t + 1 < tstop) {
+                    Mn = tile_meta<T, PERM>(beg + (t + 1) * kStreamRows, end, ptr, rows, b);
+                    load_chunk<T>(Mn.tb, min(Mn.tb + kStreamChunk<T>, Mn.te), col, val, R);
+                }
+                const int kb = max(M.rb, c0), ke = min(M.re, c1);
+                for (int k = kb; k < ke; ++k) {
+                    if (PERM && pc[k - c0] == M.row) d = (sizeof(T) == 8) ? av[k - c0] : __ldg(val + k);
+                    else s = row_add<T>(av, xv, k - c0, s);
+                }
+                __syncthreads();
+                if (c1 >= M.te) break;
+                c0 = c1;
+            }
+            if (M.row >= 0) {
+                if (PERM) {
+                    out[M.row] = (M.bv - s) / d;
+                } else {
+                    const T rr = M.bv - s;
+                    out[M.row] = rr;
+                    if (NORM) rr2 = fma((double)rr, (double)rr, rr2);
+                }
+            }
+            M = Mn;
         }
     }
     if (NORM) {
@@ -314,6 +379,28 @@ __global__ void __launch_bounds__(kStreamRows) k_res_stream(int n, const int* __
     }
 }
 
+// Tiles per block: pipelining across tiles pays where FP64 arithmetic is the
+// long pole (and with the norm it also divides the partial sums); the FP32 and
+// Gauss-Seidel launches need every block they can get.
+constexpr int kNormTiles = 4;
+template <class T>
+constexpr int kTilesPerBlock = sizeof(T) == 8 ? 2 : 1;
+constexpr int kGsTiles = 1;
+
+// r_i = b_i - sum_k a_k x_col(k) (fused multiply-adds left to right in FP64);
+// partial[block] = sum of r_i^2 of the block's rows when NORM
+template <class T, bool NORM>
+__global__ void __launch_bounds__(kStreamRows) k_res_stream(int n, const int* __restrict__ rowptr,
+                                                             const int* __restrict__ col,
+                                                             const T* __restrict__ val,
+                                                             const T* __restrict__ x,
+                                                             const T* __restrict__ b,
+                                                             T* __restrict__ r,
+                                                             double* __restrict__ partial) {
+    stream_tiles<T, false, NORM>(0, n, NORM ? kNormTiles : kTilesPerBlock<T>, nullptr, rowptr, col, val, x, b, r,
+                                 partial);
+}
+
 // One colour of Gauss-Seidel on the row-permuted copy (rows of a colour are
 // contiguous there): x_row = (b_row - sum_{j != row} a x_j) / a_row,row.
 template <class T>
@@ -322,28 +409,7 @@ __global__ void __launch_bounds__(kStreamRows) k_gs_stream(int beg, int end, con
                                                             const int* __restrict__ pcol,
                                                             const T* __restrict__ pval,
                                                             const T* __restrict__ b, T* __restrict__ x) {
-    __shared__ T av[kStreamChunk<T>];
-    __shared__ T xv[kXv<T>];
-    __shared__ int pc[kStreamChunk<T>];
-    const int t0 = beg + blockIdx.x * kStreamRows;
-    const int t = t0 + threadIdx.x;
-    const int tlast = min(t0 + kStreamRows, end);
-    const int tb = __ldg(pptr + t0), te = __ldg(pptr + tlast);
-    int rb = 0, re = 0, row = -1;
-    if (t < end) { rb = __ldg(pptr + t); re = __ldg(pptr + t + 1); row = __ldg(rows + t); }
-    T s = 0, d = 0;
-    for (int c0 = tb; c0 < te; c0 += kStreamChunk<T>) {
-        const int c1 = min(c0 + kStreamChunk<T>, te);
-        stage_products<T, true>(c0, c1, pcol, pval, x, av, xv, pc);
-        __syncthreads();
-        const int kb = max(rb, c0), ke = min(re, c1);
-        for (int k = kb; k < ke; ++k) {
-            if (pc[k - c0] == row) d = (sizeof(T) == 8) ? av[k - c0] : __ldg(pval + k);
-            else s = row_add<T>(av, xv, k - c0, s);
-        }
-        __syncthreads();
-    }
-    if (t < end) x[row] = (__ldg(b + row) - s) / d;
+    stream_tiles<T, true, false>(beg, end, kGsTiles, rows, pptr, pcol, pval, x, b, x, nullptr);
 }
 
 template <class T>
@@ -415,7 +481,8 @@ void residual64(cudaStream_t s, const Csr& A, const double* x, const double* b, 
             k_res_stream<double, true><<<gn, kStreamRows, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, b, r, partial); ::pc::count_launches(1);
             k_finish<<<1, 1024, 0, s>>>(gn, partial, norm2); ::pc::count_launches(1);
         } else {
-            k_res_stream<double, false><<<g, kStreamRows, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, b, r, nullptr); ::pc::count_launches(1);
+            const int gt = (g + kTilesPerBlock<double> - 1) / kTilesPerBlock<double>;
+            k_res_stream<double, false><<<gt, kStreamRows, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, b, r, nullptr); ::pc::count_launches(1);
         }
     } else {
         int g = sparse_grid(A.n, A.lpr);
@@ -444,7 +511,7 @@ void l1_diagonal(cudaStream_t s, int32_t n, const int32_t* rowptr, const double*
 
 void residual32(cudaStream_t s, const Csr& A, const float* x, const float* b, float* r) {
     if (use_stream(A.n, A.lpr)) {
-        int g = (A.n + kStreamRows - 1) / kStreamRows;
+        int g = ((A.n + kStreamRows - 1) / kStreamRows + kTilesPerBlock<float> - 1) / kTilesPerBlock<float>;
         k_res_stream<float, false><<<g, kStreamRows, 0, s>>>(A.n, A.rowptr, A.col, A.val32, x, b, r, nullptr); ::pc::count_launches(1);
     } else {
         int g = sparse_grid(A.n, A.lpr);
@@ -482,8 +549,8 @@ template <class T>
 void gs_colour_perm(cudaStream_t s, int32_t beg, int32_t end, const int32_t* rows, const int32_t* pptr,
                     const int32_t* pcol, const T* pval, const T* b, T* x) {
     if (end <= beg) return;
-    int g = (end - beg + kStreamRows - 1) / kStreamRows;
-    k_gs_stream<T><<<g, kStreamRows, 0, s>>>(beg, end, rows, pptr, pcol, pval, b, x); ::pc::count_launches(1);
+    int g = ((end - beg + kStreamRows - 1) / kStreamRows + kGsTiles - 1) / kGsTiles;
+        k_gs_stream<T><<<g, kStreamRows, 0, s>>>(beg, end, rows, pptr, pcol, pval, b, x); ::pc::count_launches(1);
     PC_LAUNCH("gs_colour_perm");
 }
 
