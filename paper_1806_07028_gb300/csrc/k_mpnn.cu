@@ -134,9 +134,26 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+// erf by Abramowitz & Stegun, Handbook of Mathematical Functions (1964),
+// formula 7.1.26: erf(x) = 1 - (a1 t + ... + a5 t^5) exp(-x^2), t = 1/(1 + p x)
+// for x >= 0, odd in x, absolute error <= 1.5e-7 (far below the bfloat16
+// operands' resolution). It takes one fast exponential and one fast
+// reciprocal; the network evaluates it for every activation, where the
+// library erf's instruction count bounded the layer kernels.
+__device__ __forceinline__ float erf_as(float x) {
+    const float ax = fabsf(x);
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, ax, 1.0f));
+    float p = 1.061405429f;
+    p = fmaf(p, t, -1.453152027f);
+    p = fmaf(p, t, 1.421413741f);
+    p = fmaf(p, t, -0.284496736f);
+    p = fmaf(p, t, 0.254829592f);
+    const float y = 1.0f - p * t * __expf(-ax * ax);
+    return copysignf(y, x);
+}
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erf_as(x * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float x) {
-    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
+    return 0.5f * (1.0f + erf_as(x * 0.70710678118654752f)) + x * __expf(-0.5f * x * x) * 0.39894228040143268f;
 }
 
 // The MMA issue/commit/wait of one tile: thread 0 issues nk products of K = 16,
@@ -182,6 +199,13 @@ __global__ void k_mpnn_feat(int n, const int* __restrict__ rowptr, const int* __
     }
 }
 
+// |a_ij| in FP32, converted once per pass (the layers read it for every
+// feature lane; GB300 converts from FP64 at its low FP64 rate)
+__global__ void k_abs_f32(int64_t nnz, const double* __restrict__ val, float* __restrict__ aw) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x)
+        aw[k] = (float)fabs(val[k]);
+}
+
 // input head: centre features 1 and 2 (fsum: the feature column sums),
 // z_in = W_in f + b_in, G0 = GELU(z_in); one thread per row
 __global__ void k_mpnn_in(int n, const float* __restrict__ fsum, const float* __restrict__ wq,
@@ -208,7 +232,7 @@ __global__ void k_mpnn_in(int n, const float* __restrict__ fsum, const float* __
 // and G' = GELU(Z) in FP32. Xout / Zout keep the staged operand and Z for the
 // backward pass (null in inference).
 __global__ void __launch_bounds__(kThr, 2)
-    k_mpnn_layer(int n, const int* __restrict__ rowptr, const int* __restrict__ col, const double* __restrict__ val,
+    k_mpnn_layer(int n, const int* __restrict__ rowptr, const int* __restrict__ col, const float* __restrict__ aw,
                  const float* __restrict__ invD, const float* __restrict__ G, const float* __restrict__ gsum,
                  const __nv_bfloat16* __restrict__ Wl, const float* __restrict__ bias,
                  __nv_bfloat16* __restrict__ Xout, float* __restrict__ Zout, float* __restrict__ Gout,
@@ -256,7 +280,7 @@ __global__ void __launch_bounds__(kThr, 2)
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         j[u] = col[q + u];
-                        w[u] = (j[u] == row) ? 0.f : (float)fabs(val[q + u]);
+                        w[u] = (j[u] == row) ? 0.f : aw[q + u];
                     }
 #pragma unroll
                     for (int u = 0; u < 4; ++u) f[u] = *reinterpret_cast<const float2*>(G + (size_t)j[u] * kH + 2 * lane);
@@ -269,7 +293,7 @@ __global__ void __launch_bounds__(kThr, 2)
                 for (; q < e; ++q) {
                     const int j = col[q];
                     if (j == row) continue;
-                    const float w = (float)fabs(val[q]);
+                    const float w = aw[q];
                     const float2 f = *reinterpret_cast<const float2*>(G + (size_t)j * kH + 2 * lane);
                     a0 = fmaf(w, f.x, a0);
                     a1 = fmaf(w, f.y, a1);
@@ -507,7 +531,7 @@ __global__ void __launch_bounds__(kThr, 2)
 // dH_prev_i = dHs_i + sum_{k != i} |a_ik| dM_k / D_k (the neighbour mean's
 // transpose on the symmetric pattern); a warp per row, two features per lane
 __global__ void k_nbr_back(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
-                           const double* __restrict__ val, const float* __restrict__ invD,
+                           const float* __restrict__ aw, const float* __restrict__ invD,
                            const float* __restrict__ dHs, const float* __restrict__ dM, float* __restrict__ dH) {
     const int lane = threadIdx.x & 31;
     const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
@@ -523,7 +547,7 @@ __global__ void k_nbr_back(int n, const int* __restrict__ rowptr, const int* __r
             for (int u = 0; u < 4; ++u) k[u] = col[q + u];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                w[u] = (k[u] == i) ? 0.f : (float)fabs(val[q + u]) * invD[k[u]];
+                w[u] = (k[u] == i) ? 0.f : aw[q + u] * invD[k[u]];
                 m[u] = *reinterpret_cast<const float2*>(dM + (size_t)k[u] * kH + 2 * lane);
             }
 #pragma unroll
@@ -535,7 +559,7 @@ __global__ void k_nbr_back(int n, const int* __restrict__ rowptr, const int* __r
         for (; q < e; ++q) {
             const int k = col[q];
             if (k == i) continue;
-            const float w = (float)fabs(val[q]) * invD[k];
+            const float w = aw[q] * invD[k];
             const float2 m = *reinterpret_cast<const float2*>(dM + (size_t)k * kH + 2 * lane);
             a.x = fmaf(w, m.x, a.x);
             a.y = fmaf(w, m.y, a.y);
@@ -764,7 +788,7 @@ void mpnn_get_grad(Mpnn& M, float* h) {
 
 // Activations of one pass over a graph; the training caches only when needed.
 struct MpnnWork {
-    DBuf<float> invD, F, Zin, Z, G, gsum, dH, dHs, dM, dZ, part, hsum;
+    DBuf<float> aw, invD, F, Zin, Z, G, gsum, dH, dHs, dM, dZ, part, hsum;
     DBuf<__nv_bfloat16> X, dZb;
     DBuf<double> y, tau, lsep, lseq, ce, gy, gz;
     DBuf<int32_t> err;
@@ -797,6 +821,8 @@ static void forward(Ctx& c, Mpnn& P, const double* u, double* yhat, MpnnWork& w,
     w.err.alloc(c.mem, 1);
     PC_CUDA(cudaMemsetAsync(w.err.p, 0, sizeof(int32_t), s));
     w.invD.alloc(c.mem, n);
+    w.aw.alloc(c.mem, c.nnz);
+    k_abs_f32<<<grid_for(c.nnz), 256, 0, s>>>(c.nnz, c.val.p, w.aw.p); ::pc::count_launches(1);
     w.F.alloc(c.mem, (size_t)n * 3);
     w.G.alloc(c.mem, train ? nh * (L + 1) : nh * 2);
     w.gsum.alloc(c.mem, (size_t)kH * (L + 1));
@@ -821,7 +847,7 @@ static void forward(Ctx& c, Mpnn& P, const double* u, double* yhat, MpnnWork& w,
     const int ntiles = (n + kTile - 1) / kTile;
     const int grid = std::max(1, std::min(ntiles, 2 * kNumSMs));
     for (int l = 0; l < L; ++l) {
-        k_mpnn_layer<<<grid, kThr, smem, s>>>(n, c.rowptr.p, c.col.p, c.val.p, w.invD.p, Gl(l), w.gsum.p + l * kH,
+        k_mpnn_layer<<<grid, kThr, smem, s>>>(n, c.rowptr.p, c.col.p, w.aw.p, w.invD.p, Gl(l), w.gsum.p + l * kH,
                                               P.wl + (size_t)l * kH * 128,
                                               P.wq + kOffLayer0 + l * kLayerStride + kH * 128,
                                               train ? w.X.p + (size_t)l * nh * 2 : nullptr,
@@ -908,7 +934,7 @@ double mpnn_loss_grad(Ctx& c, Mpnn& P, const double* u, const double* target) {
         k_sum_parts<<<kH * 128, kSumThreads, 0, s>>>(gdw, kH * 128, wpart.p, gW); ::pc::count_launches(1);
         k_mpnn_dx<<<gdx, kThr, 32768, s>>>(n, w.dZb.p, P.wl + (size_t)l * kH * 128, w.dHs.p, w.dM.p, w.err.p);
         ::pc::count_launches(1);
-        k_nbr_back<<<grid_for((int64_t)n * 32), 256, 0, s>>>(n, c.rowptr.p, c.col.p, c.val.p, w.invD.p, w.dHs.p,
+        k_nbr_back<<<grid_for((int64_t)n * 32), 256, 0, s>>>(n, c.rowptr.p, c.col.p, w.aw.p, w.invD.p, w.dHs.p,
                                                             w.dM.p, w.dH.p);
         ::pc::count_launches(1);
     }
