@@ -133,7 +133,7 @@ __global__ void k_rowprod_thread(int nrows, Src src, int* __restrict__ cnt,
 // of equal columns adds the run's values in contribution order. Rows with more
 // than kWarpMembers member rows or kWarpCap contributions are flagged for the
 // block kernels.
-constexpr int kWarpCap = 128;
+constexpr int kWarpCap = 256;
 constexpr int kWarpMembers = 64;
 constexpr int kWarpsPerBlock = 8;
 
@@ -517,6 +517,57 @@ __global__ void k_order_rows_thread(int n, const int* __restrict__ ptr, const in
 }
 
 // Long rows: bitonic sort of (~bits(w), col) packed as two keys via an index sort.
+// Warp per row for rows of kThreadCap+1 .. kOrderWarpCap entries: the row's
+// weights and columns staged in shared memory, its entry indices sorted by a
+// warp bitonic sort in the order (w descending, column ascending).
+constexpr int kOrderWarpCap = 256;
+struct OrderScratch {
+    double w[kOrderWarpCap];
+    int c[kOrderWarpCap];
+    uint16_t idx[kOrderWarpCap];
+};
+
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+    k_order_rows_warp(int nrows, const int* __restrict__ rows, const int* __restrict__ ptr,
+                      const int* __restrict__ col, const double* __restrict__ w, int* __restrict__ scol,
+                      double* __restrict__ sw) {
+    __shared__ OrderScratch os_all[kWarpsPerBlock];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    OrderScratch& S = os_all[wib];
+    for (int64_t i = (int64_t)blockIdx.x * kWarpsPerBlock + wib; i < nrows; i += (int64_t)gridDim.x * kWarpsPerBlock) {
+        const int u = rows[i];
+        const int b = ptr[u], len = ptr[u + 1] - b;
+        int P = 32;
+        while (P < len) P <<= 1;
+        for (int e = lane; e < P; e += 32) {
+            if (e < len) { S.w[e] = w[b + e]; S.c[e] = col[b + e]; }
+            S.idx[e] = (e < len) ? (uint16_t)e : (uint16_t)0xffff;
+        }
+        __syncwarp();
+        for (int k = 2; k <= P; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int e = lane; e < P; e += 32) {
+                    const int ex = e ^ j;
+                    if (ex > e) {
+                        const uint16_t a = S.idx[e], c2 = S.idx[ex];
+                        bool a_gt;   // a comes after c2; sentinels last
+                        if (a == 0xffff) a_gt = (c2 != 0xffff);
+                        else if (c2 == 0xffff) a_gt = false;
+                        else a_gt = (S.w[a] < S.w[c2]) || (S.w[a] == S.w[c2] && S.c[a] > S.c[c2]);
+                        if (a_gt == ((e & k) == 0)) { S.idx[e] = c2; S.idx[ex] = a; }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        for (int e = lane; e < len; e += 32) {
+            scol[b + e] = S.c[S.idx[e]];
+            sw[b + e] = S.w[S.idx[e]];
+        }
+        __syncwarp();
+    }
+}
+
 __global__ void k_order_rows_block(const int* __restrict__ rows, const int* __restrict__ ptr,
                                    const int* __restrict__ col, const double* __restrict__ w,
                                    int* __restrict__ scol, double* __restrict__ sw,
@@ -1028,24 +1079,38 @@ int32_t path_cover(Ctx& c, int32_t n, const Reweighted& t, int32_t* nbr0, int32_
         std::sort(rows.begin(), rows.end());
         std::vector<int32_t> hptr((size_t)n + 1);
         d2h(c, hptr.data(), t.ptr.p, (size_t)n + 1);
-        std::vector<int64_t> off(nlong);
+        // rows up to kOrderWarpCap entries: a warp each; longer: a block each
+        std::vector<int32_t> mid, big;
+        for (int32_t r : rows) (hptr[r + 1] - hptr[r] <= kOrderWarpCap ? mid : big).push_back(r);
+        DBuf<int32_t> dmid;
+        if (!mid.empty()) {
+            dmid.alloc(c.mem, mid.size());
+            PC_CUDA(cudaMemcpyAsync(dmid.p, mid.data(), sizeof(int32_t) * mid.size(), cudaMemcpyHostToDevice, s));
+            k_order_rows_warp<<<grid_warps((int64_t)mid.size()), kWarpsPerBlock * 32, 0, s>>>(
+                (int)mid.size(), dmid.p, t.ptr.p, t.col.p, t.w.p, scol.p, sw.p); ::pc::count_launches(1);
+            PC_LAUNCH("order_rows_warp");
+        }
+        const int32_t nbig = (int32_t)big.size();
+        std::vector<int64_t> off(nbig);
         int64_t tot = 0;
-        for (int32_t i = 0; i < nlong; ++i) {
+        for (int32_t i = 0; i < nbig; ++i) {
             off[i] = tot;
-            int64_t len = hptr[rows[i] + 1] - hptr[rows[i]], P = 1;
+            int64_t len = hptr[big[i] + 1] - hptr[big[i]], P = 1;
             while (P < len) P <<= 1;
             tot += P;
         }
         DBuf<int32_t> drows;
         DBuf<int64_t> doff;
         DBuf<uint32_t> gidx;
-        drows.alloc(c.mem, nlong);
-        doff.alloc(c.mem, nlong);
-        gidx.alloc(c.mem, tot);
-        PC_CUDA(cudaMemcpyAsync(drows.p, rows.data(), sizeof(int32_t) * nlong, cudaMemcpyHostToDevice, s));
-        PC_CUDA(cudaMemcpyAsync(doff.p, off.data(), sizeof(int64_t) * nlong, cudaMemcpyHostToDevice, s));
-        k_order_rows_block<<<nlong, kBlock, 0, s>>>(drows.p, t.ptr.p, t.col.p, t.w.p, scol.p, sw.p, gidx.p, doff.p); ::pc::count_launches(1);
-        PC_LAUNCH("order_rows_block");
+        if (nbig > 0) {
+            drows.alloc(c.mem, nbig);
+            doff.alloc(c.mem, nbig);
+            gidx.alloc(c.mem, tot);
+            PC_CUDA(cudaMemcpyAsync(drows.p, big.data(), sizeof(int32_t) * nbig, cudaMemcpyHostToDevice, s));
+            PC_CUDA(cudaMemcpyAsync(doff.p, off.data(), sizeof(int64_t) * nbig, cudaMemcpyHostToDevice, s));
+            k_order_rows_block<<<nbig, kBlock, 0, s>>>(drows.p, t.ptr.p, t.col.p, t.w.p, scol.p, sw.p, gidx.p, doff.p); ::pc::count_launches(1);
+            PC_LAUNCH("order_rows_block");
+        }
         sync(c);
     }
     DBuf<int32_t> deg, oe, cptr, bv, cf, ct, counters;
