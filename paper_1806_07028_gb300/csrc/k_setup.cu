@@ -18,6 +18,7 @@ namespace {
 
 constexpr int kThreadCap = 32;        // unique keys a thread-per-row product keeps
 constexpr int kBlockCap = 2048;       // contributions a block-per-row product stages in smem
+constexpr int kOrderWarpCap = 256;    // candidates a warp orders in shared memory
 constexpr uint32_t kSkip = 0xffffffffu;
 
 inline int grid1(int64_t n, int block = kBlock) {
@@ -263,20 +264,20 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_rowprod_warp(
     }
 }
 
-// Contribution count of every row the warp kernel takes (0 for the rows it
-// leaves to the block kernels): the temporary layout of the one-pass product.
+// Contribution count of every row a one-pass kernel takes (the warp kernel,
+// or the shared-memory block kernel up to kBlockCap contributions; 0 for the
+// larger rows): the temporary layout of the one-pass product.
 template <class Src>
 __global__ void k_rowprod_ubrow(int nrows, Src src, int64_t* __restrict__ ub) {
     FOR_EACH(r64, nrows) {
         const int r = (int)r64;
         const int nm = src.nmem(r);
         int64_t s = 0;
-        if (nm <= kWarpMembers)
-            for (int t = 0; t < nm; ++t) {
-                const int j = src.mem_row(r, t);
-                s += src.in_end(j) - src.in_beg(j);
-            }
-        ub[r] = (nm <= kWarpMembers && s <= kWarpCap) ? s : 0;
+        for (int t = 0; t < nm && s <= kBlockCap; ++t) {
+            const int j = src.mem_row(r, t);
+            s += src.in_end(j) - src.in_beg(j);
+        }
+        ub[r] = (s <= kBlockCap) ? s : 0;
     }
 }
 
@@ -296,6 +297,31 @@ __global__ void k_rowprod_compact(int nrows, const unsigned char* __restrict__ i
         for (int q = lane; q < m; q += 32) {
             ocol[o + q] = tcol[t + q];
             if (oval) oval[o + q] = tval[t + q];
+        }
+    }
+}
+
+// Split the rows the warp kernel left: up to kBlockCap contributions to the
+// shared-memory block kernel (list B), larger to the global-memory one (list
+// C, with their contribution counts). A row's result does not depend on the
+// order of the lists.
+template <class Src>
+__global__ void k_rowprod_split(int nlong, const int* __restrict__ rows, Src src, int* __restrict__ listB,
+                                int* __restrict__ listC, int64_t* __restrict__ ubC, int* __restrict__ counts) {
+    FOR_EACH(i, nlong) {
+        const int r = rows[i];
+        int64_t s = 0;
+        const int nm = src.nmem(r);
+        for (int t = 0; t < nm; ++t) {
+            const int j = src.mem_row(r, t);
+            s += src.in_end(j) - src.in_beg(j);
+        }
+        if (s <= kBlockCap) {
+            listB[atomicAdd(&counts[0], 1)] = r;
+        } else {
+            const int k = atomicAdd(&counts[1], 1);
+            listC[k] = r;
+            ubC[k] = s;
         }
     }
 }
@@ -371,11 +397,15 @@ __device__ int block_excl_scan(int flag, int* total) {
 
 // Block per long row: stage (key << 32 | seq) and values by sequence number,
 // sort, then each run of equal keys is summed in sequence order.
-template <class Src, bool FILL, bool GLOBAL>
+// MODE as for the warp kernel: 0 count, 1 fill at optr[r], 2 count and write
+// at tptr[r] of the temporary layout (clearing the row's long flag).
+template <class Src, int MODE, bool GLOBAL>
 __global__ void k_rowprod_block(const int* __restrict__ rows, Src src, int* __restrict__ cnt,
                                 const int* __restrict__ optr, int* __restrict__ ocol,
                                 double* __restrict__ oval, uint64_t* __restrict__ gkeys,
-                                double* __restrict__ gvals, const int64_t* __restrict__ goff) {
+                                double* __restrict__ gvals, const int64_t* __restrict__ goff,
+                                const int64_t* __restrict__ tptr, unsigned char* __restrict__ is_long) {
+    constexpr bool FILL = MODE != 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int r = rows[blockIdx.x];
     uint64_t* keys;
@@ -426,13 +456,14 @@ __global__ void k_rowprod_block(const int* __restrict__ rows, Src src, int* __re
                 if ((uint32_t)(kq >> 32) != kk || kq == ~0ull) break;
                 s = __dadd_rn(s, vals[(uint32_t)kq]);
             }
-            int o = optr[r] + carry + pre;
+            const int64_t o = (MODE == 1 ? (int64_t)optr[r] : tptr[r]) + carry + pre;
             ocol[o] = (int)kk;
             if (oval) oval[o] = s;
         }
         carry += tot;
     }
-    if (!FILL && threadIdx.x == 0) cnt[r] = carry;
+    if (MODE != 1 && threadIdx.x == 0) cnt[r] = carry;
+    if (MODE == 2 && threadIdx.x == 0) is_long[r] = 0;
 }
 
 // ---------------------------------------------------------------- weights
@@ -493,9 +524,10 @@ __global__ void k_order_rows_thread(int n, const int* __restrict__ ptr, const in
     FOR_EACH(u64, n) {
         int u = (int)u64;
         int b = ptr[u], len = ptr[u + 1] - b;
-        if (len > kThreadCap) {
-            is_long[u] = 1;
-            long_list[atomicAdd(long_count, 1)] = u;
+        if (len > kThreadCap) {   // 1: a warp sorts it; 2: a block (listed)
+            const bool big = len > kOrderWarpCap;
+            is_long[u] = big ? 2 : 1;
+            if (big) long_list[atomicAdd(long_count, 1)] = u;
             continue;
         }
         is_long[u] = 0;
@@ -517,10 +549,9 @@ __global__ void k_order_rows_thread(int n, const int* __restrict__ ptr, const in
 }
 
 // Long rows: bitonic sort of (~bits(w), col) packed as two keys via an index sort.
-// Warp per row for rows of kThreadCap+1 .. kOrderWarpCap entries: the row's
-// weights and columns staged in shared memory, its entry indices sorted by a
-// warp bitonic sort in the order (w descending, column ascending).
-constexpr int kOrderWarpCap = 256;
+// Warp per row for rows of kThreadCap+1 .. kOrderWarpCap entries (class 1):
+// the row's weights and columns staged in shared memory, its entry indices
+// sorted by a warp bitonic sort in the order (w descending, column ascending).
 struct OrderScratch {
     double w[kOrderWarpCap];
     int c[kOrderWarpCap];
@@ -528,14 +559,15 @@ struct OrderScratch {
 };
 
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-    k_order_rows_warp(int nrows, const int* __restrict__ rows, const int* __restrict__ ptr,
+    k_order_rows_warp(int n, const unsigned char* __restrict__ cls, const int* __restrict__ ptr,
                       const int* __restrict__ col, const double* __restrict__ w, int* __restrict__ scol,
                       double* __restrict__ sw) {
     __shared__ OrderScratch os_all[kWarpsPerBlock];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     OrderScratch& S = os_all[wib];
-    for (int64_t i = (int64_t)blockIdx.x * kWarpsPerBlock + wib; i < nrows; i += (int64_t)gridDim.x * kWarpsPerBlock) {
-        const int u = rows[i];
+    for (int64_t i = (int64_t)blockIdx.x * kWarpsPerBlock + wib; i < n; i += (int64_t)gridDim.x * kWarpsPerBlock) {
+        if (cls[i] != 1) continue;
+        const int u = (int)i;
         const int b = ptr[u], len = ptr[u + 1] - b;
         int P = 32;
         while (P < len) P <<= 1;
@@ -566,6 +598,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
         }
         __syncwarp();
     }
+}
+
+__global__ void k_row_lengths(int m, const int* __restrict__ rows, const int* __restrict__ ptr, int* __restrict__ len) {
+    FOR_EACH(i, m) len[i] = ptr[rows[i] + 1] - ptr[rows[i]];
 }
 
 __global__ void k_order_rows_block(const int* __restrict__ rows, const int* __restrict__ ptr,
@@ -965,58 +1001,52 @@ static void row_product(Ctx& c, int32_t nrows, const Src& src, DBuf<int32_t>& op
     ::pc::count_launches(1);
     PC_LAUNCH("rowprod_warp(once)");
     int32_t nlong = read_i32(c, long_count.p);
-    std::vector<int32_t> rowsB, rowsC;
-    std::vector<int64_t> ubC;
+    int32_t nB = 0, nC = 0;
     DBuf<int32_t> dB, dC;
     DBuf<int64_t> offC;
     DBuf<uint64_t> gkeys;
     DBuf<double> gvals;
     if (nlong > 0) {
-        std::vector<int32_t> rows(nlong);
-        d2h(c, rows.data(), long_list.p, nlong);
-        std::sort(rows.begin(), rows.end());   // deterministic order of the block launches
-        DBuf<int32_t> drows;
-        DBuf<int64_t> ub;
-        drows.alloc(c.mem, nlong);
-        ub.alloc(c.mem, nlong);
-        PC_CUDA(cudaMemcpyAsync(drows.p, rows.data(), sizeof(int32_t) * nlong, cudaMemcpyHostToDevice, s));
-        k_rowprod_ub<Src><<<grid1(nlong), kBlock, 0, s>>>(nlong, drows.p, src, ub.p); ::pc::count_launches(1);
-        PC_LAUNCH("rowprod_ub");
-        std::vector<int64_t> hub(nlong);
-        d2h(c, hub.data(), ub.p, nlong);
-        int64_t totC = 0;
-        std::vector<int64_t> hoff;
-        for (int32_t i = 0; i < nlong; ++i) {
-            if (hub[i] >= (int64_t)1 << 31) fail(PCAMG_ERR_INVALID, "row product: a row has 2^31 or more contributions");
-            if (hub[i] <= kBlockCap) rowsB.push_back(rows[i]);
-            else {
-                rowsC.push_back(rows[i]);
-                hoff.push_back(totC);
+        DBuf<int32_t> counts;
+        DBuf<int64_t> ubC;
+        counts.alloc(c.mem, 2);
+        dB.alloc(c.mem, nlong);
+        dC.alloc(c.mem, nlong);
+        ubC.alloc(c.mem, nlong);
+        PC_CUDA(cudaMemsetAsync(counts.p, 0, sizeof(int32_t) * 2, s));
+        k_rowprod_split<Src><<<grid1(nlong), kBlock, 0, s>>>(nlong, long_list.p, src, dB.p, dC.p, ubC.p, counts.p);
+        ::pc::count_launches(1);
+        PC_LAUNCH("rowprod_split");
+        int32_t hc[2] = {0, 0};
+        d2h(c, hc, counts.p, 2);
+        nB = hc[0];
+        nC = hc[1];
+        if (nB > 0) {   // one pass, into the temporary layout
+            size_t smem = kBlockCap * (sizeof(uint64_t) + sizeof(double));
+            k_rowprod_block<Src, 2, false><<<(unsigned)nB, kBlock, smem, s>>>(
+                dB.p, src, cnt.p, nullptr, tcol.p, oval ? tval.p : nullptr, nullptr, nullptr, nullptr, tptr.p, is_long.p);
+            ::pc::count_launches(1);
+            PC_LAUNCH("rowprod_block(once)");
+        }
+        if (nC > 0) {   // rare: staging in global memory, count then fill
+            std::vector<int64_t> hub(nC), hoff(nC);
+            d2h(c, hub.data(), ubC.p, nC);
+            int64_t totC = 0;
+            for (int32_t i = 0; i < nC; ++i) {
+                if (hub[i] >= (int64_t)1 << 31) fail(PCAMG_ERR_INVALID, "row product: a row has 2^31 or more contributions");
+                hoff[i] = totC;
                 int64_t P = 1;
                 while (P < hub[i]) P <<= 1;
                 totC += P;
             }
-        }
-        if (!rowsB.empty()) {
-            dB.alloc(c.mem, rowsB.size());
-            PC_CUDA(cudaMemcpyAsync(dB.p, rowsB.data(), sizeof(int32_t) * rowsB.size(), cudaMemcpyHostToDevice, s));
-            size_t smem = kBlockCap * (sizeof(uint64_t) + sizeof(double));
-            k_rowprod_block<Src, false, false><<<(unsigned)rowsB.size(), kBlock, smem, s>>>(
-                dB.p, src, cnt.p, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr); ::pc::count_launches(1);
-            PC_LAUNCH("rowprod_block(count)");
-        }
-        if (!rowsC.empty()) {
-            dC.alloc(c.mem, rowsC.size());
-            offC.alloc(c.mem, rowsC.size());
+            offC.alloc(c.mem, nC);
             gkeys.alloc(c.mem, totC);
             gvals.alloc(c.mem, totC);
-            PC_CUDA(cudaMemcpyAsync(dC.p, rowsC.data(), sizeof(int32_t) * rowsC.size(), cudaMemcpyHostToDevice, s));
-            PC_CUDA(cudaMemcpyAsync(offC.p, hoff.data(), sizeof(int64_t) * hoff.size(), cudaMemcpyHostToDevice, s));
-            k_rowprod_block<Src, false, true><<<(unsigned)rowsC.size(), kBlock, 0, s>>>(
-                dC.p, src, cnt.p, nullptr, nullptr, nullptr, gkeys.p, gvals.p, offC.p); ::pc::count_launches(1);
+            PC_CUDA(cudaMemcpyAsync(offC.p, hoff.data(), sizeof(int64_t) * nC, cudaMemcpyHostToDevice, s));
+            k_rowprod_block<Src, 0, true><<<(unsigned)nC, kBlock, 0, s>>>(
+                dC.p, src, cnt.p, nullptr, nullptr, nullptr, gkeys.p, gvals.p, offC.p, nullptr, nullptr); ::pc::count_launches(1);
             PC_LAUNCH("rowprod_global(count)");
         }
-        sync(c);
     }
     optr.alloc(c.mem, (size_t)nrows + 1);
     int64_t total = scan_i32(c, cnt.p, optr.p, nrows);
@@ -1028,15 +1058,9 @@ static void row_product(Ctx& c, int32_t nrows, const Src& src, DBuf<int32_t>& op
                                                                          oval ? tval.p : nullptr, optr.p, ocol.p, ov);
     ::pc::count_launches(1);
     PC_LAUNCH("rowprod_compact");
-    if (!rowsB.empty()) {
-        size_t smem = kBlockCap * (sizeof(uint64_t) + sizeof(double));
-        k_rowprod_block<Src, true, false><<<(unsigned)rowsB.size(), kBlock, smem, s>>>(
-            dB.p, src, nullptr, optr.p, ocol.p, ov, nullptr, nullptr, nullptr); ::pc::count_launches(1);
-        PC_LAUNCH("rowprod_block(fill)");
-    }
-    if (!rowsC.empty()) {
-        k_rowprod_block<Src, true, true><<<(unsigned)rowsC.size(), kBlock, 0, s>>>(
-            dC.p, src, nullptr, optr.p, ocol.p, ov, gkeys.p, gvals.p, offC.p); ::pc::count_launches(1);
+    if (nC > 0) {
+        k_rowprod_block<Src, 1, true><<<(unsigned)nC, kBlock, 0, s>>>(
+            dC.p, src, nullptr, optr.p, ocol.p, ov, gkeys.p, gvals.p, offC.p, nullptr, nullptr); ::pc::count_launches(1);
         PC_LAUNCH("rowprod_global(fill)");
     }
     *nnz_out = total;
@@ -1072,45 +1096,36 @@ int32_t path_cover(Ctx& c, int32_t n, const Reweighted& t, int32_t* nbr0, int32_
     k_order_rows_thread<<<grid1(n), kBlock, 0, s>>>(n, t.ptr.p, t.col.p, t.w.p, scol.p, sw.p,
                                                      is_long.p, long_list.p, long_count.p); ::pc::count_launches(1);
     PC_LAUNCH("order_rows");
-    int32_t nlong = read_i32(c, long_count.p);
-    if (nlong > 0) {
-        std::vector<int32_t> rows(nlong);
-        d2h(c, rows.data(), long_list.p, nlong);
-        std::sort(rows.begin(), rows.end());
-        std::vector<int32_t> hptr((size_t)n + 1);
-        d2h(c, hptr.data(), t.ptr.p, (size_t)n + 1);
-        // rows up to kOrderWarpCap entries: a warp each; longer: a block each
-        std::vector<int32_t> mid, big;
-        for (int32_t r : rows) (hptr[r + 1] - hptr[r] <= kOrderWarpCap ? mid : big).push_back(r);
-        DBuf<int32_t> dmid;
-        if (!mid.empty()) {
-            dmid.alloc(c.mem, mid.size());
-            PC_CUDA(cudaMemcpyAsync(dmid.p, mid.data(), sizeof(int32_t) * mid.size(), cudaMemcpyHostToDevice, s));
-            k_order_rows_warp<<<grid_warps((int64_t)mid.size()), kWarpsPerBlock * 32, 0, s>>>(
-                (int)mid.size(), dmid.p, t.ptr.p, t.col.p, t.w.p, scol.p, sw.p); ::pc::count_launches(1);
-            PC_LAUNCH("order_rows_warp");
-        }
-        const int32_t nbig = (int32_t)big.size();
+    k_order_rows_warp<<<grid_warps(n), kWarpsPerBlock * 32, 0, s>>>(n, is_long.p, t.ptr.p, t.col.p, t.w.p,
+                                                                     scol.p, sw.p);
+    ::pc::count_launches(1);
+    PC_LAUNCH("order_rows_warp");
+    const int32_t nbig = read_i32(c, long_count.p);
+    if (nbig > 0) {   // rare: rows longer than kOrderWarpCap, a block each
+        std::vector<int32_t> big(nbig), hl(nbig);
+        d2h(c, big.data(), long_list.p, nbig);
+        DBuf<int32_t> dlen;
+        dlen.alloc(c.mem, nbig);
+        k_row_lengths<<<grid1(nbig), kBlock, 0, s>>>(nbig, long_list.p, t.ptr.p, dlen.p); ::pc::count_launches(1);
+        d2h(c, hl.data(), dlen.p, nbig);
         std::vector<int64_t> off(nbig);
         int64_t tot = 0;
         for (int32_t i = 0; i < nbig; ++i) {
-            off[i] = tot;
-            int64_t len = hptr[big[i] + 1] - hptr[big[i]], P = 1;
+            int64_t len = hl[i], P = 1;
             while (P < len) P <<= 1;
+            off[i] = tot;
             tot += P;
         }
         DBuf<int32_t> drows;
         DBuf<int64_t> doff;
         DBuf<uint32_t> gidx;
-        if (nbig > 0) {
-            drows.alloc(c.mem, nbig);
-            doff.alloc(c.mem, nbig);
-            gidx.alloc(c.mem, tot);
-            PC_CUDA(cudaMemcpyAsync(drows.p, big.data(), sizeof(int32_t) * nbig, cudaMemcpyHostToDevice, s));
-            PC_CUDA(cudaMemcpyAsync(doff.p, off.data(), sizeof(int64_t) * nbig, cudaMemcpyHostToDevice, s));
-            k_order_rows_block<<<nbig, kBlock, 0, s>>>(drows.p, t.ptr.p, t.col.p, t.w.p, scol.p, sw.p, gidx.p, doff.p); ::pc::count_launches(1);
-            PC_LAUNCH("order_rows_block");
-        }
+        drows.alloc(c.mem, nbig);
+        doff.alloc(c.mem, nbig);
+        gidx.alloc(c.mem, tot);
+        PC_CUDA(cudaMemcpyAsync(drows.p, big.data(), sizeof(int32_t) * nbig, cudaMemcpyHostToDevice, s));
+        PC_CUDA(cudaMemcpyAsync(doff.p, off.data(), sizeof(int64_t) * nbig, cudaMemcpyHostToDevice, s));
+        k_order_rows_block<<<nbig, kBlock, 0, s>>>(drows.p, t.ptr.p, t.col.p, t.w.p, scol.p, sw.p, gidx.p, doff.p); ::pc::count_launches(1);
+        PC_LAUNCH("order_rows_block");
         sync(c);
     }
     DBuf<int32_t> deg, oe, cptr, bv, cf, ct, counters;
