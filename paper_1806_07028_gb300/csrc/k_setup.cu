@@ -517,39 +517,19 @@ __device__ __forceinline__ bool edge_before(double w1, int a1, int b1, double w2
 
 // Each row re-ordered by (w desc, column asc): the order in which a vertex
 // proposes its edges. Thread per row for short rows.
-__global__ void k_order_rows_thread(int n, const int* __restrict__ ptr, const int* __restrict__ col,
-                                    const double* __restrict__ w, int* __restrict__ scol,
-                                    double* __restrict__ sw, unsigned char* __restrict__ is_long,
-                                    int* __restrict__ long_list, int* __restrict__ long_count) {
+// Class of every row for the proposal ordering: 1 = up to kOrderWarpCap
+// candidates, sorted by a warp; 2 = longer, listed for a block each.
+__global__ void k_order_rows_classify(int n, const int* __restrict__ ptr, unsigned char* __restrict__ cls,
+                                      int* __restrict__ long_list, int* __restrict__ long_count) {
     FOR_EACH(u64, n) {
-        int u = (int)u64;
-        int b = ptr[u], len = ptr[u + 1] - b;
-        if (len > kThreadCap) {   // 1: a warp sorts it; 2: a block (listed)
-            const bool big = len > kOrderWarpCap;
-            is_long[u] = big ? 2 : 1;
-            if (big) long_list[atomicAdd(long_count, 1)] = u;
-            continue;
-        }
-        is_long[u] = 0;
-        int c[kThreadCap];
-        double x[kThreadCap];
-        int m = 0;
-        for (int k = 0; k < len; ++k) {
-            int cv = col[b + k];
-            double wv = w[b + k];
-            int p = m;
-            while (p > 0 && (x[p - 1] < wv || (x[p - 1] == wv && c[p - 1] > cv))) --p;
-            for (int q = m; q > p; --q) { c[q] = c[q - 1]; x[q] = x[q - 1]; }
-            c[p] = cv;
-            x[p] = wv;
-            ++m;
-        }
-        for (int k = 0; k < len; ++k) { scol[b + k] = c[k]; sw[b + k] = x[k]; }
+        const int u = (int)u64;
+        const bool big = ptr[u + 1] - ptr[u] > kOrderWarpCap;
+        cls[u] = big ? 2 : 1;
+        if (big) long_list[atomicAdd(long_count, 1)] = u;
     }
 }
 
-// Long rows: bitonic sort of (~bits(w), col) packed as two keys via an index sort.
-// Warp per row for rows of kThreadCap+1 .. kOrderWarpCap entries (class 1):
+// Warp per row for rows of up to kOrderWarpCap entries (class 1):
 // the row's weights and columns staged in shared memory, its entry indices
 // sorted by a warp bitonic sort in the order (w descending, column ascending).
 struct OrderScratch {
@@ -1093,8 +1073,8 @@ int32_t path_cover(Ctx& c, int32_t n, const Reweighted& t, int32_t* nbr0, int32_
     long_count.alloc(c.mem, 1);
     is_long.alloc(c.mem, n);
     PC_CUDA(cudaMemsetAsync(long_count.p, 0, sizeof(int32_t), s));
-    k_order_rows_thread<<<grid1(n), kBlock, 0, s>>>(n, t.ptr.p, t.col.p, t.w.p, scol.p, sw.p,
-                                                     is_long.p, long_list.p, long_count.p); ::pc::count_launches(1);
+    k_order_rows_classify<<<grid1(n), kBlock, 0, s>>>(n, t.ptr.p, is_long.p, long_list.p, long_count.p);
+    ::pc::count_launches(1);
     PC_LAUNCH("order_rows");
     k_order_rows_warp<<<grid_warps(n), kWarpsPerBlock * 32, 0, s>>>(n, is_long.p, t.ptr.p, t.col.p, t.w.p,
                                                                      scol.p, sw.p);
