@@ -27,6 +27,14 @@ void count_launches(int64_t k) {
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 bool capturing() { return t_capture_acc != nullptr; }
 
+static thread_local bool t_pdl_prev_copy = false;
+bool pdl_next() {
+    const bool ok = t_capture_acc != nullptr && !t_pdl_prev_copy;
+    t_pdl_prev_copy = false;
+    return ok;
+}
+void pdl_after_copy() { t_pdl_prev_copy = true; }
+
 void check_cuda(cudaError_t e, const char* what) {
     if (e == cudaSuccess) return;
     cudaGetLastError();
@@ -202,6 +210,7 @@ template <class T>
 static void cycle_body(Ctx& c, Hier& h, int gamma) {
     Level& L0 = h.lev[0];
     PC_CUDA(cudaMemsetAsync(LV<T>::x(L0), 0, sizeof(T) * L0.n, c.stream));
+    pdl_after_copy();
     cycle_level<T>(c, h, 0, gamma, false, true);
 }
 

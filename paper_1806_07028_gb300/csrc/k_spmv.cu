@@ -61,6 +61,8 @@ __global__ void __launch_bounds__(kBlock) k_residual(int n, const int* __restric
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double acc2 = 0.0;
+    pdl_wait();
+    pdl_trigger();
     for (int64_t row0 = warp * RPW; row0 < n; row0 += nwarps * RPW) {
         int64_t row = row0 + grp;
         T s = 0;
@@ -139,6 +141,8 @@ __global__ void __launch_bounds__(kBlock) k_gs(int nrows, const int* __restrict_
     const int sub = lane % LPR, grp = lane / LPR;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    pdl_wait();
+    pdl_trigger();
     for (int64_t t0 = warp * RPW; t0 < nrows; t0 += nwarps * RPW) {
         int64_t t = t0 + grp;
         T s = 0, d = 0;
@@ -166,6 +170,8 @@ template <class T>
 __global__ void k_restrict(int nc, const int* __restrict__ agg_ptr, const int* __restrict__ mem,
                            const T* __restrict__ pval, const T* __restrict__ r, T* __restrict__ bc,
                            T* __restrict__ xc, const T* __restrict__ dc) {
+    pdl_wait();
+    pdl_trigger();
     for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
         T s = 0;
         int beg = __ldg(agg_ptr + I), end = __ldg(agg_ptr + I + 1);
@@ -181,6 +187,8 @@ __global__ void k_restrict(int nc, const int* __restrict__ agg_ptr, const int* _
 template <class T>
 __global__ void k_prolong(int n, const int* __restrict__ agg, const T* __restrict__ pval,
                           const T* __restrict__ xc, T* __restrict__ x) {
+    pdl_wait();
+    pdl_trigger();
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
         T c = __ldg(xc + __ldg(agg + u));
         x[u] += pval ? __ldg(pval + u) * c : c;
@@ -287,7 +295,7 @@ struct TileMeta {
     T bv;
 };
 
-template <class T, bool PERM>
+template <class T, bool PERM, bool WITH_B = true>
 __device__ __forceinline__ TileMeta<T> tile_meta(int t0, int tend, const int* __restrict__ ptr,
                                                  const int* __restrict__ rows, const T* __restrict__ b) {
     TileMeta<T> m;
@@ -302,7 +310,7 @@ __device__ __forceinline__ TileMeta<T> tile_meta(int t0, int tend, const int* __
         m.rb = __ldg(ptr + t);
         m.re = __ldg(ptr + t + 1);
         m.row = PERM ? __ldg(rows + t) : t;
-        m.bv = __ldg(b + m.row);
+        if (WITH_B) m.bv = __ldg(b + m.row);
     }
     return m;
 }
@@ -311,7 +319,8 @@ __device__ __forceinline__ TileMeta<T> tile_meta(int t0, int tend, const int* __
 // chunk's rows from shared memory, the loads of the next chunk (of this tile or
 // the first of the next tile) and the next tile's row pointers and b are
 // already in flight, so the only exposed latency per tile is the x gather.
-// The row sums keep the CSR order of each row.
+// The row sums keep the CSR order of each row. The first tile's row pointers
+// and chunk (hierarchy data) are loaded before pdl_wait(); b and x after it.
 //   PERM = false: rows t of [0, n) (residual r = b - A x, optional ||r||^2);
 //   PERM = true:  permuted rows rows[t] of [beg, end) of one colour, Gauss-Seidel
 //                 x_row = (b_row - sum_{j != row} a x_j) / a_row,row.
@@ -328,9 +337,12 @@ __device__ __forceinline__ void stream_tiles(int beg, int end, int tpb, const in
     const int tstop = min(ntiles, tfirst + tpb);
     double rr2 = 0.0;
     if (tfirst < tstop) {
-        TileMeta<T> M = tile_meta<T, PERM>(beg + tfirst * kStreamRows, end, ptr, rows, b);
+        TileMeta<T> M = tile_meta<T, PERM, false>(beg + tfirst * kStreamRows, end, ptr, rows, b);
         ChunkRegs<T> R;
         load_chunk<T>(M.tb, min(M.tb + kStreamChunk<T>, M.te), col, val, R);
+        pdl_wait();
+        pdl_trigger();
+        if (M.row >= 0) M.bv = __ldg(b + M.row);
         for (int t = tfirst; t < tstop; ++t) {
             TileMeta<T> Mn = M;
             T s = 0, d = 0;
@@ -365,6 +377,9 @@ __device__ __forceinline__ void stream_tiles(int beg, int end, int tpb, const in
             }
             M = Mn;
         }
+    } else {
+        pdl_wait();
+        pdl_trigger();
     }
     if (NORM) {
         __shared__ double ws[kStreamRows / 32];
@@ -414,6 +429,8 @@ __global__ void __launch_bounds__(kStreamRows) k_gs_stream(int beg, int end, con
 
 template <class T>
 __global__ void k_jacobi_update(int n, const T* __restrict__ r, const T* __restrict__ d, T* __restrict__ x) {
+    pdl_wait();
+    pdl_trigger();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         x[i] += r[i] / d[i];
 }
@@ -482,14 +499,14 @@ void residual64(cudaStream_t s, const Csr& A, const double* x, const double* b, 
             k_finish<<<1, 1024, 0, s>>>(gn, partial, norm2); ::pc::count_launches(1);
         } else {
             const int gt = (g + kTilesPerBlock<double> - 1) / kTilesPerBlock<double>;
-            k_res_stream<double, false><<<gt, kStreamRows, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, b, r, nullptr); ::pc::count_launches(1);
+            launch(k_res_stream<double, false>, gt, kStreamRows, 0, s, A.n, A.rowptr, A.col, A.val, x, b, r,
+                   (double*)nullptr);
         }
     } else {
         int g = sparse_grid(A.n, A.lpr);
-#define CALL(L) k_residual<double, L><<<g, kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, b, r, nullptr)
+#define CALL(L) launch(k_residual<double, L>, g, kBlock, 0, s, A.n, A.rowptr, A.col, A.val, x, b, r, (double*)nullptr)
         PC_LPR_DISPATCH(A.lpr, CALL)
 #undef CALL
-        count_launches(1);
     }
     PC_LAUNCH("residual64");
 }
@@ -498,7 +515,7 @@ int residual_partials(int32_t n) { return (n + kStreamRows - 1) / kStreamRows; }
 
 template <class T>
 void jacobi_update(cudaStream_t s, int32_t n, const T* r, const T* d, T* x) {
-    k_jacobi_update<T><<<simple_grid(n), kBlock, 0, s>>>(n, r, d, x); ::pc::count_launches(1);
+    launch(k_jacobi_update<T>, simple_grid(n), kBlock, 0, s, n, r, d, x);
     PC_LAUNCH("jacobi_update");
 }
 template void jacobi_update<double>(cudaStream_t, int32_t, const double*, const double*, double*);
@@ -512,13 +529,13 @@ void l1_diagonal(cudaStream_t s, int32_t n, const int32_t* rowptr, const double*
 void residual32(cudaStream_t s, const Csr& A, const float* x, const float* b, float* r) {
     if (use_stream(A.n, A.lpr)) {
         int g = ((A.n + kStreamRows - 1) / kStreamRows + kTilesPerBlock<float> - 1) / kTilesPerBlock<float>;
-        k_res_stream<float, false><<<g, kStreamRows, 0, s>>>(A.n, A.rowptr, A.col, A.val32, x, b, r, nullptr); ::pc::count_launches(1);
+        launch(k_res_stream<float, false>, g, kStreamRows, 0, s, A.n, A.rowptr, A.col, A.val32, x, b, r,
+               (double*)nullptr);
     } else {
         int g = sparse_grid(A.n, A.lpr);
-#define CALL(L) k_residual<float, L><<<g, kBlock, 0, s>>>(A.n, A.rowptr, A.col, A.val32, x, b, r, nullptr)
+#define CALL(L) launch(k_residual<float, L>, g, kBlock, 0, s, A.n, A.rowptr, A.col, A.val32, x, b, r, (double*)nullptr)
         PC_LPR_DISPATCH(A.lpr, CALL)
 #undef CALL
-        count_launches(1);
     }
     PC_LAUNCH("residual32");
 }
@@ -538,10 +555,9 @@ void gs_colour(cudaStream_t s, const Csr& A, const int32_t* rows, int32_t nrows,
     int g = sparse_grid(nrows, A.lpr);
     const T* val;
     if constexpr (sizeof(T) == 8) val = A.val; else val = A.val32;
-#define CALL(L) k_gs<T, L><<<g, kBlock, 0, s>>>(nrows, rows, A.rowptr, A.col, val, b, x)
+#define CALL(L) launch(k_gs<T, L>, g, kBlock, 0, s, nrows, rows, A.rowptr, A.col, val, b, x)
     PC_LPR_DISPATCH(A.lpr, CALL)
 #undef CALL
-    count_launches(1);
     PC_LAUNCH("gs_colour");
 }
 
@@ -550,7 +566,7 @@ void gs_colour_perm(cudaStream_t s, int32_t beg, int32_t end, const int32_t* row
                     const int32_t* pcol, const T* pval, const T* b, T* x) {
     if (end <= beg) return;
     int g = ((end - beg + kStreamRows - 1) / kStreamRows + kGsTiles - 1) / kGsTiles;
-        k_gs_stream<T><<<g, kStreamRows, 0, s>>>(beg, end, rows, pptr, pcol, pval, b, x); ::pc::count_launches(1);
+    launch(k_gs_stream<T>, g, kStreamRows, 0, s, beg, end, rows, pptr, pcol, pval, b, x);
     PC_LAUNCH("gs_colour_perm");
 }
 
@@ -573,13 +589,13 @@ void permute_rows(Ctx& c, int32_t n, const int32_t* rows, const int32_t* rowptr,
 template <class T>
 void restrict_agg(cudaStream_t s, int32_t nc, const int32_t* agg_ptr, const int32_t* agg_mem,
                   const T* pval, const T* r, T* bc, T* xc, const T* dc) {
-    k_restrict<T><<<simple_grid(nc), kBlock, 0, s>>>(nc, agg_ptr, agg_mem, pval, r, bc, xc, dc); ::pc::count_launches(1);
+    launch(k_restrict<T>, simple_grid(nc), kBlock, 0, s, nc, agg_ptr, agg_mem, pval, r, bc, xc, dc);
     PC_LAUNCH("restrict");
 }
 
 template <class T>
 void prolong_add(cudaStream_t s, int32_t n, const int32_t* agg, const T* pval, const T* xc, T* x) {
-    k_prolong<T><<<simple_grid(n), kBlock, 0, s>>>(n, agg, pval, xc, x); ::pc::count_launches(1);
+    launch(k_prolong<T>, simple_grid(n), kBlock, 0, s, n, agg, pval, xc, x);
     PC_LAUNCH("prolong");
 }
 

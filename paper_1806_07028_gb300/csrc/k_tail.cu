@@ -315,6 +315,8 @@ __global__ void __launch_bounds__(kGemvWarps * 32)
     constexpr int W = 16 / sizeof(T);
     extern __shared__ __align__(16) unsigned char dyn[];
     T* vs = reinterpret_cast<T*>(dyn);
+    pdl_wait();
+    pdl_trigger();
     for (int j = threadIdx.x; j < ld; j += blockDim.x) vs[j] = (j < m) ? v[j] : T(0);
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -361,7 +363,7 @@ void tail_operator(cudaStream_t s, const TailLevel<T>* lv, const int* n, int l0,
 template <class T>
 void tail_gemv(cudaStream_t s, int m, int ld, const T* Nm, const T* v, T* x, bool accum) {
     const int grid = (m + kGemvWarps - 1) / kGemvWarps;
-    k_tail_gemv<T><<<grid, kGemvWarps * 32, sizeof(T) * ld, s>>>(m, ld, Nm, v, x, accum ? 1 : 0); ::pc::count_launches(1);
+    launch(k_tail_gemv<T>, grid, kGemvWarps * 32, sizeof(T) * ld, s, m, ld, Nm, v, x, accum ? 1 : 0);
     PC_LAUNCH("tail_gemv");
 }
 

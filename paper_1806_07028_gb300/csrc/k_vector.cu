@@ -179,67 +179,116 @@ __global__ void k_scalar(int op, double* s, int a, int b, int c) {
     }
 }
 
-// ---- scan: tile of 1024 per block (256 threads x 4) ------------------------
+// ---- scan: one pass over tiles of 1024 (256 threads x 4) -----------------
+// Decoupled look-back (Merrill and Garland, "Single-pass Parallel Prefix Scan
+// with Decoupled Look-back", 2016). Tiles take tickets in launch order; a tile
+// publishes its sum, then its inclusive prefix once it has added up its
+// predecessors' published words, nearest first, back to the first prefix. A
+// state word holds the status in its top two bits (0 nothing yet, 1 sum, 2
+// prefix) and a value below 2^62 (the scanned values are counts, never
+// negative). The word itself carries the value, so relaxed loads and stores
+// suffice. Predecessors took their tickets earlier and are running or done, so
+// the wait ends; it is bounded all the same (about two seconds of SM clock),
+// after which the tile sets ws[kScanErr] and leaves its outputs unwritten.
+constexpr int kScanErr = 0, kScanTicket = 1, kScanTotal = 2, kScanHead = 3;
+constexpr uint64_t kScanSum = 1ull << 62, kScanPrefix = 2ull << 62, kScanVal = (1ull << 62) - 1;
+
+__device__ __forceinline__ uint64_t ld_relaxed(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(uint64_t* p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 template <class TI, class TO>
-__global__ void k_scan_tiles(int64_t n, const TI* __restrict__ in, TO* __restrict__ out,
-                             int64_t* __restrict__ tile_sum) {
-    __shared__ int64_t ws[32];
-    int64_t base = (int64_t)blockIdx.x * 1024 + threadIdx.x * 4;
+__global__ void __launch_bounds__(256) k_scan(int64_t n, const TI* __restrict__ in, TO* __restrict__ out,
+                                              uint64_t* ws) {
+    __shared__ int64_t wsum[8];
+    __shared__ int64_t s_excl;
+    __shared__ int64_t s_tile;
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(ws + kScanTicket), 1ull);
+    __syncthreads();
+    const int64_t tile = s_tile;
+    uint64_t* state = ws + kScanHead;
+    const int64_t base = tile * 1024 + threadIdx.x * 4;
     int64_t v[4];
     int64_t t = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        int64_t i = base + k;
+        const int64_t i = base + k;
         v[k] = (i < n) ? (int64_t)in[i] : 0;
         t += v[k];
     }
-    // inclusive warp scan of t
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int64_t inc = t;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t inc = t;   // inclusive warp scan of the thread sums
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        const int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= o) inc += y;
     }
-    if (lane == 31) ws[wid] = inc;
+    if (lane == 31) wsum[wid] = inc;
     __syncthreads();
     if (wid == 0) {
-        int64_t w = (lane < (int)(blockDim.x >> 5)) ? ws[lane] : 0;
+        const int64_t w = lane < 8 ? wsum[lane] : 0;
         int64_t wi = w;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int64_t y = __shfl_up_sync(0xffffffffu, wi, o);
+        for (int o = 1; o < 8; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, wi, o);
             if (lane >= o) wi += y;
         }
-        if (lane < (int)(blockDim.x >> 5)) ws[lane] = wi - w;  // exclusive warp offsets
+        const int64_t agg = __shfl_sync(0xffffffffu, wi, 7);   // the tile's sum
+        if (lane < 8) wsum[lane] = wi - w;                       // exclusive warp offsets
+        int64_t excl = 0;
+        bool ok = true;
+        if (tile == 0) {
+            if (lane == 0) st_relaxed(state, kScanPrefix | (uint64_t)agg);
+        } else {
+            if (lane == 0) st_relaxed(state + tile, kScanSum | (uint64_t)agg);
+            const long long t0 = clock64();
+            for (int64_t j = tile - 1;;) {   // window j, j-1, .., j-31
+                const int64_t idx = j - lane;
+                uint64_t word;
+                for (;;) {   // both exits are warp-uniform
+                    word = idx >= 0 ? ld_relaxed(state + idx) : kScanPrefix;
+                    if (__all_sync(0xffffffffu, (word >> 62) != 0)) break;
+                    if (__any_sync(0xffffffffu, clock64() - t0 > (1ll << 32))) { ok = false; break; }
+                }
+                if (!ok) break;
+                const unsigned pre = __ballot_sync(0xffffffffu, (word >> 62) == 2);
+                const int first = pre ? __ffs(pre) - 1 : 31;   // nearest prefix, or the whole window
+                int64_t part = lane <= first ? (int64_t)(word & kScanVal) : 0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                excl += part;
+                if (pre) break;
+                j -= 32;
+            }
+            if (lane == 0) {
+                if (ok) st_relaxed(state + tile, kScanPrefix | (uint64_t)(excl + agg));
+                else atomicExch(reinterpret_cast<unsigned long long*>(ws + kScanErr), 1ull);
+            }
+        }
+        if (lane == 0) {
+            s_excl = excl;
+            s_ok = ok ? 1 : 0;
+            if (ok && (tile + 1) * 1024 >= n) {   // the last tile holds the total
+                out[n] = (TO)(excl + agg);
+                ws[kScanTotal] = (uint64_t)(excl + agg);
+            }
+        }
     }
     __syncthreads();
-    int64_t run = ws[wid] + inc - t;
+    if (!s_ok) return;
+    int64_t run = s_excl + wsum[wid] + inc - t;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        int64_t i = base + k;
+        const int64_t i = base + k;
         if (i < n) out[i] = (TO)run;
         run += v[k];
     }
-    if (threadIdx.x == blockDim.x - 1) tile_sum[blockIdx.x] = ws[wid] + inc;
-}
-
-template <class TO>
-__global__ void k_scan_add(int64_t n, TO* __restrict__ out, const int64_t* __restrict__ tile_off) {
-    int64_t i = (int64_t)blockIdx.x * 1024 + threadIdx.x;
-    int64_t add = tile_off[blockIdx.x];
-    for (int k = 0; k < 4; ++k, i += 256)
-        if (i < n) out[i] = (TO)((int64_t)out[i] + add);
-}
-
-__global__ void k_set_last(int64_t n, int64_t* __restrict__ tile_sum_total, const int64_t* __restrict__ tile_off,
-                           const int64_t* __restrict__ tile_sum, int64_t ntiles) {
-    *tile_sum_total = tile_off[ntiles - 1] + tile_sum[ntiles - 1];
-}
-
-template <class TO>
-__global__ void k_store_total(TO* __restrict__ out, int64_t n, const int64_t* __restrict__ total) {
-    out[n] = (TO)(*total);
 }
 
 inline int grid_for(int64_t n, int per_block = kBlock) {
@@ -329,32 +378,31 @@ void scalar_ops(cudaStream_t s, int op, double* slots, int a, int b, int c) {
     PC_LAUNCH("scalar_ops");
 }
 
-// Exclusive scan; out[n] receives the total. Scratch comes from the context.
+// Exclusive scan of non-negative counts; out[n] receives the total. The
+// bookkeeping words live in the context: [err, ticket, total, tile states..];
+// the error word persists, so a wait that gave up in a scan whose total is not
+// read is reported by the next scan that reads one.
 template <class TI, class TO>
 static int64_t scan_impl(Ctx& c, const TI* in, TO* out, int64_t n, bool read_total = true) {
-    int64_t ntiles = (n + 1023) / 1024;
-    if (ntiles == 0) {
-        PC_CUDA(cudaMemsetAsync(out, 0, sizeof(TO), c.stream));
-        return 0;
+    const int64_t ntiles = std::max<int64_t>(1, (n + 1023) / 1024);
+    const size_t words = (size_t)(kScanHead + ntiles);
+    if (c.scan_ws.n < words) {
+        DBuf<int64_t> grown;
+        grown.alloc(c.mem, std::max(words, (size_t)4096));
+        PC_CUDA(cudaMemsetAsync(grown.p, 0, sizeof(int64_t) * grown.n, c.stream));
+        if (c.scan_ws.p)
+            PC_CUDA(cudaMemcpyAsync(grown.p, c.scan_ws.p, sizeof(int64_t), cudaMemcpyDeviceToDevice, c.stream));
+        c.scan_ws = std::move(grown);
     }
-    DBuf<int64_t> tsum, toff;
-    tsum.alloc(c.mem, ntiles + 1);
-    toff.alloc(c.mem, ntiles + 1);
-    k_scan_tiles<TI, TO><<<(unsigned)ntiles, 256, 0, c.stream>>>(n, in, out, tsum.p); ::pc::count_launches(1);
-    PC_LAUNCH("scan_tiles");
-    if (ntiles > 1) {
-        scan_impl<int64_t, int64_t>(c, tsum.p, toff.p, ntiles, false);
-        k_scan_add<TO><<<(unsigned)ntiles, 256, 0, c.stream>>>(n, out, toff.p); ::pc::count_launches(1);
-        PC_LAUNCH("scan_add");
-    } else {
-        PC_CUDA(cudaMemsetAsync(toff.p, 0, sizeof(int64_t), c.stream));
-        PC_CUDA(cudaMemcpyAsync(toff.p + 1, tsum.p, sizeof(int64_t), cudaMemcpyDeviceToDevice, c.stream));
-    }
-    // total = toff[ntiles-1] + tsum[ntiles-1]
-    k_set_last<<<1, 1, 0, c.stream>>>(n, tsum.p + ntiles, toff.p, tsum.p, ntiles); ::pc::count_launches(1);
-    k_store_total<TO><<<1, 1, 0, c.stream>>>(out, n, tsum.p + ntiles); ::pc::count_launches(1);
-    PC_LAUNCH("scan_total");
-    return read_total ? read_i64(c, tsum.p + ntiles) : -1;
+    PC_CUDA(cudaMemsetAsync(c.scan_ws.p + kScanTicket, 0, sizeof(int64_t) * (words - kScanTicket), c.stream));
+    k_scan<TI, TO><<<(unsigned)ntiles, 256, 0, c.stream>>>(n, in, out, reinterpret_cast<uint64_t*>(c.scan_ws.p));
+    ::pc::count_launches(1);
+    PC_LAUNCH("scan");
+    if (!read_total) return -1;
+    int64_t h[kScanHead];
+    d2h(c, h, c.scan_ws.p, kScanHead);
+    if (h[kScanErr]) fail(PCAMG_ERR_CUDA, "scan: a look-back wait gave up");
+    return h[kScanTotal];
 }
 
 int64_t scan_i32(Ctx& c, const int32_t* in, int32_t* out, int64_t n) {

@@ -30,6 +30,39 @@ bool capturing();
 #define PC_LAUNCH(what) ::pc::check_cuda(cudaGetLastError(), what)
 #define PC_LAUNCHN(what, k) do { ::pc::check_cuda(cudaGetLastError(), what); ::pc::count_launches(k); } while (0)
 
+// Programmatic dependent launch of the cycle kernels. While a cycle graph is
+// captured, launch() marks each kernel launch as a programmatic dependent of
+// the kernel before it, so it may start while that kernel drains. Such a
+// kernel reads only hierarchy data (matrices, aggregates, colour permutations,
+// all written before the graph runs) ahead of pdl_wait(), which returns once
+// the previous grid has completed and its writes are visible; every block
+// reaches pdl_wait() before it exits. pdl_trigger() comes after the wait, so
+// at most two grids of the chain are in flight. Outside a programmatic launch
+// both instructions do nothing.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+// true while a cycle graph is captured and the previous captured node is a
+// kernel (a programmatic edge joins two kernels only); consumes the state
+bool pdl_next();
+void pdl_after_copy();   // the next captured node follows a memset or copy
+
+template <class... P, class... A>
+inline void launch(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A... args) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    const bool pdl = pdl_next();
+    cfg.attrs = pdl ? at : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    check_cuda(cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...), "launch");
+    count_launches(1);
+}
+
 constexpr int kMaxLevels = 32;
 constexpr int kBlock = 256;
 constexpr int kNumSMs = 152;
@@ -217,6 +250,7 @@ struct Ctx {
     double t_alg2 = 0.0, t_alg4 = 0.0;
     const double* last_e = nullptr;          // normalised error of the newest hierarchy
     std::unique_ptr<Reweighted> mpnn_cand;   // A^2 candidate pattern for the network's loss
+    DBuf<int64_t> scan_ws;                   // one-pass scan bookkeeping (k_vector.cu)
     ~Ctx();
 };
 
