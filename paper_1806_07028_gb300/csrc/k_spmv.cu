@@ -319,8 +319,10 @@ __device__ __forceinline__ TileMeta<T> tile_meta(int t0, int tend, const int* __
 // chunk's rows from shared memory, the loads of the next chunk (of this tile or
 // the first of the next tile) and the next tile's row pointers and b are
 // already in flight, so the only exposed latency per tile is the x gather.
-// The row sums keep the CSR order of each row. The first tile's row pointers
-// and chunk (hierarchy data) are loaded before pdl_wait(); b and x after it.
+// The row sums keep the CSR order of each row. Without NORM (the launches
+// inside cycle graphs) the first tile's row pointers and chunk (hierarchy
+// data) are loaded before pdl_wait(), b and x after it; the NORM form (the
+// outer FP64 residual, never a programmatic launch) has no wait.
 //   PERM = false: rows t of [0, n) (residual r = b - A x, optional ||r||^2);
 //   PERM = true:  permuted rows rows[t] of [beg, end) of one colour, Gauss-Seidel
 //                 x_row = (b_row - sum_{j != row} a x_j) / a_row,row.
@@ -336,13 +338,16 @@ __device__ __forceinline__ void stream_tiles(int beg, int end, int tpb, const in
     const int tfirst = blockIdx.x * tpb;
     const int tstop = min(ntiles, tfirst + tpb);
     double rr2 = 0.0;
+    constexpr bool kPdl = !NORM;
     if (tfirst < tstop) {
-        TileMeta<T> M = tile_meta<T, PERM, false>(beg + tfirst * kStreamRows, end, ptr, rows, b);
+        TileMeta<T> M = tile_meta<T, PERM, !kPdl>(beg + tfirst * kStreamRows, end, ptr, rows, b);
         ChunkRegs<T> R;
         load_chunk<T>(M.tb, min(M.tb + kStreamChunk<T>, M.te), col, val, R);
-        pdl_wait();
-        pdl_trigger();
-        if (M.row >= 0) M.bv = __ldg(b + M.row);
+        if (kPdl) {
+            pdl_wait();
+            pdl_trigger();
+            if (M.row >= 0) M.bv = __ldg(b + M.row);
+        }
         for (int t = tfirst; t < tstop; ++t) {
             TileMeta<T> Mn = M;
             T s = 0, d = 0;
@@ -377,7 +382,7 @@ __device__ __forceinline__ void stream_tiles(int beg, int end, int tpb, const in
             }
             M = Mn;
         }
-    } else {
+    } else if (kPdl) {
         pdl_wait();
         pdl_trigger();
     }
