@@ -45,9 +45,15 @@ def _args():
     ap.add_argument("--only-kernel", default=None, choices=["residual64", "vcycle", "wcycle", "adapt", "mpnn"],
                     help="time one kernel alone on the workload (used for ncu captures)")
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="run cycles as plain launches instead of CUDA graph replays (for profilers)")
     ap.add_argument("--summarize-launches", default=None, metavar="CSV",
                     help="reduce an ncu --csv launch list to per-kernel launches, time and share")
     return ap.parse_args()
+
+
+def _graphs(a):
+    return 0 if a.no_graphs else 1
 
 
 def barrier():
@@ -185,7 +191,7 @@ def run_ours(a):
     def step(form, profile=0):
         """One solve in a form: fp64, fp32ir, or fp32ir+learned (the shipped
         start-vector network, its forward inside the setup)."""
-        p = default_params(precision=0 if form == "fp64" else 1, profile=profile)
+        p = default_params(precision=0 if form == "fp64" else 1, profile=profile, use_graphs=_graphs(a))
         net = None
         if form.endswith("+learned"):
             if "net" not in nets:
@@ -399,7 +405,7 @@ def run_kernel(a):
         g = I.workload(a.workload)
         prec = 0 if a.form == "fp64" else 1
         dev = torch.device("cuda", 0)
-        s = Solver(_device_graph(g, dev), params=default_params(precision=prec), device=dev)
+        s = Solver(_device_graph(g, dev), params=default_params(precision=prec, use_graphs=_graphs(a)), device=dev)
         e = s.start_vector()
         s.adapt(e)
         torch.cuda.synchronize()
@@ -441,7 +447,7 @@ def run_kernel(a):
         g = I.workload(a.workload)
         prec = 0 if a.form == "fp64" else 1
         dev = torch.device("cuda", 0)
-        s = Solver(_device_graph(g, dev), params=default_params(precision=prec), device=dev)
+        s = Solver(_device_graph(g, dev), params=default_params(precision=prec, use_graphs=_graphs(a)), device=dev)
         r = torch.as_tensor(I.rhs_normal(g.n, 3), device=dev)
         gamma = 1 if a.only_kernel == "vcycle" else 2
         for _ in range(2):
