@@ -489,6 +489,26 @@ def run_kernel(a):
                       "frac": byt / ms / 1e6 / peak, "peak_kind": kind}), flush=True)
 
 
+def _kernel_short_name(full):
+    """Kernel name without its call arguments, return type and namespaces:
+    'void pc::<unnamed>::k_rowprod_warp<pc::<unnamed>::GalSrc, 2>(int, ...)'
+    becomes 'k_rowprod_warp<GalSrc, 2>'."""
+    import re
+    full = re.sub(r"(\(anonymous namespace\)|<unnamed>)::", "", full)
+    name = full
+    depth = 0
+    for i, ch in enumerate(full):   # cut at the '(' of the parameter list (outside <...>)
+        if ch == "<":
+            depth += 1
+        elif ch == ">":
+            depth -= 1
+        elif ch == "(" and depth == 0:
+            name = full[:i]
+            break
+    name = re.sub(r"^void ", "", name)
+    return re.sub(r"\bpc::", "", name).strip()
+
+
 def summarize_launches(path):
     """Per-kernel launches, total device time and share from an ncu launch list
     (--metrics gpu__time_duration.sum --csv); template arguments are kept, call
@@ -503,8 +523,7 @@ def summarize_launches(path):
         ki, vi = hdr.index("Kernel Name"), hdr.index("Metric Value")
         ui = hdr.index("Metric Unit")
         for r in rows:
-            name = re.sub(r"\(.*", "", r[ki]).replace("void ", "")
-            name = re.sub(r"^(pc::)?(<unnamed>::|unnamed>::)", "", name)
+            name = _kernel_short_name(r[ki])
             scale = {"ns": 1e-3, "usecond": 1.0, "us": 1.0, "msecond": 1e3, "ms": 1e3, "nsecond": 1e-3}.get(r[ui], 1e-3)
             by[name][0] += 1
             by[name][1] += float(r[vi].replace(",", "")) * scale
