@@ -16,7 +16,6 @@ namespace pc {
 
 namespace {
 
-constexpr int kThreadCap = 32;        // unique keys a thread-per-row product keeps
 constexpr int kBlockCap = 2048;       // contributions a block-per-row product stages in smem
 constexpr int kOrderWarpCap = 256;    // candidates a warp orders in shared memory
 constexpr uint32_t kSkip = 0xffffffffu;
@@ -76,56 +75,6 @@ struct GalSrc {
         v = pval ? __dmul_rn(__dmul_rn(pval[u], val[k]), pval[c]) : val[k];
     }
 };
-
-// Thread per row: insertion into a sorted local list. Rows whose unique keys
-// exceed kThreadCap are flagged and listed for the block kernels.
-template <class Src, bool FILL>
-__global__ void k_rowprod_thread(int nrows, Src src, int* __restrict__ cnt,
-                                 unsigned char* __restrict__ is_long, int* __restrict__ long_list,
-                                 int* __restrict__ long_count, const int* __restrict__ optr,
-                                 int* __restrict__ ocol, double* __restrict__ oval) {
-    FOR_EACH(r64, nrows) {
-        int r = (int)r64;
-        if (FILL && is_long[r]) continue;
-        uint32_t keys[kThreadCap];
-        double vals[kThreadCap];
-        int m = 0;
-        bool over = false;
-        int nm = src.nmem(r);
-        for (int t = 0; t < nm && !over; ++t) {
-            int j = src.mem_row(r, t);
-            int e = src.in_end(j);
-            for (int k = src.in_beg(j); k < e; ++k) {
-                uint32_t key;
-                double v;
-                src.kv(r, j, k, key, v);
-                if (key == kSkip) continue;
-                int p = m;
-                while (p > 0 && keys[p - 1] > key) --p;
-                if (p > 0 && keys[p - 1] == key) {
-                    vals[p - 1] = __dadd_rn(vals[p - 1], v);
-                } else {
-                    if (m == kThreadCap) { over = true; break; }
-                    for (int q = m; q > p; --q) { keys[q] = keys[q - 1]; vals[q] = vals[q - 1]; }
-                    keys[p] = key;
-                    vals[p] = v;
-                    ++m;
-                }
-            }
-        }
-        if (!FILL) {
-            is_long[r] = over ? 1 : 0;
-            cnt[r] = over ? 0 : m;
-            if (over) long_list[atomicAdd(long_count, 1)] = r;
-        } else {
-            int o = optr[r];
-            for (int q = 0; q < m; ++q) {
-                ocol[o + q] = (int)keys[q];
-                if (oval) oval[o + q] = vals[q];
-            }
-        }
-    }
-}
 
 // Warp per row. The row's contributions are numbered in their fixed order
 // (member rows one after another); lanes stage them as 64-bit keys
