@@ -310,6 +310,31 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
+def _host_cpu():
+    """The host the CPU oracle ran on: its logical core count and CPU model."""
+    import platform
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":", 1)[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+            if model is None:   # Arm: implementer and part numbers instead of a model name
+                f.seek(0)
+                ids = {}
+                for line in f:
+                    k = line.split(":", 1)[0].strip()
+                    if k in ("CPU implementer", "CPU part") and k not in ids:
+                        ids[k] = line.split(":", 1)[1].strip()
+                if ids:
+                    model = " ".join(f"{k} {v}" for k, v in ids.items())
+    except OSError:
+        pass
+    return {"logical_cores": os.cpu_count(), "machine": platform.machine(), "model": model}
+
+
 def oracle_sample(g, b, gpu_stats, max_seconds=40.0):
     """The CPU oracle (single thread) on a bounded sample of the same workload:
     its start vector, one hierarchy build (Alg. 4) and one V- and one W-cycle on
@@ -337,7 +362,7 @@ def oracle_sample(g, b, gpu_stats, max_seconds=40.0):
     nw = min(gpu_stats["resetups"], 2) * 7
     est = t_start + H * t_build + (cyc - nw) * t_v + nw * (wc if wc is not None else 2 * t_v)
     h.close()
-    return {"value": g.n / est, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": g.n / est, "unit": UNIT, "cores": 1, "kind": "oracle", "host": _host_cpu(),
             "sample": (f"oracle start vector ({t_start:.2f}s) + 1 hierarchy build ({t_build:.2f}s) + "
                        f"1 V-cycle ({t_v:.3f}s) + 1 W-cycle ({wc if wc is not None else float('nan'):.3f}s) "
                        f"on the full graph, scaled by the GPU solve's {H} builds and {cyc} cycles "
@@ -388,7 +413,7 @@ def run_reference(a):
            "warmup": a.warmup, "ms_per_step": 1e3 * t_solve, "higher_is_better": True,
            "impl": "reference", "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "n": g.n, "nnz": g.nnz, "form": "oracle fp64"},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host": _host_cpu(),
                             "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
