@@ -125,6 +125,18 @@ def test_setup_bit_exact_with_ties(P):
     _compare_hierarchy(P, g, np.zeros(g.n), 1)[0].close()
 
 
+def test_setup_bit_exact_hub_rows(P):
+    # scale-free graph (Chung-Lu, exponent 2.1, hubs of degree ~600): 1,805
+    # rows of the A^2 product have more than 256 contributions and 227 more
+    # than 2,048 (up to 15,792), so the block (shared memory) and global
+    # row products, the long-row split and the per-block proposal ordering
+    # all run, on the fine level and in the coarse Galerkin products
+    g = I.chung_lu(3000, 2.1, 10.0, seed=1)
+    e = O.start_vector(g)
+    for mode in (0, 1):
+        _compare_hierarchy(P, g, e, mode)[0].close()
+
+
 @pytest.mark.parametrize("name", ["C1", "C2-small", "er"])
 @pytest.mark.parametrize("gamma", [1, 2])
 def test_cycle_matches_oracle(P, name, gamma):
