@@ -15,8 +15,14 @@ def _pattern(g):
 
 
 # ---------------------------------------------------------------- reweighting
+def _hub_graph():
+    # scale-free (Chung-Lu, exponent 2.1): hub rows of the A^2 product reach
+    # 15,792 contributions, the case of the GPU's long-row paths
+    return I.chung_lu(3000, 2.1, 10.0, seed=1)
+
+
 @pytest.mark.parametrize("mk", [lambda: I.workload("C1"), lambda: random_graph(80, 0.05, 1),
-                                lambda: I.grid3d(5, 4, 6, "unit")])
+                                lambda: I.grid3d(5, 4, 6, "unit"), _hub_graph])
 def test_candidates_are_the_A2_pattern(mk):
     # Alg. 4 step 2: the reweighted graph lives on the pattern of A^2 (no diagonal)
     g = mk()
@@ -242,7 +248,7 @@ def test_aggregation_invariants(seed):
 
 
 def test_aggregation_invariants_grid_and_ring():
-    for g in (I.workload("C1"), I.ring(200, 4), I.grid3d(9, 8, 7, "checkerboard", block=3)):
+    for g in (I.workload("C1"), I.ring(200, 4), I.grid3d(9, 8, 7, "checkerboard", block=3), _hub_graph()):
         _check_aggregation(g, O.start_vector(g))
 
 
@@ -253,9 +259,10 @@ def _P(agg, nc, pval=None):
     return sp.csr_matrix((v, (np.arange(n), agg)), shape=(n, nc))
 
 
+@pytest.mark.parametrize("hub", [False, True])
 @pytest.mark.parametrize("mode", [O.P1_E_SCALED, O.P1_BOOLEAN])
-def test_hierarchy_galerkin_matches_dense_product(mode):
-    g = I.grid3d(10, 9, 8, "checkerboard", block=3, xscale=100.0)
+def test_hierarchy_galerkin_matches_dense_product(mode, hub):
+    g = _hub_graph() if hub else I.grid3d(10, 9, 8, "checkerboard", block=3, xscale=100.0)
     e = O.start_vector(g)
     h = O.Hierarchy(g, e, O.default_params(p1_mode=mode, n_min=20))
     assert h.nlevels >= 3
