@@ -62,6 +62,14 @@ enum { PCAMG_START_RANDOM = 0, PCAMG_START_USER = 1, PCAMG_START_LEARNED = 2 }; 
 /* A start-vector network (see the pcamg_mpnn_* calls below). */
 typedef struct pcamg_mpnn_s* pcamg_mpnn;
 enum { PCAMG_P1_E_SCALED = 0, PCAMG_P1_BOOLEAN = 1 };       /* level-1 prolongation */
+/* Alg. 5 after a re-setup. REBUILD_ONLY (default): the smooth error only drives
+ * the new hierarchy; the iterate and its residual are left as the V-cycle made
+ * them, so the next convergence factor is measured against that residual (the
+ * printed update adds e to an iterate that is never used again; this reading
+ * gives the paper's Re = Iter - 1 for Alg. 5(1) and its Re counts for Alg. 5(2)).
+ * ADD_CORRECTION: the raw PCG solution of A e = r is added to the iterate and
+ * the residual recomputed before the next step. */
+enum { PCAMG_UPD_REBUILD_ONLY = 0, PCAMG_UPD_ADD_CORRECTION = 1 };
 
 /* Parameters. Defaults (pcamg_default_params) follow Section 4 of the paper:
  * threshold 0.4 (Alg. 5(2)), numW 2, iterW 7, iterV 4, Gauss-Seidel smoothing,
@@ -108,6 +116,8 @@ typedef struct {
                               or instead of one more; -1 = no limit. Used to collect
                               the first smooth error of a run (training data). */
     pcamg_mpnn mpnn;       /* the network for PCAMG_START_LEARNED, else NULL */
+    int32_t update_mode;   /* PCAMG_UPD_*: what Alg. 5 does with the Alg. 2 smooth error
+                              after a re-setup (default PCAMG_UPD_REBUILD_ONLY) */
 } pcamg_params;
 
 typedef struct {

@@ -27,6 +27,7 @@ _lib = None
 P1_E_SCALED, P1_BOOLEAN = 0, 1
 LEFT_ROUNDS, LEFT_SEQUENTIAL = 0, 1
 COVER_LD, COVER_GREEDY = 0, 1
+UPD_REBUILD_ONLY, UPD_ADD_CORRECTION = 0, 1
 ERR = {0: "OK", 1: "INVALID", 2: "NOT_LAPLACIAN", 3: "OOM", 5: "ROUND_CAP", 6: "SINGULAR",
        7: "NOT_CONVERGED", 8: "DIVERGED", 9: "COARSE_TOO_BIG"}
 
@@ -54,7 +55,8 @@ class Params(C.Structure):
                 ("nu_pre", C.c_int32), ("nu_post", C.c_int32), ("relax_sweeps", C.c_int32),
                 ("seed", C.c_uint64), ("n_min", C.c_int32), ("max_levels", C.c_int32),
                 ("round_cap", C.c_int32), ("p1_mode", C.c_int32), ("leftover_mode", C.c_int32),
-                ("cover_mode", C.c_int32), ("dense_max", C.c_int32), ("l1jac_rows", C.c_int32)]
+                ("cover_mode", C.c_int32), ("dense_max", C.c_int32), ("l1jac_rows", C.c_int32),
+                ("update_mode", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -121,7 +123,9 @@ def lib():
                                            C.POINTER(C.c_void_p), C.c_int32, C.POINTER(Params), _f64p]
             L.orc_smooth_error.restype = C.c_int32
             L.orc_solve.argtypes = [C.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p, C.POINTER(Params),
-                                    C.c_void_p, C.POINTER(Stats), C.c_void_p, C.c_int32]
+                                    C.c_void_p, C.POINTER(Stats), C.c_void_p, C.c_int32, C.c_void_p]
+            L.orc_precond.argtypes = [C.c_int32, _i32p, _i32p, _f64p, C.POINTER(C.c_void_p),
+                                      C.c_int32, C.POINTER(Params), _f64p, _f64p]
             L.orc_solve.restype = C.c_int32
             L.orc_solve_zero_rhs.argtypes = [C.c_int32, _i32p, _i32p, _f64p, _f64p, C.POINTER(Params),
                                              C.c_void_p, C.POINTER(Stats), C.c_void_p, C.c_int32]
@@ -376,19 +380,32 @@ def smooth_error(g, r, hiers, params=None):
     return e
 
 
+def precond(g, r, hiers, params=None):
+    """The preconditioner of Alg. 2's PCG for a history of len(hiers) hierarchies."""
+    p = params if params is not None else default_params()
+    rp, ci, v = _csr(g)
+    arr = (C.c_void_p * len(hiers))(*[h._h for h in hiers])
+    z = np.empty(g.n)
+    lib().orc_precond(g.n, rp, ci, v, arr, len(hiers), C.byref(p), _f64(r), z)
+    return z
+
+
 def solve(g, b, x0=None, params=None, e0=None, hist_cap=4096):
-    """Alg. 5. Returns (x, stats dict, residual history)."""
+    """Alg. 5. Returns (x, stats dict, residual history). stats["rebuilt_after"]
+    lists the steps k after whose V-cycle a re-setup ran."""
     p = params if params is not None else default_params()
     rp, ci, v = _csr(g)
     x = np.zeros(g.n) if x0 is None else _f64(x0).copy()
     st = Stats()
     hist = np.full(hist_cap, np.nan)
+    reb = np.zeros(hist_cap, np.int32)
     ee = None if e0 is None else _f64(e0)
     lib().orc_solve(g.n, rp, ci, v, _f64(b), x, C.byref(p),
                     None if ee is None else ee.ctypes.data_as(C.c_void_p), C.byref(st),
-                    hist.ctypes.data_as(C.c_void_p), hist_cap)
+                    hist.ctypes.data_as(C.c_void_p), hist_cap, reb.ctypes.data_as(C.c_void_p))
     s = dict(iters=st.iters, resetups=st.resetups, levels=st.levels, status=ERR.get(st.status, st.status),
-             rel_res=st.rel_res, oc_mean=st.oc_mean)
+             rel_res=st.rel_res, oc_mean=st.oc_mean,
+             rebuilt_after=[int(k) for k in np.nonzero(reb[: st.iters + 1])[0]])
     return x, s, hist[: st.iters + 1]
 
 

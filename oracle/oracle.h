@@ -34,6 +34,10 @@ enum {
 enum { ORC_P1_E_SCALED = 0, ORC_P1_BOOLEAN = 1 };          /* prolongation at level 0 */
 enum { ORC_LEFT_ROUNDS = 0, ORC_LEFT_SEQUENTIAL = 1 };      /* leftover handling (Alg. 3) */
 enum { ORC_COVER_LD = 0, ORC_COVER_GREEDY = 1 };            /* path cover (Alg. 1) */
+/* Alg. 5 after a re-setup: the smooth error only drives the rebuild (the
+ * printed update lands on an iterate that is never used again), or the raw
+ * PCG solution is added to the new iterate and the residual recomputed. */
+enum { ORC_UPD_REBUILD_ONLY = 0, ORC_UPD_ADD_CORRECTION = 1 };
 
 typedef struct {
     double tol;           /* relative residual target ||b-Ax||/||b|| */
@@ -55,6 +59,7 @@ typedef struct {
     int32_t dense_max;    /* largest coarsest level solved densely */
     int32_t l1jac_rows;   /* levels >= 1 with at most this many unknowns are smoothed
                              by l1-Jacobi instead of multicolour Gauss-Seidel */
+    int32_t update_mode;  /* ORC_UPD_*: what Alg. 5 does with the smooth error */
 } orc_params;
 
 typedef struct {
@@ -164,12 +169,18 @@ int32_t orc_start_vector(int32_t n, const int32_t* rowptr, const int32_t* col,
 int32_t orc_smooth_error(int32_t n, const int32_t* rowptr, const int32_t* col,
                          const double* val, const double* r, orc_hier* const* hist,
                          int32_t re, const orc_params* p, double* e_raw);
+/* The preconditioner that Alg. 2's PCG applies: z = W-cycle of hist[re-1] when
+ * re <= numW, else the symmetric composite of V-cycles over hist[0..re-1]. */
+void orc_precond(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                 orc_hier* const* hist, int32_t re, const orc_params* p, const double* r,
+                 double* z);
 /* Alg. 5 (general b). x is the initial guess on entry and the solution on exit.
  * e0: start vector (NULL: relaxed random start). res_hist (may be NULL) gets
- * ||r_k||/||b|| for k = 0..iters. */
+ * ||r_k||/||b|| for k = 0..iters; rebuilt (may be NULL, same capacity) gets 1 at
+ * step k when a re-setup followed the k-th V-cycle, else 0. */
 int32_t orc_solve(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
                   const double* b, double* x, const orc_params* p, const double* e0,
-                  orc_stats* st, double* res_hist, int32_t res_hist_cap);
+                  orc_stats* st, double* res_hist, int32_t res_hist_cap, int32_t* rebuilt);
 /* Alg. 6 (b = 0): the iterate itself becomes the smooth error. */
 int32_t orc_solve_zero_rhs(int32_t n, const int32_t* rowptr, const int32_t* col,
                            const double* val, double* x, const orc_params* p,

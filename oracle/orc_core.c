@@ -36,6 +36,7 @@ void orc_default_params(orc_params* p) {
     p->cover_mode = ORC_COVER_LD;
     p->dense_max = 4096;
     p->l1jac_rows = 2147483647;
+    p->update_mode = ORC_UPD_REBUILD_ONLY;  /* the printed order of Alg. 5 */
 }
 
 /* ------------------------------------------------------------------------- */

@@ -112,6 +112,15 @@ static void precond(int32_t n, const int32_t* rowptr, const int32_t* col, const 
     }
 }
 
+void orc_precond(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                 orc_hier* const* hist, int32_t re, const orc_params* p, const double* r,
+                 double* z) {
+    double* t1 = (double*)orc_xmalloc(sizeof(double) * (size_t)n);
+    double* t2 = (double*)orc_xmalloc(sizeof(double) * (size_t)n);
+    precond(n, rowptr, col, val, hist, re, p, r, z, t1, t2);
+    free(t1); free(t2);
+}
+
 /* Alg. 2: flexible (Polak-Ribiere) PCG on A e = r from e = 0. */
 int32_t orc_smooth_error(int32_t n, const int32_t* rowptr, const int32_t* col,
                          const double* val, const double* rhs, orc_hier* const* hist,
@@ -160,7 +169,7 @@ int32_t orc_smooth_error(int32_t n, const int32_t* rowptr, const int32_t* col,
 
 int32_t orc_solve(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
                   const double* b, double* x, const orc_params* p, const double* e0,
-                  orc_stats* stt, double* res_hist, int32_t cap) {
+                  orc_stats* stt, double* res_hist, int32_t cap, int32_t* rebuilt) {
     orc_stats st;
     memset(&st, 0, sizeof(st));
     for (int32_t i = 0; i < n; ++i) if (!isfinite(b[i]) || !isfinite(x[i])) return ORC_ERR_INVALID;
@@ -186,6 +195,7 @@ int32_t orc_solve(int32_t n, const int32_t* rowptr, const int32_t* col, const do
     double wsum = 0.0;
     int32_t wcnt = 0;
     if (res_hist && cap > 0) res_hist[0] = res / bn;
+    if (rebuilt) for (int32_t i = 0; i < cap; ++i) rebuilt[i] = 0;
     while (k < p->max_iter && res / bn > p->tol) {
         /* x_{k+1} = V-cycle on the current hierarchy, then orthogonal to 1 */
         orc_vcycle(hist[re - 1], r, c);
@@ -211,11 +221,14 @@ int32_t orc_solve(int32_t n, const int32_t* rowptr, const int32_t* col, const do
             if (!hist[re]) break;
             oc_sum += orc_hier_oc(hist[re]);
             ++re;
-            for (int32_t i = 0; i < n; ++i) x[i] += e[i];
-            remove_mean(n, x);
-            orc_residual(n, rowptr, col, val, x, b, r);
-            res = vnorm(n, r);
-            if (res_hist && k < cap) res_hist[k] = res / bn;
+            if (rebuilt && k < cap) rebuilt[k] = 1;
+            if (p->update_mode == ORC_UPD_ADD_CORRECTION) {
+                for (int32_t i = 0; i < n; ++i) x[i] += e[i];
+                remove_mean(n, x);
+                orc_residual(n, rowptr, col, val, x, b, r);
+                res = vnorm(n, r);
+                if (res_hist && k < cap) res_hist[k] = res / bn;
+            }
             wsum = 0.0; wcnt = 0;
         }
     }

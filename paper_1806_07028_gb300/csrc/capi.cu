@@ -95,7 +95,8 @@ void check_params(const pcamg_params& p) {
         (p.start != PCAMG_START_RANDOM && p.start != PCAMG_START_USER && p.start != PCAMG_START_LEARNED) ||
         (p.start == PCAMG_START_LEARNED && !p.mpnn) || p.max_resetups < -1 || p.dense_max < 1 ||
         p.dense_max > 4096 || p.tail_rows < 0 || p.l1jac_rows < 0 || p.tail_dense < 0 ||
-        p.tail_dense > 3)
+        p.tail_dense > 3 ||
+        (p.update_mode != PCAMG_UPD_REBUILD_ONLY && p.update_mode != PCAMG_UPD_ADD_CORRECTION))
         fail(PCAMG_ERR_INVALID, "invalid parameters");
 }
 
@@ -205,6 +206,7 @@ PCAMG_API pcamg_status pcamg_default_params(pcamg_params* p) {
     p->tail_dense = 3;
     p->max_resetups = -1;
     p->mpnn = nullptr;
+    p->update_mode = PCAMG_UPD_REBUILD_ONLY;
     return PCAMG_OK;
 }
 

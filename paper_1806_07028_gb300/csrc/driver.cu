@@ -458,11 +458,13 @@ pcamg_status solve(Ctx& c, const double* b, double* x, pcamg_stats* st) {
             if (c.p.max_resetups >= 0 && (int32_t)c.hist.size() - re0 >= c.p.max_resetups) break;
             double ts = now_ms();
             rebuild(c, c.w_e.p);
-            axpy(s, c.n, 1.0, c.w_e.p, x);
-            remove_mean(c, x);
-            fine_residual(c, x, b, c.w_r.p, slot(c, S_NORM2));
-            res = read_norm(c);
-            hist_put(k, res / bn);
+            if (c.p.update_mode == PCAMG_UPD_ADD_CORRECTION) {
+                axpy(s, c.n, 1.0, c.w_e.p, x);
+                remove_mean(c, x);
+                fine_residual(c, x, b, c.w_r.p, slot(c, S_NORM2));
+                res = read_norm(c);
+                hist_put(k, res / bn);
+            }
             wsum = 0.0;
             wcnt = 0;
             t_setup += now_ms() - ts;
