@@ -1,17 +1,22 @@
 #!/usr/bin/env python
-"""Benchmark: unknowns/s to a 1e-8 relative residual with PC-alphaAMG on GB300.
+"""Benchmark: time to a 1e-8 relative residual and unknowns/s with PC-alphaAMG on
+GB300, FP32 hierarchy with the learned start inside FP64 refinement against
+plain FP64, on the same graph and right-hand side.
 
-One step = one complete adaptive solve of the 3D 7-point grid-graph Laplacian
-128^3 (n = 2,097,152) with high-contrast weights (8^3 checkerboard blocks of
-weight 1 or 1e-4, x-edges x100), right-hand side N(0,1) minus its mean:
-pcamg_setup (validation, colouring, start vector, first hierarchy) plus
-pcamg_solve (Alg. 5 with Alg. 2 re-setups) to ||b-Ax||/||b|| <= 1e-8, starting
-from the CSR already resident in HBM. value = n * ranks / step time.
-The matrix (175 MB) is larger than L2 (129 MB), so no flush is needed.
+One step = one complete adaptive solve of the workload (default C5: the 3D
+7-point grid Laplacian 256^3, n = 16,777,216, jump coefficients 10^U(-6,0) on
+16^3 blocks), right-hand side N(0,1) minus its mean: pcamg_setup (validation,
+colouring, start vector -- the learned network's forward pass in the headline
+form -- and the first hierarchy) plus pcamg_solve (Alg. 5 with Alg. 2
+re-setups) to ||b-Ax||/||b|| <= 1e-8, from the CSR already resident in HBM.
+value = n * ranks / step time. The matrix (1.4 GB) is larger than L2
+(129 MB), so no flush is needed.
 
-Forms: "fp32ir" (FP32 hierarchy and cycles inside FP64 iterative refinement,
-the headline) and "fp64" (plain FP64). --impl reference times the CPU oracle
-on a bounded sample of the same workload instead.
+Forms: "fp32ir+learned" (the headline: FP32 hierarchy and cycles inside FP64
+iterative refinement, learned start vector), "fp32ir" (same, relaxed random
+start) and "fp64" (plain FP64, relaxed random start); the two others are
+timed once each on the same graph and b. --impl reference times the CPU
+oracle on a bounded sample of the same workload instead.
 """
 from __future__ import annotations
 
@@ -28,9 +33,17 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "unknowns/s to 1e-8 relative residual (setup + adaptive solve)"
+METRIC = "time to 1e-8 residual & unknowns/s: plain FP64 vs FP32+learned form, same GB300"
 UNIT = "unknowns/s"
-WORKLOAD = "C2: 3D 7-point grid Laplacian 128^3, 8^3 checkerboard weights 1/1e-4, x-edges x100"
+GOLDEN_SOLVES = os.path.join(ROOT, "tests", "golden", "oracle_solves.json")
+# the oracle's recorded full solve whose counts stand in for a workload whose
+# own full oracle solve was not recorded (same recipe, smaller grid)
+COUNTS_FROM = {"C5": "C5-mid"}
+
+
+def workload_label(name):
+    from paper_1806_07028_gb300 import inputs as I
+    return f"{name}: {I.DESCRIPTIONS.get(name, name)}"
 
 
 def _args():
@@ -39,8 +52,8 @@ def _args():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="C2")
-    ap.add_argument("--form", default="fp32ir", choices=["fp32ir", "fp64", "fp32ir+learned"])
+    ap.add_argument("--workload", default="C5")
+    ap.add_argument("--form", default="fp32ir+learned", choices=["fp32ir", "fp64", "fp32ir+learned"])
     ap.add_argument("--no-extras", action="store_true", help="skip fp64 form, e2e and oracle legs")
     ap.add_argument("--only-kernel", default=None, choices=["residual64", "vcycle", "wcycle", "adapt", "mpnn"],
                     help="time one kernel alone on the workload (used for ncu captures)")
@@ -141,18 +154,36 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _traffic_per_launch():
-    """DRAM bytes per launch of the fine residual kernel from the committed ncu
-    summary (profiles/residual64_C2.md, line 'traffic_bytes_per_launch: N')."""
-    path = os.path.join(ROOT, "profiles", "residual64_C2.md")
+def _golden_solves():
+    """Full oracle solves recorded by tests/golden/make_oracle_solves.py."""
     try:
-        for line in open(path):
-            if line.startswith("traffic_bytes_per_launch:"):
-                v = line.split(":", 1)[1].strip()
-                return None if v in ("", "null") else float(v)
+        return json.load(open(GOLDEN_SOLVES))
     except Exception:
-        pass
-    return None
+        return {}
+
+
+def oracle_counts(workload):
+    """The oracle's own counts of one full solve (hierarchies built, cycles, W-cycles)
+    of this workload, or of the recorded same-recipe workload standing in for it."""
+    rec = _golden_solves()
+    src = workload if workload in rec else COUNTS_FROM.get(workload)
+    if src not in rec:
+        return None
+    r = rec[src]
+    return {"from": src, "builds": r["resetups"] + 1, "cycles": r["cycles"], "wcycles": r["wcycles"],
+            "iters": r["iters"], "n": r["n"], "seconds_full_solve": r["seconds"], "host": r["host"]}
+
+
+def error_vs_recorded_oracle(workload, x):
+    """||x - x_oracle|| / ||x_oracle|| on the recorded sample indices."""
+    import numpy as np
+    rec = _golden_solves().get(workload)
+    if rec is None:
+        return None
+    idx = np.asarray(rec["sample_idx"], dtype=np.int64)
+    xo = np.asarray(rec["sample_x"])
+    return {"value": float(np.linalg.norm(x[idx] - xo) / np.linalg.norm(xo)),
+            "over": f"{len(idx)} seeded sample entries of the oracle's recorded FP64 solution"}
 
 
 def _device_graph(g, device):
@@ -168,16 +199,58 @@ def _device_graph(g, device):
     return d
 
 
-def run_ours(a):
+def _oracle_sample_proc(workload, rank_seed, q):
+    """Child process (spawned before any GPU work) timing the oracle sample."""
+    try:
+        from paper_1806_07028_gb300 import inputs as I
+        g = I.workload(workload)
+        q.put(oracle_sample(g, I.rhs_normal(g.n, rank_seed), workload))
+    except Exception as ex:   # reported, never fatal to the GPU measurement
+        q.put({"error": repr(ex)})
+
+
+def _small_oracle_check(P, form_params):
+    """The oracle's full FP64 solve of C1 next to the GPU's forms on the same b:
+    the relative error of each GPU solution to the oracle's."""
     import numpy as np
-    import torch
+    import oracle as O
+    from paper_1806_07028_gb300 import inputs as I
+    g = I.workload("C1")
+    b = I.rhs_normal(g.n, 11)
+    xo, so, _ = O.solve(g, b)
+    out = {"workload": "C1", "oracle_iters": so["iters"], "oracle_resetups": so["resetups"]}
+    for form, (prm, net) in form_params.items():
+        s = P.Solver(g, params=prm, mpnn=net)
+        x, st = s.solve(b)
+        s.close()
+        x = x.cpu().numpy()
+        out[form] = {"error": float(np.linalg.norm(x - xo) / np.linalg.norm(xo)),
+                     "rel_res": float(np.linalg.norm(b - g.to_scipy() @ x) / np.linalg.norm(b)),
+                     "iters": st["iters"], "resetups": st["resetups"]}
+    return out
+
+
+def run_ours(a):
+    import multiprocessing as mp
+
+    import numpy as np
 
     rank, world, local = _dist()
+    want_cpu = (not a.no_extras) and rank == 0 and world == 1
+    oq = None
+    if want_cpu:   # the oracle sample runs on one host core while the GPU is timed
+        ctx = mp.get_context("spawn")
+        oq = ctx.Queue()
+        op = ctx.Process(target=_oracle_sample_proc, args=(a.workload, 11 + rank, oq), daemon=True)
+        op.start()
+
+    import torch
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    import paper_1806_07028_gb300 as P
     from paper_1806_07028_gb300 import Solver, default_params, inputs as I, native as N
     from paper_1806_07028_gb300 import solve_host
 
@@ -185,26 +258,29 @@ def run_ours(a):
     b_host = I.rhs_normal(g.n, 11 + rank)
     dg = _device_graph(g, dev)
     b = torch.as_tensor(b_host, device=dev)
-    prec = 0 if a.form == "fp64" else 1
     nets = {}
+
+    def net_for(form):
+        if not form.endswith("+learned"):
+            return None
+        if "net" not in nets:
+            from paper_1806_07028_gb300 import Mpnn
+            nets["net"] = Mpnn.pretrained()
+        return nets["net"]
+
+    def params_for(form, profile=0):
+        return default_params(precision=0 if form == "fp64" else 1, profile=profile, use_graphs=_graphs(a))
 
     def step(form, profile=0):
         """One solve in a form: fp64, fp32ir, or fp32ir+learned (the shipped
-        start-vector network, its forward inside the setup)."""
-        p = default_params(precision=0 if form == "fp64" else 1, profile=profile, use_graphs=_graphs(a))
-        net = None
-        if form.endswith("+learned"):
-            if "net" not in nets:
-                from paper_1806_07028_gb300 import Mpnn
-                nets["net"] = Mpnn.pretrained()
-            net = nets["net"]
-        s = Solver(dg, params=p, device=dev, mpnn=net)
+        start-vector network, its forward pass inside the setup)."""
+        s = Solver(dg, params=params_for(form, profile), device=dev, mpnn=net_for(form))
         x, st = s.solve(b)
         s.close()
         return x, st
 
     for _ in range(a.warmup):
-        step(a.form, profile=1)
+        step(a.form, profile=2)
     torch.cuda.synchronize()
     barrier()
     clocks = Clocks(local)
@@ -217,7 +293,7 @@ def run_ours(a):
     torch.cuda.nvtx.range_push("timed")   # lets a profiler select the timed steps
     stats = []
     for _ in range(a.steps):
-        x, st = step(a.form, profile=1)
+        x, st = step(a.form, profile=2)
         stats.append(st)
     torch.cuda.nvtx.range_pop()
     ev1.record()
@@ -227,41 +303,49 @@ def run_ours(a):
     clk = clocks.stop()
     ms = max_over_ranks(ms, device=dev)
     x_host = x.cpu().numpy()
-    rel = float(np.linalg.norm(b_host - g.to_scipy() @ x_host) / np.linalg.norm(b_host))
+    A = g.to_scipy()
+    rel = float(np.linalg.norm(b_host - A @ x_host) / np.linalg.norm(b_host))
     value = job_value(g.n, world, ms)
 
-    # roofline of the fine-level FP64 residual kernel (events on its own stream)
+    # roofline of the finest-level residual inside the V-cycle, timed live with
+    # CUDA events (event-record nodes in the captured cycle graph, on the
+    # library's stream) over every V-cycle of the timed solves
     peak, peak_kind = _peaks()
-    pl = sum(s["prof_launches"] for s in stats)
-    pms = sum(s["prof_ms"] for s in stats)
-    bytes_per_launch = 12.0 * g.nnz + 28.0 * g.n
-    achieved = (bytes_per_launch / (pms / pl / 1e3) / 1e9) if pl else None
-    roofline = {"bound": "hbm", "kernel": "k_res_stream<double,1> (fine-level r = b - A x with ||r||^2)",
+    cl = sum(s["cyc_launches"] for s in stats)
+    cms = sum(s["cyc_ms"] for s in stats)
+    w = 8.0 if a.form == "fp64" else 4.0
+    bytes_per_launch = (4.0 + w) * g.nnz + (4.0 + 3.0 * w) * g.n
+    achieved = (bytes_per_launch / (cms / cl / 1e3) / 1e9) if cl else None
+    kname = "k_res_stream<double,0>" if a.form == "fp64" else "k_res_stream<float,0>"
+    roofline = {"bound": "hbm", "kernel": f"{kname}, finest level (r = b - A x inside every V-cycle)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": (achieved / peak) if achieved else None,
-                "traffic": _traffic_per_launch(),
+                "frac": (achieved / peak) if achieved else None, "traffic": None,
                 "algorithmic_bytes_per_launch": bytes_per_launch,
-                "peak_kind": f"{peak_kind} (hbm_gbs)", "launches_timed": pl}
+                "mean_launch_us": (1e3 * cms / cl) if cl else None,
+                "peak_kind": f"{peak_kind} (hbm_gbs)", "launches_timed": cl,
+                "timing": "CUDA events on the library stream around every launch in the timed solves"}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
-           "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": ("f64" if not prec else "f32 cycles in f64 refinement" +
+           "warmup": a.warmup, "ms_per_step": ms, "time_to_tol_s": ms / 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": ("f64" if a.form == "fp64" else "f32 cycles in f64 refinement" +
                      (", bf16 tensor-core start network" if a.form.endswith("+learned") else "")),
            "data": "synthetic (seeded generator, same recipe as the configuration)",
-           "config": {"workload": WORKLOAD, "n": g.n, "nnz": g.nnz, "form": a.form,
+           "config": {"workload": workload_label(a.workload), "n": g.n, "nnz": g.nnz, "form": a.form,
                       "tol": 1e-8, "parallelism": "replicas" if world > 1 else "single GPU",
-                      "l2": "inputs larger than L2 (matrix 175 MB > 129 MB)"},
+                      "l2": f"inputs larger than L2 (matrix {12 * g.nnz / 1e6:.0f} MB > 129 MB)"},
            "solve": {"iters": stats[-1]["iters"], "resetups": stats[-1]["resetups"],
                      "levels": stats[-1]["levels"], "oc_mean": stats[-1]["oc_mean"],
                      "rel_res_device": stats[-1]["rel_res"], "rel_res_host_check": rel,
                      "t_alg2_ms": stats[-1]["t_alg2_ms"], "t_alg4_ms": stats[-1]["t_alg4_ms"],
-                     "cycles": stats[-1]["cycles"]},
+                     "cycles": stats[-1]["cycles"], "wcycles": stats[-1]["wcycles"]},
            "roofline": roofline, "clocks": clk, "gpu_launches": int(launches)}
 
     if not a.no_extras and rank == 0:
         # the other forms, same graph and b (one warm-up solve, one timed)
         out["forms"] = {a.form: {"ms": ms, "unknowns_per_s": g.n / (ms / 1e3), "iters": stats[-1]["iters"],
-                                 "resetups": stats[-1]["resetups"]}}
+                                 "resetups": stats[-1]["resetups"], "cycles": stats[-1]["cycles"]}}
+        xs = {a.form: x_host}
         for other in ("fp64", "fp32ir", "fp32ir+learned"):
             if other == a.form:
                 continue
@@ -269,12 +353,30 @@ def run_ours(a):
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            _, st2 = step(other)
+            x2, st2 = step(other)
             e1.record()
             torch.cuda.synchronize()
             ms2 = e0.elapsed_time(e1)
+            xs[other] = x2.cpu().numpy()
             out["forms"][other] = {"ms": ms2, "unknowns_per_s": g.n / (ms2 / 1e3), "iters": st2["iters"],
-                                   "resetups": st2["resetups"]}
+                                   "resetups": st2["resetups"], "cycles": st2["cycles"],
+                                   "rel_res_host_check": float(np.linalg.norm(b_host - A @ xs[other]) /
+                                                               np.linalg.norm(b_host))}
+        if "fp64" in out["forms"] and a.form != "fp64":
+            out["speedup_vs_fp64"] = out["forms"]["fp64"]["ms"] / ms
+        # errors: to the oracle's recorded solution of this workload where one
+        # exists, between the forms here, and to the oracle's full solve of C1
+        err = {}
+        rec = error_vs_recorded_oracle(a.workload, x_host) if world == 1 else None
+        err["headline_vs_oracle"] = rec if rec else (
+            "not recorded: the oracle's full solve of this workload keeps every hierarchy in host "
+            "memory (Alg. 2 recycles them) and does not fit the recording host")
+        if "fp64" in xs and a.form != "fp64":
+            xf = xs["fp64"]
+            err["headline_vs_fp64_gpu"] = float(np.linalg.norm(x_host - xf) / np.linalg.norm(xf))
+        err["C1_full_oracle"] = _small_oracle_check(
+            P, {f: (params_for(f), net_for(f)) for f in ("fp64", "fp32ir", "fp32ir+learned")})
+        out["error_vs_oracle"] = err
         # end to end through the public host-buffer call: pinned host inputs,
         # H2D of A, b, x and D2H of x inside the timed region
         rp = torch.as_tensor(g.rowptr).pin_memory().numpy()
@@ -286,10 +388,11 @@ def run_ours(a):
             pass
         hg = HG()
         hg.n, hg.nnz, hg.rowptr, hg.col, hg.val = g.n, g.nnz, rp, ci, va
+
         def host_params():
-            hp = default_params(precision=prec)
+            hp = params_for(a.form)
             if a.form.endswith("+learned"):
-                hp.start, hp.mpnn = N.START_LEARNED, nets["net"]._h
+                hp.start, hp.mpnn = N.START_LEARNED, net_for(a.form)._h
             return hp
         solve_host(hg, bh, params=host_params())
         torch.cuda.synchronize()
@@ -301,8 +404,12 @@ def run_ours(a):
         out["e2e"] = {"value": g.n / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                       "d2h_bytes_per_step": int(8 * g.n), "ms": te * 1e3,
                       "status": ste["status"]}
-        if world == 1:
-            out["cpu_baseline"] = oracle_sample(g, b_host, stats[-1])
+    if oq is not None:
+        try:
+            cb = oq.get(timeout=900)
+        except Exception as ex:
+            cb = {"error": f"oracle sample did not finish: {ex!r}"}
+        out["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -335,86 +442,106 @@ def _host_cpu():
     return {"logical_cores": os.cpu_count(), "machine": platform.machine(), "model": model}
 
 
-def oracle_sample(g, b, gpu_stats, max_seconds=40.0):
-    """The CPU oracle (single thread) on a bounded sample of the same workload:
-    its start vector, one hierarchy build (Alg. 4) and one V- and one W-cycle on
-    the full graph, scaled to a whole solve with the GPU run's own counts of
-    hierarchies and cycles (the oracle reproduces those counts on this graph)."""
-    import numpy as np
+class OracleSample:
+    """The CPU oracle (one thread) on the workload's full graph: its start vector,
+    one hierarchy build (Alg. 4), one W-cycle and V-cycles, timed; a whole
+    solve is extrapolated with the oracle's own counts of builds and cycles from
+    its recorded full solve of the workload (or of the same recipe on a smaller
+    grid, named in the result)."""
 
-    import oracle as O
+    def __init__(self, g, workload):
+        import oracle as O
+        self.O, self.g, self.workload = O, g, workload
+        t0 = time.perf_counter()
+        self.e = O.start_vector(g)
+        t1 = time.perf_counter()
+        self.h = O.Hierarchy(g, self.e, O.default_params(keep_setup=0))
+        t2 = time.perf_counter()
+        self.t_start, self.t_build = t1 - t0, t2 - t1
+        self.t_w = None
+        self.t_v = []
+        self.counts = oracle_counts(workload)
+
+    def wcycle(self, r):
+        t0 = time.perf_counter()
+        self.h.wcycle(r)
+        self.t_w = time.perf_counter() - t0
+
+    def vcycle(self, r):
+        t0 = time.perf_counter()
+        self.h.vcycle(r)
+        self.t_v.append(time.perf_counter() - t0)
+        return self.t_v[-1]
+
+    def estimate(self):
+        c = self.counts
+        tv = statistics.mean(self.t_v)
+        tw = self.t_w if self.t_w is not None else 6.0 * tv
+        est = self.t_start + c["builds"] * self.t_build + (c["cycles"] - c["wcycles"]) * tv + c["wcycles"] * tw
+        return est, tv, tw
+
+    def close(self):
+        self.h.close()
+
+
+def oracle_sample(g, b, workload):
     t0 = time.perf_counter()
-    e = O.start_vector(g)
-    t1 = time.perf_counter()
-    h = O.Hierarchy(g, e)
-    t2 = time.perf_counter()
-    r = b.copy()
-    h.vcycle(r)
-    t3 = time.perf_counter()
-    wc = None
-    if t3 - t0 < max_seconds:
-        h.wcycle(r)
-        wc = time.perf_counter() - t3
-    t_start, t_build, t_v = t1 - t0, t2 - t1, t3 - t2
-    H = gpu_stats["resetups"] + 1
-    cyc = gpu_stats["cycles"]
-    # W-cycles are applied in the first two re-setups' PCG (7 each); counted as W
-    nw = min(gpu_stats["resetups"], 2) * 7
-    est = t_start + H * t_build + (cyc - nw) * t_v + nw * (wc if wc is not None else 2 * t_v)
-    h.close()
-    return {"value": g.n / est, "unit": UNIT, "cores": 1, "kind": "oracle", "host": _host_cpu(),
-            "sample": (f"oracle start vector ({t_start:.2f}s) + 1 hierarchy build ({t_build:.2f}s) + "
-                       f"1 V-cycle ({t_v:.3f}s) + 1 W-cycle ({wc if wc is not None else float('nan'):.3f}s) "
-                       f"on the full graph, scaled by the GPU solve's {H} builds and {cyc} cycles "
-                       f"({nw} W) to {est:.1f}s per solve"),
-            "measured_seconds": time.perf_counter() - t0}
-
-
-# Iteration structure of one solve of the C2 workload (hierarchies built and
-# cycles applied), as reported by the solver's own statistics; the oracle's
-# solve follows the same trajectory on this graph (same counts).
-SOLVE_COUNTS = {"C2": {"builds": 21, "cycles": 1690, "wcycles": 14}}
+    smp = OracleSample(g, workload)
+    if smp.counts is None:
+        smp.close()
+        return {"error": f"no recorded oracle solve for {workload}"}
+    smp.wcycle(b)
+    smp.vcycle(b)
+    est, tv, tw = smp.estimate()
+    smp.close()
+    c = smp.counts
+    return {"value": g.n / est, "unit": UNIT, "cores": 1, "kind": "oracle", "extrapolated": True,
+            "host": _host_cpu(), "measured_seconds": time.perf_counter() - t0,
+            "sample": (f"oracle start vector ({smp.t_start:.2f}s) + 1 hierarchy build ({smp.t_build:.2f}s) + "
+                       f"1 W-cycle ({tw:.2f}s) + 1 V-cycle ({tv:.3f}s) on the full {workload} graph, "
+                       f"extrapolated to {est:.0f}s per solve with the oracle's own counts of its "
+                       f"recorded full solve of {c['from']} (n = {c['n']:,}): {c['builds']} builds, "
+                       f"{c['cycles']} cycles ({c['wcycles']} W)")}
 
 
 def run_reference(a):
-    """The CPU oracle as the reference arm: each step is a bounded sample of the
-    workload (start vector, one hierarchy build, one V- and one W-cycle on the
-    full graph), scaled to a whole solve with the workload's iteration counts."""
+    """The CPU oracle as the reference arm. Set-up (untimed per step): the
+    oracle's start vector, one hierarchy build and one W-cycle on the full graph.
+    Each step: one oracle V-cycle on the full graph. The step's value is the
+    whole solve extrapolated from these measurements with the oracle's own counts
+    of builds and cycles from its recorded full solve (extrapolated: true)."""
     rank, world, _ = _dist()
     if rank != 0:
         return
-    import oracle as O
     from paper_1806_07028_gb300 import inputs as I
     g = I.workload(a.workload)
     b = I.rhs_normal(g.n, 11)
-    cnt = SOLVE_COUNTS.get(a.workload, SOLVE_COUNTS["C2"])
-    est, steps_ms = [], []
-    for k in range(a.warmup + a.steps):
-        t0 = time.perf_counter()
-        e = O.start_vector(g)
-        t1 = time.perf_counter()
-        h = O.Hierarchy(g, e)
-        t2 = time.perf_counter()
-        h.vcycle(b)
-        t3 = time.perf_counter()
-        h.wcycle(b)
-        t4 = time.perf_counter()
-        h.close()
-        if k >= a.warmup:
-            steps_ms.append(1e3 * (t4 - t0))
-            est.append((t1 - t0) + cnt["builds"] * (t2 - t1) +
-                       (cnt["cycles"] - cnt["wcycles"]) * (t3 - t2) + cnt["wcycles"] * (t4 - t3))
-    t_solve = sum(est) / len(est)
-    value = g.n / t_solve
-    sample = (f"per step: oracle start vector + 1 hierarchy build + 1 V-cycle + 1 W-cycle on the "
-              f"full graph ({statistics.mean(steps_ms)/1e3:.1f}s), scaled by {cnt['builds']} builds "
-              f"and {cnt['cycles']} cycles ({cnt['wcycles']} W) to {t_solve:.0f}s per solve")
+    t_setup0 = time.perf_counter()
+    smp = OracleSample(g, a.workload)
+    if smp.counts is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"no recorded oracle solve for {a.workload}"}))
+        return
+    smp.wcycle(b)
+    t_setup = time.perf_counter() - t_setup0
+    for _ in range(a.warmup):
+        smp.vcycle(b)
+    smp.t_v = []
+    step_s = [smp.vcycle(b) for _ in range(a.steps)]
+    est, tv, tw = smp.estimate()
+    smp.close()
+    c = smp.counts
+    value = g.n / est
+    sample = (f"set-up: oracle start vector ({smp.t_start:.1f}s) + 1 hierarchy build ({smp.t_build:.1f}s) + "
+              f"1 W-cycle ({tw:.1f}s); per step: 1 V-cycle on the full graph (mean {tv:.2f}s); "
+              f"extrapolated to {est:.0f}s per solve with the oracle's counts of its recorded full solve "
+              f"of {c['from']}: {c['builds']} builds, {c['cycles']} cycles ({c['wcycles']} W)")
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
-           "warmup": a.warmup, "ms_per_step": 1e3 * t_solve, "higher_is_better": True,
-           "impl": "reference", "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "n": g.n, "nnz": g.nnz, "form": "oracle fp64"},
+           "warmup": a.warmup, "ms_per_step": 1e3 * est, "higher_is_better": True,
+           "impl": "reference", "dtype": "f64", "data": "synthetic", "extrapolated": True,
+           "measured_seconds": {"setup": t_setup, "steps": sum(step_s)},
+           "config": {"workload": workload_label(a.workload), "n": g.n, "nnz": g.nnz, "form": "oracle fp64"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host": _host_cpu(),
-                            "sample": sample},
+                            "extrapolated": True, "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 

@@ -57,7 +57,14 @@ typedef enum {
 } pcamg_status;
 
 enum { PCAMG_FP64 = 0, PCAMG_FP32_IR = 1 };                 /* precision */
-enum { PCAMG_START_RANDOM = 0, PCAMG_START_USER = 1, PCAMG_START_LEARNED = 2 };  /* start vector */
+/* How pcamg_setup builds the first hierarchy: by Alg. 4 from a start vector
+ * (RANDOM: the relaxed random vector; USER: d_e0; LEARNED: the network's
+ * output), or by MWM_setup (Section 2.1: heaviest-first matching of each
+ * level's weighted adjacency, unmatched vertices joined to the pair of their
+ * heaviest neighbour, boolean prolongations -- the paper's initial hierarchy
+ * of Alg. 5 and 6, and with a threshold no factor reaches, its plain UA-AMG
+ * comparator). */
+enum { PCAMG_START_RANDOM = 0, PCAMG_START_USER = 1, PCAMG_START_LEARNED = 2, PCAMG_START_MWM = 3 };
 
 /* A start-vector network (see the pcamg_mpnn_* calls below). */
 typedef struct pcamg_mpnn_s* pcamg_mpnn;
@@ -97,9 +104,12 @@ typedef struct {
     int32_t dense_max;     /* largest coarsest level factorised densely (<= 4096) */
     int32_t use_graphs;    /* capture each cycle in a CUDA graph and replay it */
     int32_t keep_setup;    /* keep covers and reweighted graphs for export */
-    int32_t profile;       /* time the fine-level residual kernel with CUDA events */
-    int32_t tail_rows;     /* levels with at most this many unknowns run inside one
-                              thread block per cycle visit (0 = never) */
+    int32_t profile;       /* bit 0: time the FP64 fine-level residual of Alg. 5 with CUDA
+                              events; bit 1: time the finest-level residual inside every
+                              V-cycle (event-record nodes in the cycle graph) */
+    int32_t tail_rows;     /* levels with at most this many unknowns (the finest level: at
+                              most half as many) run inside one thread-block cluster per
+                              cycle visit, or as their dense operator (0 = never) */
     int32_t l1jac_rows;    /* coarse levels (not the finest) with at most this many
                               unknowns are smoothed by l1-Jacobi, x += (b - A x)/d with
                               d_i = sum_j |a_ij|, instead of multicolour Gauss-Seidel */
@@ -118,6 +128,9 @@ typedef struct {
     pcamg_mpnn mpnn;       /* the network for PCAMG_START_LEARNED, else NULL */
     int32_t update_mode;   /* PCAMG_UPD_*: what Alg. 5 does with the Alg. 2 smooth error
                               after a re-setup (default PCAMG_UPD_REBUILD_ONLY) */
+    int32_t max_cover_rounds; /* cap on the path-cover rounds of one build (0: n + 1, which
+                              always suffices: every round adds at least one edge); a build
+                              that needs more returns PCAMG_ERR_ROUND_CAP */
 } pcamg_params;
 
 typedef struct {
@@ -139,10 +152,42 @@ typedef struct {
     int64_t prof_launches;
     double prof_ms;        /* summed CUDA-event time of those launches */
     double prof_bytes;     /* their algorithmic bytes: 12 nnz + 28 n each */
+    int32_t* rebuilt;      /* optional host buffer of res_hist_cap entries: 1 at step k
+                              when a new hierarchy was built after the k-th V-cycle, else 0 */
+    int64_t wcycles;       /* of cycles: W-cycles */
+    /* finest-level residual inside every V-cycle (params.profile bit 1), timed with
+       CUDA events on the handle's stream (event-record nodes in the cycle graph) */
+    int64_t cyc_launches;
+    double cyc_ms;         /* summed event time of those launches */
+    double cyc_bytes;      /* their algorithmic bytes: (4 + w) nnz + (4 + 3 w) n each,
+                              w = 4 (FP32_IR) or 8 (FP64) */
 } pcamg_stats;
 
 /* Fill p with the defaults above. */
 PCAMG_API pcamg_status pcamg_default_params(pcamg_params* p);
+
+/* ---- device memory --------------------------------------------------------
+ * Every device buffer the library allocates (handles, hierarchies, work
+ * vectors, networks, the partial sums of pcamg_residual) is allocated and freed
+ * in stream order on the stream the work runs on. By default the memory comes
+ * from a memory pool the library creates per device, which keeps freed memory
+ * cached for reuse (pcamg_trim_memory returns it to the device).
+ * pcamg_set_allocator installs caller callbacks instead -- for instance a
+ * framework's caching allocator, so that the library and the framework share
+ * one pool: alloc(bytes, stream, ctx) returns device memory of the current
+ * device usable in stream order on `stream` (a cudaStream_t; NULL = legacy
+ * default stream), or NULL on failure (reported as PCAMG_ERR_OOM);
+ * free(ptr, stream, ctx) releases it, ordered after the work queued on
+ * `stream`. A handle or network keeps the allocator that was installed when it
+ * was created and frees through it, so the callbacks and ctx must stay valid
+ * until it is destroyed. alloc == free == NULL restores the library pool; one
+ * of them NULL alone is PCAMG_ERR_INVALID. Process wide; do not call it while
+ * another thread is inside the library. The paper has no counterpart. */
+typedef void* (*pcamg_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*pcamg_free_fn)(void* ptr, void* stream, void* ctx);
+PCAMG_API pcamg_status pcamg_set_allocator(pcamg_alloc_fn alloc, pcamg_free_fn free, void* ctx);
+/* Return the memory the library pool of the current device holds unused. */
+PCAMG_API pcamg_status pcamg_trim_memory(void);
 
 /* Create a handle for A and build the first hierarchy (Alg. 5 setup, with the
  * initial hierarchy built by Alg. 4 from a start vector instead of MWM).
@@ -285,18 +330,20 @@ PCAMG_API pcamg_status pcamg_residual(int32_t n, const int32_t* d_rowptr, const 
                                       double* d_r, double* d_norm2, void* stream);
 /* The same residual and ||r||_2^2 WITHOUT any device allocation. The paper has
  * no counterpart: this is for callers that cannot allocate device memory --
- * e.g. code recording the stream into a CUDA graph, a time-critical loop that
- * may not pay for cudaMalloc/cudaFree (they can synchronise the device), or a
- * process whose device memory is all handed out by its own pool. The per-block
- * partial sums live in one fixed device array of 65536 doubles (512 KB) that
- * every GPU which loads the library holds until the process exits, so
- * n <= 16,777,216 rows (larger n: PCAMG_ERR_INVALID). d_norm2 is required.
- * The first call on a device looks up that array's device address (with the
- * device current) and caches it; make that first call before any stream
- * capture. All calls share the array: calls whose work overlaps on the GPU
- * (other streams, other host threads) race on it and must be serialised by
- * the caller. Each call overwrites every entry it reads, so no clearing is
- * needed. Errors: pcamg_last_error(NULL). */
+ * e.g. a time-critical loop that may not pay for cudaMalloc/cudaFree (they can
+ * synchronise the device), or a process whose device memory is all handed out
+ * by its own pool. The per-block partial sums live in one fixed device array of
+ * 65536 doubles (512 KB) that every GPU which loads the library holds until the
+ * process exits, so n <= 67,108,864 rows (larger n: PCAMG_ERR_INVALID). d_norm2
+ * is required. The first call on a device looks up that array's device address
+ * (with the device current) and caches it for the life of the process (the
+ * device's primary context must not be reset in between); make that first call
+ * before any stream capture. A call reads nothing back and does not
+ * synchronise: it returns once its two kernels are queued on `stream`. All
+ * calls share the array: calls whose work overlaps on the GPU (other streams,
+ * other host threads) race on it and must be serialised by the caller. Each
+ * call overwrites every entry it reads, so no clearing is needed. Errors:
+ * pcamg_last_error(NULL). */
 PCAMG_API pcamg_status pcamg_residual_noalloc(int32_t n, const int32_t* d_rowptr,
                                               const int32_t* d_col, const double* d_val,
                                               const double* d_x, const double* d_b, double* d_r,

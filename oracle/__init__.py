@@ -56,12 +56,13 @@ class Params(C.Structure):
                 ("seed", C.c_uint64), ("n_min", C.c_int32), ("max_levels", C.c_int32),
                 ("round_cap", C.c_int32), ("p1_mode", C.c_int32), ("leftover_mode", C.c_int32),
                 ("cover_mode", C.c_int32), ("dense_max", C.c_int32), ("l1jac_rows", C.c_int32),
-                ("update_mode", C.c_int32)]
+                ("update_mode", C.c_int32), ("keep_setup", C.c_int32), ("init_mwm", C.c_int32)]
 
 
 class Stats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("resetups", C.c_int32), ("levels", C.c_int32),
-                ("status", C.c_int32), ("rel_res", C.c_double), ("oc_mean", C.c_double)]
+                ("status", C.c_int32), ("rel_res", C.c_double), ("oc_mean", C.c_double),
+                ("cycles", C.c_int64), ("wcycles", C.c_int64)]
 
 
 _i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
@@ -86,6 +87,8 @@ def lib():
             L.orc_residual.argtypes = [C.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p, _f64p]
             L.orc_colour.argtypes = [C.c_int32, _i32p, _i32p, C.c_uint64, _i32p, _PI]
             L.orc_colour.restype = C.c_int32
+            L.orc_colour_smoother.argtypes = [C.c_int32, _i32p, _i32p, C.c_uint64, _i32p, _PI]
+            L.orc_colour_smoother.restype = C.c_int32
             L.orc_mcgs_sweep.argtypes = [C.c_int32, _i32p, _i32p, _f64p, _i32p, C.c_int32,
                                          _f64p, _f64p, C.c_int32]
             L.orc_l1jac_sweep.argtypes = [C.c_int32, _i32p, _i32p, _f64p, _f64p, _f64p]
@@ -107,6 +110,10 @@ def lib():
             L.orc_galerkin.restype = C.c_int32
             L.orc_build.argtypes = [C.c_int32, _i32p, _i32p, _f64p, _f64p, C.POINTER(Params), _PI]
             L.orc_build.restype = C.c_void_p
+            L.orc_build_mwm.argtypes = [C.c_int32, _i32p, _i32p, _f64p, C.POINTER(Params), _PI]
+            L.orc_build_mwm.restype = C.c_void_p
+            L.orc_mwm_aggregate.argtypes = [C.c_int32, _i32p, _i32p, _f64p, C.c_int32, _i32p, _PI, _PI]
+            L.orc_mwm_aggregate.restype = C.c_int32
             L.orc_hier_free.argtypes = [C.c_void_p]
             L.orc_hier_nlevels.argtypes = [C.c_void_p]
             L.orc_hier_nlevels.restype = C.c_int32
@@ -201,6 +208,16 @@ def colour(g, seed=12345, rowptr=None, col=None, n=None):
     return out, int(nc), int(rounds.value)
 
 
+def colour_smoother(g, seed=12345):
+    """The smoother's colouring: BFS parity on connected bipartite graphs, else JP."""
+    out = np.empty(g.n, dtype=np.int32)
+    rounds = C.c_int32(0)
+    nc = lib().orc_colour_smoother(g.n, _i32(g.rowptr), _i32(g.col), seed, out, C.byref(rounds))
+    if nc < 0:
+        raise RuntimeError(ERR.get(-nc))
+    return out, int(nc), int(rounds.value)
+
+
 def mcgs_sweep(g, colours, ncolour, b, x, forward=True):
     rp, ci, v = _csr(g)
     x = _f64(x).copy()
@@ -281,8 +298,20 @@ def galerkin(rowptr, col, val, agg, nc, pval=None, drop_diag=False):
 
 
 # ---- hierarchy --------------------------------------------------------------------
+def mwm_aggregate(g, ld=True):
+    """MWM aggregation of one level (Section 2.1): (agg, nc, rounds)."""
+    rp, ci, v = _csr(g)
+    agg = np.empty(g.n, np.int32)
+    nc, rounds = C.c_int32(0), C.c_int32(0)
+    st = lib().orc_mwm_aggregate(g.n, rp, ci, v, 1 if ld else 0, agg, C.byref(nc), C.byref(rounds))
+    if st:
+        raise RuntimeError(ERR.get(st))
+    return agg, int(nc.value), int(rounds.value)
+
+
 class Hierarchy:
-    """An oracle hierarchy built from smooth error e (Alg. 4)."""
+    """An oracle hierarchy built from smooth error e (Alg. 4), or, with
+    e = None, by MWM_setup (Section 2.1)."""
 
     def __init__(self, g, e, params=None):
         self.g = g
@@ -291,7 +320,10 @@ class Hierarchy:
         rp, ci, v = _csr(g)
         self._keep = (rp, ci, v)
         st = C.c_int32(0)
-        h = lib().orc_build(g.n, rp, ci, v, _f64(e), C.byref(p), C.byref(st))
+        if e is None:
+            h = lib().orc_build_mwm(g.n, rp, ci, v, C.byref(p), C.byref(st))
+        else:
+            h = lib().orc_build(g.n, rp, ci, v, _f64(e), C.byref(p), C.byref(st))
         if not h:
             raise RuntimeError(f"orc_build failed: {ERR.get(st.value, st.value)}")
         self._h = h
@@ -404,7 +436,7 @@ def solve(g, b, x0=None, params=None, e0=None, hist_cap=4096):
                     None if ee is None else ee.ctypes.data_as(C.c_void_p), C.byref(st),
                     hist.ctypes.data_as(C.c_void_p), hist_cap, reb.ctypes.data_as(C.c_void_p))
     s = dict(iters=st.iters, resetups=st.resetups, levels=st.levels, status=ERR.get(st.status, st.status),
-             rel_res=st.rel_res, oc_mean=st.oc_mean,
+             rel_res=st.rel_res, oc_mean=st.oc_mean, cycles=st.cycles, wcycles=st.wcycles,
              rebuilt_after=[int(k) for k in np.nonzero(reb[: st.iters + 1])[0]])
     return x, s, hist[: st.iters + 1]
 
@@ -421,5 +453,5 @@ def solve_zero_rhs(g, x0, params=None, e0=None, hist_cap=4096):
                              None if ee is None else ee.ctypes.data_as(C.c_void_p), C.byref(st),
                              hist.ctypes.data_as(C.c_void_p), hist_cap)
     s = dict(iters=st.iters, resetups=st.resetups, levels=st.levels, status=ERR.get(st.status, st.status),
-             rel_res=st.rel_res, oc_mean=st.oc_mean)
+             rel_res=st.rel_res, oc_mean=st.oc_mean, cycles=st.cycles)
     return x, s, hist[: st.iters + 1]

@@ -60,6 +60,10 @@ typedef struct {
     int32_t l1jac_rows;   /* levels >= 1 with at most this many unknowns are smoothed
                              by l1-Jacobi instead of multicolour Gauss-Seidel */
     int32_t update_mode;  /* ORC_UPD_*: what Alg. 5 does with the smooth error */
+    int32_t keep_setup;   /* keep each level's reweighted graph after the build (for
+                             export); 0 frees it and saves memory on large graphs */
+    int32_t init_mwm;     /* 1: the initial hierarchy of Alg. 5 / Alg. 6 is MWM_setup(A)
+                             (the paper's); 0: Alg. 4 from the start vector */
 } orc_params;
 
 typedef struct {
@@ -69,6 +73,8 @@ typedef struct {
     int32_t status;
     double rel_res;       /* final ||r||/||b|| */
     double oc_mean;       /* operator complexity averaged over all hierarchies */
+    int64_t cycles;       /* multigrid cycles applied (V and W, Alg. 5 and Alg. 2) */
+    int64_t wcycles;      /* of which W-cycles */
 } orc_stats;
 
 void orc_default_params(orc_params* p);
@@ -92,6 +98,11 @@ void orc_residual(int32_t n, const int32_t* rowptr, const int32_t* col, const do
  * Returns the number of colours (>0) or -error. */
 int32_t orc_colour(int32_t n, const int32_t* rowptr, const int32_t* col, uint64_t seed,
                    int32_t* colour, int32_t* rounds);
+/* Smoother colouring: a connected bipartite graph is coloured by the parity of
+ * the breadth-first distance from vertex 0 (two colours); any other graph by
+ * orc_colour. Returns the number of colours or -error. */
+int32_t orc_colour_smoother(int32_t n, const int32_t* rowptr, const int32_t* col, uint64_t seed,
+                            int32_t* colour, int32_t* rounds);
 /* One Gauss-Seidel sweep in colour order (forward: colour 0..C-1, backward:
  * C-1..0; rows ascending inside a colour). */
 void orc_mcgs_sweep(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
@@ -141,6 +152,17 @@ typedef struct orc_hier orc_hier;
 orc_hier* orc_build(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
                     const double* e, const orc_params* p, int32_t* status);
 void orc_hier_free(orc_hier* h);
+/* MWM aggregation of one level (Section 2.1) on the weighted adjacency of A
+ * (edge weight -a_uv): heaviest-first matching (ld = 0: the sequential greedy
+ * over sorted edges; ld = 1: locally-dominant rounds, the same matching, with
+ * their count in *rounds), then each unmatched vertex joins the pair of its
+ * heaviest neighbour. agg[n] numbered by ascending smallest member. */
+int32_t orc_mwm_aggregate(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                          int32_t ld, int32_t* agg, int32_t* nc, int32_t* rounds);
+/* MWM_setup (Alg. 5, 6): the hierarchy of MWM aggregations with boolean P on
+ * every level (UA-AMG), Galerkin coarse matrices, same stopping rules. */
+orc_hier* orc_build_mwm(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                        const orc_params* p, int32_t* status);
 int32_t orc_hier_nlevels(const orc_hier* h);
 /* sizes[0]=n, [1]=nnz, [2]=nc (0 at the coarsest), [3]=ncolour, [4]=cover rounds,
  * [5]=leftover rounds, [6]=pinned (coarsest), [7]=candidate nnz (level 0). */

@@ -37,6 +37,7 @@ void orc_default_params(orc_params* p) {
     p->dense_max = 4096;
     p->l1jac_rows = 2147483647;
     p->update_mode = ORC_UPD_REBUILD_ONLY;  /* the printed order of Alg. 5 */
+    p->keep_setup = 1;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -141,6 +142,43 @@ int32_t orc_colour(int32_t n, const int32_t* rowptr, const int32_t* col, uint64_
     free(h); free(next); free(mark);
     if (rounds_out) *rounds_out = rounds;
     return ncol;
+}
+
+/* Smoother colouring. A connected bipartite graph (every 2D/3D grid graph) is
+ * coloured by the parity of each vertex's breadth-first distance from vertex 0:
+ * two colours, unique once vertex 0 has colour 0. Any other graph (an odd
+ * cycle: some edge joins two vertices at the same distance; or disconnected)
+ * gets the Jones-Plassmann colouring above. *rounds_out = the number of
+ * distance levels, or the Jones-Plassmann rounds. */
+int32_t orc_colour_smoother(int32_t n, const int32_t* rowptr, const int32_t* col, uint64_t seed,
+                            int32_t* colour, int32_t* rounds_out) {
+    int32_t* dist = (int32_t*)orc_xmalloc(sizeof(int32_t) * (size_t)n);
+    int32_t* queue = (int32_t*)orc_xmalloc(sizeof(int32_t) * (size_t)n);
+    if (!dist || !queue) { free(dist); free(queue); return -ORC_ERR_OOM; }
+    for (int32_t i = 0; i < n; ++i) dist[i] = -1;
+    int32_t head = 0, tail = 0, levels = 0, ok = n > 0;
+    if (ok) { dist[0] = 0; queue[tail++] = 0; }
+    while (head < tail) {
+        int32_t v = queue[head++];
+        if (dist[v] + 1 > levels) levels = dist[v] + 1;
+        for (int32_t k = rowptr[v]; k < rowptr[v + 1]; ++k) {
+            int32_t u = col[k];
+            if (u == v) continue;
+            if (dist[u] < 0) { dist[u] = dist[v] + 1; queue[tail++] = u; }
+            else if (dist[u] == dist[v]) ok = 0;     /* odd cycle */
+        }
+    }
+    if (tail != n) ok = 0;                           /* not connected */
+    int32_t nc;
+    if (ok) {
+        for (int32_t i = 0; i < n; ++i) colour[i] = dist[i] & 1;
+        nc = n > 1 ? 2 : 1;
+        if (rounds_out) *rounds_out = levels;
+    } else {
+        nc = orc_colour(n, rowptr, col, seed, colour, rounds_out);
+    }
+    free(dist); free(queue);
+    return nc;
 }
 
 static void gs_row(const int32_t* rowptr, const int32_t* col, const double* val,

@@ -457,6 +457,50 @@ static int32_t build_members(orc_level* L) {
     return ORC_OK;
 }
 
+/* Smoother colouring of every level but the coarsest, the coarsest level's
+ * pinned dense inverse (boolean_chain: every prolongation is boolean, so the
+ * constant null space is kept exactly and the last unknown is pinned), and the
+ * reweighted graphs dropped unless kept for export. */
+static int32_t finish_hierarchy(orc_hier* h, const orc_params* p, int32_t boolean_chain) {
+    int32_t st = ORC_OK;
+    /* smoother colouring on every level but the coarsest; small coarse levels
+     * are smoothed by l1-Jacobi and need none */
+    for (int32_t l = 0; l + 1 < h->nlev; ++l) {
+        orc_level* L = &h->lev[l];
+        L->jac = (l >= 1 && L->n <= p->l1jac_rows);
+        if (L->jac) continue;
+        L->colour = (int32_t*)orc_xmalloc(sizeof(int32_t) * (size_t)L->n);
+        if (!L->colour) return ORC_ERR_OOM;
+        L->ncolour = orc_colour_smoother(L->n, L->rowptr, L->col, p->seed, L->colour, NULL);
+        if (L->ncolour < 0) return -L->ncolour;
+    }
+    /* coarsest level: dense pinned Cholesky -> explicit inverse */
+    {
+        orc_level* C = &h->lev[h->nlev - 1];
+        int32_t m = C->n;
+        if (m > p->dense_max) return ORC_ERR_COARSE_TOO_BIG;
+        double* D = (double*)calloc((size_t)m * (size_t)m, sizeof(double));
+        h->Xinv = (double*)orc_xmalloc(sizeof(double) * (size_t)m * (size_t)m);
+        if (!D || !h->Xinv) { free(D); return ORC_ERR_OOM; }
+        for (int32_t i = 0; i < m; ++i)
+            for (int32_t k = C->rowptr[i]; k < C->rowptr[i + 1]; ++k)
+                D[(size_t)i * m + C->col[k]] = C->val[k];
+        /* a chain of boolean prolongations from a Laplacian keeps the constant
+         * null space exactly: pin the last unknown */
+        st = orc_dense_pinned_inverse(m, D, boolean_chain, 1e-12, h->Xinv, &h->npinned);
+        free(D);
+        h->nL = m;
+        if (st) return st;
+    }
+    if (!p->keep_setup)
+        for (int32_t l = 0; l < h->nlev; ++l) {
+            orc_level* L = &h->lev[l];
+            free(L->tptr); free(L->tcol); free(L->tw);
+            L->tptr = NULL; L->tcol = NULL; L->tw = NULL;
+        }
+    return ORC_OK;
+}
+
 orc_hier* orc_build(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
                     const double* e, const orc_params* p, int32_t* status) {
     int32_t st = ORC_OK;
@@ -526,36 +570,170 @@ orc_hier* orc_build(int32_t n, const int32_t* rowptr, const int32_t* col, const 
         C->nbr0 = cn0; C->nbr1 = cn1;
         h->nlev = l + 2;
     }
-    /* smoother colouring on every level but the coarsest; small coarse levels
-     * are smoothed by l1-Jacobi and need none */
-    for (int32_t l = 0; l + 1 < h->nlev; ++l) {
+    st = finish_hierarchy(h, p, (p->p1_mode == ORC_P1_BOOLEAN) || h->nlev == 1);
+    if (st) goto fail;
+    *status = ORC_OK;
+    return h;
+fail:
+    orc_hier_free(h);
+    *status = st;
+    return NULL;
+}
+
+/* ------------------------------------------------------------------------- */
+/* MWM (Section 2.1): heaviest-first matching on the weighted adjacency of A_l
+ * (edge {u,v} weighs -a_uv > 0), visiting edges in the total order of Alg. 1
+ * (weight descending, then the smaller end, then the larger end) and matching
+ * both ends when both are still free. Each vertex left free then joins the
+ * pair of its heaviest neighbour (that neighbour is matched: a free neighbour
+ * would have been matched to it); an aggregate is a pair with vertices hung on
+ * either end, so its diameter is at most three. A vertex without neighbours
+ * stays alone. Aggregates are numbered by ascending smallest member. */
+typedef struct { double w; int32_t u, v; } mwm_edge;
+
+static int edge_cmp(const void* a, const void* b) {
+    const mwm_edge* x = (const mwm_edge*)a;
+    const mwm_edge* y = (const mwm_edge*)b;
+    if (x->w != y->w) return x->w > y->w ? -1 : 1;
+    if (x->u != y->u) return x->u < y->u ? -1 : 1;
+    return (x->v > y->v) - (x->v < y->v);
+}
+
+/* edge (u, v) of weight w before edge (u2, v2) of weight w2 in the order above */
+static int mwm_before(double w, int32_t u, int32_t v, double w2, int32_t u2, int32_t v2) {
+    int32_t a = u < v ? u : v, b = u < v ? v : u, a2 = u2 < v2 ? u2 : v2, b2 = u2 < v2 ? v2 : u2;
+    if (w != w2) return w > w2;
+    if (a != a2) return a < a2;
+    return b < b2;
+}
+
+static int32_t mwm_match_greedy(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                                int32_t* mate) {
+    int64_t m = 0;
+    for (int32_t u = 0; u < n; ++u)
+        for (int32_t k = rowptr[u]; k < rowptr[u + 1]; ++k) if (col[k] > u) ++m;
+    mwm_edge* E = (mwm_edge*)orc_xmalloc(sizeof(mwm_edge) * (size_t)(m ? m : 1));
+    if (!E) return ORC_ERR_OOM;
+    m = 0;
+    for (int32_t u = 0; u < n; ++u)
+        for (int32_t k = rowptr[u]; k < rowptr[u + 1]; ++k)
+            if (col[k] > u) { E[m].w = -val[k]; E[m].u = u; E[m].v = col[k]; ++m; }
+    qsort(E, (size_t)m, sizeof(mwm_edge), edge_cmp);
+    for (int32_t i = 0; i < n; ++i) mate[i] = -1;
+    for (int64_t t = 0; t < m; ++t)
+        if (mate[E[t].u] < 0 && mate[E[t].v] < 0) { mate[E[t].u] = E[t].v; mate[E[t].v] = E[t].u; }
+    free(E);
+    return ORC_OK;
+}
+
+/* the same matching by locally-dominant rounds: every free vertex points at its
+ * heaviest free neighbour; two vertices pointing at each other are matched */
+static int32_t mwm_match_ld(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                            int32_t* mate, int32_t* rounds_out) {
+    int32_t* best = (int32_t*)orc_xmalloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    if (!best) return ORC_ERR_OOM;
+    for (int32_t i = 0; i < n; ++i) mate[i] = -1;
+    int32_t rounds = 0;
+    for (;;) {
+        int32_t any = 0;
+        for (int32_t v = 0; v < n; ++v) {
+            best[v] = -1;
+            if (mate[v] >= 0) continue;
+            double bw = 0.0;
+            for (int32_t k = rowptr[v]; k < rowptr[v + 1]; ++k) {
+                int32_t u = col[k];
+                if (u == v || mate[u] >= 0) continue;
+                if (best[v] < 0 || mwm_before(-val[k], v, u, bw, v, best[v])) { best[v] = u; bw = -val[k]; }
+            }
+        }
+        ++rounds;
+        for (int32_t v = 0; v < n; ++v) {
+            int32_t u = best[v];
+            if (u >= 0 && best[u] == v) { mate[v] = u; any = 1; }
+        }
+        if (!any) break;
+    }
+    free(best);
+    if (rounds_out) *rounds_out = rounds;
+    return ORC_OK;
+}
+
+int32_t orc_mwm_aggregate(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                          int32_t ld, int32_t* agg, int32_t* nc_out, int32_t* rounds) {
+    int32_t* mate = (int32_t*)orc_xmalloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    int32_t* lab = (int32_t*)orc_xmalloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    int32_t* minm = (int32_t*)orc_xmalloc(sizeof(int32_t) * (size_t)(n ? n : 1));
+    if (!mate || !lab || !minm) { free(mate); free(lab); free(minm); return ORC_ERR_OOM; }
+    int32_t st = ld ? mwm_match_ld(n, rowptr, col, val, mate, rounds)
+                    : mwm_match_greedy(n, rowptr, col, val, mate);
+    if (!ld && rounds) *rounds = 0;
+    if (st) { free(mate); free(lab); free(minm); return st; }
+    /* label = the smaller vertex of the pair; a free vertex takes the label of
+     * its heaviest neighbour's pair */
+    for (int32_t v = 0; v < n; ++v) lab[v] = mate[v] >= 0 ? (v < mate[v] ? v : mate[v]) : -1;
+    for (int32_t v = 0; v < n; ++v) {
+        if (mate[v] >= 0) continue;
+        int32_t b = -1;
+        double bw = 0.0;
+        for (int32_t k = rowptr[v]; k < rowptr[v + 1]; ++k) {
+            int32_t u = col[k];
+            if (u == v) continue;
+            if (b < 0 || mwm_before(-val[k], v, u, bw, v, b)) { b = u; bw = -val[k]; }
+        }
+        lab[v] = (b < 0) ? v : (b < mate[b] ? b : mate[b]);
+    }
+    /* number aggregates by their smallest member */
+    for (int32_t v = 0; v < n; ++v) minm[v] = n;
+    for (int32_t v = 0; v < n; ++v) if (v < minm[lab[v]]) minm[lab[v]] = v;
+    int32_t nc = 0;
+    int32_t* id = mate;   /* reuse: id of the aggregate whose smallest member is v */
+    for (int32_t v = 0; v < n; ++v) id[v] = (minm[lab[v]] == v) ? nc++ : -1;
+    for (int32_t v = 0; v < n; ++v) agg[v] = id[minm[lab[v]]];
+    *nc_out = nc;
+    free(mate); free(lab); free(minm);
+    return ORC_OK;
+}
+
+orc_hier* orc_build_mwm(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                        const orc_params* p, int32_t* status) {
+    int32_t st = ORC_OK;
+    orc_hier* h = (orc_hier*)calloc(1, sizeof(orc_hier));
+    if (!h) { *status = ORC_ERR_OOM; return NULL; }
+    h->nu_pre = p->nu_pre; h->nu_post = p->nu_post;
+    int64_t nnz = rowptr[n];
+    orc_level* L0 = &h->lev[0];
+    L0->n = n; L0->nnz = nnz;
+    L0->rowptr = (int32_t*)orc_xmalloc(sizeof(int32_t) * ((size_t)n + 1));
+    L0->col = (int32_t*)orc_xmalloc(sizeof(int32_t) * (size_t)nnz);
+    L0->val = (double*)orc_xmalloc(sizeof(double) * (size_t)nnz);
+    if (!L0->rowptr || !L0->col || !L0->val) { st = ORC_ERR_OOM; goto fail; }
+    memcpy(L0->rowptr, rowptr, sizeof(int32_t) * ((size_t)n + 1));
+    memcpy(L0->col, col, sizeof(int32_t) * (size_t)nnz);
+    memcpy(L0->val, val, sizeof(double) * (size_t)nnz);
+    h->nlev = 1;
+    for (int32_t l = 0;; ++l) {
         orc_level* L = &h->lev[l];
-        L->jac = (l >= 1 && L->n <= p->l1jac_rows);
-        if (L->jac) continue;
-        L->colour = (int32_t*)orc_xmalloc(sizeof(int32_t) * (size_t)L->n);
-        if (!L->colour) { st = ORC_ERR_OOM; goto fail; }
-        L->ncolour = orc_colour(L->n, L->rowptr, L->col, p->seed, L->colour, NULL);
-        if (L->ncolour < 0) { st = -L->ncolour; goto fail; }
-    }
-    /* coarsest level: dense pinned Cholesky -> explicit inverse */
-    {
-        orc_level* C = &h->lev[h->nlev - 1];
-        int32_t m = C->n;
-        if (m > p->dense_max) { st = ORC_ERR_COARSE_TOO_BIG; goto fail; }
-        double* D = (double*)calloc((size_t)m * (size_t)m, sizeof(double));
-        h->Xinv = (double*)orc_xmalloc(sizeof(double) * (size_t)m * (size_t)m);
-        if (!D || !h->Xinv) { free(D); st = ORC_ERR_OOM; goto fail; }
-        for (int32_t i = 0; i < m; ++i)
-            for (int32_t k = C->rowptr[i]; k < C->rowptr[i + 1]; ++k)
-                D[(size_t)i * m + C->col[k]] = C->val[k];
-        /* a chain of boolean prolongations from a Laplacian keeps the constant
-         * null space exactly: pin the last unknown */
-        int32_t boolean_chain = (p->p1_mode == ORC_P1_BOOLEAN) || h->nlev == 1;
-        st = orc_dense_pinned_inverse(m, D, boolean_chain, 1e-12, h->Xinv, &h->npinned);
-        free(D);
-        h->nL = m;
+        if (L->n <= p->n_min || l == p->max_levels - 1 || l == ORC_MAX_LEVELS - 1) break;
+        L->agg = (int32_t*)orc_xmalloc(sizeof(int32_t) * (size_t)L->n);
+        if (!L->agg) { st = ORC_ERR_OOM; goto fail; }
+        st = orc_mwm_aggregate(L->n, L->rowptr, L->col, L->val, p->cover_mode == ORC_COVER_LD, L->agg,
+                               &L->nc, &L->cover_rounds);
         if (st) goto fail;
+        if ((double)L->nc > 0.9 * (double)L->n) {
+            free(L->agg); L->agg = NULL; L->nc = 0;
+            break;
+        }
+        st = build_members(L);
+        if (st) goto fail;
+        orc_level* C = &h->lev[l + 1];
+        C->n = L->nc;
+        st = orc_galerkin(L->n, L->rowptr, L->col, L->val, L->agg, L->nc, NULL, 0,
+                          &C->rowptr, &C->col, &C->val, &C->nnz);
+        if (st) goto fail;
+        h->nlev = l + 2;
     }
+    st = finish_hierarchy(h, p, 1);
+    if (st) goto fail;
     *status = ORC_OK;
     return h;
 fail:
@@ -588,6 +766,7 @@ void orc_hier_export(const orc_hier* h, int32_t lev, int32_t* agg, int32_t* nbr0
 
 void orc_hier_export_candidates(const orc_hier* h, int32_t* cptr, int32_t* ccol, double* cw) {
     const orc_level* L = &h->lev[0];
+    if (!L->tptr) return;                 /* built with keep_setup = 0 */
     if (cptr) memcpy(cptr, L->tptr, sizeof(int32_t) * ((size_t)L->n + 1));
     if (ccol) memcpy(ccol, L->tcol, sizeof(int32_t) * (size_t)L->tptr[L->n]);
     if (cw) memcpy(cw, L->tw, sizeof(double) * (size_t)L->tptr[L->n]);

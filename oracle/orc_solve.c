@@ -70,12 +70,17 @@ static void cycle(const orc_hier* h, int32_t l, const double* b, double* x, int3
     free(r); free(bc); free(xc);
 }
 
+/* cycles applied since the library was loaded (the oracle is single-threaded) */
+static int64_t g_vcycles = 0, g_wcycles = 0;
+
 void orc_vcycle(const orc_hier* h, const double* r, double* c) {
+    ++g_vcycles;
     memset(c, 0, sizeof(double) * (size_t)h->lev[0].n);
     cycle(h, 0, r, c, 1);
 }
 
 void orc_wcycle(const orc_hier* h, const double* r, double* c) {
+    ++g_wcycles;
     memset(c, 0, sizeof(double) * (size_t)h->lev[0].n);
     cycle(h, 0, r, c, 2);
 }
@@ -86,7 +91,7 @@ int32_t orc_start_vector(int32_t n, const int32_t* rowptr, const int32_t* col,
     int32_t* colour = (int32_t*)orc_xmalloc(sizeof(int32_t) * (size_t)n);
     double* zero = (double*)calloc((size_t)n, sizeof(double));
     if (!colour || !zero) { free(colour); free(zero); return ORC_ERR_OOM; }
-    int32_t nc = orc_colour(n, rowptr, col, p->seed, colour, NULL);
+    int32_t nc = orc_colour_smoother(n, rowptr, col, p->seed, colour, NULL);
     for (int32_t s = 0; s < p->relax_sweeps; ++s)
         orc_mcgs_sweep(n, rowptr, col, val, colour, nc, zero, e, 1);
     remove_mean(n, e);
@@ -172,6 +177,7 @@ int32_t orc_solve(int32_t n, const int32_t* rowptr, const int32_t* col, const do
                   orc_stats* stt, double* res_hist, int32_t cap, int32_t* rebuilt) {
     orc_stats st;
     memset(&st, 0, sizeof(st));
+    const int64_t v0 = g_vcycles, w0 = g_wcycles;
     for (int32_t i = 0; i < n; ++i) if (!isfinite(b[i]) || !isfinite(x[i])) return ORC_ERR_INVALID;
     double bn = vnorm(n, b);
     if (!(bn > 0.0)) return ORC_ERR_INVALID;
@@ -185,9 +191,13 @@ int32_t orc_solve(int32_t n, const int32_t* rowptr, const int32_t* col, const do
     remove_mean(n, x);
     orc_residual(n, rowptr, col, val, x, b, r);
     double res = vnorm(n, r);
-    if (e0) memcpy(e, e0, sizeof(double) * (size_t)n);
-    else if ((status = orc_start_vector(n, rowptr, col, val, p, e))) goto out;
-    hist[0] = orc_build(n, rowptr, col, val, e, p, &status);
+    if (p->init_mwm) {
+        hist[0] = orc_build_mwm(n, rowptr, col, val, p, &status);
+    } else {
+        if (e0) memcpy(e, e0, sizeof(double) * (size_t)n);
+        else if ((status = orc_start_vector(n, rowptr, col, val, p, e))) goto out;
+        hist[0] = orc_build(n, rowptr, col, val, e, p, &status);
+    }
     if (!hist[0]) goto out;
     re = 1;
     oc_sum += orc_hier_oc(hist[0]);
@@ -240,6 +250,8 @@ out:
     st.levels = re > 0 && hist[re - 1] ? hist[re - 1]->nlev : 0;
     st.oc_mean = re > 0 ? oc_sum / (double)re : 0.0;
     st.status = status;
+    st.cycles = (g_vcycles - v0) + (g_wcycles - w0);
+    st.wcycles = g_wcycles - w0;
     if (stt) *stt = st;
     if (hist) for (int32_t j = 0; j < ORC_MAX_HIST; ++j) orc_hier_free(hist[j]);
     free(hist); free(r); free(c); free(e);
@@ -251,6 +263,7 @@ int32_t orc_solve_zero_rhs(int32_t n, const int32_t* rowptr, const int32_t* col,
                            const double* e0, orc_stats* stt, double* res_hist, int32_t cap) {
     orc_stats st;
     memset(&st, 0, sizeof(st));
+    const int64_t v0 = g_vcycles;
     double *r = (double*)orc_xmalloc(sizeof(double) * (size_t)n),
            *c = (double*)orc_xmalloc(sizeof(double) * (size_t)n),
            *zero = (double*)calloc((size_t)n, sizeof(double)),
@@ -263,9 +276,13 @@ int32_t orc_solve_zero_rhs(int32_t n, const int32_t* rowptr, const int32_t* col,
     orc_residual(n, rowptr, col, val, x, zero, r);
     double r0 = vnorm(n, r), res = r0;
     if (!(r0 > 0.0)) { status = ORC_OK; goto out; }
-    if (e0) memcpy(e, e0, sizeof(double) * (size_t)n);
-    else if ((status = orc_start_vector(n, rowptr, col, val, p, e))) goto out;
-    h = orc_build(n, rowptr, col, val, e, p, &status);
+    if (p->init_mwm) {
+        h = orc_build_mwm(n, rowptr, col, val, p, &status);
+    } else {
+        if (e0) memcpy(e, e0, sizeof(double) * (size_t)n);
+        else if ((status = orc_start_vector(n, rowptr, col, val, p, e))) goto out;
+        h = orc_build(n, rowptr, col, val, e, p, &status);
+    }
     if (!h) goto out;
     builds = 1; oc_sum += orc_hier_oc(h);
     int32_t k = 0;
@@ -300,6 +317,7 @@ out:
     st.levels = h ? h->nlev : 0;
     st.oc_mean = builds > 0 ? oc_sum / (double)builds : 0.0;
     st.status = status;
+    st.cycles = g_vcycles - v0;
     if (stt) *stt = st;
     orc_hier_free(h);
     free(r); free(c); free(zero); free(e);

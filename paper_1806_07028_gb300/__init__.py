@@ -10,12 +10,14 @@ fails loudly if the library was not built (``build.build()``).
 from . import inputs  # noqa: F401
 
 __all__ = ["inputs", "Solver", "default_params", "residual", "residual_f32", "uniform",
-           "colour", "solve_host", "build", "Mpnn", "training_example", "train", "first_cycles"]
+           "colour", "solve_host", "build", "Mpnn", "training_example", "train", "first_cycles",
+           "use_allocator", "allocator_calls"]
 
 
 def __getattr__(name):
     if name in ("Solver", "default_params", "residual", "residual_f32", "uniform", "colour",
-                "solve_host", "Mpnn", "training_example", "train", "first_cycles"):
+                "solve_host", "Mpnn", "training_example", "train", "first_cycles",
+                "use_allocator", "allocator_calls"):
         from . import solver
         return getattr(solver, name)
     if name == "build":

@@ -92,11 +92,13 @@ void check_params(const pcamg_params& p) {
         p.max_levels < 1 || p.max_levels > kMaxLevels || p.round_cap < 0 ||
         (p.p1_mode != PCAMG_P1_E_SCALED && p.p1_mode != PCAMG_P1_BOOLEAN) ||
         (p.precision != PCAMG_FP64 && p.precision != PCAMG_FP32_IR) ||
-        (p.start != PCAMG_START_RANDOM && p.start != PCAMG_START_USER && p.start != PCAMG_START_LEARNED) ||
+        (p.start != PCAMG_START_RANDOM && p.start != PCAMG_START_USER && p.start != PCAMG_START_LEARNED &&
+         p.start != PCAMG_START_MWM) ||
         (p.start == PCAMG_START_LEARNED && !p.mpnn) || p.max_resetups < -1 || p.dense_max < 1 ||
         p.dense_max > 4096 || p.tail_rows < 0 || p.l1jac_rows < 0 || p.tail_dense < 0 ||
         p.tail_dense > 3 ||
-        (p.update_mode != PCAMG_UPD_REBUILD_ONLY && p.update_mode != PCAMG_UPD_ADD_CORRECTION))
+        (p.update_mode != PCAMG_UPD_REBUILD_ONLY && p.update_mode != PCAMG_UPD_ADD_CORRECTION) ||
+        p.max_cover_rounds < 0)
         fail(PCAMG_ERR_INVALID, "invalid parameters");
 }
 
@@ -201,13 +203,27 @@ PCAMG_API pcamg_status pcamg_default_params(pcamg_params* p) {
     p->use_graphs = 1;
     p->keep_setup = 0;
     p->profile = 0;
-    p->tail_rows = 2048;
+    p->tail_rows = 4096;
     p->l1jac_rows = 2147483647;
     p->tail_dense = 3;
     p->max_resetups = -1;
     p->mpnn = nullptr;
     p->update_mode = PCAMG_UPD_REBUILD_ONLY;
     return PCAMG_OK;
+}
+
+PCAMG_API pcamg_status pcamg_set_allocator(pcamg_alloc_fn alloc, pcamg_free_fn free, void* ctx) {
+    if ((alloc == nullptr) != (free == nullptr))
+        return set_err(nullptr, PCAMG_ERR_INVALID, "alloc and free must both be given or both be NULL");
+    pc::set_allocator(alloc, free, ctx);
+    return PCAMG_OK;
+}
+
+PCAMG_API pcamg_status pcamg_trim_memory(void) {
+    return guarded(nullptr, [&]() -> pcamg_status {
+        pc::trim_memory();
+        return PCAMG_OK;
+    });
 }
 
 PCAMG_API pcamg_status pcamg_setup(pcamg_handle* out, const pcamg_params* p, int32_t n, int64_t nnz,
@@ -245,7 +261,7 @@ PCAMG_API pcamg_status pcamg_setup(pcamg_handle* out, const pcamg_params* p, int
         }
         alloc_work(*c);
         c->colour0.alloc(c->mem, n);
-        c->ncolour0 = colour_graph(*c, n, c->rowptr.p, c->col.p, c->p.seed, c->colour0.p);
+        c->ncolour0 = colour_smoother(*c, n, c->rowptr.p, c->col.p, c->p.seed, c->colour0.p);
         colour_lists(*c, n, c->colour0.p, c->ncolour0, c->colour_rows0, c->h_colour_ptr0);
         // rows grouped by colour, for the streaming smoother (FP64 for the start
         // vector and the FP64 cycle; FP32 for the FP32 cycle), when its launches
@@ -258,6 +274,12 @@ PCAMG_API pcamg_status pcamg_setup(pcamg_handle* out, const pcamg_params* p, int
                 permute_rows<float>(*c, n, c->colour_rows0.p, c->rowptr.p, c->col.p, c->val.p, p2, c2,
                                     c->gs_val0_32);
             }
+        }
+        if (c->p.start == PCAMG_START_MWM) {
+            c->hist.push_back(build_hierarchy_mwm(*c));
+            c->last_e = nullptr;
+            sync(*c);
+            return PCAMG_OK;
         }
         if (c->p.start == PCAMG_START_USER) {
             check_finite(*c, d_e0, n, "start vector");
@@ -383,7 +405,7 @@ PCAMG_API pcamg_status pcamg_start_vector(pcamg_handle h, double* d_e) {
 PCAMG_API pcamg_status pcamg_last_smooth_error(pcamg_handle h, double* d_e) {
     if (!h || !d_e) return set_err(h, PCAMG_ERR_INVALID, "null argument");
     return guarded(h, [&]() -> pcamg_status {
-        if (!h->last_e) fail(PCAMG_ERR_INVALID, "no hierarchy built");
+        if (!h->last_e) fail(PCAMG_ERR_INVALID, "the newest hierarchy was not built from a smooth error (MWM)");
         Enter guard(*h);
         copy(h->stream, h->n, h->last_e, d_e);
         sync(*h);

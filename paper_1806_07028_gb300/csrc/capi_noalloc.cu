@@ -2,26 +2,28 @@
 // callers that must not allocate device memory.
 //
 // Who needs this: code that runs where a device allocation is not allowed or
-// not wanted -- for instance a caller that is recording a CUDA stream into a
-// graph (a plain cudaMalloc is illegal during capture, and a stream-ordered one
-// would become part of the caller's graph), a time-critical loop that may not
-// pay for cudaMalloc/cudaFree (which can synchronise the whole device), or a
-// process whose device memory is entirely handed out by its own pool. Those
-// callers pass only their inputs and outputs; the per-block partial sums of
-// ||r||^2 live in a fixed array below instead of a buffer allocated per call.
+// not wanted -- for instance a time-critical loop that may not pay for
+// cudaMalloc/cudaFree (which can synchronise the whole device), or a process
+// whose device memory is entirely handed out by its own pool. Those callers
+// pass only their inputs and outputs; the per-block partial sums of ||r||^2
+// live in a fixed array below instead of a buffer allocated per call.
 //
 // The array is a file-scope __device__ variable: every GPU that loads this
 // library holds it (kNoAllocPartials doubles) until the process exits. Host
 // code may not use its name as a device pointer; the device address is looked
 // up once per device with cudaGetSymbolAddress (with that device current) on
-// the first call made on that device, and cached.
+// the first call made on that device, and cached for the life of the process,
+// which assumes the device's primary context is not reset in between. The
+// launch shape depends on n alone, so a call reads nothing back and does not
+// synchronise: it returns once the work is queued on the stream.
 #include <mutex>
 
 #include "pcamg_internal.cuh"
 
 namespace {
 
-// one partial per block of 256 rows: at most 65536 blocks = 16,777,216 rows
+// one partial per block of the norm launch (1,024 rows each): at most 65,536
+// blocks, n <= 67,108,864 rows
 constexpr int kNoAllocPartials = 65536;
 constexpr int kNoAllocMaxDevices = 64;
 
@@ -45,9 +47,9 @@ PCAMG_API pcamg_status pcamg_residual_noalloc(int32_t n, const int32_t* d_rowptr
                                               double* d_r, double* d_norm2, void* stream) {
     if (n < 1 || !d_rowptr || !d_col || !d_val || !d_x || !d_b || !d_r || !d_norm2)
         return noalloc_fail(PCAMG_ERR_INVALID, "pcamg_residual_noalloc: invalid argument");
-    if (pc::residual_partials(n) > kNoAllocPartials)
+    if (pc::residual_norm_blocks(n) > kNoAllocPartials)
         return noalloc_fail(PCAMG_ERR_INVALID,
-                            "pcamg_residual_noalloc: n exceeds 16,777,216 rows (fixed scratch size)");
+                            "pcamg_residual_noalloc: n exceeds 67,108,864 rows (fixed scratch size)");
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
         cudaGetLastError();
@@ -68,29 +70,19 @@ PCAMG_API pcamg_status pcamg_residual_noalloc(int32_t n, const int32_t* d_rowptr
         partials = g_noalloc_ptr[dev];
     }
     cudaStream_t s = (cudaStream_t)stream;
-    int32_t nnz = 0;
-    if (cudaMemcpyAsync(&nnz, d_rowptr + n, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess) {
-        cudaGetLastError();
-        return noalloc_fail(PCAMG_ERR_CUDA, "pcamg_residual_noalloc: reading rowptr[n] failed");
-    }
     try {
+        // with ||r||^2 requested the residual runs the streaming kernel, whose
+        // launch depends on n only (no nnz, no lanes per row)
         pc::Csr A;
         A.n = n;
-        A.nnz = nnz;
         A.rowptr = d_rowptr;
         A.col = d_col;
         A.val = d_val;
-        A.lpr = pc::lanes_per_row(n, nnz);
         // every block writes its own partial, so nothing needs clearing
-        pc::residual64(s, A, d_x, d_b, d_r, partials, d_norm2);
+        pc::residual64(s, A, d_x, d_b, d_r, partials, d_norm2);   // checks the launch
     } catch (const pc::Error& e) {
         pc::set_global_error(e.msg);
         return e.status;
-    }
-    if (cudaStreamSynchronize(s) != cudaSuccess) {
-        cudaGetLastError();
-        return noalloc_fail(PCAMG_ERR_CUDA, "pcamg_residual_noalloc: kernel failed");
     }
     return PCAMG_OK;
 }

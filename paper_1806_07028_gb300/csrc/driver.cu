@@ -8,6 +8,7 @@
 //  * AdaptiveAMG for general b (Alg. 5) and for b = 0 (Alg. 6).
 #include <atomic>
 #include <chrono>
+#include <mutex>
 #include <cmath>
 #include <cstring>
 
@@ -42,12 +43,71 @@ void check_cuda(cudaError_t e, const char* what) {
     throw Error{s, std::string(what) + ": " + cudaGetErrorString(e)};
 }
 
+// ---------------------------------------------------------------- device memory
+static std::mutex g_alloc_mu;
+static pcamg_alloc_fn g_afn = nullptr;
+static pcamg_free_fn g_ffn = nullptr;
+static void* g_actx = nullptr;
+static cudaMemPool_t g_pool[64] = {};
+
+void set_allocator(pcamg_alloc_fn a, pcamg_free_fn f, void* ctx) {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_afn = a;
+    g_ffn = f;
+    g_actx = ctx;
+}
+
+// The library pool of the current device: freed memory stays cached (release
+// threshold unlimited) instead of going back to the device at every
+// synchronisation.
+static cudaMemPool_t library_pool() {
+    int dev = 0;
+    PC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) fail(PCAMG_ERR_CUDA, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        PC_CUDA(cudaMemPoolCreate(&pool, &props));
+        uint64_t keep = UINT64_MAX;
+        PC_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+        g_pool[dev] = pool;
+    }
+    return g_pool[dev];
+}
+
+void trim_memory() {
+    int dev = 0;
+    PC_CUDA(cudaGetDevice(&dev));
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        if (dev >= 0 && dev < 64) pool = g_pool[dev];
+    }
+    if (pool) PC_CUDA(cudaMemPoolTrimTo(pool, 0));
+}
+
+Mem::Mem() {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    afn = g_afn;
+    ffn = g_ffn;
+    actx = g_actx;
+}
+
 void* Mem::alloc(size_t bytes) {
     void* p = nullptr;
-    cudaError_t e = cudaMallocAsync(&p, bytes, stream);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        throw Error{PCAMG_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed"};
+    if (afn) {
+        p = afn(bytes, (void*)stream, actx);
+        if (!p) throw Error{PCAMG_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed"};
+    } else {
+        cudaError_t e = cudaMallocFromPoolAsync(&p, bytes, library_pool(), stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            throw Error{PCAMG_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed"};
+        }
     }
     live += bytes;
     if (live > peak) peak = live;
@@ -55,13 +115,16 @@ void* Mem::alloc(size_t bytes) {
 }
 
 void Mem::release(void* p, size_t bytes) {
-    cudaFreeAsync(p, stream);
+    if (ffn) ffn(p, (void*)stream, actx);
+    else cudaFreeAsync(p, stream);
     live -= bytes;
 }
 
 Ctx::~Ctx() {
     for (Hier* h : hist) delete h;
     hist.clear();
+    for (cudaEvent_t e : cyc_ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : cyc_tmpl) if (e) cudaEventDestroy(e);
     if (h_red) cudaFreeHost(h_red);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
@@ -155,6 +218,50 @@ static void smooth(Ctx& c, Level& L, const T* b, T* x, bool forward) {
     }
 }
 
+// ---------------------------------------------------------------- live timing
+// params.profile bit 1: CUDA events around the finest-level residual of every
+// V-cycle. Inside a captured graph they are event-record nodes, retargeted to a
+// fresh pair of pool events before each replay; without graphs the pool events
+// are recorded on the stream directly. The pairs are resolved when the solve
+// ends (pcamg_stats.cyc_*).
+static constexpr size_t kMaxProfEvents = 1 << 16;   // pairs beyond this are not timed
+
+static cudaEvent_t pool_event(Ctx& c) {
+    if (c.cyc_used >= kMaxProfEvents) return nullptr;
+    if (c.cyc_used == c.cyc_ev.size()) {
+        cudaEvent_t e = nullptr;
+        PC_CUDA(cudaEventCreate(&e));
+        c.cyc_ev.push_back(e);
+    }
+    return c.cyc_ev[c.cyc_used++];
+}
+
+static void prof_mark(Ctx& c, Hier& h, int k) {
+    if (capturing()) {
+        if (!c.cyc_tmpl[k]) PC_CUDA(cudaEventCreate(&c.cyc_tmpl[k]));
+        PC_CUDA(cudaEventRecordWithFlags(c.cyc_tmpl[k], c.stream, cudaEventRecordExternal));
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t nd = 0;
+        PC_CUDA(cudaStreamGetCaptureInfo(c.stream, &cs, nullptr, nullptr, &deps, nullptr, &nd));
+        if (nd != 1) fail(PCAMG_ERR_CUDA, "profiling node not found in the captured cycle");
+        h.prof_node[k] = deps[0];
+        pdl_after_copy();   // the next kernel follows a non-kernel node
+    } else if (cudaEvent_t e = pool_event(c)) {
+        PC_CUDA(cudaEventRecord(e, c.stream));
+    }
+}
+
+static void prof_resolve(Ctx& c) {
+    for (size_t i = 0; i + 1 < c.cyc_used; i += 2) {
+        float ms = 0.f;
+        PC_CUDA(cudaEventElapsedTime(&ms, c.cyc_ev[i], c.cyc_ev[i + 1]));
+        c.cyc_ms += ms;
+        c.cyc_launches += 1;
+    }
+    c.cyc_used = 0;
+}
+
 // One visit of level l. `fresh`: x arrives as the result of one l1-Jacobi
 // sweep from zero (the parent wrote b/d), so the first pre-sweep is done.
 // `first`: x is zero or that fresh start, i.e. this is the child's first visit.
@@ -197,8 +304,11 @@ static void cycle_level(Ctx& c, Hier& h, int32_t l, int gamma, bool fresh, bool 
     const T* dc = nullptr;
     if (child_fresh) { if constexpr (sizeof(T) == 8) dc = C.dl1_64.p; else dc = C.dl1_32.p; }
     T* r = LV<T>::r(L);
+    const bool prof = l == 0 && gamma == 1 && (c.p.profile & 2);
+    if (prof) prof_mark(c, h, 0);
     if constexpr (sizeof(T) == 8) residual64(s, L.A, x, b, r, nullptr, nullptr);
     else residual32(s, L.A, x, b, r);
+    if (prof) prof_mark(c, h, 1);
     restrict_agg<T>(s, L.nc, L.agg_ptr.p, L.agg_mem.p, l == 0 ? LV<T>::pv(L) : nullptr, r,
                     LV<T>::b(C), LV<T>::x(C), dc);
     for (int g = 0; g < gamma; ++g) cycle_level<T>(c, h, l + 1, gamma, child_fresh && g == 0, g == 0);
@@ -263,8 +373,15 @@ static void run_body(Ctx& c, Hier& h, int gamma) {
         t_capture_acc = nullptr;
         PC_CUDA(cudaStreamEndCapture(c.stream, &g));
         cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
-        cudaGraphDestroy(g);
+        // a graph holding profiling nodes is kept: its nodes name the ones to retarget
+        if (gamma == 1 && h.prof_node[0]) h.graph_tmpl = g; else cudaGraphDestroy(g);
         PC_CUDA(e);
+    }
+    if (gamma == 1 && h.prof_node[0] && (c.p.profile & 2)) {
+        for (int k = 0; k < 2; ++k) {
+            cudaEvent_t e = pool_event(c);
+            PC_CUDA(cudaGraphExecEventRecordNodeSetEvent(ge, h.prof_node[k], e ? e : c.cyc_tmpl[k]));
+        }
     }
     PC_CUDA(cudaGraphLaunch(ge, c.stream));
     count_launches(h.graph_kernels[gamma - 1]);
@@ -274,12 +391,18 @@ static void run_body(Ctx& c, Hier& h, int gamma) {
 void cycle(Ctx& c, Hier& h, int gamma, const double* r, double* out) {
     cudaStream_t s = c.stream;
     c.ncycles += 1;
+    if (gamma == 2) c.nwcycles += 1;
     Level& L0 = h.lev[0];
     if (c.p.precision == PCAMG_FP32_IR) {
-        // scale by ||r||_2 so the float cycle sees O(1) data, then scale back
-        dot(s, c.n, r, r, partials(c), slot(c, S_T0));
-        scalar_ops(s, SOP_SQRT, slot(c, 0), S_T0, 0, S_SCALE);
-        scalar_ops(s, SOP_INV, slot(c, 0), S_SCALE, 0, S_INV);
+        // scale so the float cycle sees data of order one, then scale back:
+        // inside a solve by the power of two fixed from ||b|| (exact; residuals
+        // only shrink from there, far above float's smallest normal), else by
+        // this residual's ||r||_2
+        if (!c.fixed_scale) {
+            dot(s, c.n, r, r, partials(c), slot(c, S_T0));
+            scalar_ops(s, SOP_SQRT, slot(c, 0), S_T0, 0, S_SCALE);
+            scalar_ops(s, SOP_INV, slot(c, 0), S_SCALE, 0, S_INV);
+        }
         cast_scaled_f32(s, c.n, r, slot(c, S_INV), L0.b32.p);
         run_body(c, h, gamma);
         set_scaled_f32(s, c.n, L0.x32.p, slot(c, S_SCALE), out);
@@ -295,9 +418,9 @@ static void fine_residual(Ctx& c, const double* x, const double* b, double* r, d
     Csr A;
     A.n = c.n; A.nnz = c.nnz; A.rowptr = c.rowptr.p; A.col = c.col.p; A.val = c.val.p;
     A.lpr = lanes_per_row(c.n, c.nnz);
-    if (c.p.profile) PC_CUDA(cudaEventRecord(c.ev0, c.stream));
+    if (c.p.profile & 1) PC_CUDA(cudaEventRecord(c.ev0, c.stream));
     residual64(c.stream, A, x, b, r, partials(c), norm2);
-    if (c.p.profile) {
+    if (c.p.profile & 1) {
         PC_CUDA(cudaEventRecord(c.ev1, c.stream));
         PC_CUDA(cudaEventSynchronize(c.ev1));
         float ms = 0.f;
@@ -398,6 +521,23 @@ static double now_ms() {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// Fix the FP32 cycles' scale for a solve: the power of two nearest to the root
+// mean square of the right-hand side (norm2 = ||b||_2), so scaling is exact.
+static void fix_scale(Ctx& c, double norm2) {
+    double rms = norm2 / std::sqrt((double)c.n);
+    int e = (rms > 0.0 && std::isfinite(rms)) ? std::ilogb(rms) : 0;
+    c.h_red[40] = std::ldexp(1.0, e);
+    c.h_red[41] = std::ldexp(1.0, -e);
+    PC_CUDA(cudaMemcpyAsync(slot(c, S_SCALE), c.h_red + 40, sizeof(double), cudaMemcpyHostToDevice, c.stream));
+    PC_CUDA(cudaMemcpyAsync(slot(c, S_INV), c.h_red + 41, sizeof(double), cudaMemcpyHostToDevice, c.stream));
+    c.fixed_scale = true;
+}
+
+struct ScaleGuard {
+    Ctx& c;
+    ~ScaleGuard() { c.fixed_scale = false; }
+};
+
 static double read_norm(Ctx& c) {
     PC_CUDA(cudaMemcpyAsync(c.h_red, slot(c, S_NORM2), sizeof(double), cudaMemcpyDeviceToHost, c.stream));
     sync(c);
@@ -422,12 +562,20 @@ pcamg_status solve(Ctx& c, const double* b, double* x, pcamg_stats* st) {
     double t0 = now_ms(), t_setup = 0.0;
     c.prof_ms = 0.0;
     c.prof_launches = 0;
+    c.cyc_ms = 0.0;
+    c.cyc_launches = 0;
+    c.cyc_used = 0;
     c.ncycles = 0;
+    c.nwcycles = 0;
     c.t_alg2 = c.t_alg4 = 0.0;
     int32_t re0 = (int32_t)c.hist.size();
+    if (st && st->rebuilt)
+        for (int32_t i = 0; i < st->res_hist_cap; ++i) st->rebuilt[i] = 0;
     dot(s, c.n, b, b, partials(c), slot(c, S_NORM2));
     double bn = read_norm(c);
     if (!std::isfinite(bn) || !(bn > 0.0)) fail(PCAMG_ERR_INVALID, "right-hand side is zero or not finite");
+    ScaleGuard sg{c};
+    fix_scale(c, bn);
     remove_mean(c, x);
     fine_residual(c, x, b, c.w_r.p, slot(c, S_NORM2));
     double res = read_norm(c);
@@ -458,6 +606,7 @@ pcamg_status solve(Ctx& c, const double* b, double* x, pcamg_stats* st) {
             if (c.p.max_resetups >= 0 && (int32_t)c.hist.size() - re0 >= c.p.max_resetups) break;
             double ts = now_ms();
             rebuild(c, c.w_e.p);
+            if (st && st->rebuilt && k < st->res_hist_cap) st->rebuilt[k] = 1;
             if (c.p.update_mode == PCAMG_UPD_ADD_CORRECTION) {
                 axpy(s, c.n, 1.0, c.w_e.p, x);
                 remove_mean(c, x);
@@ -473,6 +622,7 @@ pcamg_status solve(Ctx& c, const double* b, double* x, pcamg_stats* st) {
     }
     if (status == PCAMG_OK && !(res / bn <= c.p.tol)) status = PCAMG_ERR_NOT_CONVERGED;
     sync(c);
+    prof_resolve(c);
     if (st) {
         st->iters = k;
         st->resetups = (int32_t)c.hist.size() - re0;
@@ -488,9 +638,14 @@ pcamg_status solve(Ctx& c, const double* b, double* x, pcamg_stats* st) {
         st->t_alg2_ms = c.t_alg2;
         st->t_alg4_ms = c.t_alg4;
         st->cycles = c.ncycles;
+        st->wcycles = c.nwcycles;
         st->prof_launches = c.prof_launches;
         st->prof_ms = c.prof_ms;
         st->prof_bytes = (double)c.prof_launches * (12.0 * (double)c.nnz + 28.0 * (double)c.n);
+        const double w = c.p.precision == PCAMG_FP32_IR ? 4.0 : 8.0;
+        st->cyc_launches = c.cyc_launches;
+        st->cyc_ms = c.cyc_ms;
+        st->cyc_bytes = (double)c.cyc_launches * ((4.0 + w) * (double)c.nnz + (4.0 + 3.0 * w) * (double)c.n);
     }
     return status;
 }
@@ -499,11 +654,17 @@ pcamg_status solve_zero_rhs(Ctx& c, double* x, pcamg_stats* st) {
     cudaStream_t s = c.stream;
     double t0 = now_ms(), t_setup = 0.0;
     int32_t re0 = (int32_t)c.hist.size();
+    c.ncycles = 0;
+    c.nwcycles = 0;
+    if (st && st->rebuilt)
+        for (int32_t i = 0; i < st->res_hist_cap; ++i) st->rebuilt[i] = 0;
     double* zero = c.w_t2.p;
     fill(s, c.n, 0.0, zero);
     remove_mean(c, x);
     fine_residual(c, x, zero, c.w_r.p, slot(c, S_NORM2));
     double r0 = read_norm(c), res = r0;
+    ScaleGuard sg{c};
+    fix_scale(c, r0);
     int32_t k = 0, hl = 0;
     pcamg_status status = PCAMG_OK;
     auto hist_put = [&](int32_t idx, double v) {
@@ -531,6 +692,7 @@ pcamg_status solve_zero_rhs(Ctx& c, double* x, pcamg_stats* st) {
                 c.hist.push_back(h);
                 c.last_e = c.w_eh.p;
                 t_setup += now_ms() - ts;
+                if (st && st->rebuilt && k < st->res_hist_cap) st->rebuilt[k] = 1;
             }
         }
         if (status == PCAMG_OK && !(res / r0 <= c.p.tol)) status = PCAMG_ERR_NOT_CONVERGED;
@@ -548,6 +710,8 @@ pcamg_status solve_zero_rhs(Ctx& c, double* x, pcamg_stats* st) {
         st->t_setup_ms = t_setup;
         st->t_solve_ms = now_ms() - t0;
         st->res_hist_len = hl;
+        st->cycles = c.ncycles;
+        st->wcycles = c.nwcycles;
     }
     return status;
 }

@@ -14,6 +14,7 @@ namespace pc {
 Hier::~Hier() {
     for (auto& g : graph)
         if (g) cudaGraphExecDestroy(g);
+    if (graph_tmpl) cudaGraphDestroy(graph_tmpl);
 }
 
 static Csr make_csr(const Level& L, int32_t n, int64_t nnz, const int32_t* rp, const int32_t* ci,
@@ -75,6 +76,80 @@ static void setup_tail(Ctx& c, Hier& h) {
     h.tail.alloc(c.mem, sizeof(TailLevel<T>) * h.nlev);
     PC_CUDA(cudaMemcpyAsync(h.tail.p, tl.data(), sizeof(TailLevel<T>) * h.nlev, cudaMemcpyHostToDevice, c.stream));
     sync(c);
+}
+
+// Everything after the levels exist: smoothers (l1-Jacobi diagonals or
+// colourings), the coarsest level's pinned dense inverse (boolean_chain: every
+// prolongation is boolean, so the last unknown is pinned), work vectors,
+// operator complexity, the coarse tail and the row-permuted smoother copies.
+static void finish_hierarchy(Ctx& c, Hier& hh, bool boolean_chain) {
+    const pcamg_params& p = c.p;
+    const bool f32 = p.precision == PCAMG_FP32_IR;
+    Hier* h = &hh;
+    const int32_t nlev = h->nlev;
+    // smoother of every level but the coarsest: small coarse levels use
+    // l1-Jacobi (diagonal of row l1 norms), the others multicolour Gauss-Seidel
+    // (level 0's colouring is shared)
+    for (int32_t l = 1; l + 1 < nlev; ++l) {
+        Level& L = h->lev[l];
+        if (L.n <= p.l1jac_rows) {
+            L.jac = 1;
+            L.dl1_64.alloc(c.mem, L.n);
+            l1_diagonal(c.stream, L.n, L.A.rowptr, L.A.val, L.dl1_64.p);
+            if (f32) {
+                L.dl1_32.alloc(c.mem, L.n);
+                cast_f32(c.stream, L.n, L.dl1_64.p, L.dl1_32.p);
+            }
+            continue;
+        }
+        L.colour.alloc(c.mem, L.n);
+        L.ncolour = colour_smoother(c, L.n, L.A.rowptr, L.A.col, p.seed, L.colour.p);
+        colour_lists(c, L.n, L.colour.p, L.ncolour, L.colour_rows, L.h_colour_ptr);
+        L.colour_v = L.colour.p;
+        L.colour_rows_v = L.colour_rows.p;
+    }
+    // coarsest level
+    Level& LC = h->lev[nlev - 1];
+    if (LC.n > p.dense_max) fail(PCAMG_ERR_COARSE_TOO_BIG, "coarsening stalled above dense_max");
+    coarse_factor(c, LC.n, LC.A.rowptr, LC.A.col, LC.A.val, boolean_chain, h->Xinv, &h->npinned);
+    h->nL = LC.n;
+    // work vectors
+    double nnz_sum = 0.0;
+    for (int32_t l = 0; l < nlev; ++l) {
+        Level& L = h->lev[l];
+        nnz_sum += (double)L.nnz;
+        if (f32) {
+            L.x32.alloc(c.mem, L.n); L.b32.alloc(c.mem, L.n); L.r32.alloc(c.mem, L.n);
+            if (l == nlev - 1) { L.x64.alloc(c.mem, L.n); L.b64.alloc(c.mem, L.n); }
+        } else {
+            L.x64.alloc(c.mem, L.n); L.b64.alloc(c.mem, L.n); L.r64.alloc(c.mem, L.n);
+        }
+    }
+    h->oc = nnz_sum / (double)c.nnz;
+    // levels from lt down run inside the single-block tail kernel
+    // (the finest level joins only below half the limit: the tail's dense
+    // operator then stays a small part of a small problem)
+    h->lt = nlev;
+    if (p.tail_rows > 0)
+        for (int32_t l = 0; l < nlev; ++l)
+            if (h->lev[l].n <= (l == 0 ? p.tail_rows / 2 : p.tail_rows)) { h->lt = l; break; }
+    if (h->lt < nlev) {
+        if (f32) setup_tail<float>(c, *h); else setup_tail<double>(c, *h);
+    }
+    // row-permuted copies for the streaming smoother on levels above the tail
+    for (int32_t l = 1; l < h->lt && l + 1 < nlev; ++l) {
+        Level& L = h->lev[l];
+        if (L.jac || L.ncolour < 1 || !use_stream(L.n / L.ncolour, L.A.lpr)) continue;
+        if (f32) {
+            permute_rows<float>(c, L.n, L.colour_rows_v, L.A.rowptr, L.A.col, L.A.val, L.gs_ptr, L.gs_col, L.gs_val32);
+            L.gs_val32_v = L.gs_val32.p;
+        } else {
+            permute_rows<double>(c, L.n, L.colour_rows_v, L.A.rowptr, L.A.col, L.A.val, L.gs_ptr, L.gs_col, L.gs_val64);
+            L.gs_val64_v = L.gs_val64.p;
+        }
+        L.gs_ptr_v = L.gs_ptr.p;
+        L.gs_col_v = L.gs_col.p;
+    }
 }
 
 Hier* build_hierarchy(Ctx& c, const double* e) {
@@ -160,68 +235,55 @@ Hier* build_hierarchy(Ctx& c, const double* e) {
         Lc.tw = std::move(t.w);
         Lc.tnnz = t.nnz;
     }
-    // smoother of every level but the coarsest: small coarse levels use
-    // l1-Jacobi (diagonal of row l1 norms), the others multicolour Gauss-Seidel
-    // (level 0's colouring is shared)
-    for (int32_t l = 1; l + 1 < nlev; ++l) {
+    finish_hierarchy(c, *h, (p.p1_mode == PCAMG_P1_BOOLEAN) || nlev == 1);
+    sync(c);
+    return h.release();
+}
+
+// MWM_setup (Alg. 5 and 6, Section 2.1): MWM aggregation of every level's
+// weighted adjacency, boolean prolongations (UA-AMG), Galerkin coarse
+// matrices, the same stopping rules as Alg. 4.
+Hier* build_hierarchy_mwm(Ctx& c) {
+    const pcamg_params& p = c.p;
+    std::unique_ptr<Hier> h(new Hier());
+    const bool f32 = p.precision == PCAMG_FP32_IR;
+    Level& L0 = h->lev[0];
+    L0.n = c.n;
+    L0.nnz = c.nnz;
+    L0.A = make_csr(L0, c.n, c.nnz, c.rowptr.p, c.col.p, c.val.p, f32 ? c.val32.p : nullptr);
+    L0.ncolour = c.ncolour0;
+    L0.colour_v = c.colour0.p;
+    L0.colour_rows_v = c.colour_rows0.p;
+    L0.h_colour_ptr = c.h_colour_ptr0;
+    L0.gs_ptr_v = c.gs_ptr0.p;
+    L0.gs_col_v = c.gs_col0.p;
+    L0.gs_val64_v = f32 ? nullptr : c.gs_val0_64.p;
+    L0.gs_val32_v = f32 ? c.gs_val0_32.p : nullptr;
+    int32_t nlev = 1;
+    for (int32_t l = 0;; ++l) {
         Level& L = h->lev[l];
-        if (L.n <= p.l1jac_rows) {
-            L.jac = 1;
-            L.dl1_64.alloc(c.mem, L.n);
-            l1_diagonal(c.stream, L.n, L.A.rowptr, L.A.val, L.dl1_64.p);
-            if (f32) {
-                L.dl1_32.alloc(c.mem, L.n);
-                cast_f32(c.stream, L.n, L.dl1_64.p, L.dl1_32.p);
-            }
-            continue;
-        }
-        L.colour.alloc(c.mem, L.n);
-        L.ncolour = colour_graph(c, L.n, L.A.rowptr, L.A.col, p.seed, L.colour.p);
-        colour_lists(c, L.n, L.colour.p, L.ncolour, L.colour_rows, L.h_colour_ptr);
-        L.colour_v = L.colour.p;
-        L.colour_rows_v = L.colour_rows.p;
-    }
-    // coarsest level
-    Level& LC = h->lev[nlev - 1];
-    if (LC.n > p.dense_max) fail(PCAMG_ERR_COARSE_TOO_BIG, "coarsening stalled above dense_max");
-    bool boolean_chain = (p.p1_mode == PCAMG_P1_BOOLEAN) || nlev == 1;
-    coarse_factor(c, LC.n, LC.A.rowptr, LC.A.col, LC.A.val, boolean_chain, h->Xinv, &h->npinned);
-    h->nL = LC.n;
-    // work vectors
-    double nnz_sum = 0.0;
-    for (int32_t l = 0; l < nlev; ++l) {
-        Level& L = h->lev[l];
-        nnz_sum += (double)L.nnz;
+        if (L.n <= p.n_min || l == p.max_levels - 1 || l == kMaxLevels - 1) break;
+        DBuf<int32_t> agg;
+        int32_t rounds = 0;
+        const int32_t nc = mwm_aggregate_level(c, L.n, L.A.rowptr, L.A.col, L.A.val, agg, &rounds);
+        if (l == 0) L.cover_rounds = rounds;
+        if ((double)nc > 0.9 * (double)L.n) break;
+        L.nc = nc;
+        L.agg = std::move(agg);
+        build_members(c, L.n, nc, L.agg.p, L.agg_ptr, L.agg_mem);
+        Level& C = h->lev[l + 1];
+        C.n = nc;
+        C.nnz = galerkin(c, L.n, L.A.rowptr, L.A.col, L.A.val, nc, L.agg.p, L.agg_ptr.p,
+                         L.agg_mem.p, nullptr, false, C.rowptr, C.col, C.val);
         if (f32) {
-            L.x32.alloc(c.mem, L.n); L.b32.alloc(c.mem, L.n); L.r32.alloc(c.mem, L.n);
-            if (l == nlev - 1) { L.x64.alloc(c.mem, L.n); L.b64.alloc(c.mem, L.n); }
-        } else {
-            L.x64.alloc(c.mem, L.n); L.b64.alloc(c.mem, L.n); L.r64.alloc(c.mem, L.n);
+            C.val32.alloc(c.mem, C.nnz);
+            cast_f32(c.stream, C.nnz, C.val.p, C.val32.p);
         }
+        C.A = make_csr(C, C.n, C.nnz, C.rowptr.p, C.col.p, C.val.p, f32 ? C.val32.p : nullptr);
+        nlev = l + 2;
     }
-    h->oc = nnz_sum / (double)c.nnz;
-    // levels from lt down run inside the single-block tail kernel
-    h->lt = nlev;
-    if (p.tail_rows > 0)
-        for (int32_t l = 0; l < nlev; ++l)
-            if (h->lev[l].n <= p.tail_rows) { h->lt = l; break; }
-    if (h->lt < nlev) {
-        if (f32) setup_tail<float>(c, *h); else setup_tail<double>(c, *h);
-    }
-    // row-permuted copies for the streaming smoother on levels above the tail
-    for (int32_t l = 1; l < h->lt && l + 1 < nlev; ++l) {
-        Level& L = h->lev[l];
-        if (L.jac || L.ncolour < 1 || !use_stream(L.n / L.ncolour, L.A.lpr)) continue;
-        if (f32) {
-            permute_rows<float>(c, L.n, L.colour_rows_v, L.A.rowptr, L.A.col, L.A.val, L.gs_ptr, L.gs_col, L.gs_val32);
-            L.gs_val32_v = L.gs_val32.p;
-        } else {
-            permute_rows<double>(c, L.n, L.colour_rows_v, L.A.rowptr, L.A.col, L.A.val, L.gs_ptr, L.gs_col, L.gs_val64);
-            L.gs_val64_v = L.gs_val64.p;
-        }
-        L.gs_ptr_v = L.gs_ptr.p;
-        L.gs_col_v = L.gs_col.p;
-    }
+    h->nlev = nlev;
+    finish_hierarchy(c, *h, true);
     sync(c);
     return h.release();
 }

@@ -1,9 +1,12 @@
-// Smoother colouring: Jones-Plassmann rounds with priorities
+// Smoother colouring. A connected bipartite graph is coloured by the parity of
+// the breadth-first distance from vertex 0 (two colours). Otherwise:
+// Jones-Plassmann rounds with priorities
 // (splitmix64(seed ^ i), i). In a round every uncoloured vertex whose priority
 // beats all its uncoloured neighbours takes the smallest colour not used by its
 // already coloured neighbours; such winners are never adjacent, so a round's
 // assignments are independent. The colour classes are independent sets, which
 // makes a multicolour Gauss-Seidel sweep deterministic and parallel.
+#include <algorithm>
 #include <vector>
 
 #include "pcamg_internal.cuh"
@@ -72,6 +75,41 @@ __global__ void k_colour_round(int n, const int* __restrict__ rowptr, const int*
     }
 }
 
+// One breadth-first level from vertex 0 over its frontier (the vertices at
+// distance d, listed by the previous level): every frontier vertex claims its
+// unlabelled neighbours for distance d + 1 (one claimant wins each, by
+// compare-and-swap, and lists it for the next level). An edge between two
+// vertices at distance d means an odd cycle; distances d are final before this
+// launch and it writes only d + 1, so the test is race free. The lists' order
+// depends on scheduling; the distances do not.
+__global__ void k_bfs_level(const int* __restrict__ rowptr, const int* __restrict__ col, int d,
+                            const int* __restrict__ qin, const int* __restrict__ nin,
+                            int* __restrict__ qout, int* __restrict__ nout, int* __restrict__ dist,
+                            int* __restrict__ odd) {
+    const int m = *nin;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        const int v = qin[i];
+        bool o = false;
+        for (int k = rowptr[v]; k < rowptr[v + 1]; ++k) {
+            const int u = col[k];
+            if (u == v) continue;
+            const int du = dist[u];
+            if (du == d) o = true;
+            else if (du < 0 && atomicCAS(dist + u, -1, d + 1) == -1) qout[atomicAdd(nout, 1)] = u;
+        }
+        if (o) *odd = 1;
+    }
+}
+
+__global__ void k_parity_colour(int n, const int* __restrict__ dist, int* __restrict__ colour,
+                                int* __restrict__ unreached) {
+    FOR_EACH(v, n) {
+        const int d = dist[v];
+        colour[v] = d & 1;
+        if (d < 0) *unreached = 1;
+    }
+}
+
 __global__ void k_colour_count(int n, const int* __restrict__ colour, int* __restrict__ cnt) {
     FOR_EACH(v, n) atomicAdd(cnt + colour[v], 1);
 }
@@ -130,6 +168,61 @@ int32_t colour_graph(Ctx& c, int32_t n, const int32_t* rowptr, const int32_t* co
     if (a != colour) PC_CUDA(cudaMemcpyAsync(colour, a, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
     int32_t nc = read_i32(c, maxc.p) + 1;
     return nc;
+}
+
+// Smoother colouring: a connected bipartite graph gets the parity of each
+// vertex's breadth-first distance from vertex 0 (two colours); any other graph
+// the Jones-Plassmann colouring. Levels run in batches with one read of their
+// flags per batch (a level past the last labels nothing); an odd cycle ends the
+// search early.
+int32_t colour_smoother(Ctx& c, int32_t n, const int32_t* rowptr, const int32_t* col, uint64_t seed,
+                        int32_t* colour) {
+    cudaStream_t s = c.stream;
+    if (n < 2) return colour_graph(c, n, rowptr, col, seed, colour);
+    constexpr int kMaxBatch = 64;
+    DBuf<int32_t> dist, q0, q1, cnt;
+    dist.alloc(c.mem, n);
+    q0.alloc(c.mem, n);
+    q1.alloc(c.mem, n);
+    cnt.alloc(c.mem, kMaxBatch + 3);   // [frontier sizes of the batch's levels..., odd, unreached]
+    fill_i32(s, n, -1, dist.p);
+    PC_CUDA(cudaMemsetAsync(dist.p, 0, sizeof(int32_t), s));   // vertex 0 at distance 0
+    PC_CUDA(cudaMemsetAsync(q0.p, 0, sizeof(int32_t), s));     // frontier of level 0: {0}
+    int32_t* odd = cnt.p + kMaxBatch + 1;
+    int32_t* unreached = cnt.p + kMaxBatch + 2;
+    PC_CUDA(cudaMemsetAsync(odd, 0, sizeof(int32_t) * 2, s));
+    const int one = 1;
+    int32_t h[kMaxBatch + 2];
+    bool bipartite = true;
+    int32_t* qa = q0.p;
+    int32_t* qb = q1.p;
+    for (int d = 0, batch = 8;; batch = std::min(batch * 2, kMaxBatch)) {
+        // cnt[0] = size of level d's frontier (carried over), cnt[1..batch] filled here
+        if (d == 0) PC_CUDA(cudaMemcpyAsync(cnt.p, &one, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        PC_CUDA(cudaMemsetAsync(cnt.p + 1, 0, sizeof(int32_t) * batch, s));
+        const int grid = kNumSMs * 4;
+        for (int k = 0; k < batch; ++k) {
+            k_bfs_level<<<grid, kBlock, 0, s>>>(rowptr, col, d + k, qa, cnt.p + k, qb, cnt.p + k + 1,
+                                                dist.p, odd);
+            ::pc::count_launches(1);
+            int32_t* t = qa; qa = qb; qb = t;
+        }
+        PC_LAUNCH("bfs_level");
+        d2h(c, h, cnt.p, batch + 1);
+        d2h(c, h + batch + 1, odd, 1);
+        d += batch;
+        if (h[batch + 1]) { bipartite = false; break; }
+        if (h[batch] == 0) break;
+        // the last level's frontier size starts the next batch
+        PC_CUDA(cudaMemcpyAsync(cnt.p, cnt.p + batch, sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        if (d > n + batch) fail(PCAMG_ERR_ROUND_CAP, "breadth-first levels exceeded n");
+    }
+    if (bipartite) {
+        k_parity_colour<<<gridc(n), kBlock, 0, s>>>(n, dist.p, colour, unreached); ::pc::count_launches(1);
+        PC_LAUNCH("parity_colour");
+        if (read_i32(c, unreached) == 0) return 2;
+    }
+    return colour_graph(c, n, rowptr, col, seed, colour);
 }
 
 // Rows grouped by colour (segments in colour order).

@@ -723,6 +723,9 @@ int grid_for(int64_t work, int block = 256) {
 
 // ---------------------------------------------------------------- host side
 struct Mpnn {
+    Mem mem;   // the legacy default stream: the network's calls are synchronous
+    DBuf<float> w_, m_, v_, g_, wq_;
+    DBuf<__nv_bfloat16> wl_;
     float *w = nullptr, *m = nullptr, *v = nullptr, *g = nullptr, *wq = nullptr;
     __nv_bfloat16* wl = nullptr;
     int64_t t = 0;
@@ -734,37 +737,20 @@ static void mpnn_refresh(Mpnn& M) {
 }
 
 Mpnn* mpnn_create(const float* h_params) {
-    Mpnn* M = new Mpnn();
-    const size_t b = sizeof(float) * kMpnnParams;
-    float** arr[] = {&M->w, &M->m, &M->v, &M->g, &M->wq};
-    for (float** p : arr) {
-        if (cudaMalloc(p, b) != cudaSuccess) {
-            cudaGetLastError();
-            mpnn_destroy(M);
-            fail(PCAMG_ERR_OOM, "mpnn allocation");
-        }
-    }
-    if (cudaMalloc(&M->wl, sizeof(__nv_bfloat16) * 4 * kH * 128) != cudaSuccess) {
-        cudaGetLastError();
-        mpnn_destroy(M);
-        fail(PCAMG_ERR_OOM, "mpnn allocation");
-    }
-    try {
-        PC_CUDA(cudaMemset(M->g, 0, b));
-        mpnn_set_params(*M, h_params);
-    } catch (...) {
-        mpnn_destroy(M);
-        throw;
-    }
-    return M;
+    std::unique_ptr<Mpnn> M(new Mpnn());
+    const size_t nb = kMpnnParams;
+    M->w_.alloc(M->mem, nb); M->m_.alloc(M->mem, nb); M->v_.alloc(M->mem, nb);
+    M->g_.alloc(M->mem, nb); M->wq_.alloc(M->mem, nb);
+    M->wl_.alloc(M->mem, (size_t)4 * kH * 128);
+    M->w = M->w_.p; M->m = M->m_.p; M->v = M->v_.p; M->g = M->g_.p; M->wq = M->wq_.p; M->wl = M->wl_.p;
+    PC_CUDA(cudaMemsetAsync(M->g, 0, sizeof(float) * nb, nullptr));
+    mpnn_set_params(*M, h_params);
+    return M.release();
 }
 
 void mpnn_destroy(Mpnn* M) {
     if (!M) return;
-    float* arr[] = {M->w, M->m, M->v, M->g, M->wq};
-    for (float* p : arr)
-        if (p) cudaFree(p);
-    if (M->wl) cudaFree(M->wl);
+    cudaDeviceSynchronize();   // the network's buffers may still be read by queued work
     delete M;
 }
 

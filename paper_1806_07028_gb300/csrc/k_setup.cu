@@ -8,6 +8,7 @@
 //    (Alg. 3), aggregate numbering, members, P values and path shortening.
 // Every integer result is deterministic and independent of thread scheduling.
 #include <algorithm>
+#include <climits>
 #include <cstring>
 
 #include "pcamg_internal.cuh"
@@ -94,6 +95,71 @@ struct WarpScratch {
     int mrow[kWarpMembers];
 };
 
+// Ascending bitonic sort of 32*R 64-bit keys held in registers: key i lives in
+// lane i % 32, register i / 32. Partners closer than 32 positions are exchanged
+// by warp shuffles, farther ones inside the thread.
+template <int R>
+__device__ __forceinline__ void sort_keys_regs(uint64_t (&key)[R], int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32 * R; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int rp = r ^ (j >> 5);
+                    if (rp > r) {
+                        const bool up = ((lane + 32 * r) & k) == 0;
+                        if ((key[r] > key[rp]) == up) { const uint64_t t = key[r]; key[r] = key[rp]; key[rp] = t; }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const uint64_t pk = __shfl_xor_sync(0xffffffffu, key[r], j);
+                    const bool up = ((lane + 32 * r) & k) == 0;
+                    const bool lower = (lane & j) == 0;
+                    // the lower position keeps the smaller key when up, the larger when down
+                    const bool take = (lower == up) ? (pk < key[r]) : (pk > key[r]);
+                    if (take) key[r] = pk;
+                }
+            }
+        }
+    }
+}
+
+// Stage the row's contributions (numbered e = 0..total-1 in their fixed order)
+// as keys (column << 32 | e) in registers and values in W.val[e], sort the
+// keys and store them in W.key in sorted order. Keys of skipped contributions
+// and of the padding are ~0 and sort last.
+template <int R, class Src>
+__device__ __forceinline__ void stage_sort_keys(int lane, int r, int nm, int total, const Src& src,
+                                                WarpScratch& W) {
+    uint64_t key[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int e = lane + 32 * q;
+        key[q] = ~0ull;
+        double v = 0.0;
+        if (e < total) {
+            int lo = 0, hi = nm - 1;          // member t with mpre[t] <= e < mpre[t+1]
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (W.mpre[mid] <= e) lo = mid; else hi = mid - 1;
+            }
+            const int j = W.mrow[lo];
+            const int k = src.in_beg(j) + (e - W.mpre[lo]);
+            uint32_t kk;
+            src.kv(r, j, k, kk, v);
+            if (kk != kSkip) key[q] = ((uint64_t)kk << 32) | (uint64_t)e;
+        }
+        W.val[e] = v;
+    }
+    sort_keys_regs<R>(key, lane);
+#pragma unroll
+    for (int q = 0; q < R; ++q) W.key[lane + 32 * q] = key[q];
+}
+
 // MODE 0: count the row's distinct columns (cnt) and flag long rows;
 // MODE 1: write the row at optr[r] (counts known);
 // MODE 2: both at once -- count, flag, and write the row at tptr[r] of a
@@ -148,38 +214,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_rowprod_warp(
             __syncwarp();
             int P = 32;
             while (P < total) P <<= 1;
-            for (int e = lane; e < P; e += 32) {
-                uint64_t key = ~0ull;
-                double v = 0.0;
-                if (e < total) {
-                    int lo = 0, hi = nm - 1;          // member t with mpre[t] <= e < mpre[t+1]
-                    while (lo < hi) {
-                        int mid = (lo + hi + 1) >> 1;
-                        if (W.mpre[mid] <= e) lo = mid; else hi = mid - 1;
-                    }
-                    const int j = W.mrow[lo];
-                    const int k = src.in_beg(j) + (e - W.mpre[lo]);
-                    uint32_t kk;
-                    src.kv(r, j, k, kk, v);
-                    if (kk != kSkip) key = ((uint64_t)kk << 32) | (uint64_t)e;
-                }
-                W.key[e] = key;
-                W.val[e] = v;
-            }
+            if (P == 32) stage_sort_keys<1>(lane, r, nm, total, src, W);
+            else if (P == 64) stage_sort_keys<2>(lane, r, nm, total, src, W);
+            else if (P == 128) stage_sort_keys<4>(lane, r, nm, total, src, W);
+            else stage_sort_keys<8>(lane, r, nm, total, src, W);
             __syncwarp();
-            for (int kk = 2; kk <= P; kk <<= 1) {
-                for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-                    for (int i = lane; i < P; i += 32) {
-                        int ixj = i ^ jj;
-                        if (ixj > i) {
-                            uint64_t a = W.key[i], b = W.key[ixj];
-                            bool up = (i & kk) == 0;
-                            if ((a > b) == up) { W.key[i] = b; W.key[ixj] = a; }
-                        }
-                    }
-                    __syncwarp();
-                }
-            }
             // runs of equal columns
             int carry = 0;
             const int64_t o = (MODE == 1) ? (int64_t)optr[r] : (MODE == 2 ? tptr[r] : 0);
@@ -478,54 +517,96 @@ __global__ void k_order_rows_classify(int n, const int* __restrict__ ptr, unsign
     }
 }
 
-// Warp per row for rows of up to kOrderWarpCap entries (class 1):
-// the row's weights and columns staged in shared memory, its entry indices
-// sorted by a warp bitonic sort in the order (w descending, column ascending).
-struct OrderScratch {
-    double w[kOrderWarpCap];
-    int c[kOrderWarpCap];
-    uint16_t idx[kOrderWarpCap];
-};
+// Warp per row for rows of up to kOrderWarpCap entries (class 1), sorted in
+// the order (w descending, column ascending) by a bitonic network held in
+// registers: element i of the padded row lives in lane i % 32, register i / 32;
+// partners closer than 32 positions are exchanged by warp shuffles, farther
+// ones inside the thread. Weights are positive, so their IEEE bit patterns
+// compare as unsigned integers exactly as the doubles do; the sort compares
+// bits on the integer pipe (GB300's FP64 pipe issues a comparison at a small
+// fraction of the integer rate). Padding entries (bits 0, column INT_MAX) sort
+// last. Columns are distinct within a row, so the order is strict and the
+// result unique.
+__device__ __forceinline__ bool order_before(uint64_t w1, int c1, uint64_t w2, int c2) {
+    return (w1 > w2) || (w1 == w2 && c1 < c2);
+}
+
+template <int R>
+__device__ __forceinline__ void order_row_regs(int lane, int b, int len, const int* __restrict__ col,
+                                               const double* __restrict__ w, int* __restrict__ scol,
+                                               double* __restrict__ sw) {
+    uint64_t kw[R];
+    int kc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = lane + 32 * r;
+        kw[r] = (i < len) ? (uint64_t)__double_as_longlong(w[b + i]) : 0ull;
+        kc[r] = (i < len) ? col[b + i] : INT_MAX;
+    }
+#pragma unroll
+    for (int k = 2; k <= 32 * R; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {   // partner in register r ^ (j / 32) of the same lane
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int rp = r ^ (j >> 5);
+                    if (rp > r) {
+                        const int i = lane + 32 * r;
+                        const bool up = (i & k) == 0;
+                        // ascending in "before" order when up: position r first
+                        const bool swap = up ? order_before(kw[rp], kc[rp], kw[r], kc[r])
+                                             : order_before(kw[r], kc[r], kw[rp], kc[rp]);
+                        if (swap) {
+                            const uint64_t tw = kw[r]; kw[r] = kw[rp]; kw[rp] = tw;
+                            const int tc = kc[r]; kc[r] = kc[rp]; kc[rp] = tc;
+                        }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const uint64_t pw = __shfl_xor_sync(0xffffffffu, kw[r], j);
+                    const int pc = __shfl_xor_sync(0xffffffffu, kc[r], j);
+                    const int i = lane + 32 * r;
+                    const bool up = (i & k) == 0;
+                    const bool lower = (lane & j) == 0;
+                    const bool pb = order_before(pw, pc, kw[r], kc[r]);   // partner first?
+                    const bool mb = order_before(kw[r], kc[r], pw, pc);   // me first?
+                    // the lower position keeps the earlier element when up, the later when down
+                    const bool take = (lower == up) ? pb : mb;
+                    if (take) { kw[r] = pw; kc[r] = pc; }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = lane + 32 * r;
+        if (i < len) { scol[b + i] = kc[r]; sw[b + i] = __longlong_as_double((long long)kw[r]); }
+    }
+}
 
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     k_order_rows_warp(int n, const unsigned char* __restrict__ cls, const int* __restrict__ ptr,
                       const int* __restrict__ col, const double* __restrict__ w, int* __restrict__ scol,
                       double* __restrict__ sw) {
-    __shared__ OrderScratch os_all[kWarpsPerBlock];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    OrderScratch& S = os_all[wib];
     for (int64_t i = (int64_t)blockIdx.x * kWarpsPerBlock + wib; i < n; i += (int64_t)gridDim.x * kWarpsPerBlock) {
         if (cls[i] != 1) continue;
         const int u = (int)i;
         const int b = ptr[u], len = ptr[u + 1] - b;
-        int P = 32;
-        while (P < len) P <<= 1;
-        for (int e = lane; e < P; e += 32) {
-            if (e < len) { S.w[e] = w[b + e]; S.c[e] = col[b + e]; }
-            S.idx[e] = (e < len) ? (uint16_t)e : (uint16_t)0xffff;
+        if (len <= 1) {
+            if (len == 1 && lane == 0) { scol[b] = col[b]; sw[b] = w[b]; }
+        } else if (len <= 32) {
+            order_row_regs<1>(lane, b, len, col, w, scol, sw);
+        } else if (len <= 64) {
+            order_row_regs<2>(lane, b, len, col, w, scol, sw);
+        } else if (len <= 128) {
+            order_row_regs<4>(lane, b, len, col, w, scol, sw);
+        } else {
+            order_row_regs<8>(lane, b, len, col, w, scol, sw);
         }
-        __syncwarp();
-        for (int k = 2; k <= P; k <<= 1) {
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int e = lane; e < P; e += 32) {
-                    const int ex = e ^ j;
-                    if (ex > e) {
-                        const uint16_t a = S.idx[e], c2 = S.idx[ex];
-                        bool a_gt;   // a comes after c2; sentinels last
-                        if (a == 0xffff) a_gt = (c2 != 0xffff);
-                        else if (c2 == 0xffff) a_gt = false;
-                        else a_gt = (S.w[a] < S.w[c2]) || (S.w[a] == S.w[c2] && S.c[a] > S.c[c2]);
-                        if (a_gt == ((e & k) == 0)) { S.idx[e] = c2; S.idx[ex] = a; }
-                    }
-                }
-                __syncwarp();
-            }
-        }
-        for (int e = lane; e < len; e += 32) {
-            scol[b + e] = S.c[S.idx[e]];
-            sw[b + e] = S.w[S.idx[e]];
-        }
-        __syncwarp();
     }
 }
 
@@ -578,12 +659,35 @@ __global__ void k_cover_init(int n, const int* __restrict__ ptr, int* deg, int* 
     }
 }
 
+// The rounds run over a list of live vertices: endpoints (degree < 2) that
+// still had a proposal when the list was last compacted. Degrees only grow and
+// eligibility is only lost, so a vertex that dropped out never proposes again,
+// and its proposal slot stays -1.
+__global__ void k_cover_iota(int n, int* __restrict__ list, int* __restrict__ cnt) {
+    FOR_EACH(u, n) list[u] = (int)u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *cnt = n;
+}
+
+__global__ void k_cover_compact(const int* __restrict__ list, const int* __restrict__ cnt,
+                                const int* __restrict__ deg, const int* __restrict__ bv,
+                                int* __restrict__ out, int* __restrict__ ocnt) {
+    const int m = *cnt;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        const int u = list[i];
+        if (deg[u] < 2 && bv[u] >= 0) out[atomicAdd(ocnt, 1)] = u;
+    }
+}
+
+#define FOR_LIST(u, list, cnt) \
+    for (int i_ = blockIdx.x * blockDim.x + threadIdx.x, m_ = *(cnt); i_ < m_; i_ += gridDim.x * blockDim.x) \
+        for (int u = (list)[i_], once_ = 1; once_; once_ = 0)
+
 // 1. each endpoint advances to its best eligible edge (ineligible edges stay so)
-__global__ void k_cover_best(int n, const int* __restrict__ ptr, const int* __restrict__ scol,
+__global__ void k_cover_best(const int* __restrict__ list, const int* __restrict__ cnt,
+                             const int* __restrict__ ptr, const int* __restrict__ scol,
                              const int* __restrict__ deg, const int* __restrict__ oe,
                              int* __restrict__ cptr, int* __restrict__ bv) {
-    FOR_EACH(u64, n) {
-        int u = (int)u64;
+    FOR_LIST(u, list, cnt) {
         if (deg[u] >= 2) continue;
         int p = cptr[u], e = ptr[u + 1], o = oe[u];
         while (p < e) {
@@ -595,16 +699,16 @@ __global__ void k_cover_best(int n, const int* __restrict__ ptr, const int* __re
     }
 }
 
-// 2. each path keeps the better proposal of its two endpoints
-__global__ void k_cover_choose(int n, const int* __restrict__ deg, const int* __restrict__ oe,
+// 2. each path keeps the better proposal of its two endpoints (both live
+// endpoints of a path compute the same choice; either may be the one listed)
+__global__ void k_cover_choose(const int* __restrict__ list, const int* __restrict__ cnt,
+                               const int* __restrict__ deg, const int* __restrict__ oe,
                                const int* __restrict__ cptr, const int* __restrict__ bv,
                                const double* __restrict__ sw, int* __restrict__ cf,
                                int* __restrict__ ct) {
-    FOR_EACH(u64, n) {
-        int u = (int)u64;
+    FOR_LIST(u, list, cnt) {
         if (deg[u] >= 2) continue;
         int o = oe[u];
-        if (u > o) continue;
         int x = -1, y = -1;
         double wx = 0.0;
         if (bv[u] >= 0) { x = u; y = bv[u]; wx = sw[cptr[u]]; }
@@ -617,12 +721,12 @@ __global__ void k_cover_choose(int n, const int* __restrict__ deg, const int* __
 }
 
 // 3. an edge chosen by both of its paths joins them
-__global__ void k_cover_accept(int n, int* __restrict__ deg, int* __restrict__ oe,
+__global__ void k_cover_accept(const int* __restrict__ list, const int* __restrict__ cnt,
+                               int* __restrict__ deg, int* __restrict__ oe,
                                const int* __restrict__ cf, const int* __restrict__ ct,
                                int* __restrict__ nbr0, int* __restrict__ nbr1,
                                int* __restrict__ counter) {
-    FOR_EACH(u64, n) {
-        int u = (int)u64;
+    FOR_LIST(u, list, cnt) {
         if (cf[u] != u) continue;
         int y = ct[u];
         if (y < 0 || y < u) continue;
@@ -741,11 +845,12 @@ __global__ void k_best(int n, const int* __restrict__ ptr, const int* __restrict
                        int* __restrict__ lab, int* __restrict__ size) {
     FOR_EACH(u64, n) {
         int u = (int)u64;
+        // positive weights: their bit patterns order as the values do
         int bb = -1;
-        double bw = 0.0;
+        uint64_t bw = 0;
         for (int k = ptr[u]; k < ptr[u + 1]; ++k) {
-            double x = w[k];
-            int c = col[k];
+            const uint64_t x = (uint64_t)__double_as_longlong(w[k]);
+            const int c = col[k];
             if (bb < 0 || x > bw || (x == bw && c < bb)) { bb = c; bw = x; }
         }
         best[u] = bb;
@@ -847,6 +952,76 @@ __global__ void k_isfirst(int n, const int* __restrict__ lab, const int* __restr
 __global__ void k_agg_ids(int n, const int* __restrict__ lab, const int* __restrict__ minmem,
                           const int* __restrict__ cidat, int* __restrict__ agg) {
     FOR_EACH(u, n) agg[u] = cidat[minmem[lab[u]]];
+}
+
+// ---------------------------------------------------------------- MWM (Section 2.1)
+// Heaviest-first matching on the weighted adjacency of A_l (edge {u,v} weighs
+// -a_uv > 0) as locally-dominant rounds: every free vertex points at its best
+// free neighbour in the order of Alg. 1 (weight descending, then the smaller
+// end, then the larger end); two vertices pointing at each other are matched.
+// Each round matches the best free edge overall, and a matched edge is one the
+// sequential heaviest-first pass over sorted edges also takes, so the rounds
+// give that matching. Weights compare through their bit patterns (positive).
+__device__ __forceinline__ bool mwm_before(uint64_t w1, int a1, int b1, uint64_t w2, int a2, int b2) {
+    if (w1 != w2) return w1 > w2;
+    const int lo1 = min(a1, b1), lo2 = min(a2, b2);
+    if (lo1 != lo2) return lo1 < lo2;
+    return max(a1, b1) < max(a2, b2);
+}
+
+__device__ __forceinline__ uint64_t neg_bits(double a) { return (uint64_t)__double_as_longlong(-a); }
+
+__global__ void k_mwm_best(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                           const double* __restrict__ val, const int* __restrict__ mate,
+                           int* __restrict__ best) {
+    FOR_EACH(v64, n) {
+        const int v = (int)v64;
+        int b = -1;
+        uint64_t bw = 0;
+        if (mate[v] < 0) {
+            for (int k = rowptr[v]; k < rowptr[v + 1]; ++k) {
+                const int u = col[k];
+                if (u == v || mate[u] >= 0) continue;
+                const uint64_t w = neg_bits(val[k]);
+                if (b < 0 || mwm_before(w, v, u, bw, v, b)) { b = u; bw = w; }
+            }
+        }
+        best[v] = b;
+    }
+}
+
+__global__ void k_mwm_accept(int n, const int* __restrict__ best, int* __restrict__ mate,
+                             int* __restrict__ counter) {
+    FOR_EACH(v64, n) {
+        const int v = (int)v64;
+        const int u = best[v];
+        if (u >= 0 && best[u] == v) {
+            mate[v] = u;
+            if (v < u) atomicAdd(counter, 1);
+        }
+    }
+}
+
+// pair label = the pair's smaller vertex; a free vertex (all its neighbours are
+// matched once the rounds end) takes the label of its heaviest neighbour's pair;
+// a vertex without neighbours labels itself
+__global__ void k_mwm_label(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                            const double* __restrict__ val, const int* __restrict__ mate,
+                            int* __restrict__ lab) {
+    FOR_EACH(v64, n) {
+        const int v = (int)v64;
+        const int m = mate[v];
+        if (m >= 0) { lab[v] = min(v, m); continue; }
+        int b = -1;
+        uint64_t bw = 0;
+        for (int k = rowptr[v]; k < rowptr[v + 1]; ++k) {
+            const int u = col[k];
+            if (u == v) continue;
+            const uint64_t w = neg_bits(val[k]);
+            if (b < 0 || mwm_before(w, v, u, bw, v, b)) { b = u; bw = w; }
+        }
+        lab[v] = (b < 0) ? v : min(b, mate[b]);
+    }
 }
 
 // coarse cover: matched pair k of a path is joined to pairs k-1 and k+1
@@ -1066,13 +1241,23 @@ int32_t path_cover(Ctx& c, int32_t n, const Reweighted& t, int32_t* nbr0, int32_
     fill_i32(s, n, -1, cf.p);
     int32_t rounds = 0, batch = 4;
     std::vector<int32_t> hc(kBatchMax);
+    DBuf<int32_t> la, lb, lcnt;
+    la.alloc(c.mem, n); lb.alloc(c.mem, n); lcnt.alloc(c.mem, 2);
+    k_cover_iota<<<grid1(n), kBlock, 0, s>>>(n, la.p, lcnt.p); ::pc::count_launches(1);
+    int32_t *list = la.p, *spare = lb.p, *cnt = lcnt.p, *scnt = lcnt.p + 1;
+    const int lgrid = kNumSMs * 8;
     for (;;) {
         PC_CUDA(cudaMemsetAsync(counters.p, 0, sizeof(int32_t) * batch, s));
         for (int r = 0; r < batch; ++r) {
-            k_cover_best<<<grid1(n), kBlock, 0, s>>>(n, t.ptr.p, scol.p, deg.p, oe.p, cptr.p, bv.p); ::pc::count_launches(1);
-            k_cover_choose<<<grid1(n), kBlock, 0, s>>>(n, deg.p, oe.p, cptr.p, bv.p, sw.p, cf.p, ct.p); ::pc::count_launches(1);
-            k_cover_accept<<<grid1(n), kBlock, 0, s>>>(n, deg.p, oe.p, cf.p, ct.p, nbr0, nbr1, counters.p + r); ::pc::count_launches(1);
+            k_cover_best<<<lgrid, kBlock, 0, s>>>(list, cnt, t.ptr.p, scol.p, deg.p, oe.p, cptr.p, bv.p); ::pc::count_launches(1);
+            k_cover_choose<<<lgrid, kBlock, 0, s>>>(list, cnt, deg.p, oe.p, cptr.p, bv.p, sw.p, cf.p, ct.p); ::pc::count_launches(1);
+            k_cover_accept<<<lgrid, kBlock, 0, s>>>(list, cnt, deg.p, oe.p, cf.p, ct.p, nbr0, nbr1, counters.p + r); ::pc::count_launches(1);
         }
+        // drop the vertices that can no longer propose
+        PC_CUDA(cudaMemsetAsync(scnt, 0, sizeof(int32_t), s));
+        k_cover_compact<<<lgrid, kBlock, 0, s>>>(list, cnt, deg.p, bv.p, spare, scnt); ::pc::count_launches(1);
+        std::swap(list, spare);
+        std::swap(cnt, scnt);
         PC_LAUNCH("cover rounds");
         d2h(c, hc.data(), counters.p, batch);
         bool done = false;
@@ -1081,9 +1266,13 @@ int32_t path_cover(Ctx& c, int32_t n, const Reweighted& t, int32_t* nbr0, int32_
             if (hc[r] == 0) { done = true; break; }
         }
         if (done) break;
-        if (rounds > n + 1) fail(PCAMG_ERR_ROUND_CAP, "path cover rounds exceeded n");
+        const int64_t cap = c.p.max_cover_rounds > 0 ? (int64_t)c.p.max_cover_rounds : (int64_t)n + 1;
+        if (rounds > cap) fail(PCAMG_ERR_ROUND_CAP, "path cover rounds exceeded their cap");
         batch = std::min(batch * 2, kBatchMax);
     }
+    // rounds that added edges (the last round found none)
+    if (c.p.max_cover_rounds > 0 && rounds - 1 > c.p.max_cover_rounds)
+        fail(PCAMG_ERR_ROUND_CAP, "path cover rounds exceeded their cap");
     k_canonical<<<grid1(n), kBlock, 0, s>>>(n, nbr0, nbr1); ::pc::count_launches(1);
     PC_LAUNCH("canonical");
     sync(c);
@@ -1126,26 +1315,46 @@ int32_t aggregate_level(Ctx& c, int32_t n, const int32_t* nbr0, const int32_t* n
                                        sprev.p, snext.p, ishead.p); ::pc::count_launches(1);
     k_best<<<grid1(n), kBlock, 0, s>>>(n, t.ptr.p, t.col.p, t.w.p, best.p, lab.p, size.p); ::pc::count_launches(1);
     PC_LAUNCH("pair/best");
-    int32_t rounds = 0;
+    // Leftover rounds are launched in batches and their leftover counts read
+    // once per batch: a round that finds no leftover vertex changes nothing
+    // (every vertex is classified 0, so no pair, joiner or list entry arises),
+    // so rounds past the last productive one are harmless no-ops. The rounds
+    // counted are those that found leftovers, as in a round-by-round loop.
+    int32_t rounds = 0, batch = 2;
+    constexpr int kLeftBatchMax = 16;
+    DBuf<int32_t> nl;
+    nl.alloc(c.mem, kLeftBatchMax);
+    int32_t hn[kLeftBatchMax];
     for (;;) {
-        PC_CUDA(cudaMemsetAsync(gcnt.p, 0, sizeof(int32_t) * n, s));
-        PC_CUDA(cudaMemsetAsync(nleft.p, 0, sizeof(int32_t), s));
-        k_left_classify<<<grid1(n), kBlock, 0, s>>>(n, lab.p, best.p, st.p, jg.p, gcnt.p, nleft.p); ::pc::count_launches(1);
-        PC_LAUNCH("left_classify");
-        if (read_i32(c, nleft.p) == 0) break;
-        if (rounds >= c.p.round_cap) {
+        const int B = std::min(batch, c.p.round_cap - rounds);
+        if (B <= 0) {   // cap reached: the paper's sequential loop finishes if needed
+            PC_CUDA(cudaMemsetAsync(gcnt.p, 0, sizeof(int32_t) * n, s));
+            PC_CUDA(cudaMemsetAsync(nleft.p, 0, sizeof(int32_t), s));
+            k_left_classify<<<grid1(n), kBlock, 0, s>>>(n, lab.p, best.p, st.p, jg.p, gcnt.p, nleft.p); ::pc::count_launches(1);
+            PC_LAUNCH("left_classify");
+            if (read_i32(c, nleft.p) == 0) break;
             k_left_tail<<<1, 1, 0, s>>>(n, best.p, lab.p, size.p); ::pc::count_launches(1);
             PC_LAUNCH("left_tail");
             ++rounds;
             break;
         }
-        k_left_case1<<<grid1(n), kBlock, 0, s>>>(n, st.p, best.p, lab.p, size.p); ::pc::count_launches(1);
-        scan_i32_device(c, gcnt.p, goff.p, n);
-        PC_CUDA(cudaMemsetAsync(gfill.p, 0, sizeof(int32_t) * n, s));
-        k_left_fill<<<grid1(n), kBlock, 0, s>>>(n, st.p, jg.p, goff.p, gfill.p, list.p); ::pc::count_launches(1);
-        k_left_join<<<grid1(n), kBlock, 0, s>>>(n, goff.p, list.p, best.p, lab.p, size.p); ::pc::count_launches(1);
-        PC_LAUNCH("left_round");
-        ++rounds;
+        PC_CUDA(cudaMemsetAsync(nl.p, 0, sizeof(int32_t) * B, s));
+        for (int r = 0; r < B; ++r) {
+            PC_CUDA(cudaMemsetAsync(gcnt.p, 0, sizeof(int32_t) * n, s));
+            k_left_classify<<<grid1(n), kBlock, 0, s>>>(n, lab.p, best.p, st.p, jg.p, gcnt.p, nl.p + r); ::pc::count_launches(1);
+            k_left_case1<<<grid1(n), kBlock, 0, s>>>(n, st.p, best.p, lab.p, size.p); ::pc::count_launches(1);
+            scan_i32_device(c, gcnt.p, goff.p, n);
+            PC_CUDA(cudaMemsetAsync(gfill.p, 0, sizeof(int32_t) * n, s));
+            k_left_fill<<<grid1(n), kBlock, 0, s>>>(n, st.p, jg.p, goff.p, gfill.p, list.p); ::pc::count_launches(1);
+            k_left_join<<<grid1(n), kBlock, 0, s>>>(n, goff.p, list.p, best.p, lab.p, size.p); ::pc::count_launches(1);
+            PC_LAUNCH("left_round");
+        }
+        d2h(c, hn, nl.p, B);
+        int j = 0;
+        while (j < B && hn[j] > 0) ++j;
+        rounds += j;
+        if (j < B) break;
+        batch = std::min(batch * 2, kLeftBatchMax);
     }
     // numbering by smallest member
     DBuf<int32_t> minmem, flag, cidat;
@@ -1164,6 +1373,48 @@ int32_t aggregate_level(Ctx& c, int32_t n, const int32_t* nbr0, const int32_t* n
     k_shorten<<<grid1(n), kBlock, 0, s>>>(n, ishead.p, sprev.p, snext.p, minmem.p, cidat.p, cnbr0.p, cnbr1.p); ::pc::count_launches(1);
     PC_LAUNCH("agg/shorten");
     sync(c);
+    if (rounds_out) *rounds_out = rounds;
+    return nc;
+}
+
+int32_t mwm_aggregate_level(Ctx& c, int32_t n, const int32_t* rowptr, const int32_t* col,
+                            const double* val, DBuf<int32_t>& agg, int32_t* rounds_out) {
+    cudaStream_t s = c.stream;
+    DBuf<int32_t> mate, best, counters, lab, minmem, flag, cidat;
+    mate.alloc(c.mem, n); best.alloc(c.mem, n); lab.alloc(c.mem, n);
+    const int kBatchMax = 64;
+    counters.alloc(c.mem, kBatchMax);
+    fill_i32(s, n, -1, mate.p);
+    int32_t rounds = 0, batch = 4;
+    int32_t hc[kBatchMax];
+    // rounds in batches; a round after the last productive one matches nothing
+    for (;;) {
+        PC_CUDA(cudaMemsetAsync(counters.p, 0, sizeof(int32_t) * batch, s));
+        for (int r = 0; r < batch; ++r) {
+            k_mwm_best<<<grid1(n), kBlock, 0, s>>>(n, rowptr, col, val, mate.p, best.p); ::pc::count_launches(1);
+            k_mwm_accept<<<grid1(n), kBlock, 0, s>>>(n, best.p, mate.p, counters.p + r); ::pc::count_launches(1);
+        }
+        PC_LAUNCH("mwm rounds");
+        d2h(c, hc, counters.p, batch);
+        bool done = false;
+        for (int r = 0; r < batch; ++r) {
+            ++rounds;
+            if (hc[r] == 0) { done = true; break; }
+        }
+        if (done) break;
+        if (rounds > n + 1) fail(PCAMG_ERR_ROUND_CAP, "matching rounds exceeded n");
+        batch = std::min(batch * 2, kBatchMax);
+    }
+    k_mwm_label<<<grid1(n), kBlock, 0, s>>>(n, rowptr, col, val, mate.p, lab.p); ::pc::count_launches(1);
+    minmem.alloc(c.mem, n); flag.alloc(c.mem, n); cidat.alloc(c.mem, (size_t)n + 1);
+    fill_i32(s, n, 0x7fffffff, minmem.p);
+    k_minmem<<<grid1(n), kBlock, 0, s>>>(n, lab.p, minmem.p); ::pc::count_launches(1);
+    k_isfirst<<<grid1(n), kBlock, 0, s>>>(n, lab.p, minmem.p, flag.p); ::pc::count_launches(1);
+    PC_LAUNCH("mwm numbering");
+    const int32_t nc = (int32_t)scan_i32(c, flag.p, cidat.p, n);
+    agg.alloc(c.mem, n);
+    k_agg_ids<<<grid1(n), kBlock, 0, s>>>(n, lab.p, minmem.p, cidat.p, agg.p); ::pc::count_launches(1);
+    PC_LAUNCH("mwm ids");
     if (rounds_out) *rounds_out = rounds;
     return nc;
 }

@@ -517,6 +517,7 @@ void residual64(cudaStream_t s, const Csr& A, const double* x, const double* b, 
 }
 
 int residual_partials(int32_t n) { return (n + kStreamRows - 1) / kStreamRows; }
+int residual_norm_blocks(int32_t n) { return (residual_partials(n) + kNormTiles - 1) / kNormTiles; }
 
 template <class T>
 void jacobi_update(cudaStream_t s, int32_t n, const T* r, const T* d, T* x) {

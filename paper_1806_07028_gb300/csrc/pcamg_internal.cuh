@@ -68,10 +68,16 @@ constexpr int kBlock = 256;
 constexpr int kNumSMs = 152;
 
 // ---------------------------------------------------------------- memory
-// Device allocations are stream ordered (cudaMallocAsync on the handle stream).
+// Device allocations are stream ordered on `stream`: from the caller's
+// callbacks (pcamg_set_allocator) current when this Mem was made, else from the
+// library's per-device pool (freed memory kept cached).
 struct Mem {
     cudaStream_t stream = nullptr;
     size_t live = 0, peak = 0;
+    pcamg_alloc_fn afn = nullptr;
+    pcamg_free_fn ffn = nullptr;
+    void* actx = nullptr;
+    Mem();
     void* alloc(size_t bytes);
     void release(void* p, size_t bytes);
 };
@@ -200,6 +206,10 @@ struct Hier {
     // CUDA graphs of the correction cycle (index: gamma-1)
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t graph_kernels[2] = {0, 0};
+    // event-record nodes around the finest-level residual of the V-cycle graph
+    // (params.profile bit 1), retargeted to fresh events before each replay
+    cudaGraphNode_t prof_node[2] = {nullptr, nullptr};
+    cudaGraph_t graph_tmpl = nullptr;   // the V-cycle graph those nodes belong to
     ~Hier();
 };
 
@@ -246,7 +256,16 @@ struct Ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int64_t prof_launches = 0;
     double prof_ms = 0.0;
+    // timing of the V-cycle's finest-level residual (params.profile bit 1):
+    // event pairs recorded around it, resolved when the solve ends
+    std::vector<cudaEvent_t> cyc_ev;
+    size_t cyc_used = 0;
+    cudaEvent_t cyc_tmpl[2] = {nullptr, nullptr};   // events named in the captured nodes
+    int64_t cyc_launches = 0;
+    double cyc_ms = 0.0;
     int64_t ncycles = 0;
+    int64_t nwcycles = 0;
+    bool fixed_scale = false;   // FP32 cycle scale set once for the running solve
     double t_alg2 = 0.0, t_alg4 = 0.0;
     const double* last_e = nullptr;          // normalised error of the newest hierarchy
     std::unique_ptr<Reweighted> mpnn_cand;   // A^2 candidate pattern for the network's loss
@@ -292,6 +311,7 @@ template <class T>
 void permute_rows(Ctx& c, int32_t n, const int32_t* rows, const int32_t* rowptr, const int32_t* col,
                   const double* val, DBuf<int32_t>& pptr, DBuf<int32_t>& pcol, DBuf<T>& pval);
 int residual_partials(int32_t n);
+int residual_norm_blocks(int32_t n);   // partials the ||r||^2 launch of residual64 writes
 bool use_stream(int32_t rows, int lpr);  // streaming kernels pay off for this launch
 template <class T>
 void jacobi_update(cudaStream_t s, int32_t n, const T* r, const T* d, T* x);   // x += r / d
@@ -316,6 +336,9 @@ int32_t path_cover(Ctx& c, int32_t n, const Reweighted& t, int32_t* nbr0, int32_
 int32_t aggregate_level(Ctx& c, int32_t n, const int32_t* nbr0, const int32_t* nbr1,
                         const Reweighted& t, DBuf<int32_t>& agg, DBuf<int32_t>& cnbr0,
                         DBuf<int32_t>& cnbr1, int32_t* rounds);
+// MWM aggregation of one level (Section 2.1); returns the number of aggregates
+int32_t mwm_aggregate_level(Ctx& c, int32_t n, const int32_t* rowptr, const int32_t* col,
+                            const double* val, DBuf<int32_t>& agg, int32_t* rounds_out);
 void build_members(Ctx& c, int32_t n, int32_t nc, const int32_t* agg, DBuf<int32_t>& agg_ptr,
                    DBuf<int32_t>& agg_mem);
 void build_pval(Ctx& c, int32_t n, int32_t nc, const int32_t* agg_ptr, const int32_t* agg_mem,
@@ -325,6 +348,8 @@ int64_t galerkin(Ctx& c, int32_t n, const int32_t* rowptr, const int32_t* col, c
                  int32_t nc, const int32_t* agg, const int32_t* agg_ptr, const int32_t* agg_mem,
                  const double* pval, bool drop_diag, DBuf<int32_t>& optr, DBuf<int32_t>& ocol,
                  DBuf<double>& oval);
+int32_t colour_smoother(Ctx& c, int32_t n, const int32_t* rowptr, const int32_t* col, uint64_t seed,
+                        int32_t* colour);
 int32_t colour_graph(Ctx& c, int32_t n, const int32_t* rowptr, const int32_t* col, uint64_t seed,
                      int32_t* colour);
 void colour_lists(Ctx& c, int32_t n, const int32_t* colour, int32_t ncolour,
@@ -334,6 +359,7 @@ void coarse_factor(Ctx& c, int32_t m, const int32_t* rowptr, const int32_t* col,
 
 // hierarchy + driver (hierarchy.cu, driver.cu)
 Hier* build_hierarchy(Ctx& c, const double* e_normalised);
+Hier* build_hierarchy_mwm(Ctx& c);   // MWM_setup: boolean UA-AMG hierarchy (Section 2.1)
 void cycle(Ctx& c, Hier& h, int gamma, const double* r, double* out);
 void smooth_error(Ctx& c, const double* r, double* e);
 void start_vector(Ctx& c, double* e);
@@ -348,6 +374,9 @@ const double* norm_slot(Ctx& c);     // ||e - mean|| of the last normalise_orth
 constexpr int kMpnnHidden = 64;
 constexpr int kMpnnLayers = 4;
 constexpr int kMpnnParams = 64 * 3 + 64 + 4 * (64 * 128 + 64) + 64 + 1;   // 33345
+void set_allocator(pcamg_alloc_fn a, pcamg_free_fn f, void* ctx);
+void trim_memory();
+
 struct Mpnn;
 Mpnn* mpnn_create(const float* h_params);
 void mpnn_destroy(Mpnn* m);

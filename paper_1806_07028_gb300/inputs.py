@@ -278,6 +278,8 @@ def workload(name, seed=None):
         return grid3d(256, 256, 256, "jumps", block=16, xscale=1.0, seed=5000 + s)
     if name == "C5-small":
         return grid3d(32, 32, 32, "jumps", block=16, xscale=1.0, seed=5000 + s)
+    if name == "C5-mid":
+        return grid3d(128, 128, 128, "jumps", block=16, xscale=1.0, seed=5000 + s)
     if name.startswith("grid2d-unit-"):
         k = int(name.rsplit("-", 1)[1])
         return grid2d(k, k, "unit")
@@ -287,7 +289,25 @@ def workload(name, seed=None):
 
 
 WORKLOADS = ["C1", "C2", "C2-small", "C2-mid", "C3", "C3-small", "C4", "C4-small",
-             "C5", "C5-small"]
+             "C5", "C5-small", "C5-mid"]
+
+# One-line statement of each workload's recipe and size, for reports.
+DESCRIPTIONS = {
+    "C1": "2D 4-neighbour grid Laplacian 64x64 (n = 4,096), edge weights 10^U(-3,0)",
+    "C2": "3D 7-point grid Laplacian 128^3 (n = 2,097,152), 8^3 checkerboard weights 1 / 1e-4, "
+          "x-edges x100",
+    "C2-small": "3D 7-point grid 32^3, C2's checkerboard weights and anisotropy",
+    "C2-mid": "3D 7-point grid 64^3, C2's checkerboard weights and anisotropy",
+    "C3": "Chung-Lu scale-free graph, exponent 2.1, n = 1,000,000, mean degree 10, largest component, "
+          "weights U(0,1]",
+    "C3-small": "Chung-Lu scale-free graph, exponent 2.1, n = 20,000, largest component",
+    "C4": "random geometric graph in the unit square, n = 2,000,000, mean degree 12, largest component, "
+          "weights 1/distance",
+    "C4-small": "random geometric graph, n = 20,000, mean degree 12",
+    "C5": "3D 7-point grid Laplacian 256^3 (n = 16,777,216), jump coefficients 10^U(-6,0) on 16^3 blocks",
+    "C5-small": "3D 7-point grid 32^3, C5's block jump coefficients",
+    "C5-mid": "3D 7-point grid 128^3 (n = 2,097,152), C5's block jump coefficients on 16^3 blocks",
+}
 
 
 def mpnn_init_params(seed=0):

@@ -18,7 +18,7 @@ _lib = None
 OK, ERR_INVALID, ERR_NOT_LAPLACIAN, ERR_OOM, ERR_CUDA, ERR_ROUND_CAP, ERR_SINGULAR, \
     ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_COARSE_TOO_BIG, ERR_UNSUPPORTED = range(11)
 FP64, FP32_IR = 0, 1
-START_RANDOM, START_USER, START_LEARNED = 0, 1, 2
+START_RANDOM, START_USER, START_LEARNED, START_MWM = 0, 1, 2, 3
 P1_E_SCALED, P1_BOOLEAN = 0, 1
 
 # every entry point of include/pcamg.h
@@ -31,7 +31,8 @@ EXPORTS = [
     "pcamg_kernel_launches", "pcamg_residual_noalloc", "pcamg_last_smooth_error",
     "pcamg_mpnn_num_params", "pcamg_mpnn_create", "pcamg_mpnn_destroy", "pcamg_mpnn_get_params",
     "pcamg_mpnn_set_params", "pcamg_mpnn_get_grad", "pcamg_mpnn_forward", "pcamg_mpnn_loss_grad",
-    "pcamg_mpnn_adam_step", "pcamg_mpnn_save", "pcamg_mpnn_load",
+    "pcamg_mpnn_adam_step", "pcamg_mpnn_save", "pcamg_mpnn_load", "pcamg_set_allocator",
+    "pcamg_trim_memory",
 ]
 
 
@@ -54,7 +55,7 @@ class Params(C.Structure):
                 ("start", C.c_int32), ("dense_max", C.c_int32), ("use_graphs", C.c_int32),
                 ("keep_setup", C.c_int32), ("profile", C.c_int32), ("tail_rows", C.c_int32),
                 ("l1jac_rows", C.c_int32), ("tail_dense", C.c_int32), ("max_resetups", C.c_int32),
-                ("mpnn", C.c_void_p), ("update_mode", C.c_int32)]
+                ("mpnn", C.c_void_p), ("update_mode", C.c_int32), ("max_cover_rounds", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -64,7 +65,9 @@ class Stats(C.Structure):
                 ("t_alg2_ms", C.c_double), ("t_alg4_ms", C.c_double), ("cycles", C.c_int64),
                 ("res_hist", C.POINTER(C.c_double)), ("res_hist_cap", C.c_int32),
                 ("res_hist_len", C.c_int32), ("prof_launches", C.c_int64),
-                ("prof_ms", C.c_double), ("prof_bytes", C.c_double)]
+                ("prof_ms", C.c_double), ("prof_bytes", C.c_double),
+                ("rebuilt", C.POINTER(C.c_int32)), ("wcycles", C.c_int64),
+                ("cyc_launches", C.c_int64), ("cyc_ms", C.c_double), ("cyc_bytes", C.c_double)]
 
 
 def lib():
@@ -113,6 +116,8 @@ def lib():
                 "pcamg_mpnn_adam_step": ([vp, C.c_float], i32),
                 "pcamg_mpnn_save": ([vp, C.c_char_p], i32),
                 "pcamg_mpnn_load": ([P(vp), C.c_char_p], i32),
+                "pcamg_set_allocator": ([vp, vp, vp], i32),
+                "pcamg_trim_memory": ([], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)

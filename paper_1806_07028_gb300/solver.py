@@ -37,6 +37,58 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+# ---- device memory through PyTorch -------------------------------------------
+# The library allocates every device buffer through callbacks when they are
+# installed (pcamg_set_allocator); these route them to PyTorch's caching
+# allocator, so that the library and torch share one pool of device memory.
+_ALLOC_T = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_FREE_T = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+_allocator = {"kind": None, "fns": None, "calls": [0, 0]}
+
+
+def _torch_alloc(nbytes, stream, ctx):
+    torch = _torch()
+    _allocator["calls"][0] += 1
+    try:
+        return torch.cuda.caching_allocator_alloc(int(nbytes), device=torch.cuda.current_device(),
+                                                  stream=int(stream or 0))
+    except Exception:
+        return None
+
+
+def _torch_free(ptr, stream, ctx):
+    _allocator["calls"][1] += 1
+    _torch().cuda.caching_allocator_delete(int(ptr))
+
+
+def use_allocator(kind="torch"):
+    """Where the library's device memory comes from from now on: "torch" (the
+    PyTorch caching allocator, the default of this binding) or "library" (the
+    library's own cached pool). Handles and networks made earlier keep theirs."""
+    if kind == _allocator["kind"]:
+        return
+    if kind == "torch":
+        fns = (_ALLOC_T(_torch_alloc), _FREE_T(_torch_free))
+        N.check(N.lib().pcamg_set_allocator(C.cast(fns[0], C.c_void_p), C.cast(fns[1], C.c_void_p), None))
+        _allocator["fns"] = fns   # the callbacks must outlive every handle made with them
+    elif kind == "library":
+        N.check(N.lib().pcamg_set_allocator(None, None, None))
+    else:
+        raise ValueError(kind)
+    _allocator["kind"] = kind
+
+
+def allocator_calls():
+    """(allocations, frees) made through the torch callbacks so far."""
+    return tuple(_allocator["calls"])
+
+
+def _ensure_allocator():
+    if _allocator["kind"] is None:
+        import os
+        use_allocator(os.environ.get("PCAMG_ALLOCATOR", "torch"))
+
+
 def default_params(**kw) -> N.Params:
     p = N.Params()
     N.check(N.lib().pcamg_default_params(C.byref(p)))
@@ -47,10 +99,12 @@ def default_params(**kw) -> N.Params:
     return p
 
 
-def _stats_dict(st, hist):
-    d = {f: getattr(st, f) for f, _ in N.Stats._fields_ if f != "res_hist"}
+def _stats_dict(st, hist, rebuilt=None):
+    d = {f: getattr(st, f) for f, _ in N.Stats._fields_ if f not in ("res_hist", "rebuilt")}
     d["status"] = N.status_name(st.status)
     d["res_hist"] = hist[: st.res_hist_len].copy() if hist is not None else None
+    if rebuilt is not None:
+        d["rebuilt_after"] = [int(k) for k in np.nonzero(rebuilt[: max(st.res_hist_len, 1)])[0]]
     return d
 
 
@@ -60,6 +114,7 @@ class Solver:
     def __init__(self, graph, params: N.Params | None = None, e0=None, device="cuda:0",
                  stream=None, mpnn=None):
         torch = _torch()
+        _ensure_allocator()
         self.device = torch.device(device)
         self.params = params if params is not None else default_params()
         if e0 is not None:
@@ -116,13 +171,15 @@ class Solver:
             xt = (torch.zeros(self.n, dtype=torch.float64, device=self.device) if x0 is None
                   else _dev(x0, torch.float64, self.device).clone())
             hist = np.zeros(hist_cap)
+            reb = np.zeros(hist_cap, np.int32)
             st = N.Stats()
             st.res_hist = hist.ctypes.data_as(C.POINTER(C.c_double))
+            st.rebuilt = reb.ctypes.data_as(C.POINTER(C.c_int32))
             st.res_hist_cap = hist_cap
             status = N.lib().pcamg_solve(self._h, _ptr(bt), _ptr(xt), C.byref(st))
             if raise_on_error and status not in (N.OK, N.ERR_NOT_CONVERGED):
                 N.check(status, self._h)
-            return xt, _stats_dict(st, hist)
+            return xt, _stats_dict(st, hist, reb)
 
     def solve_zero_rhs(self, x0, hist_cap=4096):
         """Alg. 6 (b = 0) from initial guess x0."""
@@ -130,13 +187,15 @@ class Solver:
         with torch.cuda.device(self.device):
             xt = _dev(x0, torch.float64, self.device).clone()
             hist = np.zeros(hist_cap)
+            reb = np.zeros(hist_cap, np.int32)
             st = N.Stats()
             st.res_hist = hist.ctypes.data_as(C.POINTER(C.c_double))
+            st.rebuilt = reb.ctypes.data_as(C.POINTER(C.c_int32))
             st.res_hist_cap = hist_cap
             status = N.lib().pcamg_solve_zero_rhs(self._h, _ptr(xt), C.byref(st))
             if status not in (N.OK, N.ERR_NOT_CONVERGED):
                 N.check(status, self._h)
-            return xt, _stats_dict(st, hist)
+            return xt, _stats_dict(st, hist, reb)
 
     def cycle(self, r, hist=-1, gamma=1):
         """One V- (gamma=1) or W-cycle (gamma=2) correction of hierarchy `hist`."""
@@ -225,6 +284,7 @@ class Solver:
 def residual(rowptr, col, val, x, b, want_norm=True, stream=None):
     """r = b - A x and ||r||^2 on the device (torch tensors in, tensors out)."""
     torch = _torch()
+    _ensure_allocator()
     n = rowptr.numel() - 1
     r = torch.empty(n, dtype=torch.float64, device=x.device)
     nrm = torch.zeros(1, dtype=torch.float64, device=x.device) if want_norm else None
@@ -261,6 +321,7 @@ def colour(rowptr, col, seed, stream=None):
 
 def solve_host(graph, b, x0=None, params=None):
     """End-to-end call on host numpy buffers (copies happen inside the library)."""
+    _ensure_allocator()
     p = params if params is not None else default_params()
     rp = np.ascontiguousarray(graph.rowptr, np.int32)
     ci = np.ascontiguousarray(graph.col, np.int32)
@@ -290,6 +351,7 @@ class Mpnn:
         w = np.ascontiguousarray(params, dtype=np.float32)
         if w.size != self.num_params():
             raise ValueError(f"expected {self.num_params()} parameters, got {w.size}")
+        _ensure_allocator()
         h = C.c_void_p()
         N.check(N.lib().pcamg_mpnn_create(C.byref(h), w.ctypes.data_as(C.c_void_p)))
         self._h = h
@@ -308,6 +370,7 @@ class Mpnn:
 
     @classmethod
     def load(cls, path):
+        _ensure_allocator()
         h = C.c_void_p()
         N.check(N.lib().pcamg_mpnn_load(C.byref(h), str(path).encode()))
         return cls(_handle=h)

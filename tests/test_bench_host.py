@@ -1,6 +1,6 @@
 """Host-side helpers of the benchmark, on the CPU: the reduction of an ncu
-launch list to per-kernel shares, kernel-name shortening, the whole-job value
-and the traffic figure read from the committed residual profile."""
+launch list to per-kernel shares, kernel-name shortening, the whole-job value,
+and the oracle's recorded counts and sampled solution."""
 import os
 import sys
 
@@ -53,10 +53,19 @@ def test_job_value_counts_every_rank():
     assert bench.job_value(1000, 4, 500.0) == 8000.0
 
 
-def test_traffic_figure_is_read_from_the_residual_profile():
-    t = bench._traffic_per_launch()
-    text = open(os.path.join(ROOT, "profiles", "residual64_C2.md")).read()
-    line = [ln for ln in text.splitlines() if ln.startswith("traffic_bytes_per_launch:")]
-    assert len(line) == 1
-    v = line[0].split(":", 1)[1].strip()
-    assert (t is None) if v in ("", "null") else (t == float(v))
+def test_oracle_counts_and_sample_error(tmp_path, monkeypatch):
+    import json
+
+    import numpy as np
+    rec = {"C5-mid": {"resetups": 6, "cycles": 300, "wcycles": 14, "iters": 20, "n": 10,
+                      "seconds": 1.0, "host": "h", "sample_idx": [1, 3], "sample_x": [2.0, -1.0]}}
+    p = tmp_path / "solves.json"
+    p.write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "GOLDEN_SOLVES", str(p))
+    c = bench.oracle_counts("C5")          # stands in through the same recipe
+    assert c["from"] == "C5-mid" and c["builds"] == 7 and c["cycles"] == 300 and c["wcycles"] == 14
+    assert bench.oracle_counts("C2") is None
+    x = np.zeros(10); x[1], x[3] = 2.0, -1.0 + 1e-3
+    e = bench.error_vs_recorded_oracle("C5-mid", x)
+    assert abs(e["value"] - 1e-3 / np.sqrt(5.0)) < 1e-12
+    assert bench.error_vs_recorded_oracle("C5", x) is None

@@ -103,3 +103,25 @@ def test_l1_jacobi_sweep(mk):
     assert np.allclose(x1, x0 + (b - A @ x0) / d, rtol=1e-13, atol=1e-13 * np.abs(x1).max())
     e0, e1 = xs - x0, xs - x1
     assert e1 @ (A @ e1) < e0 @ (A @ e0)
+
+
+def test_smoother_colouring_rule():
+    # connected bipartite graphs (grids): two colours, the parity of the
+    # breadth-first distance from vertex 0, so every edge joins both colours
+    import scipy.sparse.csgraph as csg
+    for g in (I.grid2d(9, 7), I.grid3d(5, 4, 3, "unit"), I.workload("C2-small")):
+        col, nc, levels = O.colour_smoother(g)
+        A = g.to_scipy().tocoo()
+        off = A.row != A.col
+        d = csg.shortest_path(g.to_scipy().astype(bool).astype(float), unweighted=True, indices=0)
+        assert nc == 2 and col[0] == 0
+        assert np.array_equal(col, d.astype(np.int64) % 2)
+        assert np.all(col[A.row[off]] != col[A.col[off]])
+        assert levels == int(d.max()) + 1
+    # an odd cycle (rings with k = 4 have triangles) or a disconnected graph:
+    # the Jones-Plassmann colouring
+    for g in (I.ring(40, 4), I.workload("C4-small"),
+              I.laplacian_from_edges(6, [0, 1, 3, 4], [1, 2, 4, 5], [1.0] * 4)):
+        col, nc, _ = O.colour_smoother(g, seed=77)
+        ref, ncr, _ = O.colour(g, seed=77)
+        assert nc == ncr and np.array_equal(col, ref)

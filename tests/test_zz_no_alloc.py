@@ -1,7 +1,7 @@
 """The allocation-free residual entry point, for callers that cannot allocate
-device memory (graph capture in progress, allocation-free hot loops, memory
-fully owned by a pool). It must give the same r and ||r||^2 as the ordinary
-entry point, including on a second call that reuses its fixed scratch array.
+device memory (allocation-free hot loops, memory fully owned by a pool). It
+must give the same r and ||r||^2 as the ordinary entry point and as the CPU
+oracle, including on a second call that reuses its fixed scratch array.
 
 This file is collected last on purpose, and also runs alone in a fresh process.
 """
@@ -10,6 +10,7 @@ import ctypes as C
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_1806_07028_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -58,13 +59,16 @@ def test_noalloc_residual_matches_allocating_entry_point(lib, name):
         tol = 32 * EPS * (rowabs @ np.abs(x.cpu().numpy()) + np.abs(b.cpu().numpy()))
         assert np.all(np.abs(r.cpu().numpy() - r_ref.cpu().numpy()) <= tol)
         assert abs(nr.item() - n_ref.item()) <= 1e-12 * n_ref.item()
+        ro = O.residual(g, x.cpu().numpy(), b.cpu().numpy())     # the oracle's r = b - A x
+        assert np.all(np.abs(r.cpu().numpy() - ro) <= tol)
+        assert abs(nr.item() - ro @ ro) <= 1e-12 * (ro @ ro)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(lib):
     N = lib
     one = C.c_void_p(1)   # never dereferenced: the size check comes first
-    st = N.lib().pcamg_residual_noalloc(16_777_217, one, one, one, one, one, one, one, None)
+    st = N.lib().pcamg_residual_noalloc(67_108_865, one, one, one, one, one, one, one, None)
     assert st == N.ERR_INVALID          # null d_norm2 is rejected first
-    st = N.lib().pcamg_residual_noalloc(16_777_217, one, one, one, one, one, one, one, one)
+    st = N.lib().pcamg_residual_noalloc(67_108_865, one, one, one, one, one, one, one, one)
     assert st == N.ERR_INVALID
-    assert b"16,777,216" in N.lib().pcamg_last_error(None)
+    assert b"67,108,864" in N.lib().pcamg_last_error(None)
