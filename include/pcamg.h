@@ -77,6 +77,12 @@ enum { PCAMG_P1_E_SCALED = 0, PCAMG_P1_BOOLEAN = 1 };       /* level-1 prolongat
  * ADD_CORRECTION: the raw PCG solution of A e = r is added to the iterate and
  * the residual recomputed before the next step. */
 enum { PCAMG_UPD_REBUILD_ONLY = 0, PCAMG_UPD_ADD_CORRECTION = 1 };
+/* Outer iteration of pcamg_solve. STATIONARY (default): Alg. 5 as the paper
+ * gives it, x <- x + V r. FCG: flexible conjugate gradients (Polak-Ribiere)
+ * preconditioned by the current hierarchy's V-cycle, x <- x + alpha p; the
+ * re-setup rule is Alg. 5's, and a re-setup restarts the search direction.
+ * The paper uses plain V-cycles; FCG is this library's addition. */
+enum { PCAMG_OUTER_STATIONARY = 0, PCAMG_OUTER_FCG = 1 };
 
 /* Parameters. Defaults (pcamg_default_params) follow Section 4 of the paper:
  * threshold 0.4 (Alg. 5(2)), numW 2, iterW 7, iterV 4, Gauss-Seidel smoothing,
@@ -131,6 +137,7 @@ typedef struct {
     int32_t max_cover_rounds; /* cap on the path-cover rounds of one build (0: n + 1, which
                               always suffices: every round adds at least one edge); a build
                               that needs more returns PCAMG_ERR_ROUND_CAP */
+    int32_t outer;         /* PCAMG_OUTER_*: stationary Alg. 5 (default) or flexible CG */
 } pcamg_params;
 
 typedef struct {

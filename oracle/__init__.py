@@ -28,6 +28,7 @@ P1_E_SCALED, P1_BOOLEAN = 0, 1
 LEFT_ROUNDS, LEFT_SEQUENTIAL = 0, 1
 COVER_LD, COVER_GREEDY = 0, 1
 UPD_REBUILD_ONLY, UPD_ADD_CORRECTION = 0, 1
+OUTER_STATIONARY, OUTER_FCG = 0, 1
 ERR = {0: "OK", 1: "INVALID", 2: "NOT_LAPLACIAN", 3: "OOM", 5: "ROUND_CAP", 6: "SINGULAR",
        7: "NOT_CONVERGED", 8: "DIVERGED", 9: "COARSE_TOO_BIG"}
 
@@ -56,7 +57,8 @@ class Params(C.Structure):
                 ("seed", C.c_uint64), ("n_min", C.c_int32), ("max_levels", C.c_int32),
                 ("round_cap", C.c_int32), ("p1_mode", C.c_int32), ("leftover_mode", C.c_int32),
                 ("cover_mode", C.c_int32), ("dense_max", C.c_int32), ("l1jac_rows", C.c_int32),
-                ("update_mode", C.c_int32), ("keep_setup", C.c_int32), ("init_mwm", C.c_int32)]
+                ("update_mode", C.c_int32), ("keep_setup", C.c_int32), ("init_mwm", C.c_int32),
+                ("outer", C.c_int32)]
 
 
 class Stats(C.Structure):

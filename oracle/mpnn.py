@@ -222,6 +222,41 @@ def backward(g, u, theta, ehat, cand=None):
     return L, flatten(grads)
 
 
+def backward_magnitude(g, u, theta, ehat, cand=None):
+    """Per parameter, the sum of the absolute values of the terms whose sum the
+    backward pass forms for it: every product and sum of the backward pass of
+    `backward` taken over absolute values (|dy|, |W|, |X|, |gelu'|, ...). A
+    rounding of relative size u in any operand of those terms moves the
+    gradient entry by at most about u times this magnitude, whatever
+    cancellation the signed sum has."""
+    if cand is None:
+        cand = candidate_pattern(g)
+    yhat, C = forward(g, u, theta, keep=True)
+    P, W, Dinv = C["P"], C["W"], C["Dinv"]
+    _, gy = loss_and_grad(cand, yhat, ehat)
+    gz = (np.abs(gy) + np.abs(yhat) * (np.abs(yhat) @ np.abs(gy))) / C["nrm"]
+    dy = gz + gz.mean()
+    grads = {}
+    hL = np.abs(C["hs"][-1])
+    grads["w_out"] = hL.T @ dy
+    grads["b_out"] = np.array([dy.sum()])
+    dh = np.outer(dy, np.abs(P["w_out"]))
+    WT = W.T.tocsr()
+    for l in reversed(range(LAYERS)):
+        z, h, m = C["zs"][l], C["hs"][l], C["ms"][l]
+        dz = (dh + dh.mean(axis=0)) * np.abs(gelu_grad(z))
+        X = np.abs(np.concatenate([h, m], axis=1))
+        grads[f"W{l}"] = dz.T @ X
+        grads[f"b{l}"] = dz.sum(axis=0)
+        dX = dz @ np.abs(P[f"W{l}"])
+        dm = dX[:, HIDDEN:]
+        dh = dX[:, :HIDDEN] + WT @ (dm * Dinv[:, None])
+    dz_in = (dh + dh.mean(axis=0)) * np.abs(gelu_grad(C["z_in"]))
+    grads["W_in"] = dz_in.T @ np.abs(C["F"])
+    grads["b_in"] = dz_in.sum(axis=0)
+    return flatten(grads)
+
+
 def loss(g, u, theta, ehat, cand=None):
     if cand is None:
         cand = candidate_pattern(g)

@@ -38,6 +38,11 @@ enum { ORC_COVER_LD = 0, ORC_COVER_GREEDY = 1 };            /* path cover (Alg. 
  * printed update lands on an iterate that is never used again), or the raw
  * PCG solution is added to the new iterate and the residual recomputed. */
 enum { ORC_UPD_REBUILD_ONLY = 0, ORC_UPD_ADD_CORRECTION = 1 };
+/* Outer iteration of Alg. 5: the paper's stationary V-cycle iteration, or
+ * flexible conjugate gradients preconditioned by the current hierarchy's
+ * V-cycle (not in the paper; the re-setup rule is the same, and a re-setup
+ * restarts the search direction). */
+enum { ORC_OUTER_STATIONARY = 0, ORC_OUTER_FCG = 1 };
 
 typedef struct {
     double tol;           /* relative residual target ||b-Ax||/||b|| */
@@ -64,6 +69,7 @@ typedef struct {
                              export); 0 frees it and saves memory on large graphs */
     int32_t init_mwm;     /* 1: the initial hierarchy of Alg. 5 / Alg. 6 is MWM_setup(A)
                              (the paper's); 0: Alg. 4 from the start vector */
+    int32_t outer;        /* ORC_OUTER_*: the outer iteration of Alg. 5 */
 } orc_params;
 
 typedef struct {

@@ -206,10 +206,43 @@ int32_t orc_solve(int32_t n, const int32_t* rowptr, const int32_t* col, const do
     int32_t wcnt = 0;
     if (res_hist && cap > 0) res_hist[0] = res / bn;
     if (rebuilt) for (int32_t i = 0; i < cap; ++i) rebuilt[i] = 0;
+    /* flexible CG state (outer = FCG): direction, A times it, previous r and z */
+    double *fp = NULL, *fq = NULL, *frold = NULL, *fzold = NULL, *fzero = NULL;
+    int32_t restart = 1;
+    if (p->outer == ORC_OUTER_FCG) {
+        fp = (double*)orc_xmalloc(sizeof(double) * (size_t)n);
+        fq = (double*)orc_xmalloc(sizeof(double) * (size_t)n);
+        frold = (double*)orc_xmalloc(sizeof(double) * (size_t)n);
+        fzold = (double*)orc_xmalloc(sizeof(double) * (size_t)n);
+        fzero = (double*)calloc((size_t)n, sizeof(double));
+        if (!fp || !fq || !frold || !fzold || !fzero) { status = ORC_ERR_OOM; goto fcg_out; }
+    }
     while (k < p->max_iter && res / bn > p->tol) {
-        /* x_{k+1} = V-cycle on the current hierarchy, then orthogonal to 1 */
+        /* z = V-cycle on the current hierarchy */
         orc_vcycle(hist[re - 1], r, c);
-        for (int32_t i = 0; i < n; ++i) x[i] += c[i];
+        if (p->outer == ORC_OUTER_FCG) {
+            /* flexible CG: p = z + beta p (Polak-Ribiere beta; restart after a
+             * re-setup), x += alpha p, alpha = r.z / p.Ap */
+            double rz = vdot(n, r, c);
+            if (restart) {
+                memcpy(fp, c, sizeof(double) * (size_t)n);
+                restart = 0;
+            } else {
+                double num = 0.0, den = vdot(n, fzold, frold);
+                for (int32_t i = 0; i < n; ++i) num += c[i] * (r[i] - frold[i]);
+                double beta = (den != 0.0) ? num / den : 0.0;
+                for (int32_t i = 0; i < n; ++i) fp[i] = c[i] + beta * fp[i];
+            }
+            orc_residual(n, rowptr, col, val, fp, fzero, fq);   /* fq = -A p */
+            double pq = -vdot(n, fp, fq);
+            double alpha = (pq > 0.0 && rz > 0.0) ? rz / pq : 0.0;
+            for (int32_t i = 0; i < n; ++i) x[i] += alpha * fp[i];
+            memcpy(frold, r, sizeof(double) * (size_t)n);
+            memcpy(fzold, c, sizeof(double) * (size_t)n);
+        } else {
+            /* x_{k+1} = x_k + V-cycle correction */
+            for (int32_t i = 0; i < n; ++i) x[i] += c[i];
+        }
         remove_mean(n, x);
         orc_residual(n, rowptr, col, val, x, b, r);
         double nres = vnorm(n, r);
@@ -232,6 +265,7 @@ int32_t orc_solve(int32_t n, const int32_t* rowptr, const int32_t* col, const do
             oc_sum += orc_hier_oc(hist[re]);
             ++re;
             if (rebuilt && k < cap) rebuilt[k] = 1;
+            restart = 1;
             if (p->update_mode == ORC_UPD_ADD_CORRECTION) {
                 for (int32_t i = 0; i < n; ++i) x[i] += e[i];
                 remove_mean(n, x);
@@ -245,6 +279,8 @@ int32_t orc_solve(int32_t n, const int32_t* rowptr, const int32_t* col, const do
     st.iters = k;
     st.rel_res = res / bn;
     if (status == ORC_OK && !(st.rel_res <= p->tol)) status = ORC_ERR_NOT_CONVERGED;
+fcg_out:
+    free(fp); free(fq); free(frold); free(fzold); free(fzero);
 out:
     st.resetups = re > 0 ? re - 1 : 0;
     st.levels = re > 0 && hist[re - 1] ? hist[re - 1]->nlev : 0;

@@ -98,7 +98,7 @@ void check_params(const pcamg_params& p) {
         p.dense_max > 4096 || p.tail_rows < 0 || p.l1jac_rows < 0 || p.tail_dense < 0 ||
         p.tail_dense > 3 ||
         (p.update_mode != PCAMG_UPD_REBUILD_ONLY && p.update_mode != PCAMG_UPD_ADD_CORRECTION) ||
-        p.max_cover_rounds < 0)
+        p.max_cover_rounds < 0 || (p.outer != PCAMG_OUTER_STATIONARY && p.outer != PCAMG_OUTER_FCG))
         fail(PCAMG_ERR_INVALID, "invalid parameters");
 }
 
@@ -138,6 +138,11 @@ void alloc_work(Ctx& c) {
     DBuf<double>* vs[] = {&c.w_r, &c.w_c, &c.w_e, &c.w_t1, &c.w_t2, &c.w_z, &c.w_p,
                           &c.w_q, &c.w_rold, &c.w_eh, &c.w_ein, &c.w_cin};
     for (auto* v : vs) v->alloc(c.mem, c.n);
+    if (c.p.precision == PCAMG_FP32_IR) {
+        c.l0_x32.alloc(c.mem, c.n); c.l0_b32.alloc(c.mem, c.n); c.l0_r32.alloc(c.mem, c.n);
+    } else {
+        c.l0_x64.alloc(c.mem, c.n); c.l0_b64.alloc(c.mem, c.n); c.l0_r64.alloc(c.mem, c.n);
+    }
     c.npartials = std::max<int64_t>(4096, residual_partials(c.n));
     c.red.alloc(c.mem, c.npartials + 64);
     PC_CUDA(cudaMemsetAsync(c.red.p, 0, sizeof(double) * (c.npartials + 64), c.stream));

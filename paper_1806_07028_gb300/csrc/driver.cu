@@ -161,7 +161,8 @@ double read_f64(Ctx& c, const double* dev) {
 }
 
 // scalar slots after the reduction partials
-enum Slot { S_T0 = 0, S_T1, S_T2, S_NORM2, S_RZ, S_PQ, S_ALPHA, S_NUM, S_BETA, S_SCALE, S_INV, S_SUM, S_NSLOTS };
+enum Slot { S_T0 = 0, S_T1, S_T2, S_NORM2, S_RZ, S_PQ, S_ALPHA, S_NUM, S_BETA, S_SCALE, S_INV, S_SUM,
+            S_FRZ, S_FPQ, S_FALPHA, S_FNUM, S_FDEN, S_FBETA, S_NSLOTS };
 static double* slot(Ctx& c, int k) { return c.red.p + c.npartials + k; }
 static double* partials(Ctx& c) { return c.red.p; }
 
@@ -184,16 +185,16 @@ template <class T>
 struct LV;
 template <>
 struct LV<double> {
-    static double* x(Level& L) { return L.x64.p; }
-    static double* b(Level& L) { return L.b64.p; }
-    static double* r(Level& L) { return L.r64.p; }
+    static double* x(Level& L) { return L.x64v; }
+    static double* b(Level& L) { return L.b64v; }
+    static double* r(Level& L) { return L.r64v; }
     static const double* pv(Level& L) { return L.pval.p; }
 };
 template <>
 struct LV<float> {
-    static float* x(Level& L) { return L.x32.p; }
-    static float* b(Level& L) { return L.b32.p; }
-    static float* r(Level& L) { return L.r32.p; }
+    static float* x(Level& L) { return L.x32v; }
+    static float* b(Level& L) { return L.b32v; }
+    static float* r(Level& L) { return L.r32v; }
     static const float* pv(Level& L) { return L.pval32.p; }
 };
 
@@ -202,7 +203,7 @@ static void smooth(Ctx& c, Level& L, const T* b, T* x, bool forward) {
     if (L.jac) {   // l1-Jacobi: x += (b - A x) / d
         T* r;
         const T* d;
-        if constexpr (sizeof(T) == 8) { r = L.r64.p; d = L.dl1_64.p; } else { r = L.r32.p; d = L.dl1_32.p; }
+        if constexpr (sizeof(T) == 8) { r = L.r64v; d = L.dl1_64.p; } else { r = L.r32v; d = L.dl1_32.p; }
         if constexpr (sizeof(T) == 8) residual64(c.stream, L.A, x, b, r, nullptr, nullptr);
         else residual32(c.stream, L.A, x, b, r);
         jacobi_update<T>(c.stream, L.n, r, d, x);
@@ -245,7 +246,7 @@ static void prof_mark(Ctx& c, Hier& h, int k) {
         size_t nd = 0;
         PC_CUDA(cudaStreamGetCaptureInfo(c.stream, &cs, nullptr, nullptr, &deps, nullptr, &nd));
         if (nd != 1) fail(PCAMG_ERR_CUDA, "profiling node not found in the captured cycle");
-        h.prof_node[k] = deps[0];
+        h.prof_node[c.cur_kind][k] = deps[0];
         pdl_after_copy();   // the next kernel follows a non-kernel node
     } else if (cudaEvent_t e = pool_event(c)) {
         PC_CUDA(cudaEventRecord(e, c.stream));
@@ -316,12 +317,17 @@ static void cycle_level(Ctx& c, Hier& h, int32_t l, int gamma, bool fresh, bool 
     for (int32_t k = 0; k < c.p.nu_post; ++k) smooth<T>(c, L, b, x, false);
 }
 
+// kind 0: V-cycle from zero, 1: W-cycle from zero, 2: V-cycle continuing from
+// the finest level's current x (x <- x + B (b - A x): a cycle from a start
+// vector is the zero-start cycle applied to the start's residual)
 template <class T>
-static void cycle_body(Ctx& c, Hier& h, int gamma) {
+static void cycle_body(Ctx& c, Hier& h, int kind) {
     Level& L0 = h.lev[0];
-    PC_CUDA(cudaMemsetAsync(LV<T>::x(L0), 0, sizeof(T) * L0.n, c.stream));
-    pdl_after_copy();
-    cycle_level<T>(c, h, 0, gamma, false, true);
+    if (kind != 2) {
+        PC_CUDA(cudaMemsetAsync(LV<T>::x(L0), 0, sizeof(T) * L0.n, c.stream));
+        pdl_after_copy();
+    }
+    cycle_level<T>(c, h, 0, kind == 1 ? 2 : 1, false, kind != 2);
 }
 
 // Forms the tail levels' dense operator for this cycle kind once per
@@ -349,21 +355,23 @@ static void ensure_tail_op(Ctx& c, Hier& h, int gamma) {
                      c.p.nu_pre, c.p.nu_post, h.Xinv.p, reinterpret_cast<T*>(h.tail_op[k].p), h.tail_ld, nsm);
 }
 
-static void run_body(Ctx& c, Hier& h, int gamma) {
+static void run_body(Ctx& c, Hier& h, int kind) {
+    const int gamma = kind == 1 ? 2 : 1;
     bool f32 = c.p.precision == PCAMG_FP32_IR;
     if (f32) ensure_tail_op<float>(c, h, gamma); else ensure_tail_op<double>(c, h, gamma);
+    c.cur_kind = kind;
     if (!c.p.use_graphs) {
-        if (f32) cycle_body<float>(c, h, gamma); else cycle_body<double>(c, h, gamma);
+        if (f32) cycle_body<float>(c, h, kind); else cycle_body<double>(c, h, kind);
         return;
     }
-    cudaGraphExec_t& ge = h.graph[gamma - 1];
+    cudaGraphExec_t& ge = h.graph[kind];
     if (!ge) {
         cudaGraph_t g = nullptr;
-        h.graph_kernels[gamma - 1] = 0;
+        h.graph_kernels[kind] = 0;
         PC_CUDA(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal));
-        t_capture_acc = &h.graph_kernels[gamma - 1];
+        t_capture_acc = &h.graph_kernels[kind];
         try {
-            if (f32) cycle_body<float>(c, h, gamma); else cycle_body<double>(c, h, gamma);
+            if (f32) cycle_body<float>(c, h, kind); else cycle_body<double>(c, h, kind);
         } catch (...) {
             t_capture_acc = nullptr;
             cudaStreamEndCapture(c.stream, &g);
@@ -374,17 +382,17 @@ static void run_body(Ctx& c, Hier& h, int gamma) {
         PC_CUDA(cudaStreamEndCapture(c.stream, &g));
         cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
         // a graph holding profiling nodes is kept: its nodes name the ones to retarget
-        if (gamma == 1 && h.prof_node[0]) h.graph_tmpl = g; else cudaGraphDestroy(g);
+        if (h.prof_node[kind][0]) h.graph_tmpl[kind] = g; else cudaGraphDestroy(g);
         PC_CUDA(e);
     }
-    if (gamma == 1 && h.prof_node[0] && (c.p.profile & 2)) {
+    if (h.prof_node[kind][0] && (c.p.profile & 2)) {
         for (int k = 0; k < 2; ++k) {
             cudaEvent_t e = pool_event(c);
-            PC_CUDA(cudaGraphExecEventRecordNodeSetEvent(ge, h.prof_node[k], e ? e : c.cyc_tmpl[k]));
+            PC_CUDA(cudaGraphExecEventRecordNodeSetEvent(ge, h.prof_node[kind][k], e ? e : c.cyc_tmpl[k]));
         }
     }
     PC_CUDA(cudaGraphLaunch(ge, c.stream));
-    count_launches(h.graph_kernels[gamma - 1]);
+    count_launches(h.graph_kernels[kind]);
 }
 
 // out = B r, the correction of one cycle from a zero start
@@ -403,14 +411,59 @@ void cycle(Ctx& c, Hier& h, int gamma, const double* r, double* out) {
             scalar_ops(s, SOP_SQRT, slot(c, 0), S_T0, 0, S_SCALE);
             scalar_ops(s, SOP_INV, slot(c, 0), S_SCALE, 0, S_INV);
         }
-        cast_scaled_f32(s, c.n, r, slot(c, S_INV), L0.b32.p);
-        run_body(c, h, gamma);
-        set_scaled_f32(s, c.n, L0.x32.p, slot(c, S_SCALE), out);
+        cast_scaled_f32(s, c.n, r, slot(c, S_INV), L0.b32v);
+        run_body(c, h, gamma - 1);
+        set_scaled_f32(s, c.n, L0.x32v, slot(c, S_SCALE), out);
     } else {
-        copy(s, c.n, r, L0.b64.p);
-        run_body(c, h, gamma);
-        copy(s, c.n, L0.x64.p, out);
+        copy(s, c.n, r, L0.b64v);
+        run_body(c, h, gamma - 1);
+        copy(s, c.n, L0.x64v, out);
     }
+}
+
+// z = the symmetric composite of V-cycles over hist[0..re-1] applied to r
+// (Alg. 2): z starts at 0 and each factor continues from it,
+// z <- z + B_j (r - A z) for j = 1..re, re..1. The finest-level cycle vectors
+// are shared by all hierarchies, so z stays in them between the factors.
+static void composite(Ctx& c, const double* r, double* z) {
+    cudaStream_t s = c.stream;
+    const int32_t re = (int32_t)c.hist.size();
+    const bool f32 = c.p.precision == PCAMG_FP32_IR;
+    bool single = false;   // a one-level hierarchy is a bare coarse solve, x = X b
+    for (Hier* h : c.hist) single = single || h->nlev < 2;
+    if (single) {          // then each factor runs explicitly on r - A z
+        fill(s, c.n, 0.0, z);
+        Csr A;
+        A.n = c.n; A.nnz = c.nnz; A.rowptr = c.rowptr.p; A.col = c.col.p; A.val = c.val.p;
+        A.lpr = lanes_per_row(c.n, c.nnz);
+        for (int32_t k = 0; k < 2 * re; ++k) {
+            const int32_t j = (k < re) ? k : 2 * re - 1 - k;
+            residual64(s, A, z, r, c.w_t1.p, nullptr, nullptr);
+            cycle(c, *c.hist[j], 1, c.w_t1.p, c.w_t2.p);
+            axpy(s, c.n, 1.0, c.w_t2.p, z);
+        }
+        return;
+    }
+    Level& L0 = c.hist[0]->lev[0];
+    if (f32) {
+        if (!c.fixed_scale) {
+            dot(s, c.n, r, r, partials(c), slot(c, S_T0));
+            scalar_ops(s, SOP_SQRT, slot(c, 0), S_T0, 0, S_SCALE);
+            scalar_ops(s, SOP_INV, slot(c, 0), S_SCALE, 0, S_INV);
+        }
+        cast_scaled_f32(s, c.n, r, slot(c, S_INV), L0.b32v);
+        PC_CUDA(cudaMemsetAsync(L0.x32v, 0, sizeof(float) * c.n, s));
+    } else {
+        copy(s, c.n, r, L0.b64v);
+        PC_CUDA(cudaMemsetAsync(L0.x64v, 0, sizeof(double) * c.n, s));
+    }
+    for (int32_t k = 0; k < 2 * re; ++k) {
+        const int32_t j = (k < re) ? k : 2 * re - 1 - k;
+        c.ncycles += 1;
+        run_body(c, *c.hist[j], 2);
+    }
+    if (f32) set_scaled_f32(s, c.n, L0.x32v, slot(c, S_SCALE), z);
+    else copy(s, c.n, L0.x64v, z);
 }
 
 // ---------------------------------------------------------------- residual with profiling
@@ -444,22 +497,12 @@ static void remove_mean(Ctx& c, double* x) {
 
 // ---------------------------------------------------------------- Alg. 2
 static void precond(Ctx& c, const double* r, double* z) {
-    cudaStream_t s = c.stream;
     int32_t re = (int32_t)c.hist.size();
     if (re <= c.p.numW) {
         cycle(c, *c.hist[re - 1], 2, r, z);
         return;
     }
-    fill(s, c.n, 0.0, z);
-    for (int32_t k = 0; k < 2 * re; ++k) {
-        int32_t j = (k < re) ? k : 2 * re - 1 - k;
-        Csr A;
-        A.n = c.n; A.nnz = c.nnz; A.rowptr = c.rowptr.p; A.col = c.col.p; A.val = c.val.p;
-        A.lpr = lanes_per_row(c.n, c.nnz);
-        residual64(s, A, z, r, c.w_t1.p, nullptr, nullptr);
-        cycle(c, *c.hist[j], 1, c.w_t1.p, c.w_t2.p);
-        axpy(s, c.n, 1.0, c.w_t2.p, z);
-    }
+    composite(c, r, z);
 }
 
 void smooth_error(Ctx& c, const double* rhs, double* e) {
@@ -588,10 +631,38 @@ pcamg_status solve(Ctx& c, const double* b, double* x, pcamg_stats* st) {
         if (st && st->res_hist && idx < st->res_hist_cap) { st->res_hist[idx] = v; if (idx + 1 > hl) hl = idx + 1; }
     };
     hist_put(0, res / bn);
+    // flexible CG outer iteration (params.outer): direction, A times it, the
+    // previous residual and preconditioned residual; a re-setup restarts it
+    const bool fcg = c.p.outer == PCAMG_OUTER_FCG;
+    bool restart = true;
+    double *fp = c.w_p.p, *fq = c.w_q.p, *frold = c.w_rold.p, *fzold = c.w_cin.p;
     while (k < c.p.max_iter && res / bn > c.p.tol) {
         Hier& h = *c.hist.back();
         cycle(c, h, 1, c.w_r.p, c.w_c.p);
-        axpy(s, c.n, 1.0, c.w_c.p, x);
+        if (fcg) {
+            const double* z = c.w_c.p;
+            const double* r = c.w_r.p;
+            dot(s, c.n, r, z, partials(c), slot(c, S_FRZ));
+            if (restart) {
+                copy(s, c.n, z, fp);
+                restart = false;
+            } else {   // Polak-Ribiere: beta = z.(r - r_old) / (z_old.r_old)
+                copy(s, c.n, r, c.w_t1.p);
+                axpy(s, c.n, -1.0, frold, c.w_t1.p);
+                dot(s, c.n, z, c.w_t1.p, partials(c), slot(c, S_FNUM));
+                dot(s, c.n, fzold, frold, partials(c), slot(c, S_FDEN));
+                scalar_ops(s, SOP_DIV, slot(c, 0), S_FNUM, S_FDEN, S_FBETA);
+                xpby_dev(s, c.n, z, slot(c, S_FBETA), fp);          // p = z + beta p
+            }
+            spmv_A(c, fp, fq);
+            dot(s, c.n, fp, fq, partials(c), slot(c, S_FPQ));
+            scalar_ops(s, SOP_PCG_ALPHA, slot(c, 0), S_FRZ, S_FPQ, S_FALPHA);
+            axpy_dev(s, c.n, slot(c, S_FALPHA), 1.0, fp, x);         // x += alpha p
+            copy(s, c.n, r, frold);
+            copy(s, c.n, z, fzold);
+        } else {
+            axpy(s, c.n, 1.0, c.w_c.p, x);
+        }
         remove_mean(c, x);
         fine_residual(c, x, b, c.w_r.p, slot(c, S_NORM2));
         double nres = read_norm(c);
@@ -606,6 +677,7 @@ pcamg_status solve(Ctx& c, const double* b, double* x, pcamg_stats* st) {
             if (c.p.max_resetups >= 0 && (int32_t)c.hist.size() - re0 >= c.p.max_resetups) break;
             double ts = now_ms();
             rebuild(c, c.w_e.p);
+            restart = true;
             if (st && st->rebuilt && k < st->res_hist_cap) st->rebuilt[k] = 1;
             if (c.p.update_mode == PCAMG_UPD_ADD_CORRECTION) {
                 axpy(s, c.n, 1.0, c.w_e.p, x);

@@ -14,7 +14,8 @@ namespace pc {
 Hier::~Hier() {
     for (auto& g : graph)
         if (g) cudaGraphExecDestroy(g);
-    if (graph_tmpl) cudaGraphDestroy(graph_tmpl);
+    for (auto& g : graph_tmpl)
+        if (g) cudaGraphDestroy(g);
 }
 
 static Csr make_csr(const Level& L, int32_t n, int64_t nnz, const int32_t* rp, const int32_t* ci,
@@ -32,11 +33,11 @@ static Csr make_csr(const Level& L, int32_t n, int64_t nnz, const int32_t* rp, c
 }
 
 template <class T>
-static T* vx(Level& L) { if constexpr (sizeof(T) == 8) return L.x64.p; else return L.x32.p; }
+static T* vx(Level& L) { if constexpr (sizeof(T) == 8) return L.x64v; else return L.x32v; }
 template <class T>
-static T* vb(Level& L) { if constexpr (sizeof(T) == 8) return L.b64.p; else return L.b32.p; }
+static T* vb(Level& L) { if constexpr (sizeof(T) == 8) return L.b64v; else return L.b32v; }
 template <class T>
-static T* vr(Level& L) { if constexpr (sizeof(T) == 8) return L.r64.p; else return L.r32.p; }
+static T* vr(Level& L) { if constexpr (sizeof(T) == 8) return L.r64v; else return L.r32v; }
 
 template <class T>
 static void setup_tail(Ctx& c, Hier& h) {
@@ -119,10 +120,19 @@ static void finish_hierarchy(Ctx& c, Hier& hh, bool boolean_chain) {
         Level& L = h->lev[l];
         nnz_sum += (double)L.nnz;
         if (f32) {
-            L.x32.alloc(c.mem, L.n); L.b32.alloc(c.mem, L.n); L.r32.alloc(c.mem, L.n);
+            if (l > 0) { L.x32.alloc(c.mem, L.n); L.b32.alloc(c.mem, L.n); L.r32.alloc(c.mem, L.n); }
             if (l == nlev - 1) { L.x64.alloc(c.mem, L.n); L.b64.alloc(c.mem, L.n); }
-        } else {
+        } else if (l > 0) {
             L.x64.alloc(c.mem, L.n); L.b64.alloc(c.mem, L.n); L.r64.alloc(c.mem, L.n);
+        }
+        if (l == 0) {   // the finest level's vectors are the context's
+            L.x32v = c.l0_x32.p; L.b32v = c.l0_b32.p; L.r32v = c.l0_r32.p;
+            L.x64v = L.x64.p ? L.x64.p : c.l0_x64.p;
+            L.b64v = L.b64.p ? L.b64.p : c.l0_b64.p;
+            L.r64v = c.l0_r64.p;
+        } else {
+            L.x32v = L.x32.p; L.b32v = L.b32.p; L.r32v = L.r32.p;
+            L.x64v = L.x64.p; L.b64v = L.b64.p; L.r64v = L.r64.p;
         }
     }
     h->oc = nnz_sum / (double)c.nnz;

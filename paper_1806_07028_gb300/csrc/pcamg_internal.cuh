@@ -146,9 +146,13 @@ struct Level {
     DBuf<double> tw;
     int64_t tnnz = 0;
     int32_t cover_rounds = 0, leftover_rounds = 0;
-    // cycle work vectors (sized n)
+    // cycle work vectors (sized n); the views are what the cycle uses: a level's
+    // own buffers, or for the finest level the context's (shared by all
+    // hierarchies: a cycle of one hierarchy can continue from another's result)
     DBuf<double> x64, b64, r64;
     DBuf<float> x32, b32, r32;
+    double *x64v = nullptr, *b64v = nullptr, *r64v = nullptr;
+    float *x32v = nullptr, *b32v = nullptr, *r32v = nullptr;
     DBuf<int32_t> d_cptr;  // colour offsets on the device (levels run by the tail kernel)
     // row-permuted copy (rows grouped by colour) for the streaming smoother
     DBuf<int32_t> gs_ptr, gs_col;
@@ -203,13 +207,14 @@ struct Hier {
     DBuf<unsigned char> tail_op[2];
     bool tail_op_tried[2] = {false, false};
     int32_t tail_ld = 0;
-    // CUDA graphs of the correction cycle (index: gamma-1)
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    int64_t graph_kernels[2] = {0, 0};
-    // event-record nodes around the finest-level residual of the V-cycle graph
+    // CUDA graphs of the cycle: 0 V-cycle from zero, 1 W-cycle from zero,
+    // 2 V-cycle continuing from the finest level's current x
+    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+    int64_t graph_kernels[3] = {0, 0, 0};
+    // event-record nodes around the finest-level residual of the V-cycle graphs
     // (params.profile bit 1), retargeted to fresh events before each replay
-    cudaGraphNode_t prof_node[2] = {nullptr, nullptr};
-    cudaGraph_t graph_tmpl = nullptr;   // the V-cycle graph those nodes belong to
+    cudaGraphNode_t prof_node[3][2] = {};
+    cudaGraph_t graph_tmpl[3] = {nullptr, nullptr, nullptr};   // graphs those nodes belong to
     ~Hier();
 };
 
@@ -249,6 +254,9 @@ struct Ctx {
     std::vector<Hier*> hist;
     // driver work vectors (length n)
     DBuf<double> w_r, w_c, w_e, w_t1, w_t2, w_z, w_p, w_q, w_rold, w_eh, w_ein, w_cin;
+    // finest-level cycle vectors shared by every hierarchy (cycle precision)
+    DBuf<double> l0_x64, l0_b64, l0_r64;
+    DBuf<float> l0_x32, l0_b32, l0_r32;
     DBuf<double> red;     // reduction partials + scalar slots
     int64_t npartials = 4096;
     double* h_red = nullptr;  // pinned host mirror of the scalar slots
@@ -266,6 +274,7 @@ struct Ctx {
     int64_t ncycles = 0;
     int64_t nwcycles = 0;
     bool fixed_scale = false;   // FP32 cycle scale set once for the running solve
+    int cur_kind = 0;           // cycle graph kind being run or captured
     double t_alg2 = 0.0, t_alg4 = 0.0;
     const double* last_e = nullptr;          // normalised error of the newest hierarchy
     std::unique_ptr<Reweighted> mpnn_cand;   // A^2 candidate pattern for the network's loss

@@ -55,7 +55,8 @@ class Params(C.Structure):
                 ("start", C.c_int32), ("dense_max", C.c_int32), ("use_graphs", C.c_int32),
                 ("keep_setup", C.c_int32), ("profile", C.c_int32), ("tail_rows", C.c_int32),
                 ("l1jac_rows", C.c_int32), ("tail_dense", C.c_int32), ("max_resetups", C.c_int32),
-                ("mpnn", C.c_void_p), ("update_mode", C.c_int32), ("max_cover_rounds", C.c_int32)]
+                ("mpnn", C.c_void_p), ("update_mode", C.c_int32), ("max_cover_rounds", C.c_int32),
+                ("outer", C.c_int32)]
 
 
 class Stats(C.Structure):

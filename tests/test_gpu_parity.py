@@ -395,3 +395,26 @@ def test_mwm_comparator_and_mwm_start_follow_the_oracle(P, name, nmin):
         hg = st["res_hist"]
         assert np.all(np.abs(hg[: k1 + 1] - ho[: k1 + 1]) <= 1e-9 * ho[: k1 + 1])
         assert np.all(np.abs(hg - ho) <= 1e-3 * ho)
+
+
+# ---- flexible-CG outer iteration (not in the paper) ------------------------------
+@pytest.mark.parametrize("name", ["C1", "C5-small", "er"])
+def test_fcg_outer_follows_the_oracle(P, name):
+    g = TRAJ.get(name) or GRAPHS[name]
+    b = I.rhs_normal(g.n, 11)
+    e0 = O.start_vector(g)
+    xo, so, ho = O.solve(g, b, e0=e0, params=O.default_params(outer=1))
+    for prec in (0, 1):
+        s = P.Solver(g, params=P.default_params(precision=prec, outer=1), e0=e0)
+        x, st = s.solve(b)
+        s.close()
+        x = x.cpu().numpy()
+        rel = np.linalg.norm(b - g.to_scipy() @ x) / np.linalg.norm(b)
+        assert st["status"] == "OK" and rel <= 1e-8, (st, rel)
+        if prec == 0:
+            assert (st["iters"], st["resetups"]) == (so["iters"], so["resetups"])
+            assert st["rebuilt_after"] == so["rebuilt_after"]
+            k1 = so["rebuilt_after"][0] if so["rebuilt_after"] else len(ho) - 1
+            hg = st["res_hist"]
+            assert np.all(np.abs(hg[: k1 + 1] - ho[: k1 + 1]) <= 1e-9 * ho[: k1 + 1])
+            assert np.linalg.norm(x - xo) <= 1e-8 * np.linalg.norm(xo)

@@ -167,3 +167,25 @@ def test_paper_tables_context_ring_alg5():
             assert st["status"] == "OK"
             assert st["iters"] <= 2 * row[it]
             assert abs(st["oc_mean"] - row[oc]) < 0.15
+
+
+@pytest.mark.parametrize("name", ["C1", "C5-small", "C4-small"])
+def test_fcg_outer_iteration(name):
+    # flexible CG preconditioned by the adaptive V-cycle (not in the paper):
+    # reaches the tolerance (checked with scipy), keeps x orthogonal to 1, and
+    # its first step equals the stationary one scaled by the exact line search
+    g = I.workload(name)
+    A = g.to_scipy()
+    b = I.rhs_normal(g.n, 11)
+    x, st, hist = O.solve(g, b, params=O.default_params(outer=1))
+    assert st["status"] == "OK"
+    assert np.linalg.norm(b - A @ x) <= 1e-8 * np.linalg.norm(b)
+    assert abs(x.mean()) < 1e-12 * np.abs(x).max()
+    # one step: x1 = alpha z, z = V b, alpha = b.z / z.Az (exact line search)
+    x1, s1, h1 = O.solve(g, b, params=O.default_params(outer=1, max_iter=1, threshold=10.0))
+    e = O.start_vector(g)
+    z = O.Hierarchy(g, e).vcycle(b)
+    alpha = (b @ z) / (z @ (A @ z))
+    ref = alpha * z
+    ref -= ref.mean()
+    assert np.linalg.norm(x1 - ref) <= 1e-10 * np.linalg.norm(ref)
