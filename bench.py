@@ -261,7 +261,7 @@ def run_ours(a):
     nets = {}
 
     def net_for(form):
-        if not form.endswith("+learned"):
+        if "+learned" not in form:
             return None
         if "net" not in nets:
             from paper_1806_07028_gb300 import Mpnn
@@ -269,7 +269,8 @@ def run_ours(a):
         return nets["net"]
 
     def params_for(form, profile=0):
-        return default_params(precision=0 if form == "fp64" else 1, profile=profile, use_graphs=_graphs(a))
+        return default_params(precision=0 if form == "fp64" else 1, profile=profile, use_graphs=_graphs(a),
+                              outer=1 if form.endswith("+fcg") else 0)
 
     def step(form, profile=0):
         """One solve in a form: fp64, fp32ir, or fp32ir+learned (the shipped
@@ -346,7 +347,8 @@ def run_ours(a):
         out["forms"] = {a.form: {"ms": ms, "unknowns_per_s": g.n / (ms / 1e3), "iters": stats[-1]["iters"],
                                  "resetups": stats[-1]["resetups"], "cycles": stats[-1]["cycles"]}}
         xs = {a.form: x_host}
-        for other in ("fp64", "fp32ir", "fp32ir+learned"):
+        # "+fcg": flexible CG outer iteration instead of the paper's stationary one
+        for other in ("fp64", "fp32ir", "fp32ir+learned", "fp32ir+learned+fcg"):
             if other == a.form:
                 continue
             step(other)

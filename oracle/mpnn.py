@@ -196,8 +196,15 @@ def backward(g, u, theta, ehat, cand=None):
     if cand is None:
         cand = candidate_pattern(g)
     yhat, C = forward(g, u, theta, keep=True)
-    P, W, Dinv = C["P"], C["W"], C["Dinv"]
     L, gy = loss_and_grad(cand, yhat, ehat)
+    return L, backward_from(C, yhat, gy)
+
+
+def backward_from(C, yhat, gy):
+    """The gradient with respect to the parameters given the network's kept
+    values C (forward(..., keep=True)), its output y-hat and the loss gradient
+    gy with respect to y-hat."""
+    P, W, Dinv = C["P"], C["W"], C["Dinv"]
     # y-hat = (y - mean y) / ||y - mean y||
     gz = (gy - yhat * (yhat @ gy)) / C["nrm"]
     dy = gz - gz.mean()
@@ -219,7 +226,7 @@ def backward(g, u, theta, ehat, cand=None):
     dz_in = centre(dh) * gelu_grad(C["z_in"])
     grads["W_in"] = dz_in.T @ C["F"]
     grads["b_in"] = dz_in.sum(axis=0)
-    return L, flatten(grads)
+    return flatten(grads)
 
 
 def backward_magnitude(g, u, theta, ehat, cand=None):

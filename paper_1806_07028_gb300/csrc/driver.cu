@@ -198,8 +198,23 @@ struct LV<float> {
     static const float* pv(Level& L) { return L.pval32.p; }
 };
 
+// The buffer that holds level L's iterate now, and the other one (l1-Jacobi
+// levels with a second buffer alternate between them)
+template <class T>
+static T* xalt(Level& L) { if constexpr (sizeof(T) == 8) return L.xa64.p; else return L.xa32.p; }
+template <class T>
+static T* X(Level& L) { return L.xcur ? xalt<T>(L) : LV<T>::x(L); }
+
 template <class T>
 static void smooth(Ctx& c, Level& L, const T* b, T* x, bool forward) {
+    if (L.jac && xalt<T>(L)) {   // l1-Jacobi in one pass: x' = x + (b - A x) / d
+        const T* d;
+        if constexpr (sizeof(T) == 8) d = L.dl1_64.p; else d = L.dl1_32.p;
+        T* out = L.xcur ? LV<T>::x(L) : xalt<T>(L);
+        jacobi_sweep<T>(c.stream, L.A, x, b, d, out);
+        L.xcur ^= 1;
+        return;
+    }
     if (L.jac) {   // l1-Jacobi: x += (b - A x) / d
         T* r;
         const T* d;
@@ -295,9 +310,9 @@ static void cycle_level(Ctx& c, Hier& h, int32_t l, int gamma, bool fresh, bool 
         coarse_apply<T>(s, L.n, h.Xinv.p, LV<T>::b(L), LV<T>::x(L));
         return;
     }
-    T* x = LV<T>::x(L);
     T* b = LV<T>::b(L);
-    for (int32_t k = fresh ? 1 : 0; k < c.p.nu_pre; ++k) smooth<T>(c, L, b, x, true);
+    for (int32_t k = fresh ? 1 : 0; k < c.p.nu_pre; ++k) smooth<T>(c, L, b, X<T>(L), true);
+    T* x = X<T>(L);
     Level& C = h.lev[l + 1];
     // the child starts from zero; an l1-Jacobi child's first sweep from zero is
     // b/d, written by the restriction itself (the tail child does the same)
@@ -311,10 +326,10 @@ static void cycle_level(Ctx& c, Hier& h, int32_t l, int gamma, bool fresh, bool 
     else residual32(s, L.A, x, b, r);
     if (prof) prof_mark(c, h, 1);
     restrict_agg<T>(s, L.nc, L.agg_ptr.p, L.agg_mem.p, l == 0 ? LV<T>::pv(L) : nullptr, r,
-                    LV<T>::b(C), LV<T>::x(C), dc);
+                    LV<T>::b(C), X<T>(C), dc);
     for (int g = 0; g < gamma; ++g) cycle_level<T>(c, h, l + 1, gamma, child_fresh && g == 0, g == 0);
-    prolong_add<T>(s, L.n, L.agg.p, l == 0 ? LV<T>::pv(L) : nullptr, LV<T>::x(C), x);
-    for (int32_t k = 0; k < c.p.nu_post; ++k) smooth<T>(c, L, b, x, false);
+    prolong_add<T>(s, L.n, L.agg.p, l == 0 ? LV<T>::pv(L) : nullptr, X<T>(C), x);
+    for (int32_t k = 0; k < c.p.nu_post; ++k) smooth<T>(c, L, b, X<T>(L), false);
 }
 
 // kind 0: V-cycle from zero, 1: W-cycle from zero, 2: V-cycle continuing from
@@ -322,6 +337,7 @@ static void cycle_level(Ctx& c, Hier& h, int32_t l, int gamma, bool fresh, bool 
 // vector is the zero-start cycle applied to the start's residual)
 template <class T>
 static void cycle_body(Ctx& c, Hier& h, int kind) {
+    for (int32_t l = 0; l < h.nlev; ++l) h.lev[l].xcur = 0;
     Level& L0 = h.lev[0];
     if (kind != 2) {
         PC_CUDA(cudaMemsetAsync(LV<T>::x(L0), 0, sizeof(T) * L0.n, c.stream));

@@ -146,6 +146,12 @@ static void finish_hierarchy(Ctx& c, Hier& hh, bool boolean_chain) {
     if (h->lt < nlev) {
         if (f32) setup_tail<float>(c, *h); else setup_tail<double>(c, *h);
     }
+    // second iterate buffers of the l1-Jacobi levels the cycle runs level by level
+    for (int32_t l = 1; l < h->lt && l + 1 < nlev; ++l) {
+        Level& L = h->lev[l];
+        if (!L.jac) continue;
+        if (f32) L.xa32.alloc(c.mem, L.n); else L.xa64.alloc(c.mem, L.n);
+    }
     // row-permuted copies for the streaming smoother on levels above the tail
     for (int32_t l = 1; l < h->lt && l + 1 < nlev; ++l) {
         Level& L = h->lev[l];

@@ -93,6 +93,7 @@ struct WarpScratch {
     double val[kWarpCap];
     int mpre[kWarpMembers + 1];
     int mrow[kWarpMembers];
+    int mbeg[kWarpMembers];   // first input entry of each member row
 };
 
 // Ascending bitonic sort of 32*R 64-bit keys held in registers: key i lives in
@@ -148,7 +149,7 @@ __device__ __forceinline__ void stage_sort_keys(int lane, int r, int nm, int tot
                 if (W.mpre[mid] <= e) lo = mid; else hi = mid - 1;
             }
             const int j = W.mrow[lo];
-            const int k = src.in_beg(j) + (e - W.mpre[lo]);
+            const int k = W.mbeg[lo] + (e - W.mpre[lo]);
             uint32_t kk;
             src.kv(r, j, k, kk, v);
             if (kk != kSkip) key[q] = ((uint64_t)kk << 32) | (uint64_t)e;
@@ -185,8 +186,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_rowprod_warp(
         int total = 0;
         if (!over) {
             // member rows and the prefix of their lengths
-            int len = 0, mr = 0;
-            if (lane < nm) { mr = src.mem_row(r, lane); len = src.in_end(mr) - src.in_beg(mr); }
+            int len = 0, mr = 0, mb = 0;
+            if (lane < nm) { mr = src.mem_row(r, lane); mb = src.in_beg(mr); len = src.in_end(mr) - mb; }
             int inc = len;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -194,17 +195,17 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_rowprod_warp(
                 if (lane >= o) inc += y;
             }
             total = __shfl_sync(0xffffffffu, inc, 31);
-            if (lane < nm) { W.mpre[lane + 1] = inc; W.mrow[lane] = mr; }
+            if (lane < nm) { W.mpre[lane + 1] = inc; W.mrow[lane] = mr; W.mbeg[lane] = mb; }
             if (nm > 32) {
-                int len2 = 0, mr2 = 0;
-                if (lane + 32 < nm) { mr2 = src.mem_row(r, lane + 32); len2 = src.in_end(mr2) - src.in_beg(mr2); }
+                int len2 = 0, mr2 = 0, mb2 = 0;
+                if (lane + 32 < nm) { mr2 = src.mem_row(r, lane + 32); mb2 = src.in_beg(mr2); len2 = src.in_end(mr2) - mb2; }
                 int inc2 = len2;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
                     int y = __shfl_up_sync(0xffffffffu, inc2, o);
                     if (lane >= o) inc2 += y;
                 }
-                if (lane + 32 < nm) { W.mpre[lane + 33] = total + inc2; W.mrow[lane + 32] = mr2; }
+                if (lane + 32 < nm) { W.mpre[lane + 33] = total + inc2; W.mrow[lane + 32] = mr2; W.mbeg[lane + 32] = mb2; }
                 total += __shfl_sync(0xffffffffu, inc2, 31);
             }
             if (lane == 0) W.mpre[0] = 0;

@@ -48,13 +48,16 @@ inline int sparse_grid(int64_t rows, int lpr, int block = kBlock) {
 }
 
 // r = b - A x; when partial != null, block b writes sum of r_i^2 of its rows.
+// With dl1 given the launch is one l1-Jacobi sweep instead: r receives the new
+// iterate x_i + (b_i - sum_j a_ij x_j) / dl1_i (x is not written).
 template <class T, int LPR>
 __global__ void __launch_bounds__(kBlock) k_residual(int n, const int* __restrict__ rowptr,
                                                      const int* __restrict__ col,
                                                      const T* __restrict__ val,
                                                      const T* __restrict__ x,
                                                      const T* __restrict__ b, T* __restrict__ r,
-                                                     double* __restrict__ partial) {
+                                                     double* __restrict__ partial,
+                                                     const T* __restrict__ dl1 = nullptr) {
     constexpr int RPW = 32 / LPR;
     const int lane = threadIdx.x & 31;
     const int sub = lane % LPR, grp = lane / LPR;
@@ -65,15 +68,17 @@ __global__ void __launch_bounds__(kBlock) k_residual(int n, const int* __restric
     pdl_trigger();
     for (int64_t row0 = warp * RPW; row0 < n; row0 += nwarps * RPW) {
         int64_t row = row0 + grp;
-        T s = 0;
+        T s = 0, xr = 0, dr = 1;
         if (row < n) {
+            if (dl1 && sub == 0) { xr = x[row]; dr = __ldg(dl1 + row); }   // loaded ahead of the sum
             int beg = __ldg(rowptr + row), end = __ldg(rowptr + row + 1);
             for (int k = beg + sub; k < end; k += LPR) s = fma_t(__ldg(val + k), __ldg(x + __ldg(col + k)), s);
         }
         s = group_sum<LPR>(s);
         if (sub == 0 && row < n) {
             T rr = __ldg(b + row) - s;
-            r[row] = rr;
+            if (dl1) r[row] = xr + rr / dr;
+            else r[row] = rr;
             acc2 += (double)rr * (double)rr;
         }
     }
@@ -292,12 +297,14 @@ __device__ __forceinline__ T row_add(const T* av, const T* xv, int i, T s) {
 template <class T>
 struct TileMeta {
     int tb, te, rb, re, row;
-    T bv;
+    T bv, xv, dv;   // b, and for an l1-Jacobi sweep x and d, at this thread's row
 };
 
+// b (and, when dl1 is given, x and d) at the row are loaded here, early
 template <class T, bool PERM, bool WITH_B = true>
 __device__ __forceinline__ TileMeta<T> tile_meta(int t0, int tend, const int* __restrict__ ptr,
-                                                 const int* __restrict__ rows, const T* __restrict__ b) {
+                                                 const int* __restrict__ rows, const T* __restrict__ b,
+                                                 const T* x = nullptr, const T* __restrict__ dl1 = nullptr) {
     TileMeta<T> m;
     const int tl = min(t0 + kStreamRows, tend);
     const int t = t0 + threadIdx.x;
@@ -305,12 +312,16 @@ __device__ __forceinline__ TileMeta<T> tile_meta(int t0, int tend, const int* __
     m.te = __ldg(ptr + tl);
     m.rb = m.re = 0;
     m.row = -1;
-    m.bv = T(0);
+    m.bv = m.xv = T(0);
+    m.dv = T(1);
     if (t < tend) {
         m.rb = __ldg(ptr + t);
         m.re = __ldg(ptr + t + 1);
         m.row = PERM ? __ldg(rows + t) : t;
-        if (WITH_B) m.bv = __ldg(b + m.row);
+        if (WITH_B) {
+            m.bv = __ldg(b + m.row);
+            if (dl1) { m.xv = x[m.row]; m.dv = __ldg(dl1 + m.row); }
+        }
     }
     return m;
 }
@@ -330,7 +341,8 @@ template <class T, bool PERM, bool NORM>
 __device__ __forceinline__ void stream_tiles(int beg, int end, int tpb, const int* __restrict__ rows,
                                              const int* __restrict__ ptr, const int* __restrict__ col,
                                              const T* __restrict__ val, const T* x_in, const T* __restrict__ b,
-                                             T* out, double* __restrict__ partial) {
+                                             T* out, double* __restrict__ partial,
+                                             const T* __restrict__ dl1 = nullptr) {
     __shared__ T av[kStreamChunk<T>];
     __shared__ T xv[kXv<T>];
     __shared__ int pc[PERM ? kStreamChunk<T> : 1];
@@ -346,7 +358,10 @@ __device__ __forceinline__ void stream_tiles(int beg, int end, int tpb, const in
         if (kPdl) {
             pdl_wait();
             pdl_trigger();
-            if (M.row >= 0) M.bv = __ldg(b + M.row);
+            if (M.row >= 0) {
+                M.bv = __ldg(b + M.row);
+                if (dl1) { M.xv = x_in[M.row]; M.dv = __ldg(dl1 + M.row); }
+            }
         }
         for (int t = tfirst; t < tstop; ++t) {
             TileMeta<T> Mn = M;
@@ -359,7 +374,7 @@ __device__ __forceinline__ void stream_tiles(int beg, int end, int tpb, const in
                 if (c1 < M.te) {
                     load_chunk<T>(c1, min(c1 + kStreamChunk<T>, M.te), col, val, R);
                 } else if (t + 1 < tstop) {
-                    Mn = tile_meta<T, PERM>(beg + (t + 1) * kStreamRows, end, ptr, rows, b);
+                    Mn = tile_meta<T, PERM>(beg + (t + 1) * kStreamRows, end, ptr, rows, b, x_in, dl1);
                     load_chunk<T>(Mn.tb, min(Mn.tb + kStreamChunk<T>, Mn.te), col, val, R);
                 }
                 const int kb = max(M.rb, c0), ke = min(M.re, c1);
@@ -376,7 +391,8 @@ __device__ __forceinline__ void stream_tiles(int beg, int end, int tpb, const in
                     out[M.row] = (M.bv - s) / d;
                 } else {
                     const T rr = M.bv - s;
-                    out[M.row] = rr;
+                    if (dl1) out[M.row] = M.xv + rr / M.dv;   // l1-Jacobi sweep
+                    else out[M.row] = rr;
                     if (NORM) rr2 = fma((double)rr, (double)rr, rr2);
                 }
             }
@@ -416,9 +432,10 @@ __global__ void __launch_bounds__(kStreamRows) k_res_stream(int n, const int* __
                                                              const T* __restrict__ x,
                                                              const T* __restrict__ b,
                                                              T* __restrict__ r,
-                                                             double* __restrict__ partial) {
+                                                             double* __restrict__ partial,
+                                                             const T* __restrict__ dl1 = nullptr) {
     stream_tiles<T, false, NORM>(0, n, NORM ? kNormTiles : kTilesPerBlock<T>, nullptr, rowptr, col, val, x, b, r,
-                                 partial);
+                                 partial, dl1);
 }
 
 // One colour of Gauss-Seidel on the row-permuted copy (rows of a colour are
@@ -505,11 +522,11 @@ void residual64(cudaStream_t s, const Csr& A, const double* x, const double* b, 
         } else {
             const int gt = (g + kTilesPerBlock<double> - 1) / kTilesPerBlock<double>;
             launch(k_res_stream<double, false>, gt, kStreamRows, 0, s, A.n, A.rowptr, A.col, A.val, x, b, r,
-                   (double*)nullptr);
+                   (double*)nullptr, (const double*)nullptr);
         }
     } else {
         int g = sparse_grid(A.n, A.lpr);
-#define CALL(L) launch(k_residual<double, L>, g, kBlock, 0, s, A.n, A.rowptr, A.col, A.val, x, b, r, (double*)nullptr)
+#define CALL(L) launch(k_residual<double, L>, g, kBlock, 0, s, A.n, A.rowptr, A.col, A.val, x, b, r, (double*)nullptr, (const double*)nullptr)
         PC_LPR_DISPATCH(A.lpr, CALL)
 #undef CALL
     }
@@ -518,6 +535,27 @@ void residual64(cudaStream_t s, const Csr& A, const double* x, const double* b, 
 
 int residual_partials(int32_t n) { return (n + kStreamRows - 1) / kStreamRows; }
 int residual_norm_blocks(int32_t n) { return (residual_partials(n) + kNormTiles - 1) / kNormTiles; }
+
+// One l1-Jacobi sweep into another buffer: xout = x + (b - A x) / d, the same
+// arithmetic as a residual followed by jacobi_update, in one pass over A.
+template <class T>
+void jacobi_sweep(cudaStream_t s, const Csr& A, const T* x, const T* b, const T* d, T* xout) {
+    const T* val;
+    if constexpr (sizeof(T) == 8) val = A.val; else val = A.val32;
+    if (use_stream(A.n, A.lpr)) {
+        int g = ((A.n + kStreamRows - 1) / kStreamRows + kTilesPerBlock<T> - 1) / kTilesPerBlock<T>;
+        launch(k_res_stream<T, false>, g, kStreamRows, 0, s, A.n, A.rowptr, A.col, val, x, b, xout,
+               (double*)nullptr, d);
+    } else {
+        int g = sparse_grid(A.n, A.lpr);
+#define CALL(L) launch(k_residual<T, L>, g, kBlock, 0, s, A.n, A.rowptr, A.col, val, x, b, xout, (double*)nullptr, d)
+        PC_LPR_DISPATCH(A.lpr, CALL)
+#undef CALL
+    }
+    PC_LAUNCH("jacobi_sweep");
+}
+template void jacobi_sweep<double>(cudaStream_t, const Csr&, const double*, const double*, const double*, double*);
+template void jacobi_sweep<float>(cudaStream_t, const Csr&, const float*, const float*, const float*, float*);
 
 template <class T>
 void jacobi_update(cudaStream_t s, int32_t n, const T* r, const T* d, T* x) {
@@ -536,10 +574,10 @@ void residual32(cudaStream_t s, const Csr& A, const float* x, const float* b, fl
     if (use_stream(A.n, A.lpr)) {
         int g = ((A.n + kStreamRows - 1) / kStreamRows + kTilesPerBlock<float> - 1) / kTilesPerBlock<float>;
         launch(k_res_stream<float, false>, g, kStreamRows, 0, s, A.n, A.rowptr, A.col, A.val32, x, b, r,
-               (double*)nullptr);
+               (double*)nullptr, (const float*)nullptr);
     } else {
         int g = sparse_grid(A.n, A.lpr);
-#define CALL(L) launch(k_residual<float, L>, g, kBlock, 0, s, A.n, A.rowptr, A.col, A.val32, x, b, r, (double*)nullptr)
+#define CALL(L) launch(k_residual<float, L>, g, kBlock, 0, s, A.n, A.rowptr, A.col, A.val32, x, b, r, (double*)nullptr, (const float*)nullptr)
         PC_LPR_DISPATCH(A.lpr, CALL)
 #undef CALL
     }

@@ -153,6 +153,12 @@ struct Level {
     DBuf<float> x32, b32, r32;
     double *x64v = nullptr, *b64v = nullptr, *r64v = nullptr;
     float *x32v = nullptr, *b32v = nullptr, *r32v = nullptr;
+    // l1-Jacobi levels above the coarse tail keep a second iterate buffer: a
+    // sweep reads one and writes the other (one pass over A); xcur tracks, while
+    // a cycle is recorded, which of the two holds x
+    DBuf<double> xa64;
+    DBuf<float> xa32;
+    int xcur = 0;
     DBuf<int32_t> d_cptr;  // colour offsets on the device (levels run by the tail kernel)
     // row-permuted copy (rows grouped by colour) for the streaming smoother
     DBuf<int32_t> gs_ptr, gs_col;
@@ -324,6 +330,9 @@ int residual_norm_blocks(int32_t n);   // partials the ||r||^2 launch of residua
 bool use_stream(int32_t rows, int lpr);  // streaming kernels pay off for this launch
 template <class T>
 void jacobi_update(cudaStream_t s, int32_t n, const T* r, const T* d, T* x);   // x += r / d
+// xout = x + (b - A x) / d in one pass (an l1-Jacobi sweep into another buffer)
+template <class T>
+void jacobi_sweep(cudaStream_t s, const Csr& A, const T* x, const T* b, const T* d, T* xout);
 void l1_diagonal(cudaStream_t s, int32_t n, const int32_t* rowptr, const double* val, double* d);
 template <class T>
 void restrict_agg(cudaStream_t s, int32_t nc, const int32_t* agg_ptr, const int32_t* agg_mem,

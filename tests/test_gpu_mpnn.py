@@ -82,27 +82,43 @@ def test_forward_matches_oracle(P, name):
 
 
 @pytest.mark.parametrize("name", ["rgg", "er"])
-def test_loss_and_gradient_match_oracle(P, name):
+@pytest.mark.parametrize("seed", [2, 4])
+def test_loss_and_gradient_match_oracle(P, name, seed):
+    # The loss gradient with respect to the output is a steep function of the
+    # output (softmax of |y_i - y_j| / tau_i), so the forward pass's bfloat16
+    # error alone moves it by a few per cent. The backward pass is therefore
+    # checked from the GPU's own output: the oracle evaluates the loss gradient
+    # at the GPU's y-hat and carries it back through its FP64 network. What is
+    # left is the backward pass's own rounding: every product it forms has its
+    # two factors staged in bfloat16 (relative 2^-9 each), so each gradient
+    # entry may move by at most about 2^-8 times the sum of the absolute values
+    # of its terms (oracle.mpnn.backward_magnitude), whatever cancellation the
+    # signed sum has. Each parameter group must also agree to 5 % in 2-norm.
     g = GRAPHS[name]()
-    net, s, u, th = _case(P, g, seed=2)
+    net, s, u, th = _case(P, g, seed=seed)
     t = _smooth_target(g)
+    y_gpu = net.forward(s, u).cpu().numpy()
     L = net.loss_grad(s, u, t)
     gg = net.grad().astype(np.float64)
-    Lr, gr = M.backward(g, u.cpu().numpy(), th, t)
+    uu = u.cpu().numpy()
+    Lr, _ = M.backward(g, uu, th, t)
     assert abs(L - Lr) <= 2e-2 * abs(Lr), (L, Lr)
+    cand = M.candidate_pattern(g)
+    y_orc, C = M.forward(g, uu, th, keep=True)
+    _, gy_at_gpu = M.loss_and_grad(cand, y_gpu, t)
+    ref = M.backward_from(C, y_orc, gy_at_gpu)
+    mag = M.backward_magnitude(g, uu, th, t)
     off = 0
     for name_, sh in M.param_shapes():
         sz = int(np.prod(sh))
-        a, b = gg[off:off + sz], gr[off:off + sz]
+        a, b, m = gg[off:off + sz], ref[off:off + sz], mag[off:off + sz]
         off += sz
         if name_ == "b_out":
             # y-hat does not depend on b_out: its gradient is zero up to rounding
             assert np.abs(a).max() <= 1e-4 * np.abs(gg).max()
             continue
-        nb = np.linalg.norm(b)
-        cos = a @ b / (np.linalg.norm(a) * nb)
-        assert cos >= 0.97, (name_, cos)
-        assert 0.85 <= np.linalg.norm(a) / nb <= 1.15, (name_, np.linalg.norm(a) / nb)
+        assert np.all(np.abs(a - b) <= 2.0**-8 * m), (name_, (np.abs(a - b) / (2.0**-8 * m)).max())
+        assert np.linalg.norm(a - b) <= 0.05 * np.linalg.norm(b), (name_, np.linalg.norm(a - b) / np.linalg.norm(b))
     s.close()
     net.close()
 
