@@ -35,6 +35,7 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 __global__ void k_colour_round(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
                                uint64_t seed, const int* __restrict__ cin, int* __restrict__ cout,
                                int* __restrict__ left, int* __restrict__ maxc) {
+    int nleft = 0, cmax = -1;
     FOR_EACH(v64, n) {
         int v = (int)v64;
         int cv = cin[v];
@@ -48,7 +49,7 @@ __global__ void k_colour_round(int n, const int* __restrict__ rowptr, const int*
             uint64_t hu = splitmix64(seed ^ (uint64_t)(int64_t)u);
             if (hu > hv || (hu == hv && u > v)) win = false;
         }
-        if (!win) { cout[v] = -1; atomicAdd(left, 1); continue; }
+        if (!win) { cout[v] = -1; ++nleft; continue; }
         uint64_t mask = 0;
         for (int k = beg; k < end; ++k) {
             int u = col[k];
@@ -71,8 +72,17 @@ __global__ void k_colour_round(int n, const int* __restrict__ rowptr, const int*
             }
         }
         cout[v] = c;
-        atomicMax(maxc, c);
+        cmax = max(cmax, c);
     }
+    block_count(left, nleft);
+    // largest colour of the block, one atomic per block
+    __shared__ int s_max;
+    if (threadIdx.x == 0) s_max = -1;
+    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) cmax = max(cmax, __shfl_down_sync(0xffffffffu, cmax, o));
+    if ((threadIdx.x & 31) == 0 && cmax >= 0) atomicMax(&s_max, cmax);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_max >= 0) atomicMax(maxc, s_max);
 }
 
 // One breadth-first level from vertex 0 over its frontier (the vertices at
@@ -87,18 +97,18 @@ __global__ void k_bfs_level(const int* __restrict__ rowptr, const int* __restric
                             int* __restrict__ qout, int* __restrict__ nout, int* __restrict__ dist,
                             int* __restrict__ odd) {
     const int m = *nin;
+    int o = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
         const int v = qin[i];
-        bool o = false;
         for (int k = rowptr[v]; k < rowptr[v + 1]; ++k) {
             const int u = col[k];
             if (u == v) continue;
             const int du = dist[u];
-            if (du == d) o = true;
+            if (du == d) o = 1;
             else if (du < 0 && atomicCAS(dist + u, -1, d + 1) == -1) qout[atomicAdd(nout, 1)] = u;
         }
-        if (o) *odd = 1;
     }
+    block_flag(odd, o);
 }
 
 __global__ void k_parity_colour(int n, const int* __restrict__ dist, int* __restrict__ colour,

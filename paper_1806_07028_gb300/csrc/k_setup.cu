@@ -9,6 +9,7 @@
 // Every integer result is deterministic and independent of thread scheduling.
 #include <algorithm>
 #include <climits>
+#include <type_traits>
 #include <cstring>
 
 #include "pcamg_internal.cuh"
@@ -129,18 +130,53 @@ __device__ __forceinline__ void sort_keys_regs(uint64_t (&key)[R], int lane) {
     }
 }
 
+// The same network on 32-bit keys (one shuffle and one integer compare per
+// exchange instead of two and a 64-bit compare).
+template <int R>
+__device__ __forceinline__ void sort_keys_regs32(uint32_t (&key)[R], int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32 * R; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int rp = r ^ (j >> 5);
+                    if (rp > r) {
+                        const bool up = ((lane + 32 * r) & k) == 0;
+                        if ((key[r] > key[rp]) == up) { const uint32_t t = key[r]; key[r] = key[rp]; key[rp] = t; }
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const uint32_t pk = __shfl_xor_sync(0xffffffffu, key[r], j);
+                    const bool up = ((lane + 32 * r) & k) == 0;
+                    const bool lower = (lane & j) == 0;
+                    const bool take = (lower == up) ? (pk < key[r]) : (pk > key[r]);
+                    if (take) key[r] = pk;
+                }
+            }
+        }
+    }
+}
+
 // Stage the row's contributions (numbered e = 0..total-1 in their fixed order)
-// as keys (column << 32 | e) in registers and values in W.val[e], sort the
-// keys and store them in W.key in sorted order. Keys of skipped contributions
-// and of the padding are ~0 and sort last.
-template <int R, class Src>
+// as keys (column, e) in registers and values in W.val[e], sort the keys and
+// store them in W.key as (column << 32 | e) in sorted order. Keys of skipped
+// contributions and of the padding are ~0 and sort last. NARROW packs a key
+// into 32 bits, column << 8 | e, when every column is below 2^24 and e below
+// 255 (so no real key equals the padding); the order is the same.
+template <int R, bool NARROW, class Src>
 __device__ __forceinline__ void stage_sort_keys(int lane, int r, int nm, int total, const Src& src,
                                                 WarpScratch& W) {
-    uint64_t key[R];
+    using K = typename std::conditional<NARROW, uint32_t, uint64_t>::type;
+    constexpr K kPad = NARROW ? (K)0xffffffffu : (K)~0ull;
+    K key[R];
 #pragma unroll
     for (int q = 0; q < R; ++q) {
         const int e = lane + 32 * q;
-        key[q] = ~0ull;
+        key[q] = kPad;
         double v = 0.0;
         if (e < total) {
             int lo = 0, hi = nm - 1;          // member t with mpre[t] <= e < mpre[t+1]
@@ -152,13 +188,21 @@ __device__ __forceinline__ void stage_sort_keys(int lane, int r, int nm, int tot
             const int k = W.mbeg[lo] + (e - W.mpre[lo]);
             uint32_t kk;
             src.kv(r, j, k, kk, v);
-            if (kk != kSkip) key[q] = ((uint64_t)kk << 32) | (uint64_t)e;
+            if (kk != kSkip) key[q] = NARROW ? (K)((kk << 8) | (uint32_t)e) : (K)(((uint64_t)kk << 32) | (uint64_t)e);
         }
         W.val[e] = v;
     }
-    sort_keys_regs<R>(key, lane);
+    if constexpr (NARROW) {
+        sort_keys_regs32<R>(key, lane);
 #pragma unroll
-    for (int q = 0; q < R; ++q) W.key[lane + 32 * q] = key[q];
+        for (int q = 0; q < R; ++q)
+            W.key[lane + 32 * q] = (key[q] == kPad) ? ~0ull
+                                                    : (((uint64_t)(key[q] >> 8) << 32) | (uint64_t)(key[q] & 255u));
+    } else {
+        sort_keys_regs<R>(key, lane);
+#pragma unroll
+        for (int q = 0; q < R; ++q) W.key[lane + 32 * q] = key[q];
+    }
 }
 
 // MODE 0: count the row's distinct columns (cnt) and flag long rows;
@@ -176,6 +220,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_rowprod_warp(
     __shared__ WarpScratch ws_all[kWarpsPerBlock];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     WarpScratch& W = ws_all[wib];
+    const bool narrow = nrows <= (1 << 24);   // every column fits 24 bits
     const int64_t gw = (int64_t)blockIdx.x * kWarpsPerBlock + wib;
     const int64_t nw = (int64_t)gridDim.x * kWarpsPerBlock;
     for (int64_t r64 = gw; r64 < nrows; r64 += nw) {
@@ -215,10 +260,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_rowprod_warp(
             __syncwarp();
             int P = 32;
             while (P < total) P <<= 1;
-            if (P == 32) stage_sort_keys<1>(lane, r, nm, total, src, W);
-            else if (P == 64) stage_sort_keys<2>(lane, r, nm, total, src, W);
-            else if (P == 128) stage_sort_keys<4>(lane, r, nm, total, src, W);
-            else stage_sort_keys<8>(lane, r, nm, total, src, W);
+            // columns of a square product are row numbers, below nrows
+            if (narrow && P == 32) stage_sort_keys<1, true>(lane, r, nm, total, src, W);
+            else if (narrow && P == 64) stage_sort_keys<2, true>(lane, r, nm, total, src, W);
+            else if (narrow && P == 128) stage_sort_keys<4, true>(lane, r, nm, total, src, W);
+            else if (P == 32) stage_sort_keys<1, false>(lane, r, nm, total, src, W);
+            else if (P == 64) stage_sort_keys<2, false>(lane, r, nm, total, src, W);
+            else if (P == 128) stage_sort_keys<4, false>(lane, r, nm, total, src, W);
+            else stage_sort_keys<8, false>(lane, r, nm, total, src, W);
             __syncwarp();
             // runs of equal columns
             int carry = 0;
@@ -675,7 +724,9 @@ __global__ void k_cover_compact(const int* __restrict__ list, const int* __restr
     const int m = *cnt;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
         const int u = list[i];
-        if (deg[u] < 2 && bv[u] >= 0) out[atomicAdd(ocnt, 1)] = u;
+        const bool keep = deg[u] < 2 && bv[u] >= 0;
+        const int slot = warp_append(ocnt, keep);
+        if (keep) out[slot] = u;
     }
 }
 
@@ -727,6 +778,7 @@ __global__ void k_cover_accept(const int* __restrict__ list, const int* __restri
                                const int* __restrict__ cf, const int* __restrict__ ct,
                                int* __restrict__ nbr0, int* __restrict__ nbr1,
                                int* __restrict__ counter) {
+    int added = 0;
     FOR_LIST(u, list, cnt) {
         if (cf[u] != u) continue;
         int y = ct[u];
@@ -740,8 +792,9 @@ __global__ void k_cover_accept(const int* __restrict__ list, const int* __restri
         if (nbr0[y] < 0) nbr0[y] = u; else nbr1[y] = u;
         deg[u] += 1;
         deg[y] += 1;
-        atomicAdd(counter, 1);
+        ++added;
     }
+    block_count(counter, added);
 }
 
 __global__ void k_canonical(int n, int* __restrict__ nbr0, int* __restrict__ nbr1) {
@@ -756,41 +809,39 @@ __global__ void k_canonical(int n, int* __restrict__ nbr0, int* __restrict__ nbr
 // Half-edge h = 2u+k points from u to nbr_k(u). Its successor continues away
 // from u at the head. Pointer jumping gives each half-edge the path end it
 // reaches and the number of edges to it.
+// List ranking state of half-edge h = 2u + k (u's k-th cover neighbour): the
+// half-edge it jumps to (-1 at the path's end), the distance covered and the
+// end vertex reached, in one 16-byte record so that a jump gathers one sector.
 __global__ void k_rank_init(int n, const int* __restrict__ nbr0, const int* __restrict__ nbr1,
-                            int* __restrict__ jmp, int* __restrict__ dist, int* __restrict__ endv) {
+                            int4* __restrict__ st) {
     FOR_EACH(u64, n) {
         int u = (int)u64;
         for (int k = 0; k < 2; ++k) {
             int h = 2 * u + k;
             int v = k ? nbr1[u] : nbr0[u];
-            if (v < 0) { jmp[h] = -1; dist[h] = 0; endv[h] = -1; continue; }
+            if (v < 0) { st[h] = make_int4(-1, 0, -1, 0); continue; }
             int w0 = nbr0[v], w1 = nbr1[v];
             int w = (w0 >= 0 && w0 != u) ? w0 : ((w1 >= 0 && w1 != u) ? w1 : -1);
-            jmp[h] = (w < 0) ? -1 : (2 * v + (w0 == w ? 0 : 1));
-            dist[h] = 1;
-            endv[h] = v;
+            st[h] = make_int4((w < 0) ? -1 : (2 * v + (w0 == w ? 0 : 1)), 1, v, 0);
         }
     }
 }
 
-__global__ void k_rank_jump(int nh, const int* __restrict__ jmp, const int* __restrict__ dist,
-                            const int* __restrict__ endv, int* __restrict__ jmp2,
-                            int* __restrict__ dist2, int* __restrict__ endv2,
+// one pointer jump: (jmp, dist, endv) of h <- (jmp[j], dist[h] + dist[j], endv[j]), j = jmp[h]
+__global__ void k_rank_jump(int nh, const int4* __restrict__ st, int4* __restrict__ st2,
                             int* __restrict__ active) {
+    int more = 0;
     FOR_EACH(h, nh) {
-        int j = jmp[h];
-        if (j >= 0) {
-            dist2[h] = dist[h] + dist[j];
-            endv2[h] = endv[j];
-            int jj = jmp[j];
-            jmp2[h] = jj;
-            if (jj >= 0) *active = 1;
+        const int4 a = st[h];
+        if (a.x >= 0) {
+            const int4 b = st[a.x];
+            st2[h] = make_int4(b.x, a.y + b.y, b.z, 0);
+            if (b.x >= 0) more = 1;
         } else {
-            dist2[h] = dist[h];
-            endv2[h] = endv[h];
-            jmp2[h] = j;
+            st2[h] = a;
         }
     }
+    block_flag(active, more);
 }
 
 // Positions from the canonical end (the endpoint with the smaller id), then the
@@ -798,7 +849,7 @@ __global__ void k_rank_jump(int nh, const int* __restrict__ jmp, const int* __re
 // by their first vertex; links to the previous and next matched pair of the
 // same path are kept for path shortening.
 __global__ void k_pair(int n, const int* __restrict__ nbr0, const int* __restrict__ nbr1,
-                       const int* __restrict__ dist, const int* __restrict__ endv,
+                       const int4* __restrict__ st,
                        int* __restrict__ lab, int* __restrict__ size, int* __restrict__ sprev,
                        int* __restrict__ snext, unsigned char* __restrict__ ishead) {
     FOR_EACH(u64, n) {
@@ -811,12 +862,14 @@ __global__ void k_pair(int n, const int* __restrict__ nbr0, const int* __restric
         if (deg == 0) continue;
         int L, pos, toward = -1, away = -1;
         if (deg == 1) {
-            int E = endv[2 * u], d = dist[2 * u];
+            const int4 h0 = st[2 * u];
+            int E = h0.z, d = h0.y;
             L = d + 1;
             if (u < E) { pos = 0; away = a; }
             else { pos = d; toward = a; }
         } else {
-            int E0 = endv[2 * u], d0 = dist[2 * u], E1 = endv[2 * u + 1], d1 = dist[2 * u + 1];
+            const int4 h0 = st[2 * u], h1 = st[2 * u + 1];
+            int E0 = h0.z, d0 = h0.y, E1 = h1.z, d1 = h1.y;
             L = d0 + d1 + 1;
             if (E0 < E1) { pos = d0; toward = a; away = b; }
             else { pos = d1; toward = b; away = a; }
@@ -864,15 +917,17 @@ __global__ void k_best(int n, const int* __restrict__ ptr, const int* __restrict
 __global__ void k_left_classify(int n, const int* __restrict__ lab, const int* __restrict__ best,
                                 int* __restrict__ st, int* __restrict__ jg, int* __restrict__ gcnt,
                                 int* __restrict__ nleft) {
+    int left = 0;
     FOR_EACH(u64, n) {
         int u = (int)u64;
         if (lab[u] >= 0) { st[u] = 0; continue; }
-        atomicAdd(nleft, 1);
+        ++left;
         int v = best[u];
         int g = lab[v];
         if (g >= 0) { st[u] = 2; jg[u] = g; atomicAdd(gcnt + g, 1); }
         else st[u] = 1;
     }
+    block_count(nleft, left);
 }
 
 // case 1: mutual best pairs among the waiting vertices
@@ -993,14 +1048,16 @@ __global__ void k_mwm_best(int n, const int* __restrict__ rowptr, const int* __r
 
 __global__ void k_mwm_accept(int n, const int* __restrict__ best, int* __restrict__ mate,
                              int* __restrict__ counter) {
+    int matched = 0;
     FOR_EACH(v64, n) {
         const int v = (int)v64;
         const int u = best[v];
         if (u >= 0 && best[u] == v) {
             mate[v] = u;
-            if (v < u) atomicAdd(counter, 1);
+            if (v < u) ++matched;
         }
     }
+    block_count(counter, matched);
 }
 
 // pair label = the pair's smaller vertex; a free vertex (all its neighbours are
@@ -1285,10 +1342,11 @@ int32_t aggregate_level(Ctx& c, int32_t n, const int32_t* nbr0, const int32_t* n
                         DBuf<int32_t>& cnbr1, int32_t* rounds_out) {
     cudaStream_t s = c.stream;
     int64_t nh = 2 * (int64_t)n;
-    DBuf<int32_t> jmp[2], dist[2], endv[2], active;
-    for (int k = 0; k < 2; ++k) { jmp[k].alloc(c.mem, nh); dist[k].alloc(c.mem, nh); endv[k].alloc(c.mem, nh); }
+    DBuf<int4> rk[2];
+    DBuf<int32_t> active;
+    for (int k = 0; k < 2; ++k) rk[k].alloc(c.mem, nh);
     active.alloc(c.mem, 1);
-    k_rank_init<<<grid1(n), kBlock, 0, s>>>(n, nbr0, nbr1, jmp[0].p, dist[0].p, endv[0].p); ::pc::count_launches(1);
+    k_rank_init<<<grid1(n), kBlock, 0, s>>>(n, nbr0, nbr1, rk[0].p); ::pc::count_launches(1);
     PC_LAUNCH("rank_init");
     // pointer jumping: the active flag is read every 4 rounds (rounds after the
     // last jump copy their input)
@@ -1296,8 +1354,7 @@ int32_t aggregate_level(Ctx& c, int32_t n, const int32_t* nbr0, const int32_t* n
     for (int it = 0;; it += 4) {
         PC_CUDA(cudaMemsetAsync(active.p, 0, sizeof(int32_t), s));
         for (int k = 0; k < 4; ++k) {
-            k_rank_jump<<<grid1(nh), kBlock, 0, s>>>((int)nh, jmp[cur].p, dist[cur].p, endv[cur].p,
-                                                     jmp[1 - cur].p, dist[1 - cur].p, endv[1 - cur].p, active.p); ::pc::count_launches(1);
+            k_rank_jump<<<grid1(nh), kBlock, 0, s>>>((int)nh, rk[cur].p, rk[1 - cur].p, active.p); ::pc::count_launches(1);
             cur = 1 - cur;
         }
         PC_LAUNCH("rank_jump");
@@ -1312,7 +1369,7 @@ int32_t aggregate_level(Ctx& c, int32_t n, const int32_t* nbr0, const int32_t* n
     ishead.alloc(c.mem, n);
     fill_i32(s, n, -1, lab.p);
     fill_i32(s, n, 0, size.p);
-    k_pair<<<grid1(n), kBlock, 0, s>>>(n, nbr0, nbr1, dist[cur].p, endv[cur].p, lab.p, size.p,
+    k_pair<<<grid1(n), kBlock, 0, s>>>(n, nbr0, nbr1, rk[cur].p, lab.p, size.p,
                                        sprev.p, snext.p, ishead.p); ::pc::count_launches(1);
     k_best<<<grid1(n), kBlock, 0, s>>>(n, t.ptr.p, t.col.p, t.w.p, best.p, lab.p, size.p); ::pc::count_launches(1);
     PC_LAUNCH("pair/best");

@@ -300,8 +300,8 @@ struct TileMeta {
     T bv, xv, dv;   // b, and for an l1-Jacobi sweep x and d, at this thread's row
 };
 
-// b (and, when dl1 is given, x and d) at the row are loaded here, early
-template <class T, bool PERM, bool WITH_B = true>
+// b (and, for an l1-Jacobi sweep (JAC), x and d) at the row are loaded here, early
+template <class T, bool PERM, bool WITH_B = true, bool JAC = false>
 __device__ __forceinline__ TileMeta<T> tile_meta(int t0, int tend, const int* __restrict__ ptr,
                                                  const int* __restrict__ rows, const T* __restrict__ b,
                                                  const T* x = nullptr, const T* __restrict__ dl1 = nullptr) {
@@ -320,7 +320,7 @@ __device__ __forceinline__ TileMeta<T> tile_meta(int t0, int tend, const int* __
         m.row = PERM ? __ldg(rows + t) : t;
         if (WITH_B) {
             m.bv = __ldg(b + m.row);
-            if (dl1) { m.xv = x[m.row]; m.dv = __ldg(dl1 + m.row); }
+            if (JAC) { m.xv = x[m.row]; m.dv = __ldg(dl1 + m.row); }
         }
     }
     return m;
@@ -337,7 +337,7 @@ __device__ __forceinline__ TileMeta<T> tile_meta(int t0, int tend, const int* __
 //   PERM = false: rows t of [0, n) (residual r = b - A x, optional ||r||^2);
 //   PERM = true:  permuted rows rows[t] of [beg, end) of one colour, Gauss-Seidel
 //                 x_row = (b_row - sum_{j != row} a x_j) / a_row,row.
-template <class T, bool PERM, bool NORM>
+template <class T, bool PERM, bool NORM, bool JAC = false>
 __device__ __forceinline__ void stream_tiles(int beg, int end, int tpb, const int* __restrict__ rows,
                                              const int* __restrict__ ptr, const int* __restrict__ col,
                                              const T* __restrict__ val, const T* x_in, const T* __restrict__ b,
@@ -360,7 +360,7 @@ __device__ __forceinline__ void stream_tiles(int beg, int end, int tpb, const in
             pdl_trigger();
             if (M.row >= 0) {
                 M.bv = __ldg(b + M.row);
-                if (dl1) { M.xv = x_in[M.row]; M.dv = __ldg(dl1 + M.row); }
+                if (JAC) { M.xv = x_in[M.row]; M.dv = __ldg(dl1 + M.row); }
             }
         }
         for (int t = tfirst; t < tstop; ++t) {
@@ -374,7 +374,7 @@ __device__ __forceinline__ void stream_tiles(int beg, int end, int tpb, const in
                 if (c1 < M.te) {
                     load_chunk<T>(c1, min(c1 + kStreamChunk<T>, M.te), col, val, R);
                 } else if (t + 1 < tstop) {
-                    Mn = tile_meta<T, PERM>(beg + (t + 1) * kStreamRows, end, ptr, rows, b, x_in, dl1);
+                    Mn = tile_meta<T, PERM, true, JAC>(beg + (t + 1) * kStreamRows, end, ptr, rows, b, x_in, dl1);
                     load_chunk<T>(Mn.tb, min(Mn.tb + kStreamChunk<T>, Mn.te), col, val, R);
                 }
                 const int kb = max(M.rb, c0), ke = min(M.re, c1);
@@ -391,7 +391,7 @@ __device__ __forceinline__ void stream_tiles(int beg, int end, int tpb, const in
                     out[M.row] = (M.bv - s) / d;
                 } else {
                     const T rr = M.bv - s;
-                    if (dl1) out[M.row] = M.xv + rr / M.dv;   // l1-Jacobi sweep
+                    if (JAC) out[M.row] = M.xv + rr / M.dv;   // l1-Jacobi sweep
                     else out[M.row] = rr;
                     if (NORM) rr2 = fma((double)rr, (double)rr, rr2);
                 }
@@ -432,10 +432,22 @@ __global__ void __launch_bounds__(kStreamRows) k_res_stream(int n, const int* __
                                                              const T* __restrict__ x,
                                                              const T* __restrict__ b,
                                                              T* __restrict__ r,
-                                                             double* __restrict__ partial,
-                                                             const T* __restrict__ dl1 = nullptr) {
+                                                             double* __restrict__ partial) {
     stream_tiles<T, false, NORM>(0, n, NORM ? kNormTiles : kTilesPerBlock<T>, nullptr, rowptr, col, val, x, b, r,
-                                 partial, dl1);
+                                 partial);
+}
+
+// One l1-Jacobi sweep into another buffer: xout_i = x_i + (b_i - sum_j a_ij x_j) / dl1_i
+template <class T>
+__global__ void __launch_bounds__(kStreamRows, 5) k_jac_stream(int n, const int* __restrict__ rowptr,
+                                                             const int* __restrict__ col,
+                                                             const T* __restrict__ val,
+                                                             const T* __restrict__ x,
+                                                             const T* __restrict__ b,
+                                                             const T* __restrict__ dl1,
+                                                             T* __restrict__ xout) {
+    stream_tiles<T, false, false, true>(0, n, kTilesPerBlock<T>, nullptr, rowptr, col, val, x, b, xout, nullptr,
+                                        dl1);
 }
 
 // One colour of Gauss-Seidel on the row-permuted copy (rows of a colour are
@@ -522,7 +534,7 @@ void residual64(cudaStream_t s, const Csr& A, const double* x, const double* b, 
         } else {
             const int gt = (g + kTilesPerBlock<double> - 1) / kTilesPerBlock<double>;
             launch(k_res_stream<double, false>, gt, kStreamRows, 0, s, A.n, A.rowptr, A.col, A.val, x, b, r,
-                   (double*)nullptr, (const double*)nullptr);
+                   (double*)nullptr);
         }
     } else {
         int g = sparse_grid(A.n, A.lpr);
@@ -544,8 +556,7 @@ void jacobi_sweep(cudaStream_t s, const Csr& A, const T* x, const T* b, const T*
     if constexpr (sizeof(T) == 8) val = A.val; else val = A.val32;
     if (use_stream(A.n, A.lpr)) {
         int g = ((A.n + kStreamRows - 1) / kStreamRows + kTilesPerBlock<T> - 1) / kTilesPerBlock<T>;
-        launch(k_res_stream<T, false>, g, kStreamRows, 0, s, A.n, A.rowptr, A.col, val, x, b, xout,
-               (double*)nullptr, d);
+        launch(k_jac_stream<T>, g, kStreamRows, 0, s, A.n, A.rowptr, A.col, val, x, b, d, xout);
     } else {
         int g = sparse_grid(A.n, A.lpr);
 #define CALL(L) launch(k_residual<T, L>, g, kBlock, 0, s, A.n, A.rowptr, A.col, val, x, b, xout, (double*)nullptr, d)
@@ -574,7 +585,7 @@ void residual32(cudaStream_t s, const Csr& A, const float* x, const float* b, fl
     if (use_stream(A.n, A.lpr)) {
         int g = ((A.n + kStreamRows - 1) / kStreamRows + kTilesPerBlock<float> - 1) / kTilesPerBlock<float>;
         launch(k_res_stream<float, false>, g, kStreamRows, 0, s, A.n, A.rowptr, A.col, A.val32, x, b, r,
-               (double*)nullptr, (const float*)nullptr);
+               (double*)nullptr);
     } else {
         int g = sparse_grid(A.n, A.lpr);
 #define CALL(L) launch(k_residual<float, L>, g, kBlock, 0, s, A.n, A.rowptr, A.col, A.val32, x, b, r, (double*)nullptr, (const float*)nullptr)

@@ -63,6 +63,38 @@ inline void launch(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cud
     count_launches(1);
 }
 
+// Counters and flags that many threads of a launch bump: one atomic per warp
+// (or per block) instead of one per thread, so a busy launch does not queue
+// millions of updates on one address. Every thread of the block must call the
+// block forms; the warp forms are called by the lanes active at that point.
+__device__ __forceinline__ void warp_count(int* counter, bool pred) {
+    const unsigned m = __ballot_sync(__activemask(), pred);
+    if (pred && (int)(threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(counter, __popc(m));
+}
+// slot in a list for the lanes with pred (order between warps is arbitrary)
+__device__ __forceinline__ int warp_append(int* counter, bool pred) {
+    const unsigned act = __activemask();
+    const unsigned m = __ballot_sync(act, pred);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    int base = 0;
+    if (m && lane == leader) base = atomicAdd(counter, __popc(m));
+    base = __shfl_sync(act, base, m ? leader : __ffs(act) - 1);
+    return base + __popc(m & ((1u << lane) - 1u));
+}
+__device__ __forceinline__ void block_count(int* counter, int local) {
+    __shared__ int s_cnt;
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_down_sync(0xffffffffu, local, o);
+    if ((threadIdx.x & 31) == 0 && local) atomicAdd(&s_cnt, local);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_cnt) atomicAdd(counter, s_cnt);
+}
+__device__ __forceinline__ void block_flag(int* flag, int local) {
+    if (__syncthreads_or(local) && threadIdx.x == 0) *flag = 1;
+}
+
 constexpr int kMaxLevels = 32;
 constexpr int kBlock = 256;
 constexpr int kNumSMs = 152;
