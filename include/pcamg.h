@@ -123,8 +123,9 @@ typedef struct {
                               kinds the levels below tail_rows are applied as their
                               dense linear operator N (formed once per hierarchy, on
                               first use: one visit of those levels from a zero start is
-                              x = N b, later visits x += N (b - A x)), instead of
-                              recursing through them. Same result up to rounding; used
+                              x = N b, later visits x += N (b - A x); a W-cycle's two
+                              visits from the level above are one operator and one
+                              product), instead of recursing through them. Same result up to rounding; used
                               when the tail has two or more levels and its vectors fit
                               one block's shared memory, else the recursion runs. */
     int32_t max_resetups;  /* pcamg_solve builds at most this many new hierarchies and

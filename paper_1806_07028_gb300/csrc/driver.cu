@@ -286,8 +286,9 @@ static void cycle_level(Ctx& c, Hier& h, int32_t l, int gamma, bool fresh, bool 
     cudaStream_t s = c.stream;
     Level& L = h.lev[l];
     if (l == h.lt && h.tail_op[gamma - 1].p) {
-        // the tail levels as their dense operator N: a visit from a zero start
-        // is x = N b; a later visit continues from x, x += N (b - A x)
+        // the tail levels as their dense operator N (reached here for the
+        // finest level only, lt = 0: one visit per product): a visit from a
+        // zero start is x = N b; a later visit continues from x, x += N (b - A x)
         const T* Nm = reinterpret_cast<const T*>(h.tail_op[gamma - 1].p);
         T* x = LV<T>::x(L);
         T* b = LV<T>::b(L);
@@ -314,9 +315,12 @@ static void cycle_level(Ctx& c, Hier& h, int32_t l, int gamma, bool fresh, bool 
     for (int32_t k = fresh ? 1 : 0; k < c.p.nu_pre; ++k) smooth<T>(c, L, b, X<T>(L), true);
     T* x = X<T>(L);
     Level& C = h.lev[l + 1];
+    // the child is the tail levels as one dense operator standing for all
+    // gamma visits: x_c = N b_c, one product
+    const bool child_dense = l + 1 == h.lt && h.tail_op[gamma - 1].p && h.tail_visits[gamma - 1] == gamma;
     // the child starts from zero; an l1-Jacobi child's first sweep from zero is
     // b/d, written by the restriction itself (the tail child does the same)
-    const bool child_fresh = C.jac && c.p.nu_pre >= 1 && l + 1 < h.nlev - 1;
+    const bool child_fresh = !child_dense && C.jac && c.p.nu_pre >= 1 && l + 1 < h.nlev - 1;
     const T* dc = nullptr;
     if (child_fresh) { if constexpr (sizeof(T) == 8) dc = C.dl1_64.p; else dc = C.dl1_32.p; }
     T* r = LV<T>::r(L);
@@ -326,8 +330,12 @@ static void cycle_level(Ctx& c, Hier& h, int32_t l, int gamma, bool fresh, bool 
     else residual32(s, L.A, x, b, r);
     if (prof) prof_mark(c, h, 1);
     restrict_agg<T>(s, L.nc, L.agg_ptr.p, L.agg_mem.p, l == 0 ? LV<T>::pv(L) : nullptr, r,
-                    LV<T>::b(C), X<T>(C), dc);
-    for (int g = 0; g < gamma; ++g) cycle_level<T>(c, h, l + 1, gamma, child_fresh && g == 0, g == 0);
+                    LV<T>::b(C), child_dense ? nullptr : X<T>(C), dc);
+    if (child_dense)
+        tail_gemv<T>(s, C.n, h.tail_ld, reinterpret_cast<const T*>(h.tail_op[gamma - 1].p), LV<T>::b(C),
+                     LV<T>::x(C), false);
+    else
+        for (int g = 0; g < gamma; ++g) cycle_level<T>(c, h, l + 1, gamma, child_fresh && g == 0, g == 0);
     prolong_add<T>(s, L.n, L.agg.p, l == 0 ? LV<T>::pv(L) : nullptr, X<T>(C), x);
     for (int32_t k = 0; k < c.p.nu_post; ++k) smooth<T>(c, L, b, X<T>(L), false);
 }
@@ -367,8 +375,10 @@ static void ensure_tail_op(Ctx& c, Hier& h, int gamma) {
     int dev = 0, nsm = 0;
     PC_CUDA(cudaGetDevice(&dev));
     PC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    h.tail_visits[k] = h.lt >= 1 ? gamma : 1;
     tail_operator<T>(c.stream, reinterpret_cast<const TailLevel<T>*>(h.tail.p), n, h.lt, h.nlev, gamma,
-                     c.p.nu_pre, c.p.nu_post, h.Xinv.p, reinterpret_cast<T*>(h.tail_op[k].p), h.tail_ld, nsm);
+                     c.p.nu_pre, c.p.nu_post, h.Xinv.p, reinterpret_cast<T*>(h.tail_op[k].p), h.tail_ld, nsm,
+                     h.tail_visits[k]);
 }
 
 static void run_body(Ctx& c, Hier& h, int kind) {

@@ -50,6 +50,12 @@ inline int sparse_grid(int64_t rows, int lpr, int block = kBlock) {
 // r = b - A x; when partial != null, block b writes sum of r_i^2 of its rows.
 // With dl1 given the launch is one l1-Jacobi sweep instead: r receives the new
 // iterate x_i + (b_i - sum_j a_ij x_j) / dl1_i (x is not written).
+// A lane's first kPre entries of its row (column, value) and the row's dl1 are
+// hierarchy data, loaded ahead of pdl_wait(); after it only x and b are read,
+// so a cycle launch's dependent chain starts at the x gathers. A lane adds its
+// entries in the same order either way.
+constexpr int kPre = 2;
+
 template <class T, int LPR>
 __global__ void __launch_bounds__(kBlock) k_residual(int n, const int* __restrict__ rowptr,
                                                      const int* __restrict__ col,
@@ -64,15 +70,39 @@ __global__ void __launch_bounds__(kBlock) k_residual(int n, const int* __restric
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double acc2 = 0.0;
+    int64_t row0 = warp * RPW;
+    // this group's first row: its hierarchy data before the wait
+    int beg = 0, end = 0;
+    int pc[kPre];
+    T pv[kPre];
+    T dr = 1;
+    auto prefetch = [&](int64_t row) {
+        beg = end = 0;
+        dr = 1;
+        if (row < n) {
+            beg = __ldg(rowptr + row);
+            end = __ldg(rowptr + row + 1);
+            if (dl1 && sub == 0) dr = __ldg(dl1 + row);
+        }
+#pragma unroll
+        for (int q = 0; q < kPre; ++q) {
+            const int k = beg + sub + q * LPR;
+            pc[q] = k < end ? __ldg(col + k) : 0;
+            pv[q] = k < end ? __ldg(val + k) : T(0);
+        }
+    };
+    prefetch(row0 + grp);
     pdl_wait();
     pdl_trigger();
-    for (int64_t row0 = warp * RPW; row0 < n; row0 += nwarps * RPW) {
-        int64_t row = row0 + grp;
-        T s = 0, xr = 0, dr = 1;
+    for (; row0 < n; row0 += nwarps * RPW) {
+        const int64_t row = row0 + grp;
+        T s = 0, xr = 0;
         if (row < n) {
-            if (dl1 && sub == 0) { xr = x[row]; dr = __ldg(dl1 + row); }   // loaded ahead of the sum
-            int beg = __ldg(rowptr + row), end = __ldg(rowptr + row + 1);
-            for (int k = beg + sub; k < end; k += LPR) s = fma_t(__ldg(val + k), __ldg(x + __ldg(col + k)), s);
+            if (dl1 && sub == 0) xr = x[row];
+#pragma unroll
+            for (int q = 0; q < kPre; ++q)
+                if (beg + sub + q * LPR < end) s = fma_t(pv[q], __ldg(x + pc[q]), s);
+            for (int k = beg + sub + kPre * LPR; k < end; k += LPR) s = fma_t(__ldg(val + k), __ldg(x + __ldg(col + k)), s);
         }
         s = group_sum<LPR>(s);
         if (sub == 0 && row < n) {
@@ -81,6 +111,7 @@ __global__ void __launch_bounds__(kBlock) k_residual(int n, const int* __restric
             else r[row] = rr;
             acc2 += (double)rr * (double)rr;
         }
+        if (row0 + nwarps * RPW < n) prefetch(row0 + nwarps * RPW + grp);
     }
     if (partial) {
         __shared__ double ws[kBlock / 32];
@@ -175,28 +206,52 @@ template <class T>
 __global__ void k_restrict(int nc, const int* __restrict__ agg_ptr, const int* __restrict__ mem,
                            const T* __restrict__ pval, const T* __restrict__ r, T* __restrict__ bc,
                            T* __restrict__ xc, const T* __restrict__ dc) {
+    // the aggregate's first two members and their p are hierarchy data, read
+    // ahead of the wait (aggregates of paths are mostly pairs)
+    const int stride = gridDim.x * blockDim.x;
+    int I = blockIdx.x * blockDim.x + threadIdx.x;
+    int beg = 0, end = 0, u0 = 0, u1 = 0;
+    T p0 = 1, p1 = 1;
+    auto prefetch = [&](int J) {
+        if (J >= nc) return;
+        beg = __ldg(agg_ptr + J);
+        end = __ldg(agg_ptr + J + 1);
+        u0 = beg < end ? __ldg(mem + beg) : 0;
+        u1 = beg + 1 < end ? __ldg(mem + beg + 1) : u0;
+        if (pval) { p0 = __ldg(pval + u0); p1 = __ldg(pval + u1); }
+    };
+    prefetch(I);
     pdl_wait();
     pdl_trigger();
-    for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < nc; I += gridDim.x * blockDim.x) {
+    for (; I < nc; I += stride) {
         T s = 0;
-        int beg = __ldg(agg_ptr + I), end = __ldg(agg_ptr + I + 1);
-        for (int t = beg; t < end; ++t) {
+        if (beg < end) s += pval ? p0 * __ldg(r + u0) : __ldg(r + u0);
+        if (beg + 1 < end) s += pval ? p1 * __ldg(r + u1) : __ldg(r + u1);
+        for (int t = beg + 2; t < end; ++t) {
             int u = __ldg(mem + t);
             s += pval ? __ldg(pval + u) * __ldg(r + u) : __ldg(r + u);
         }
         bc[I] = s;
         if (xc) xc[I] = dc ? s / __ldg(dc + I) : T(0);
+        prefetch(I + stride);
     }
 }
 
 template <class T>
 __global__ void k_prolong(int n, const int* __restrict__ agg, const T* __restrict__ pval,
                           const T* __restrict__ xc, T* __restrict__ x) {
+    // agg and p at the row are hierarchy data, read ahead of the wait
+    const int stride = gridDim.x * blockDim.x;
+    int u = blockIdx.x * blockDim.x + threadIdx.x;
+    int a = 0;
+    T p = 1;
+    if (u < n) { a = __ldg(agg + u); if (pval) p = __ldg(pval + u); }
     pdl_wait();
     pdl_trigger();
-    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
-        T c = __ldg(xc + __ldg(agg + u));
-        x[u] += pval ? __ldg(pval + u) * c : c;
+    for (; u < n; u += stride) {
+        T c = __ldg(xc + a);
+        x[u] += pval ? p * c : c;
+        if (u + stride < n) { a = __ldg(agg + u + stride); if (pval) p = __ldg(pval + u + stride); }
     }
 }
 

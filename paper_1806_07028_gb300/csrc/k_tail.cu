@@ -263,11 +263,14 @@ __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kTailThreads)
 // matrix N is the visit applied to the unit vector e_j. Each block takes
 // columns j = blockIdx.x, blockIdx.x + gridDim.x, ... and runs the same state
 // machine as the cluster kernel on one block, with every level's x, b and r in
-// its shared memory; N is stored row-major with row stride ld.
+// its shared memory; N is stored row-major with row stride ld. With visits > 1
+// the column is that many consecutive visits, each continuing from the last
+// one's x (a W-cycle's parent visits its child twice with the same b: the two
+// visits are one linear map, applied by one product instead of two).
 template <class T>
 __global__ void __launch_bounds__(kTailThreads, 1)
     k_tail_columns(const TailLevel<T>* __restrict__ lvg, int l0, int L, int gamma, int nu_pre,
-                   int nu_post, const double* __restrict__ Xinv, T* __restrict__ Nout, int ld) {
+                   int nu_post, const double* __restrict__ Xinv, T* __restrict__ Nout, int ld, int visits) {
     extern __shared__ __align__(16) unsigned char dyn[];
     __shared__ TailLevel<T> lvs[kMaxLevels];
     if (threadIdx.x == 0) {
@@ -290,7 +293,7 @@ __global__ void __launch_bounds__(kTailThreads, 1)
             x[i] = T(0);
         }
         __syncthreads();
-        tail_body<T, 1, true>(lvs, l0, L, gamma, nu_pre, nu_post, Xinv, 0);
+        for (int v = 0; v < visits; ++v) tail_body<T, 1, true>(lvs, l0, L, gamma, nu_pre, nu_post, Xinv, 0);
         for (int i = threadIdx.x; i < m; i += kTailThreads) Nout[(size_t)i * ld + j] = x[i];
         __syncthreads();
     }
@@ -350,13 +353,13 @@ bool tail_operator_fits(const int* n, int l0, int L) {
 
 template <class T>
 void tail_operator(cudaStream_t s, const TailLevel<T>* lv, const int* n, int l0, int L, int gamma,
-                   int nu_pre, int nu_post, const double* Xinv, T* Nout, int ld, int nsm) {
+                   int nu_pre, int nu_post, const double* Xinv, T* Nout, int ld, int nsm, int visits) {
     const size_t dyn = tail_operator_smem<T>(n, l0, L);
     if (!tail_operator_fits<T>(n, l0, L)) fail(PCAMG_ERR_INVALID, "tail operator: levels exceed shared memory");
     PC_CUDA(cudaFuncSetAttribute(k_tail_columns<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     const int m = n[l0];
     const int grid = std::max(1, std::min(m, nsm));
-    k_tail_columns<T><<<grid, kTailThreads, dyn, s>>>(lv, l0, L, gamma, nu_pre, nu_post, Xinv, Nout, ld); ::pc::count_launches(1);
+    k_tail_columns<T><<<grid, kTailThreads, dyn, s>>>(lv, l0, L, gamma, nu_pre, nu_post, Xinv, Nout, ld, visits); ::pc::count_launches(1);
     PC_LAUNCH("tail_operator");
 }
 
@@ -371,8 +374,8 @@ template size_t tail_operator_smem<float>(const int*, int, int);
 template size_t tail_operator_smem<double>(const int*, int, int);
 template bool tail_operator_fits<float>(const int*, int, int);
 template bool tail_operator_fits<double>(const int*, int, int);
-template void tail_operator<float>(cudaStream_t, const TailLevel<float>*, const int*, int, int, int, int, int, const double*, float*, int, int);
-template void tail_operator<double>(cudaStream_t, const TailLevel<double>*, const int*, int, int, int, int, int, const double*, double*, int, int);
+template void tail_operator<float>(cudaStream_t, const TailLevel<float>*, const int*, int, int, int, int, int, const double*, float*, int, int, int);
+template void tail_operator<double>(cudaStream_t, const TailLevel<double>*, const int*, int, int, int, int, int, const double*, double*, int, int, int);
 template void tail_gemv<float>(cudaStream_t, int, int, const float*, const float*, float*, bool);
 template void tail_gemv<double>(cudaStream_t, int, int, const double*, const double*, double*, bool);
 

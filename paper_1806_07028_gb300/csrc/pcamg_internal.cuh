@@ -220,13 +220,14 @@ struct TailLevel {
 template <class T>
 void tail_cycle(cudaStream_t s, const TailLevel<T>* lv, int l0, int L, int gamma, int nu_pre,
                 int nu_post, const double* Xinv, int fresh);
-// The tail's operator N (x = N b for one visit from a zero start), formed
-// column by column; n[l] = unknowns of level l; N row-major, row stride ld.
+// The tail's operator N (x = N b for `visits` consecutive visits, the first
+// from a zero start), formed column by column; n[l] = unknowns of level l; N
+// row-major, row stride ld.
 template <class T>
 bool tail_operator_fits(const int* n, int l0, int L);
 template <class T>
 void tail_operator(cudaStream_t s, const TailLevel<T>* lv, const int* n, int l0, int L, int gamma,
-                   int nu_pre, int nu_post, const double* Xinv, T* Nout, int ld, int nsm);
+                   int nu_pre, int nu_post, const double* Xinv, T* Nout, int ld, int nsm, int visits);
 // x = N v, or x += N v (accum)
 template <class T>
 void tail_gemv(cudaStream_t s, int m, int ld, const T* Nm, const T* v, T* x, bool accum);
@@ -244,6 +245,9 @@ struct Hier {
     // params.tail_dense selects it; row-major m x tail_ld, m = lev[lt].n
     DBuf<unsigned char> tail_op[2];
     bool tail_op_tried[2] = {false, false};
+    // visits of the tail's first level that one product with tail_op[k] stands
+    // for: gamma when the parent (level lt - 1) applies it, 1 when lt = 0
+    int tail_visits[2] = {1, 1};
     int32_t tail_ld = 0;
     // CUDA graphs of the cycle: 0 V-cycle from zero, 1 W-cycle from zero,
     // 2 V-cycle continuing from the finest level's current x
