@@ -279,6 +279,17 @@ PCAMG_API pcamg_status pcamg_setup(pcamg_handle* out, const pcamg_params* p, int
                 permute_rows<float>(*c, n, c->colour_rows0.p, c->rowptr.p, c->col.p, c->val.p, p2, c2,
                                     c->gs_val0_32);
             }
+            // the cycles then keep the finest level in colour order, unless it
+            // joins the coarse tail (which works in row order): columns of the
+            // copy become positions, so a colour's rows read b and write x
+            // contiguously and gather their neighbours by position
+            if (c->p.tail_rows == 0 || n > c->p.tail_rows / 2) {
+                c->iperm0.alloc(c->mem, n);
+                invert_perm(c->stream, n, c->colour_rows0.p, c->iperm0.p);
+                map_index(c->stream, nnz, c->iperm0.p, c->gs_col0.p, c->gs_col0.p);
+                mark_diagonal(c->stream, n, c->gs_ptr0.p, c->gs_col0.p);
+                c->perm0 = true;
+            }
         }
         if (c->p.start == PCAMG_START_MWM) {
             c->hist.push_back(build_hierarchy_mwm(*c));

@@ -188,14 +188,14 @@ struct LV<double> {
     static double* x(Level& L) { return L.x64v; }
     static double* b(Level& L) { return L.b64v; }
     static double* r(Level& L) { return L.r64v; }
-    static const double* pv(Level& L) { return L.pval.p; }
+    static const double* pv(Level& L) { return L.perm ? L.pvalp.p : L.pval.p; }
 };
 template <>
 struct LV<float> {
     static float* x(Level& L) { return L.x32v; }
     static float* b(Level& L) { return L.b32v; }
     static float* r(Level& L) { return L.r32v; }
-    static const float* pv(Level& L) { return L.pval32.p; }
+    static const float* pv(Level& L) { return L.perm ? L.pvalp32.p : L.pval32.p; }
 };
 
 // The buffer that holds level L's iterate now, and the other one (l1-Jacobi
@@ -229,7 +229,7 @@ static void smooth(Ctx& c, Level& L, const T* b, T* x, bool forward) {
     for (int32_t t = 0; t < L.ncolour; ++t) {
         int32_t k = forward ? t : L.ncolour - 1 - t;
         int32_t beg = L.h_colour_ptr[k], end = L.h_colour_ptr[k + 1];
-        if (pv) gs_colour_perm<T>(c.stream, beg, end, L.colour_rows_v, L.gs_ptr_v, L.gs_col_v, pv, b, x);
+        if (pv) gs_colour_perm<T>(c.stream, beg, end, L.perm ? nullptr : L.colour_rows_v, L.gs_ptr_v, L.gs_col_v, pv, b, x);
         else gs_colour<T>(c.stream, L.A, L.colour_rows_v + beg, end - beg, b, x);
     }
 }
@@ -326,17 +326,18 @@ static void cycle_level(Ctx& c, Hier& h, int32_t l, int gamma, bool fresh, bool 
     T* r = LV<T>::r(L);
     const bool prof = l == 0 && gamma == 1 && (c.p.profile & 2);
     if (prof) prof_mark(c, h, 0);
-    if constexpr (sizeof(T) == 8) residual64(s, L.A, x, b, r, nullptr, nullptr);
-    else residual32(s, L.A, x, b, r);
+    const Csr& A = L.perm ? L.Ap : L.A;
+    if constexpr (sizeof(T) == 8) residual64(s, A, x, b, r, nullptr, nullptr);
+    else residual32(s, A, x, b, r);
     if (prof) prof_mark(c, h, 1);
-    restrict_agg<T>(s, L.nc, L.agg_ptr.p, L.agg_mem.p, l == 0 ? LV<T>::pv(L) : nullptr, r,
+    restrict_agg<T>(s, L.nc, L.agg_ptr.p, L.perm ? L.memp.p : L.agg_mem.p, l == 0 ? LV<T>::pv(L) : nullptr, r,
                     LV<T>::b(C), child_dense ? nullptr : X<T>(C), dc);
     if (child_dense)
         tail_gemv<T>(s, C.n, h.tail_ld, reinterpret_cast<const T*>(h.tail_op[gamma - 1].p), LV<T>::b(C),
                      LV<T>::x(C), false);
     else
         for (int g = 0; g < gamma; ++g) cycle_level<T>(c, h, l + 1, gamma, child_fresh && g == 0, g == 0);
-    prolong_add<T>(s, L.n, L.agg.p, l == 0 ? LV<T>::pv(L) : nullptr, X<T>(C), x);
+    prolong_add<T>(s, L.n, L.perm ? L.aggp.p : L.agg.p, l == 0 ? LV<T>::pv(L) : nullptr, X<T>(C), x);
     for (int32_t k = 0; k < c.p.nu_post; ++k) smooth<T>(c, L, b, X<T>(L), false);
 }
 
@@ -421,6 +422,27 @@ static void run_body(Ctx& c, Hier& h, int kind) {
     count_launches(h.graph_kernels[kind]);
 }
 
+// Vectors into and out of the finest level's cycle vectors: scaled to float
+// (FP32 cycles) and, when the finest level is kept in colour order, gathered
+// into it (position t holds row colour_rows0[t]) and back (row u from
+// position iperm0[u]).
+static void to_cycle_f32(Ctx& c, Level& L0, const double* r, float* b) {
+    if (L0.perm) gather_scaled_f32(c.stream, c.n, c.colour_rows0.p, r, slot(c, S_INV), b);
+    else cast_scaled_f32(c.stream, c.n, r, slot(c, S_INV), b);
+}
+static void from_cycle_f32(Ctx& c, Level& L0, const float* x, double* out) {
+    if (L0.perm) gather_set_scaled_f32(c.stream, c.n, c.iperm0.p, x, slot(c, S_SCALE), out);
+    else set_scaled_f32(c.stream, c.n, x, slot(c, S_SCALE), out);
+}
+static void to_cycle_f64(Ctx& c, Level& L0, const double* r, double* b) {
+    if (L0.perm) gather<double>(c.stream, c.n, c.colour_rows0.p, r, b);
+    else copy(c.stream, c.n, r, b);
+}
+static void from_cycle_f64(Ctx& c, Level& L0, const double* x, double* out) {
+    if (L0.perm) gather<double>(c.stream, c.n, c.iperm0.p, x, out);
+    else copy(c.stream, c.n, x, out);
+}
+
 // out = B r, the correction of one cycle from a zero start
 void cycle(Ctx& c, Hier& h, int gamma, const double* r, double* out) {
     cudaStream_t s = c.stream;
@@ -437,13 +459,13 @@ void cycle(Ctx& c, Hier& h, int gamma, const double* r, double* out) {
             scalar_ops(s, SOP_SQRT, slot(c, 0), S_T0, 0, S_SCALE);
             scalar_ops(s, SOP_INV, slot(c, 0), S_SCALE, 0, S_INV);
         }
-        cast_scaled_f32(s, c.n, r, slot(c, S_INV), L0.b32v);
+        to_cycle_f32(c, L0, r, L0.b32v);
         run_body(c, h, gamma - 1);
-        set_scaled_f32(s, c.n, L0.x32v, slot(c, S_SCALE), out);
+        from_cycle_f32(c, L0, L0.x32v, out);
     } else {
-        copy(s, c.n, r, L0.b64v);
+        to_cycle_f64(c, L0, r, L0.b64v);
         run_body(c, h, gamma - 1);
-        copy(s, c.n, L0.x64v, out);
+        from_cycle_f64(c, L0, L0.x64v, out);
     }
 }
 
@@ -477,10 +499,10 @@ static void composite(Ctx& c, const double* r, double* z) {
             scalar_ops(s, SOP_SQRT, slot(c, 0), S_T0, 0, S_SCALE);
             scalar_ops(s, SOP_INV, slot(c, 0), S_SCALE, 0, S_INV);
         }
-        cast_scaled_f32(s, c.n, r, slot(c, S_INV), L0.b32v);
+        to_cycle_f32(c, L0, r, L0.b32v);
         PC_CUDA(cudaMemsetAsync(L0.x32v, 0, sizeof(float) * c.n, s));
     } else {
-        copy(s, c.n, r, L0.b64v);
+        to_cycle_f64(c, L0, r, L0.b64v);
         PC_CUDA(cudaMemsetAsync(L0.x64v, 0, sizeof(double) * c.n, s));
     }
     for (int32_t k = 0; k < 2 * re; ++k) {
@@ -488,8 +510,8 @@ static void composite(Ctx& c, const double* r, double* z) {
         c.ncycles += 1;
         run_body(c, *c.hist[j], 2);
     }
-    if (f32) set_scaled_f32(s, c.n, L0.x32v, slot(c, S_SCALE), z);
-    else copy(s, c.n, L0.x64v, z);
+    if (f32) from_cycle_f32(c, L0, L0.x32v, z);
+    else from_cycle_f64(c, L0, L0.x64v, z);
 }
 
 // ---------------------------------------------------------------- residual with profiling
@@ -572,16 +594,23 @@ void start_vector(Ctx& c, double* e) {
     Csr A;
     A.n = c.n; A.nnz = c.nnz; A.rowptr = c.rowptr.p; A.col = c.col.p; A.val = c.val.p;
     A.lpr = lanes_per_row(c.n, c.nnz);
+    // with the finest level in colour order the sweeps run on e in that order
+    double* ep = e;
+    if (c.perm0 && c.p.relax_sweeps > 0) {
+        ep = (e == c.w_q.p) ? c.w_p.p : c.w_q.p;
+        gather<double>(s, c.n, c.colour_rows0.p, e, ep);
+    }
     for (int32_t k = 0; k < c.p.relax_sweeps; ++k) {
         for (int32_t t = 0; t < c.ncolour0; ++t) {
             int32_t beg = c.h_colour_ptr0[t], end = c.h_colour_ptr0[t + 1];
             if (c.gs_val0_64.p)
-                gs_colour_perm<double>(s, beg, end, c.colour_rows0.p, c.gs_ptr0.p, c.gs_col0.p,
-                                       c.gs_val0_64.p, c.w_t1.p, e);
+                gs_colour_perm<double>(s, beg, end, c.perm0 ? nullptr : c.colour_rows0.p, c.gs_ptr0.p,
+                                       c.gs_col0.p, c.gs_val0_64.p, c.w_t1.p, ep);
             else
                 gs_colour<double>(s, A, c.colour_rows0.p + beg, end - beg, c.w_t1.p, e);
         }
     }
+    if (ep != e) gather<double>(s, c.n, c.iperm0.p, ep, e);
     normalise_orth(c, e, e);
 }
 

@@ -166,6 +166,27 @@ static void finish_hierarchy(Ctx& c, Hier& hh, bool boolean_chain) {
         L.gs_ptr_v = L.gs_ptr.p;
         L.gs_col_v = L.gs_col.p;
     }
+    // the finest level in colour order (the context keeps its matrix that way):
+    // restate this hierarchy's level-0 transfer data by position
+    Level& L0 = h->lev[0];
+    if (c.perm0 && nlev > 1 && h->lt >= 1) {
+        L0.perm = true;
+        L0.Ap = make_csr(L0, c.n, c.nnz, c.gs_ptr0.p, c.gs_col0.p, c.gs_val0_64.p, f32 ? c.gs_val0_32.p : nullptr);
+        L0.Ap.dmark = true;
+        L0.aggp.alloc(c.mem, L0.n);
+        gather<int32_t>(c.stream, L0.n, c.colour_rows0.p, L0.agg.p, L0.aggp.p);
+        L0.memp.alloc(c.mem, L0.n);
+        map_index(c.stream, L0.n, c.iperm0.p, L0.agg_mem.p, L0.memp.p);
+        if (L0.pval.p) {
+            if (f32) {
+                L0.pvalp32.alloc(c.mem, L0.n);
+                gather<float>(c.stream, L0.n, c.colour_rows0.p, L0.pval32.p, L0.pvalp32.p);
+            } else {
+                L0.pvalp.alloc(c.mem, L0.n);
+                gather<double>(c.stream, L0.n, c.colour_rows0.p, L0.pval.p, L0.pvalp.p);
+            }
+        }
+    }
 }
 
 Hier* build_hierarchy(Ctx& c, const double* e) {

@@ -319,22 +319,38 @@ __device__ __forceinline__ void load_chunk(int c0, int c1, const int* __restrict
 
 // Stage entries [c0, c1) held in R: gather x_col(k) (ordinary loads: the GS
 // kernel writes x) and store value and x (FP64) or their product (FP32), and
-// the column (GS) in shared memory.
-template <class T, bool KEEP_COL>
+// the column (KEEP_COL, GS on a row list) in shared memory.
+// DM: diagonal entries are marked (column ~row) and the rows are in place. A
+// residual (GS = false) decodes the column; a Gauss-Seidel colour (GS = true)
+// stages a zero contribution for the diagonal entry, gathers nothing for it
+// and keeps its value in dsm[row - r0] (r0 = the tile's first row), so a row's
+// sum is its off-diagonal terms in CSR order, as without the mark.
+template <class T, bool KEEP_COL, bool DM = false, bool GS = false>
 __device__ __forceinline__ void stage_regs(int c0, int c1, const ChunkRegs<T>& R, const T* x, T* av, T* xv,
-                                           int* pc) {
+                                           int* pc, T* dsm = nullptr, int r0 = 0) {
     T xg[kUnroll<T>];
 #pragma unroll
     for (int u = 0; u < kUnroll<T>; ++u) {
         const int k = c0 + threadIdx.x + u * kStreamRows;
-        xg[u] = (k < c1) ? x[R.cj[u]] : T(0);
+        int j = R.cj[u];
+        bool on = k < c1;
+        if (DM) {
+            if (GS) on = on && j >= 0;
+            else j = j < 0 ? ~j : j;
+        }
+        xg[u] = on ? x[j] : T(0);
     }
 #pragma unroll
     for (int u = 0; u < kUnroll<T>; ++u) {
         const int k = c0 + threadIdx.x + u * kStreamRows;
         if (k < c1) {
-            if constexpr (sizeof(T) == 8) { av[k - c0] = R.cv[u]; xv[k - c0] = xg[u]; }
-            else av[k - c0] = R.cv[u] * xg[u];
+            T a = R.cv[u];
+            if (DM && GS && R.cj[u] < 0) {
+                dsm[~R.cj[u] - r0] = a;
+                a = T(0);
+            }
+            if constexpr (sizeof(T) == 8) { av[k - c0] = a; xv[k - c0] = xg[u]; }
+            else av[k - c0] = a * xg[u];
             if (KEEP_COL) pc[k - c0] = R.cj[u];
         }
     }
@@ -392,22 +408,26 @@ __device__ __forceinline__ TileMeta<T> tile_meta(int t0, int tend, const int* __
 //   PERM = false: rows t of [0, n) (residual r = b - A x, optional ||r||^2);
 //   PERM = true:  permuted rows rows[t] of [beg, end) of one colour, Gauss-Seidel
 //                 x_row = (b_row - sum_{j != row} a x_j) / a_row,row.
-template <class T, bool PERM, bool NORM, bool JAC = false>
+//   DM:           diagonal entries marked (column ~row), rows in place (rows is
+//                 not read); the colour-ordered finest level.
+template <class T, bool PERM, bool NORM, bool JAC = false, bool DM = false>
 __device__ __forceinline__ void stream_tiles(int beg, int end, int tpb, const int* __restrict__ rows,
                                              const int* __restrict__ ptr, const int* __restrict__ col,
                                              const T* __restrict__ val, const T* x_in, const T* __restrict__ b,
                                              T* out, double* __restrict__ partial,
                                              const T* __restrict__ dl1 = nullptr) {
+    constexpr bool KEEP = PERM && !DM;   // GS on a row list finds the diagonal by its column
     __shared__ T av[kStreamChunk<T>];
     __shared__ T xv[kXv<T>];
-    __shared__ int pc[PERM ? kStreamChunk<T> : 1];
+    __shared__ int pc[KEEP ? kStreamChunk<T> : 1];
+    __shared__ T dsm[PERM && DM ? kStreamRows : 1];
     const int ntiles = (end - beg + kStreamRows - 1) / kStreamRows;
     const int tfirst = blockIdx.x * tpb;
     const int tstop = min(ntiles, tfirst + tpb);
     double rr2 = 0.0;
     constexpr bool kPdl = !NORM;
     if (tfirst < tstop) {
-        TileMeta<T> M = tile_meta<T, PERM, !kPdl>(beg + tfirst * kStreamRows, end, ptr, rows, b);
+        TileMeta<T> M = tile_meta<T, PERM && !DM, !kPdl>(beg + tfirst * kStreamRows, end, ptr, rows, b);
         ChunkRegs<T> R;
         load_chunk<T>(M.tb, min(M.tb + kStreamChunk<T>, M.te), col, val, R);
         if (kPdl) {
@@ -423,20 +443,23 @@ __device__ __forceinline__ void stream_tiles(int beg, int end, int tpb, const in
             T s = 0, d = 0;
             for (int c0 = M.tb;;) {
                 const int c1 = min(c0 + kStreamChunk<T>, M.te);
-                stage_regs<T, PERM>(c0, c1, R, x_in, av, xv, pc);
+                stage_regs<T, KEEP, DM, PERM>(c0, c1, R, x_in, av, xv, pc, dsm, beg + t * kStreamRows);
                 __syncthreads();
                 // R is free again: start the loads the next round needs
                 if (c1 < M.te) {
                     load_chunk<T>(c1, min(c1 + kStreamChunk<T>, M.te), col, val, R);
                 } else if (t + 1 < tstop) {
-                    Mn = tile_meta<T, PERM, true, JAC>(beg + (t + 1) * kStreamRows, end, ptr, rows, b, x_in, dl1);
+                    Mn = tile_meta<T, PERM && !DM, true, JAC>(beg + (t + 1) * kStreamRows, end, ptr, rows, b, x_in, dl1);
                     load_chunk<T>(Mn.tb, min(Mn.tb + kStreamChunk<T>, Mn.te), col, val, R);
                 }
                 const int kb = max(M.rb, c0), ke = min(M.re, c1);
                 for (int k = kb; k < ke; ++k) {
-                    if (PERM && pc[k - c0] == M.row) d = (sizeof(T) == 8) ? av[k - c0] : __ldg(val + k);
+                    if (KEEP && pc[k - c0] == M.row) d = (sizeof(T) == 8) ? av[k - c0] : __ldg(val + k);
                     else s = row_add<T>(av, xv, k - c0, s);
                 }
+                // the tile's diagonal values are all staged once its last chunk is
+                // (read before the barrier: the next tile overwrites them)
+                if (PERM && DM && c1 >= M.te && M.row >= 0) d = dsm[M.row - (beg + t * kStreamRows)];
                 __syncthreads();
                 if (c1 >= M.te) break;
                 c0 = c1;
@@ -476,11 +499,17 @@ __device__ __forceinline__ void stream_tiles(int beg, int end, int tpb, const in
 constexpr int kNormTiles = 4;
 template <class T>
 constexpr int kTilesPerBlock = sizeof(T) == 8 ? 2 : 1;
-constexpr int kGsTiles = 1;
+// Gauss-Seidel colours: two tiles per block (the second tile's loads overlap
+// the first's sums) at five resident blocks per SM in FP32 (the best of 1-4
+// tiles and 5-8 blocks measured on the 256^3 grid)
+constexpr int kGsTiles = 2;
+template <class T>
+constexpr int kGsMinBlocks = sizeof(T) == 8 ? 4 : 5;
 
 // r_i = b_i - sum_k a_k x_col(k) (fused multiply-adds left to right in FP64);
-// partial[block] = sum of r_i^2 of the block's rows when NORM
-template <class T, bool NORM>
+// partial[block] = sum of r_i^2 of the block's rows when NORM; DM: diagonal
+// entries marked (column ~i)
+template <class T, bool NORM, bool DM = false>
 __global__ void __launch_bounds__(kStreamRows) k_res_stream(int n, const int* __restrict__ rowptr,
                                                              const int* __restrict__ col,
                                                              const T* __restrict__ val,
@@ -488,8 +517,8 @@ __global__ void __launch_bounds__(kStreamRows) k_res_stream(int n, const int* __
                                                              const T* __restrict__ b,
                                                              T* __restrict__ r,
                                                              double* __restrict__ partial) {
-    stream_tiles<T, false, NORM>(0, n, NORM ? kNormTiles : kTilesPerBlock<T>, nullptr, rowptr, col, val, x, b, r,
-                                 partial);
+    stream_tiles<T, false, NORM, false, DM>(0, n, NORM ? kNormTiles : kTilesPerBlock<T>, nullptr, rowptr, col, val,
+                                            x, b, r, partial);
 }
 
 // One l1-Jacobi sweep into another buffer: xout_i = x_i + (b_i - sum_j a_ij x_j) / dl1_i
@@ -507,13 +536,23 @@ __global__ void __launch_bounds__(kStreamRows, 5) k_jac_stream(int n, const int*
 
 // One colour of Gauss-Seidel on the row-permuted copy (rows of a colour are
 // contiguous there): x_row = (b_row - sum_{j != row} a x_j) / a_row,row.
-template <class T>
-__global__ void __launch_bounds__(kStreamRows) k_gs_stream(int beg, int end, const int* __restrict__ rows,
-                                                            const int* __restrict__ pptr,
-                                                            const int* __restrict__ pcol,
-                                                            const T* __restrict__ pval,
-                                                            const T* __restrict__ b, T* __restrict__ x) {
-    stream_tiles<T, true, false>(beg, end, kGsTiles, rows, pptr, pcol, pval, x, b, x, nullptr);
+// DM: the vectors are in the copy's order (row = position, columns are
+// positions, the diagonal marked); otherwise rows[t] names the row.
+template <class T, bool DM>
+__global__ void __launch_bounds__(kStreamRows, kGsMinBlocks<T>) k_gs_stream(int beg, int end, const int* __restrict__ rows,
+                                                               const int* __restrict__ pptr,
+                                                               const int* __restrict__ pcol,
+                                                               const T* __restrict__ pval,
+                                                               const T* __restrict__ b, T* __restrict__ x) {
+    stream_tiles<T, true, false, false, DM>(beg, end, kGsTiles, rows, pptr, pcol, pval, x, b, x, nullptr);
+}
+
+// column of the diagonal entry of row i -> ~i (the rows' own columns are in
+// the same numbering as the rows)
+__global__ void k_mark_diag(int n, const int* __restrict__ ptr, int* __restrict__ col) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        for (int k = ptr[i]; k < ptr[i + 1]; ++k)
+            if (col[k] == i) col[k] = ~i;
 }
 
 template <class T>
@@ -580,6 +619,14 @@ bool use_stream(int32_t rows, int lpr) { return lpr <= 8 && rows >= kStreamMinRo
 
 void residual64(cudaStream_t s, const Csr& A, const double* x, const double* b, double* r,
                 double* partial, double* norm2) {
+    if (A.dmark) {   // the colour-ordered finest level (always large enough to stream)
+        if (norm2 || !use_stream(A.n, A.lpr)) fail(PCAMG_ERR_INVALID, "marked diagonal: streaming residual only");
+        const int gt = ((A.n + kStreamRows - 1) / kStreamRows + kTilesPerBlock<double> - 1) / kTilesPerBlock<double>;
+        launch(k_res_stream<double, false, true>, gt, kStreamRows, 0, s, A.n, A.rowptr, A.col, A.val, x, b, r,
+               (double*)nullptr);
+        PC_LAUNCH("residual64");
+        return;
+    }
     if (use_stream(A.n, A.lpr) || norm2) {
         int g = (A.n + kStreamRows - 1) / kStreamRows;
         if (norm2) {
@@ -637,10 +684,15 @@ void l1_diagonal(cudaStream_t s, int32_t n, const int32_t* rowptr, const double*
 }
 
 void residual32(cudaStream_t s, const Csr& A, const float* x, const float* b, float* r) {
+    if (A.dmark && !use_stream(A.n, A.lpr)) fail(PCAMG_ERR_INVALID, "marked diagonal: streaming residual only");
     if (use_stream(A.n, A.lpr)) {
         int g = ((A.n + kStreamRows - 1) / kStreamRows + kTilesPerBlock<float> - 1) / kTilesPerBlock<float>;
-        launch(k_res_stream<float, false>, g, kStreamRows, 0, s, A.n, A.rowptr, A.col, A.val32, x, b, r,
-               (double*)nullptr);
+        if (A.dmark)
+            launch(k_res_stream<float, false, true>, g, kStreamRows, 0, s, A.n, A.rowptr, A.col, A.val32, x, b, r,
+                   (double*)nullptr);
+        else
+            launch(k_res_stream<float, false>, g, kStreamRows, 0, s, A.n, A.rowptr, A.col, A.val32, x, b, r,
+                   (double*)nullptr);
     } else {
         int g = sparse_grid(A.n, A.lpr);
 #define CALL(L) launch(k_residual<float, L>, g, kBlock, 0, s, A.n, A.rowptr, A.col, A.val32, x, b, r, (double*)nullptr, (const float*)nullptr)
@@ -676,7 +728,8 @@ void gs_colour_perm(cudaStream_t s, int32_t beg, int32_t end, const int32_t* row
                     const int32_t* pcol, const T* pval, const T* b, T* x) {
     if (end <= beg) return;
     int g = ((end - beg + kStreamRows - 1) / kStreamRows + kGsTiles - 1) / kGsTiles;
-    launch(k_gs_stream<T>, g, kStreamRows, 0, s, beg, end, rows, pptr, pcol, pval, b, x);
+    if (rows) launch(k_gs_stream<T, false>, g, kStreamRows, 0, s, beg, end, rows, pptr, pcol, pval, b, x);
+    else launch(k_gs_stream<T, true>, g, kStreamRows, 0, s, beg, end, rows, pptr, pcol, pval, b, x);
     PC_LAUNCH("gs_colour_perm");
 }
 
@@ -694,6 +747,11 @@ void permute_rows(Ctx& c, int32_t n, const int32_t* rows, const int32_t* rowptr,
     pval.alloc(c.mem, nnz);
     k_perm_fill<T><<<simple_grid(n), kBlock, 0, s>>>(n, rows, rowptr, col, val, pptr.p, pcol.p, pval.p); ::pc::count_launches(1);
     PC_LAUNCH("permute_rows");
+}
+
+void mark_diagonal(cudaStream_t s, int32_t n, const int32_t* ptr, int32_t* col) {
+    k_mark_diag<<<simple_grid(n), kBlock, 0, s>>>(n, ptr, col); ::pc::count_launches(1);
+    PC_LAUNCH("mark_diagonal");
 }
 
 template <class T>

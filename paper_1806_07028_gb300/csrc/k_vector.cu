@@ -136,6 +136,40 @@ __global__ void k_add_scaled_f32(int64_t n, const float* __restrict__ c, const d
         x[i] += f * (double)c[i];
 }
 
+// gathers through an index: y_t = x_idx(t) (scaled and rounded to float, or
+// copied), for moving vectors between the row order and the finest level's
+// colour order; the writes are coalesced
+__global__ void k_gather_scaled_f32(int64_t n, const int* __restrict__ idx, const double* __restrict__ x,
+                                    const double* __restrict__ inv, float* __restrict__ y) {
+    const double f = inv ? *inv : 1.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (float)(x[__ldg(idx + i)] * f);
+}
+
+__global__ void k_gather_set_scaled_f32(int64_t n, const int* __restrict__ idx, const float* __restrict__ c,
+                                        const double* __restrict__ sc, double* __restrict__ x) {
+    const double f = *sc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = f * (double)c[__ldg(idx + i)];
+}
+
+template <class T>
+__global__ void k_gather(int64_t n, const int* __restrict__ idx, const T* __restrict__ x, T* __restrict__ y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = x[__ldg(idx + i)];
+}
+
+// inv[idx[t]] = t
+__global__ void k_invert_perm(int n, const int* __restrict__ idx, int* __restrict__ inv) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) inv[__ldg(idx + i)] = i;
+}
+
+// y[k] = map[x[k]] (indices renamed in place when y == x)
+__global__ void k_map_index(int64_t n, const int* __restrict__ map, const int* x, int* y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = __ldg(map + x[i]);
+}
+
 __global__ void k_set_scaled_f32(int64_t n, const float* __restrict__ c, const double* __restrict__ sc,
                                  double* __restrict__ x) {
     double f = *sc;
@@ -386,6 +420,31 @@ void add_scaled_f32(cudaStream_t s, int64_t n, const float* c, const double* sca
 void set_scaled_f32(cudaStream_t s, int64_t n, const float* c, const double* scale, double* x) {
     k_set_scaled_f32<<<grid_for((n + 3) / 4), kBlock, 0, s>>>(n, c, scale, x); ::pc::count_launches(1);
     PC_LAUNCH("set_scaled_f32");
+}
+void gather_scaled_f32(cudaStream_t s, int64_t n, const int32_t* idx, const double* x, const double* inv, float* y) {
+    k_gather_scaled_f32<<<grid_for(n), kBlock, 0, s>>>(n, idx, x, inv, y); ::pc::count_launches(1);
+    PC_LAUNCH("gather_scaled_f32");
+}
+void gather_set_scaled_f32(cudaStream_t s, int64_t n, const int32_t* idx, const float* c, const double* scale,
+                           double* x) {
+    k_gather_set_scaled_f32<<<grid_for(n), kBlock, 0, s>>>(n, idx, c, scale, x); ::pc::count_launches(1);
+    PC_LAUNCH("gather_set_scaled_f32");
+}
+template <class T>
+void gather(cudaStream_t s, int64_t n, const int32_t* idx, const T* x, T* y) {
+    k_gather<T><<<grid_for(n), kBlock, 0, s>>>(n, idx, x, y); ::pc::count_launches(1);
+    PC_LAUNCH("gather");
+}
+template void gather<double>(cudaStream_t, int64_t, const int32_t*, const double*, double*);
+template void gather<float>(cudaStream_t, int64_t, const int32_t*, const float*, float*);
+template void gather<int32_t>(cudaStream_t, int64_t, const int32_t*, const int32_t*, int32_t*);
+void invert_perm(cudaStream_t s, int32_t n, const int32_t* idx, int32_t* inv) {
+    k_invert_perm<<<grid_for(n), kBlock, 0, s>>>(n, idx, inv); ::pc::count_launches(1);
+    PC_LAUNCH("invert_perm");
+}
+void map_index(cudaStream_t s, int64_t n, const int32_t* map, const int32_t* x, int32_t* y) {
+    k_map_index<<<grid_for(n), kBlock, 0, s>>>(n, map, x, y); ::pc::count_launches(1);
+    PC_LAUNCH("map_index");
 }
 void cast_f64(cudaStream_t s, int64_t n, const float* x, double* y) {
     k_cast_f64<<<grid_for(n), kBlock, 0, s>>>(n, x, y); ::pc::count_launches(1);

@@ -150,6 +150,9 @@ struct Csr {
     const double* val = nullptr;
     const float* val32 = nullptr;
     int lpr = 8;  // lanes per row in the sparse kernels (power of two, 2..32)
+    // diagonal entries marked: row i stores its diagonal's column as ~i
+    // (negative); the streaming kernels decode it (the colour-ordered copy)
+    bool dmark = false;
 };
 int lanes_per_row(int32_t n, int64_t nnz);
 
@@ -203,6 +206,16 @@ struct Level {
     int32_t jac = 0;
     DBuf<double> dl1_64;
     DBuf<float> dl1_32;
+    // finest level in colour order (perm): the cycle's vectors are indexed by
+    // position t in the colour-grouped row order (row colour_rows0[t]); Ap is A
+    // in that order (the permuted copy with renumbered columns), and the
+    // transfer data are restated for it: aggp[t] = agg[row], memp = positions of
+    // agg_mem (same order), pvalp[t] = pval[row]
+    bool perm = false;
+    Csr Ap;
+    DBuf<int32_t> aggp, memp;
+    DBuf<double> pvalp;
+    DBuf<float> pvalp32;
 };
 
 // Level view used by the single-block coarse tail (k_tail.cu).
@@ -293,6 +306,10 @@ struct Ctx {
     DBuf<int32_t> gs_ptr0, gs_col0;   // row-permuted copy of A by colour
     DBuf<double> gs_val0_64;
     DBuf<float> gs_val0_32;
+    // perm0: the cycles keep the finest level in colour order; gs_col0 then
+    // holds positions (iperm0[column]) and iperm0[row] = position of the row
+    bool perm0 = false;
+    DBuf<int32_t> iperm0;
     std::vector<Hier*> hist;
     // driver work vectors (length n)
     DBuf<double> w_r, w_c, w_e, w_t1, w_t2, w_z, w_p, w_q, w_rold, w_eh, w_ein, w_cin;
@@ -341,6 +358,15 @@ void fill_i32(cudaStream_t s, int64_t n, int32_t v, int32_t* y);
 void cast_scaled_f32(cudaStream_t s, int64_t n, const double* x, const double* inv_scale, float* y);
 void add_scaled_f32(cudaStream_t s, int64_t n, const float* c, const double* scale, double* x);  // x += scale*c
 void set_scaled_f32(cudaStream_t s, int64_t n, const float* c, const double* scale, double* x);  // x = scale*c
+// y_t = (float)(x_idx(t) * inv); x_t = scale * c_idx(t); y_t = x_idx(t)
+void gather_scaled_f32(cudaStream_t s, int64_t n, const int32_t* idx, const double* x, const double* inv, float* y);
+void gather_set_scaled_f32(cudaStream_t s, int64_t n, const int32_t* idx, const float* c, const double* scale,
+                           double* x);
+template <class T>
+void gather(cudaStream_t s, int64_t n, const int32_t* idx, const T* x, T* y);
+void invert_perm(cudaStream_t s, int32_t n, const int32_t* idx, int32_t* inv);       // inv[idx[t]] = t
+void mark_diagonal(cudaStream_t s, int32_t n, const int32_t* ptr, int32_t* col);     // col == i -> ~i in row i
+void map_index(cudaStream_t s, int64_t n, const int32_t* map, const int32_t* x, int32_t* y);  // y = map[x]
 void cast_f32(cudaStream_t s, int64_t n, const double* x, float* y);
 void cast_f64(cudaStream_t s, int64_t n, const float* x, double* y);
 void philox_uniform(cudaStream_t s, uint64_t seed, int64_t n, double* out);

@@ -94,6 +94,28 @@ def test_fullsize_first_hierarchy(P, C2):
     s.close()
 
 
+def test_fullsize_cycles_and_start_match_oracle(P, C2):
+    # at this size the cycles keep the finest level in colour order (its
+    # colours fill the streaming smoother): the start vector's relaxation in
+    # that order, and V- and W-cycles through it, against the oracle
+    g = C2
+    s = P.Solver(g)
+    e_gpu = s.start_vector().cpu().numpy()
+    s.close()
+    e = O.start_vector(g)
+    assert np.linalg.norm(e_gpu - e) <= 1e-10 * np.linalg.norm(e)
+    h = O.Hierarchy(g, e)
+    r = I.rhs_normal(g.n, 6)
+    for gamma in (1, 2):
+        ref = h.vcycle(r) if gamma == 1 else h.wcycle(r)
+        for precision, tol in ((0, 1e-9), (1, 2e-4)):
+            s = P.Solver(g, params=P.default_params(precision=precision), e0=e)
+            for _ in range(2):   # capture, then replay
+                c = s.cycle(r, hist=0, gamma=gamma).cpu().numpy()
+                assert np.linalg.norm(c - ref) <= tol * np.linalg.norm(ref), (gamma, precision)
+            s.close()
+
+
 def test_fullsize_boolean_hierarchy_is_laplacian(P, C2):
     # with a boolean P_1 every coarse matrix is a weighted graph Laplacian:
     # symmetric, nonpositive off-diagonals, zero row sums
