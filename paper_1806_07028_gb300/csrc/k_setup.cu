@@ -46,6 +46,8 @@ struct CandSrc {
     const int* __restrict__ col;
     __device__ int nmem(int r) const { return rowptr[r + 1] - rowptr[r]; }
     __device__ int mem_row(int r, int t) const { return col[rowptr[r] + t]; }
+    __device__ int mbase(int r) const { return rowptr[r]; }
+    __device__ int mem_at(int base, int t) const { return col[base + t]; }
     __device__ int in_beg(int j) const { return rowptr[j]; }
     __device__ int in_end(int j) const { return rowptr[j + 1]; }
     __device__ void kv(int r, int, int k, uint32_t& key, double& v) const {
@@ -68,6 +70,8 @@ struct GalSrc {
     int drop_diag;
     __device__ int nmem(int r) const { return agg_ptr[r + 1] - agg_ptr[r]; }
     __device__ int mem_row(int r, int t) const { return mem[agg_ptr[r] + t]; }
+    __device__ int mbase(int r) const { return agg_ptr[r]; }
+    __device__ int mem_at(int base, int t) const { return mem[base + t]; }
     __device__ int in_beg(int u) const { return rowptr[u]; }
     __device__ int in_end(int u) const { return rowptr[u + 1]; }
     __device__ void kv(int r, int u, int k, uint32_t& key, double& v) const {
@@ -84,8 +88,9 @@ struct GalSrc {
 // the keys (bitonic, padded to a power of two), and the first lane of each run
 // of equal columns adds the run's values in contribution order. Rows with more
 // than kWarpMembers member rows or kWarpCap contributions are flagged for the
-// block kernels.
-constexpr int kWarpCap = 256;
+// block kernels. (128 keeps a warp's scratch at 2.8 KB, so the block's eight
+// warps fit eight times per SM; the rare longer rows take the block kernels.)
+constexpr int kWarpCap = 128;
 constexpr int kWarpMembers = 64;
 constexpr int kWarpsPerBlock = 8;
 
@@ -210,8 +215,10 @@ __device__ __forceinline__ void stage_sort_keys(int lane, int r, int nm, int tot
 // MODE 2: both at once -- count, flag, and write the row at tptr[r] of a
 //         temporary layout sized by each row's contribution count (compacted
 //         afterwards), so the sort-reduce runs once.
+// (eight blocks of eight warps per SM: the row's sort-reduce is a long chain
+// of dependent shuffles and compares, so resident warps are what hides it)
 template <class Src, int MODE>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_rowprod_warp(
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 8) k_rowprod_warp(
         int nrows, Src src, int* __restrict__ cnt, unsigned char* __restrict__ is_long,
         int* __restrict__ long_list, int* __restrict__ long_count, const int* __restrict__ optr,
         int* __restrict__ ocol, double* __restrict__ oval, const int64_t* __restrict__ tptr) {
@@ -223,16 +230,39 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_rowprod_warp(
     const bool narrow = nrows <= (1 << 24);   // every column fits 24 bits
     const int64_t gw = (int64_t)blockIdx.x * kWarpsPerBlock + wib;
     const int64_t nw = (int64_t)gridDim.x * kWarpsPerBlock;
+    // Software pipeline over the warp's rows r, r + nw, r + 2 nw, ...: each
+    // step issues the member range of the row three steps ahead, the member
+    // rows of the row two steps ahead and the entry ranges of the next row's
+    // member rows (lane t: member t < 32), each from data that arrived a step
+    // earlier, so a row's member data are in registers when its turn comes.
+    struct Stage {
+        int base = 0, nm = 0, mr = 0, mb = 0, len = 0;
+    };
+    auto s1 = [&](int64_t rr, Stage& q) {
+        q = Stage();
+        if (rr < nrows) { q.base = src.mbase((int)rr); q.nm = src.nmem((int)rr); }
+    };
+    auto s2 = [&](Stage& q) { if (lane < q.nm && lane < 32) q.mr = src.mem_at(q.base, lane); };
+    auto s3 = [&](Stage& q) {
+        if (lane < q.nm && lane < 32) { q.mb = src.in_beg(q.mr); q.len = src.in_end(q.mr) - q.mb; }
+    };
+    Stage p1, p2, p3;
+    s1(gw, p3); s2(p3); s3(p3);
+    s1(gw + nw, p2); s2(p2);
+    s1(gw + 2 * nw, p1);
     for (int64_t r64 = gw; r64 < nrows; r64 += nw) {
         const int r = (int)r64;
+        const Stage cur = p3;
+        p3 = p2; s3(p3);
+        p2 = p1; s2(p2);
+        s1(r64 + 3 * nw, p1);
         if (MODE == 1 && is_long[r]) continue;
-        const int nm = src.nmem(r);
+        const int nm = cur.nm;
         bool over = nm > kWarpMembers;
         int total = 0;
         if (!over) {
             // member rows and the prefix of their lengths
-            int len = 0, mr = 0, mb = 0;
-            if (lane < nm) { mr = src.mem_row(r, lane); mb = src.in_beg(mr); len = src.in_end(mr) - mb; }
+            const int len = cur.len, mr = cur.mr, mb = cur.mb;
             int inc = len;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -243,7 +273,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_rowprod_warp(
             if (lane < nm) { W.mpre[lane + 1] = inc; W.mrow[lane] = mr; W.mbeg[lane] = mb; }
             if (nm > 32) {
                 int len2 = 0, mr2 = 0, mb2 = 0;
-                if (lane + 32 < nm) { mr2 = src.mem_row(r, lane + 32); mb2 = src.in_beg(mr2); len2 = src.in_end(mr2) - mb2; }
+                if (lane + 32 < nm) { mr2 = src.mem_at(cur.base, lane + 32); mb2 = src.in_beg(mr2); len2 = src.in_end(mr2) - mb2; }
                 int inc2 = len2;
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) {
@@ -266,8 +296,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_rowprod_warp(
             else if (narrow && P == 128) stage_sort_keys<4, true>(lane, r, nm, total, src, W);
             else if (P == 32) stage_sort_keys<1, false>(lane, r, nm, total, src, W);
             else if (P == 64) stage_sort_keys<2, false>(lane, r, nm, total, src, W);
-            else if (P == 128) stage_sort_keys<4, false>(lane, r, nm, total, src, W);
-            else stage_sort_keys<8, false>(lane, r, nm, total, src, W);
+            else stage_sort_keys<4, false>(lane, r, nm, total, src, W);
             __syncwarp();
             // runs of equal columns
             int carry = 0;
