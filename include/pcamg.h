@@ -111,8 +111,9 @@ typedef struct {
     int32_t use_graphs;    /* capture each cycle in a CUDA graph and replay it */
     int32_t keep_setup;    /* keep covers and reweighted graphs for export */
     int32_t profile;       /* bit 0: time the FP64 fine-level residual of Alg. 5 with CUDA
-                              events; bit 1: time the finest-level residual inside every
-                              V-cycle (event-record nodes in the cycle graph) */
+                              events; bit 1: time the finest-level pre-smoothing sweep and
+                              residual inside every V-cycle (event-record nodes in the
+                              cycle graph) */
     int32_t tail_rows;     /* levels with at most this many unknowns (the finest level: at
                               most half as many) run inside one thread-block cluster per
                               cycle visit, or as their dense operator (0 = never) */
@@ -169,6 +170,12 @@ typedef struct {
     double cyc_ms;         /* summed event time of those launches */
     double cyc_bytes;      /* their algorithmic bytes: (4 + w) nnz + (4 + 3 w) n each,
                               w = 4 (FP32_IR) or 8 (FP64) */
+    /* the finest level's pre-smoothing sweep of every V-cycle (all colours of the
+       Gauss-Seidel sweep), timed the same way (params.profile bit 1) */
+    int64_t gs_sweeps;
+    double gs_ms;          /* summed event time of those sweeps */
+    double gs_bytes;       /* their algorithmic bytes, (4 + w) nnz + (4 + 3 w) n each: A,
+                              b, x written, and every x gathered once by the other colours */
 } pcamg_stats;
 
 /* Fill p with the defaults above. */

@@ -240,7 +240,7 @@ static void smooth(Ctx& c, Level& L, const T* b, T* x, bool forward) {
 // fresh pair of pool events before each replay; without graphs the pool events
 // are recorded on the stream directly. The pairs are resolved when the solve
 // ends (pcamg_stats.cyc_*).
-static constexpr size_t kMaxProfEvents = 1 << 16;   // pairs beyond this are not timed
+static constexpr size_t kMaxProfEvents = 1 << 16;   // events beyond this are not recorded (4 per V-cycle)
 
 static cudaEvent_t pool_event(Ctx& c) {
     if (c.cyc_used >= kMaxProfEvents) return nullptr;
@@ -268,10 +268,14 @@ static void prof_mark(Ctx& c, Hier& h, int k) {
     }
 }
 
+// events come in fours per V-cycle: pre-sweep start, end, residual start, end
 static void prof_resolve(Ctx& c) {
-    for (size_t i = 0; i + 1 < c.cyc_used; i += 2) {
+    for (size_t i = 0; i + 3 < c.cyc_used; i += 4) {
         float ms = 0.f;
         PC_CUDA(cudaEventElapsedTime(&ms, c.cyc_ev[i], c.cyc_ev[i + 1]));
+        c.gs_ms += ms;
+        c.gs_sweeps += 1;
+        PC_CUDA(cudaEventElapsedTime(&ms, c.cyc_ev[i + 2], c.cyc_ev[i + 3]));
         c.cyc_ms += ms;
         c.cyc_launches += 1;
     }
@@ -312,7 +316,10 @@ static void cycle_level(Ctx& c, Hier& h, int32_t l, int gamma, bool fresh, bool 
         return;
     }
     T* b = LV<T>::b(L);
+    const bool prof = l == 0 && gamma == 1 && (c.p.profile & 2);
+    if (prof) prof_mark(c, h, 0);
     for (int32_t k = fresh ? 1 : 0; k < c.p.nu_pre; ++k) smooth<T>(c, L, b, X<T>(L), true);
+    if (prof) prof_mark(c, h, 1);
     T* x = X<T>(L);
     Level& C = h.lev[l + 1];
     // the child is the tail levels as one dense operator standing for all
@@ -324,12 +331,11 @@ static void cycle_level(Ctx& c, Hier& h, int32_t l, int gamma, bool fresh, bool 
     const T* dc = nullptr;
     if (child_fresh) { if constexpr (sizeof(T) == 8) dc = C.dl1_64.p; else dc = C.dl1_32.p; }
     T* r = LV<T>::r(L);
-    const bool prof = l == 0 && gamma == 1 && (c.p.profile & 2);
-    if (prof) prof_mark(c, h, 0);
+    if (prof) prof_mark(c, h, 2);
     const Csr& A = L.perm ? L.Ap : L.A;
     if constexpr (sizeof(T) == 8) residual64(s, A, x, b, r, nullptr, nullptr);
     else residual32(s, A, x, b, r);
-    if (prof) prof_mark(c, h, 1);
+    if (prof) prof_mark(c, h, 3);
     restrict_agg<T>(s, L.nc, L.agg_ptr.p, L.perm ? L.memp.p : L.agg_mem.p, l == 0 ? LV<T>::pv(L) : nullptr, r,
                     LV<T>::b(C), child_dense ? nullptr : X<T>(C), dc);
     if (child_dense)
@@ -413,7 +419,7 @@ static void run_body(Ctx& c, Hier& h, int kind) {
         PC_CUDA(e);
     }
     if (h.prof_node[kind][0] && (c.p.profile & 2)) {
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < 4; ++k) {
             cudaEvent_t e = pool_event(c);
             PC_CUDA(cudaGraphExecEventRecordNodeSetEvent(ge, h.prof_node[kind][k], e ? e : c.cyc_tmpl[k]));
         }
@@ -662,6 +668,8 @@ pcamg_status solve(Ctx& c, const double* b, double* x, pcamg_stats* st) {
     c.prof_launches = 0;
     c.cyc_ms = 0.0;
     c.cyc_launches = 0;
+    c.gs_ms = 0.0;
+    c.gs_sweeps = 0;
     c.cyc_used = 0;
     c.ncycles = 0;
     c.nwcycles = 0;
@@ -773,6 +781,9 @@ pcamg_status solve(Ctx& c, const double* b, double* x, pcamg_stats* st) {
         st->cyc_launches = c.cyc_launches;
         st->cyc_ms = c.cyc_ms;
         st->cyc_bytes = (double)c.cyc_launches * ((4.0 + w) * (double)c.nnz + (4.0 + 3.0 * w) * (double)c.n);
+        st->gs_sweeps = c.gs_sweeps;
+        st->gs_ms = c.gs_ms;
+        st->gs_bytes = (double)c.gs_sweeps * ((4.0 + w) * (double)c.nnz + (4.0 + 3.0 * w) * (double)c.n);
     }
     return status;
 }

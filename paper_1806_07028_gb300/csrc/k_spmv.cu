@@ -497,28 +497,51 @@ __device__ __forceinline__ void stream_tiles(int beg, int end, int tpb, const in
 // long pole (and with the norm it also divides the partial sums); the FP32 and
 // Gauss-Seidel launches need every block they can get.
 constexpr int kNormTiles = 4;
+// tiles per block of a launch over rows [0, n): the host picks the grid
+// (stream_grid), every block takes this many consecutive tiles
+__device__ __forceinline__ int grid_tiles(int n) {
+    const int ntiles = (n + kStreamRows - 1) / kStreamRows;
+    return (ntiles + (int)gridDim.x - 1) / (int)gridDim.x;
+}
+// Tiles per block of the residual and Jacobi launches: pipelining across tiles
+// pays where FP64 arithmetic is the long pole, and in FP32 on large levels (a
+// block's second tile loads while its first is summed); smaller FP32 levels
+// need every block they can get (measured on the 256^3 grid's levels).
 template <class T>
-constexpr int kTilesPerBlock = sizeof(T) == 8 ? 2 : 1;
+inline int stream_tiles_per_block(int64_t rows, bool dmark) {
+    if (sizeof(T) == 8 || dmark) return 2;
+    return rows >= (3 << 20) ? 2 : 1;
+}
+template <class T>
+inline int stream_grid(int64_t rows, bool dmark) {
+    const int64_t nt = (rows + kStreamRows - 1) / kStreamRows;
+    const int tpb = stream_tiles_per_block<T>(rows, dmark);
+    return (int)std::max<int64_t>(1, (nt + tpb - 1) / tpb);
+}
 // Gauss-Seidel colours: two tiles per block (the second tile's loads overlap
 // the first's sums) at five resident blocks per SM in FP32 (the best of 1-4
 // tiles and 5-8 blocks measured on the 256^3 grid)
 constexpr int kGsTiles = 2;
 template <class T>
 constexpr int kGsMinBlocks = sizeof(T) == 8 ? 4 : 5;
+// residual launches: five resident blocks per SM in FP32 (the colour-ordered
+// finest level's residual: 282 -> 244 us on the 256^3 grid, with two tiles)
+template <class T, bool DM>
+constexpr int kResMinBlocks = sizeof(T) == 4 ? 5 : 0;
 
 // r_i = b_i - sum_k a_k x_col(k) (fused multiply-adds left to right in FP64);
 // partial[block] = sum of r_i^2 of the block's rows when NORM; DM: diagonal
 // entries marked (column ~i)
 template <class T, bool NORM, bool DM = false>
-__global__ void __launch_bounds__(kStreamRows) k_res_stream(int n, const int* __restrict__ rowptr,
+__global__ void __launch_bounds__(kStreamRows, kResMinBlocks<T, DM>) k_res_stream(int n, const int* __restrict__ rowptr,
                                                              const int* __restrict__ col,
                                                              const T* __restrict__ val,
                                                              const T* __restrict__ x,
                                                              const T* __restrict__ b,
                                                              T* __restrict__ r,
                                                              double* __restrict__ partial) {
-    stream_tiles<T, false, NORM, false, DM>(0, n, NORM ? kNormTiles : kTilesPerBlock<T>, nullptr, rowptr, col, val,
-                                            x, b, r, partial);
+    stream_tiles<T, false, NORM, false, DM>(0, n, NORM ? kNormTiles : grid_tiles(n), nullptr, rowptr, col, val, x,
+                                            b, r, partial);
 }
 
 // One l1-Jacobi sweep into another buffer: xout_i = x_i + (b_i - sum_j a_ij x_j) / dl1_i
@@ -530,8 +553,7 @@ __global__ void __launch_bounds__(kStreamRows, 5) k_jac_stream(int n, const int*
                                                              const T* __restrict__ b,
                                                              const T* __restrict__ dl1,
                                                              T* __restrict__ xout) {
-    stream_tiles<T, false, false, true>(0, n, kTilesPerBlock<T>, nullptr, rowptr, col, val, x, b, xout, nullptr,
-                                        dl1);
+    stream_tiles<T, false, false, true>(0, n, grid_tiles(n), nullptr, rowptr, col, val, x, b, xout, nullptr, dl1);
 }
 
 // One colour of Gauss-Seidel on the row-permuted copy (rows of a colour are
@@ -621,7 +643,7 @@ void residual64(cudaStream_t s, const Csr& A, const double* x, const double* b, 
                 double* partial, double* norm2) {
     if (A.dmark) {   // the colour-ordered finest level (always large enough to stream)
         if (norm2 || !use_stream(A.n, A.lpr)) fail(PCAMG_ERR_INVALID, "marked diagonal: streaming residual only");
-        const int gt = ((A.n + kStreamRows - 1) / kStreamRows + kTilesPerBlock<double> - 1) / kTilesPerBlock<double>;
+        const int gt = stream_grid<double>(A.n, true);
         launch(k_res_stream<double, false, true>, gt, kStreamRows, 0, s, A.n, A.rowptr, A.col, A.val, x, b, r,
                (double*)nullptr);
         PC_LAUNCH("residual64");
@@ -634,7 +656,7 @@ void residual64(cudaStream_t s, const Csr& A, const double* x, const double* b, 
             k_res_stream<double, true><<<gn, kStreamRows, 0, s>>>(A.n, A.rowptr, A.col, A.val, x, b, r, partial); ::pc::count_launches(1);
             k_finish<<<1, 1024, 0, s>>>(gn, partial, norm2); ::pc::count_launches(1);
         } else {
-            const int gt = (g + kTilesPerBlock<double> - 1) / kTilesPerBlock<double>;
+            const int gt = stream_grid<double>(A.n, false);
             launch(k_res_stream<double, false>, gt, kStreamRows, 0, s, A.n, A.rowptr, A.col, A.val, x, b, r,
                    (double*)nullptr);
         }
@@ -657,7 +679,7 @@ void jacobi_sweep(cudaStream_t s, const Csr& A, const T* x, const T* b, const T*
     const T* val;
     if constexpr (sizeof(T) == 8) val = A.val; else val = A.val32;
     if (use_stream(A.n, A.lpr)) {
-        int g = ((A.n + kStreamRows - 1) / kStreamRows + kTilesPerBlock<T> - 1) / kTilesPerBlock<T>;
+        int g = stream_grid<T>(A.n, false);
         launch(k_jac_stream<T>, g, kStreamRows, 0, s, A.n, A.rowptr, A.col, val, x, b, d, xout);
     } else {
         int g = sparse_grid(A.n, A.lpr);
@@ -686,9 +708,10 @@ void l1_diagonal(cudaStream_t s, int32_t n, const int32_t* rowptr, const double*
 void residual32(cudaStream_t s, const Csr& A, const float* x, const float* b, float* r) {
     if (A.dmark && !use_stream(A.n, A.lpr)) fail(PCAMG_ERR_INVALID, "marked diagonal: streaming residual only");
     if (use_stream(A.n, A.lpr)) {
-        int g = ((A.n + kStreamRows - 1) / kStreamRows + kTilesPerBlock<float> - 1) / kTilesPerBlock<float>;
+        const int g = stream_grid<float>(A.n, false);
+        const int gdm = stream_grid<float>(A.n, true);
         if (A.dmark)
-            launch(k_res_stream<float, false, true>, g, kStreamRows, 0, s, A.n, A.rowptr, A.col, A.val32, x, b, r,
+            launch(k_res_stream<float, false, true>, gdm, kStreamRows, 0, s, A.n, A.rowptr, A.col, A.val32, x, b, r,
                    (double*)nullptr);
         else
             launch(k_res_stream<float, false>, g, kStreamRows, 0, s, A.n, A.rowptr, A.col, A.val32, x, b, r,

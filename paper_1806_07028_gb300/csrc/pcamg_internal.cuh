@@ -268,7 +268,7 @@ struct Hier {
     int64_t graph_kernels[3] = {0, 0, 0};
     // event-record nodes around the finest-level residual of the V-cycle graphs
     // (params.profile bit 1), retargeted to fresh events before each replay
-    cudaGraphNode_t prof_node[3][2] = {};
+    cudaGraphNode_t prof_node[3][4] = {};   // finest-level pre-sweep start/end, residual start/end
     cudaGraph_t graph_tmpl[3] = {nullptr, nullptr, nullptr};   // graphs those nodes belong to
     ~Hier();
 };
@@ -327,9 +327,11 @@ struct Ctx {
     // event pairs recorded around it, resolved when the solve ends
     std::vector<cudaEvent_t> cyc_ev;
     size_t cyc_used = 0;
-    cudaEvent_t cyc_tmpl[2] = {nullptr, nullptr};   // events named in the captured nodes
+    cudaEvent_t cyc_tmpl[4] = {nullptr, nullptr, nullptr, nullptr};   // events named in the captured nodes
     int64_t cyc_launches = 0;
     double cyc_ms = 0.0;
+    int64_t gs_sweeps = 0;   // finest-level pre-smoothing sweeps timed
+    double gs_ms = 0.0;
     int64_t ncycles = 0;
     int64_t nwcycles = 0;
     bool fixed_scale = false;   // FP32 cycle scale set once for the running solve

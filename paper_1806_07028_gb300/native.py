@@ -68,7 +68,8 @@ class Stats(C.Structure):
                 ("res_hist_len", C.c_int32), ("prof_launches", C.c_int64),
                 ("prof_ms", C.c_double), ("prof_bytes", C.c_double),
                 ("rebuilt", C.POINTER(C.c_int32)), ("wcycles", C.c_int64),
-                ("cyc_launches", C.c_int64), ("cyc_ms", C.c_double), ("cyc_bytes", C.c_double)]
+                ("cyc_launches", C.c_int64), ("cyc_ms", C.c_double), ("cyc_bytes", C.c_double),
+                ("gs_sweeps", C.c_int64), ("gs_ms", C.c_double), ("gs_bytes", C.c_double)]
 
 
 def lib():
