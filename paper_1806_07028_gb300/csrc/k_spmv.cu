@@ -96,9 +96,12 @@ __global__ void __launch_bounds__(kBlock) k_residual(int n, const int* __restric
     pdl_trigger();
     for (; row0 < n; row0 += nwarps * RPW) {
         const int64_t row = row0 + grp;
-        T s = 0, xr = 0;
+        T s = 0, xr = 0, bv = 0;
         if (row < n) {
-            if (dl1 && sub == 0) xr = x[row];
+            if (sub == 0) {   // issued with the gathers, not after the sum
+                bv = __ldg(b + row);
+                if (dl1) xr = x[row];
+            }
 #pragma unroll
             for (int q = 0; q < kPre; ++q)
                 if (beg + sub + q * LPR < end) s = fma_t(pv[q], __ldg(x + pc[q]), s);
@@ -106,7 +109,7 @@ __global__ void __launch_bounds__(kBlock) k_residual(int n, const int* __restric
         }
         s = group_sum<LPR>(s);
         if (sub == 0 && row < n) {
-            T rr = __ldg(b + row) - s;
+            T rr = bv - s;
             if (dl1) r[row] = xr + rr / dr;
             else r[row] = rr;
             acc2 += (double)rr * (double)rr;

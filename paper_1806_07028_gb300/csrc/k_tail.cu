@@ -309,7 +309,13 @@ __device__ __forceinline__ float dot16(float4 a, float4 b) { return a.x * b.x + 
 __device__ __forceinline__ double dot16(double2 a, double2 b) { return a.x * b.x + a.y * b.y; }
 
 // x = N v (accum = 0) or x += N v (accum = 1); one warp per row of N, v staged
-// in shared memory with zeros up to ld, rows read as 16-byte vectors.
+// in shared memory with zeros up to ld, rows read as 16-byte vectors. N is
+// hierarchy data: a lane's first kGemvPre vectors of its row are loaded ahead
+// of pdl_wait(), so in a cycle graph they arrive while the previous kernel
+// runs; the rest follow kGemvUnroll at a time, all independent.
+constexpr int kGemvPre = 8;
+constexpr int kGemvUnroll = 8;
+
 template <class T>
 __global__ void __launch_bounds__(kGemvWarps * 32)
     k_tail_gemv(int m, int ld, const T* __restrict__ Nm, const T* __restrict__ v, T* __restrict__ x,
@@ -318,18 +324,41 @@ __global__ void __launch_bounds__(kGemvWarps * 32)
     constexpr int W = 16 / sizeof(T);
     extern __shared__ __align__(16) unsigned char dyn[];
     T* vs = reinterpret_cast<T*>(dyn);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = blockIdx.x * kGemvWarps + warp;
+    const int nq = ld / W;
+    const V* a = reinterpret_cast<const V*>(Nm + (size_t)(row < m ? row : 0) * ld);
+    V pre[kGemvPre];
+#pragma unroll
+    for (int u = 0; u < kGemvPre; ++u) {
+        const int q = lane + 32 * u;
+        pre[u] = (row < m && q < nq) ? __ldg(a + q) : V{};
+    }
     pdl_wait();
     pdl_trigger();
     for (int j = threadIdx.x; j < ld; j += blockDim.x) vs[j] = (j < m) ? v[j] : T(0);
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = blockIdx.x * kGemvWarps + warp;
     if (row >= m) return;
-    const V* a = reinterpret_cast<const V*>(Nm + (size_t)row * ld);
     const V* vv = reinterpret_cast<const V*>(vs);
     T s = 0;
-#pragma unroll 4
-    for (int q = lane; q < ld / W; q += 32) s += dot16(__ldg(a + q), vv[q]);
+#pragma unroll
+    for (int u = 0; u < kGemvPre; ++u) {
+        const int q = lane + 32 * u;
+        if (q < nq) s += dot16(pre[u], vv[q]);
+    }
+    for (int q0 = lane + 32 * kGemvPre; q0 < nq; q0 += 32 * kGemvUnroll) {
+        V t[kGemvUnroll];
+#pragma unroll
+        for (int u = 0; u < kGemvUnroll; ++u) {
+            const int q = q0 + 32 * u;
+            t[u] = q < nq ? __ldg(a + q) : V{};
+        }
+#pragma unroll
+        for (int u = 0; u < kGemvUnroll; ++u) {
+            const int q = q0 + 32 * u;
+            if (q < nq) s += dot16(t[u], vv[q]);
+        }
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (lane == 0) x[row] = accum ? x[row] + s : s;
