@@ -348,22 +348,57 @@ __global__ void k_rowprod_ubrow(int nrows, Src src, int64_t* __restrict__ ub) {
     }
 }
 
-// Copy the rows written in the temporary layout to their final place (a warp per row).
+// Copy the rows written in the temporary layout to their final place. A warp
+// takes 32 consecutive rows: their counts and offsets are one coalesced load
+// per lane, then the rows' first 32 entries are copied eight rows at a time
+// (loads of the eight issued before their stores), longer rows' remainders
+// after them.
 __global__ void k_rowprod_compact(int nrows, const unsigned char* __restrict__ is_long, const int* __restrict__ cnt,
                                   const int64_t* __restrict__ tptr, const int* __restrict__ tcol,
                                   const double* __restrict__ tval, const int* __restrict__ optr,
                                   int* __restrict__ ocol, double* __restrict__ oval) {
+    constexpr int kGroup = 8;
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r = w0; r < nrows; r += nw) {
-        if (is_long[r]) continue;
-        const int m = cnt[r];
-        const int64_t t = tptr[r];
-        const int o = optr[r];
-        for (int q = lane; q < m; q += 32) {
-            ocol[o + q] = tcol[t + q];
-            if (oval) oval[o + q] = tval[t + q];
+    for (int64_t r0 = w0 * 32; r0 < nrows; r0 += nw * 32) {
+        const int64_t r = r0 + lane;
+        int m = 0, o = 0;
+        int64_t t = 0;
+        if (r < nrows && !is_long[r]) { m = cnt[r]; t = tptr[r]; o = optr[r]; }
+        for (int j0 = 0; j0 < 32; j0 += kGroup) {
+            int cv[kGroup];
+            double vv[kGroup];
+            int mj[kGroup], oj[kGroup];
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u) {
+                mj[u] = __shfl_sync(0xffffffffu, m, j0 + u);
+                oj[u] = __shfl_sync(0xffffffffu, o, j0 + u);
+                const int64_t tj = __shfl_sync(0xffffffffu, t, j0 + u);
+                const bool on = lane < mj[u];
+                cv[u] = on ? tcol[tj + lane] : 0;
+                vv[u] = (on && oval) ? tval[tj + lane] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u) {
+                if (lane < mj[u]) {
+                    ocol[oj[u] + lane] = cv[u];
+                    if (oval) oval[oj[u] + lane] = vv[u];
+                }
+            }
+        }
+        // entries beyond the first 32 of long rows
+        unsigned longer = __ballot_sync(0xffffffffu, m > 32);
+        while (longer) {
+            const int j = __ffs(longer) - 1;
+            longer &= longer - 1;
+            const int mj = __shfl_sync(0xffffffffu, m, j);
+            const int oj = __shfl_sync(0xffffffffu, o, j);
+            const int64_t tj = __shfl_sync(0xffffffffu, t, j);
+            for (int q = 32 + lane; q < mj; q += 32) {
+                ocol[oj + q] = tcol[tj + q];
+                if (oval) oval[oj + q] = tval[tj + q];
+            }
         }
     }
 }
@@ -1245,7 +1280,8 @@ static void row_product(Ctx& c, int32_t nrows, const Src& src, DBuf<int32_t>& op
     ocol.alloc(c.mem, total);
     double* ov = nullptr;
     if (oval) { oval->alloc(c.mem, total); ov = oval->p; }
-    k_rowprod_compact<<<grid_warps(nrows), kWarpsPerBlock * 32, 0, s>>>(nrows, is_long.p, cnt.p, tptr.p, tcol.p,
+    const int gcompact = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)nrows + 255) / 256, (int64_t)kNumSMs * 16));
+    k_rowprod_compact<<<gcompact, kWarpsPerBlock * 32, 0, s>>>(nrows, is_long.p, cnt.p, tptr.p, tcol.p,
                                                                          oval ? tval.p : nullptr, optr.p, ocol.p, ov);
     ::pc::count_launches(1);
     PC_LAUNCH("rowprod_compact");
