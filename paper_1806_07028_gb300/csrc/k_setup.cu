@@ -1295,8 +1295,19 @@ static void row_product(Ctx& c, int32_t nrows, const Src& src, DBuf<int32_t>& op
 }
 
 void build_candidates(Ctx& c, const double* e, Reweighted& out) {
-    CandSrc src{c.rowptr.p, c.col.p};
-    row_product(c, c.n, src, out.ptr, out.col, nullptr, &out.nnz);
+    // the A^2 pattern depends on A alone: formed by the first build, copied
+    // for the later ones (only the weights follow the new e)
+    if (c.cand_nnz < 0) {
+        CandSrc src{c.rowptr.p, c.col.p};
+        row_product(c, c.n, src, c.cand_ptr, c.cand_col, nullptr, &c.cand_nnz);
+    }
+    out.nnz = c.cand_nnz;
+    out.ptr.alloc(c.mem, (size_t)c.n + 1);
+    out.col.alloc(c.mem, (size_t)out.nnz);
+    PC_CUDA(cudaMemcpyAsync(out.ptr.p, c.cand_ptr.p, sizeof(int32_t) * ((size_t)c.n + 1), cudaMemcpyDeviceToDevice,
+                            c.stream));
+    PC_CUDA(cudaMemcpyAsync(out.col.p, c.cand_col.p, sizeof(int32_t) * (size_t)out.nnz, cudaMemcpyDeviceToDevice,
+                            c.stream));
     out.w.alloc(c.mem, out.nnz);
     int nb = 256;
     DBuf<double> part;

@@ -339,6 +339,10 @@ struct Ctx {
     double t_alg2 = 0.0, t_alg4 = 0.0;
     const double* last_e = nullptr;          // normalised error of the newest hierarchy
     std::unique_ptr<Reweighted> mpnn_cand;   // A^2 candidate pattern for the network's loss
+    // the A^2 candidate pattern of Alg. 4 step 2 (row pointers and columns):
+    // it depends on A alone, so the first build forms it and later builds copy it
+    DBuf<int32_t> cand_ptr, cand_col;
+    int64_t cand_nnz = -1;
     DBuf<int64_t> scan_ws;                   // one-pass scan bookkeeping (k_vector.cu)
     ~Ctx();
 };
