@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(kTailThreads, 1)
     }
 }
 
-constexpr int kGemvWarps = 16;
+constexpr int kGemvWarpsMax = 32;   // warps (rows) per block at most
 
 template <class T> struct Vec16;
 template <> struct Vec16<float> { using V = float4; };
@@ -317,7 +317,7 @@ constexpr int kGemvPre = 8;
 constexpr int kGemvUnroll = 8;
 
 template <class T>
-__global__ void __launch_bounds__(kGemvWarps * 32)
+__global__ void __launch_bounds__(kGemvWarpsMax * 32)
     k_tail_gemv(int m, int ld, const T* __restrict__ Nm, const T* __restrict__ v, T* __restrict__ x,
                 int accum) {
     using V = typename Vec16<T>::V;
@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(kGemvWarps * 32)
     extern __shared__ __align__(16) unsigned char dyn[];
     T* vs = reinterpret_cast<T*>(dyn);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = blockIdx.x * kGemvWarps + warp;
+    const int row = blockIdx.x * (int)(blockDim.x >> 5) + warp;
     const int nq = ld / W;
     const V* a = reinterpret_cast<const V*>(Nm + (size_t)(row < m ? row : 0) * ld);
     V pre[kGemvPre];
@@ -394,8 +394,17 @@ void tail_operator(cudaStream_t s, const TailLevel<T>* lv, const int* n, int l0,
 
 template <class T>
 void tail_gemv(cudaStream_t s, int m, int ld, const T* Nm, const T* v, T* x, bool accum) {
-    const int grid = (m + kGemvWarps - 1) / kGemvWarps;
-    launch(k_tail_gemv<T>, grid, kGemvWarps * 32, sizeof(T) * ld, s, m, ld, Nm, v, x, accum ? 1 : 0);
+    // rows spread evenly over the SMs: one block per SM with ceil(m / SMs)
+    // warps (a warp per row), so no SM takes a second block
+    static int nsm = 0;
+    if (!nsm) {
+        int dev = 0;
+        PC_CUDA(cudaGetDevice(&dev));
+        PC_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    }
+    const int warps = std::max(1, std::min(kGemvWarpsMax, (m + nsm - 1) / nsm));
+    const int grid = (m + warps - 1) / warps;
+    launch(k_tail_gemv<T>, grid, warps * 32, sizeof(T) * ld, s, m, ld, Nm, v, x, accum ? 1 : 0);
     PC_LAUNCH("tail_gemv");
 }
 
