@@ -269,34 +269,28 @@ __global__ void __launch_bounds__(kThr, 2)
                 const float2 g = *reinterpret_cast<const float2*>(G + (size_t)row * kH + 2 * lane);
                 h0 = g.x - mu0;
                 h1 = g.y - mu1;
-                // four neighbours per step, their rows loaded before any is used
-                // (the diagonal entry contributes with weight zero)
+                // eight neighbours per step, their rows loaded before any is used
+                // (the diagonal entry and the slots past the row's end add
+                // 0 * G[row], which leaves the sums unchanged: the same
+                // products in the same order as one neighbour at a time)
                 const int e = rowptr[row + 1];
-                int q = rowptr[row];
-                for (; q + 4 <= e; q += 4) {
-                    int j[4];
-                    float w[4];
-                    float2 f[4];
+                for (int q = rowptr[row]; q < e; q += 8) {
+                    int j[8];
+                    float w[8];
+                    float2 f[8];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        j[u] = col[q + u];
-                        w[u] = (j[u] == row) ? 0.f : aw[q + u];
+                    for (int u = 0; u < 8; ++u) {
+                        const bool on = q + u < e;
+                        j[u] = on ? col[q + u] : row;
+                        w[u] = (!on || j[u] == row) ? 0.f : aw[q + u];
                     }
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) f[u] = *reinterpret_cast<const float2*>(G + (size_t)j[u] * kH + 2 * lane);
+                    for (int u = 0; u < 8; ++u) f[u] = *reinterpret_cast<const float2*>(G + (size_t)j[u] * kH + 2 * lane);
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
+                    for (int u = 0; u < 8; ++u) {
                         a0 = fmaf(w[u], f[u].x, a0);
                         a1 = fmaf(w[u], f[u].y, a1);
                     }
-                }
-                for (; q < e; ++q) {
-                    const int j = col[q];
-                    if (j == row) continue;
-                    const float w = aw[q];
-                    const float2 f = *reinterpret_cast<const float2*>(G + (size_t)j * kH + 2 * lane);
-                    a0 = fmaf(w, f.x, a0);
-                    a1 = fmaf(w, f.y, a1);
                 }
                 const float s = invD[row];
                 a0 = a0 * s - mu0;
