@@ -139,6 +139,10 @@ def lib():
             L.orc_solve_zero_rhs.argtypes = [C.c_int32, _i32p, _i32p, _f64p, _f64p, C.POINTER(Params),
                                              C.c_void_p, C.POINTER(Stats), C.c_void_p, C.c_int32]
             L.orc_solve_zero_rhs.restype = C.c_int32
+            L.orc_solve_multi.argtypes = [C.c_int32, _i32p, _i32p, _f64p, C.c_int32, _f64p, _f64p,
+                                          C.POINTER(Params), C.POINTER(C.c_void_p), C.c_int32, C.c_void_p,
+                                          C.c_void_p]
+            L.orc_solve_multi.restype = C.c_int32
             _lib = L
     return _lib
 
@@ -422,6 +426,24 @@ def precond(g, r, hiers, params=None):
     z = np.empty(g.n)
     lib().orc_precond(g.n, rp, ci, v, arr, len(hiers), C.byref(p), _f64(r), z)
     return z
+
+
+def solve_multi(g, B, hiers, X0=None, params=None):
+    """Several right-hand sides (the columns of B, n x k): each column's outer
+    iteration of Alg. 5 without re-setup, preconditioned by the composite of
+    V-cycles over hiers. Returns (X n x k, iters, rel_res, status)."""
+    p = params if params is not None else default_params()
+    rp, ci, v = _csr(g)
+    Bc = np.ascontiguousarray(np.asarray(B, dtype=np.float64).reshape(g.n, -1).T)   # k x n: column-major
+    k = Bc.shape[0]
+    Xc = (np.zeros_like(Bc) if X0 is None else
+          np.ascontiguousarray(np.asarray(X0, dtype=np.float64).reshape(g.n, k).T))
+    arr = (C.c_void_p * len(hiers))(*[h._h for h in hiers])
+    iters = np.zeros(k, np.int32)
+    rel = np.zeros(k)
+    st = lib().orc_solve_multi(g.n, rp, ci, v, k, Bc, Xc, C.byref(p), arr, len(hiers),
+                               iters.ctypes.data_as(C.c_void_p), rel.ctypes.data_as(C.c_void_p))
+    return Xc.T.copy(), iters, rel, ERR.get(st, st)
 
 
 def solve(g, b, x0=None, params=None, e0=None, hist_cap=4096):

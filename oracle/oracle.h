@@ -209,6 +209,13 @@ void orc_precond(int32_t n, const int32_t* rowptr, const int32_t* col, const dou
 int32_t orc_solve(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
                   const double* b, double* x, const orc_params* p, const double* e0,
                   orc_stats* st, double* res_hist, int32_t res_hist_cap, int32_t* rebuilt);
+/* Several right-hand sides (B, X column-major n x k), each column by the outer
+ * iteration of Alg. 5 without re-setup (p->outer), preconditioned by Alg. 2's
+ * composite product of V-cycles over hist[0..re-1]. iters, rel_res: k entries
+ * each (may be NULL). */
+int32_t orc_solve_multi(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                        int32_t k, const double* B, double* X, const orc_params* p,
+                        orc_hier* const* hist, int32_t re, int32_t* iters, double* rel_res);
 /* Alg. 6 (b = 0): the iterate itself becomes the smooth error. */
 int32_t orc_solve_zero_rhs(int32_t n, const int32_t* rowptr, const int32_t* col,
                            const double* val, double* x, const orc_params* p,

@@ -126,6 +126,78 @@ void orc_precond(int32_t n, const int32_t* rowptr, const int32_t* col, const dou
     free(t1); free(t2);
 }
 
+/* Several right-hand sides of one operator, column by column: the outer
+ * iteration of Alg. 5 (stationary x += z, or flexible CG with the same
+ * Polak-Ribiere update as orc_solve) without re-setup, z the symmetric
+ * composite product of V-cycles over hist[0..re-1] (Alg. 2's preconditioner
+ * with every hierarchy given, applied as z += B_j (r - A z) for j = 1..re,
+ * re..1 from z = 0). B, X column-major n x k; X holds the initial guesses and
+ * receives the solutions. */
+int32_t orc_solve_multi(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                        int32_t k, const double* B, double* X, const orc_params* p,
+                        orc_hier* const* hist, int32_t re, int32_t* iters, double* rel_res) {
+    if (k < 1 || re < 1) return ORC_ERR_INVALID;
+    orc_params q = *p;
+    q.numW = 0;   /* the composite product for every re */
+    double *r = (double*)orc_xmalloc(sizeof(double) * (size_t)n),
+           *z = (double*)orc_xmalloc(sizeof(double) * (size_t)n),
+           *t1 = (double*)orc_xmalloc(sizeof(double) * (size_t)n),
+           *t2 = (double*)orc_xmalloc(sizeof(double) * (size_t)n),
+           *fp = (double*)orc_xmalloc(sizeof(double) * (size_t)n),
+           *fq = (double*)orc_xmalloc(sizeof(double) * (size_t)n),
+           *frold = (double*)orc_xmalloc(sizeof(double) * (size_t)n),
+           *fzold = (double*)orc_xmalloc(sizeof(double) * (size_t)n),
+           *fzero = (double*)calloc((size_t)n, sizeof(double));
+    int32_t status = ORC_OK;
+    if (!r || !z || !t1 || !t2 || !fp || !fq || !frold || !fzold || !fzero) { status = ORC_ERR_OOM; goto out; }
+    for (int32_t c = 0; c < k; ++c) {
+        const double* b = B + (size_t)c * n;
+        double* x = X + (size_t)c * n;
+        for (int32_t i = 0; i < n; ++i) if (!isfinite(b[i]) || !isfinite(x[i])) { status = ORC_ERR_INVALID; goto out; }
+        const double bn = vnorm(n, b);
+        if (!(bn > 0.0)) { status = ORC_ERR_INVALID; goto out; }
+        remove_mean(n, x);
+        orc_residual(n, rowptr, col, val, x, b, r);
+        double res = vnorm(n, r);
+        int32_t it = 0, restart = 1;
+        while (it < p->max_iter && res / bn > p->tol) {
+            precond(n, rowptr, col, val, hist, re, &q, r, z, t1, t2);
+            if (p->outer == ORC_OUTER_FCG) {
+                double rz = vdot(n, r, z);
+                if (restart) {
+                    memcpy(fp, z, sizeof(double) * (size_t)n);
+                    restart = 0;
+                } else {
+                    double num = 0.0, den = vdot(n, fzold, frold);
+                    for (int32_t i = 0; i < n; ++i) num += z[i] * (r[i] - frold[i]);
+                    double beta = (den != 0.0) ? num / den : 0.0;
+                    for (int32_t i = 0; i < n; ++i) fp[i] = z[i] + beta * fp[i];
+                }
+                orc_residual(n, rowptr, col, val, fp, fzero, fq);   /* fq = -A p */
+                double pq = -vdot(n, fp, fq);
+                double alpha = (pq > 0.0 && rz > 0.0) ? rz / pq : 0.0;
+                for (int32_t i = 0; i < n; ++i) x[i] += alpha * fp[i];
+                memcpy(frold, r, sizeof(double) * (size_t)n);
+                memcpy(fzold, z, sizeof(double) * (size_t)n);
+            } else {
+                for (int32_t i = 0; i < n; ++i) x[i] += z[i];
+            }
+            remove_mean(n, x);
+            orc_residual(n, rowptr, col, val, x, b, r);
+            double nres = vnorm(n, r);
+            ++it;
+            if (!isfinite(nres)) { status = ORC_ERR_DIVERGED; res = nres; break; }
+            res = nres;
+        }
+        if (iters) iters[c] = it;
+        if (rel_res) rel_res[c] = res / bn;
+        if (status == ORC_OK && !(res / bn <= p->tol)) status = ORC_ERR_NOT_CONVERGED;
+    }
+out:
+    free(r); free(z); free(t1); free(t2); free(fp); free(fq); free(frold); free(fzold); free(fzero);
+    return status;
+}
+
 /* Alg. 2: flexible (Polak-Ribiere) PCG on A e = r from e = 0. */
 int32_t orc_smooth_error(int32_t n, const int32_t* rowptr, const int32_t* col,
                          const double* val, const double* rhs, orc_hier* const* hist,
