@@ -236,6 +236,28 @@ PCAMG_API pcamg_status pcamg_solve(pcamg_handle h, const double* d_b, double* d_
  * to the first residual. */
 PCAMG_API pcamg_status pcamg_solve_zero_rhs(pcamg_handle h, double* d_x, pcamg_stats* st);
 
+/* Several right-hand sides at once: A X = B for k columns. Adaptivity is per
+ * operator, so no column builds a hierarchy: every column runs the outer
+ * iteration of Alg. 5 without re-setup -- stationary (x += z) or flexible CG
+ * (params.outer), the column's residual and stopping test in FP64 as in
+ * pcamg_solve -- with z = M r, M Alg. 2's symmetric composite product of
+ * V-cycles over every hierarchy the handle holds (those pcamg_setup,
+ * pcamg_adapt and earlier solves built; z += B_j (r - A z) for j = 1..Re,
+ * Re..1 from z = 0). The cycles of up to 8 columns run together: every pass
+ * over a level's matrix serves all of them (the level's vectors
+ * row-interleaved, K = 1, 2, 4 or 8 per pass). A column agrees with the same
+ * iteration on that column alone to rounding (the batched row sums take the
+ * sub-warp order).
+ * d_B, d_X: device, column-major n x k (column c at offset c*n); d_X holds the
+ * initial guesses and receives the solutions (each with zero mean). iters,
+ * rel_res: optional host arrays of k entries (V-cycles done, final
+ * ||b - A x|| / ||b|| per column). Returns PCAMG_OK when every column reached
+ * params.tol, PCAMG_ERR_NOT_CONVERGED when one stopped at params.max_iter,
+ * PCAMG_ERR_DIVERGED on a non-finite residual, PCAMG_ERR_INVALID for k < 1 or
+ * a zero or non-finite column of B. */
+PCAMG_API pcamg_status pcamg_solve_multi(pcamg_handle h, int32_t k, const double* d_B, double* d_X,
+                                         int32_t* iters, double* rel_res);
+
 /* End-to-end call on HOST buffers: copies A, b, x to the device, runs
  * pcamg_setup + pcamg_solve, copies x back, frees everything. */
 PCAMG_API pcamg_status pcamg_solve_host(const pcamg_params* p, int32_t n, int64_t nnz,

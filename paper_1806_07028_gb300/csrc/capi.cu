@@ -350,6 +350,19 @@ PCAMG_API pcamg_status pcamg_solve_zero_rhs(pcamg_handle h, double* d_x, pcamg_s
     });
 }
 
+PCAMG_API pcamg_status pcamg_solve_multi(pcamg_handle h, int32_t k, const double* d_B, double* d_X,
+                                         int32_t* iters, double* rel_res) {
+    if (!h || !d_B || !d_X || k < 1) return set_err(h, PCAMG_ERR_INVALID, "invalid argument");
+    return guarded(h, [&]() -> pcamg_status {
+        Enter guard(*h);
+        for (int32_t j = 0; j < k; ++j) {
+            check_finite(*h, d_B + (size_t)j * h->n, h->n, "B");
+            check_finite(*h, d_X + (size_t)j * h->n, h->n, "X");
+        }
+        return solve_multi(*h, k, d_B, d_X, iters, rel_res);
+    });
+}
+
 PCAMG_API pcamg_status pcamg_solve_host(const pcamg_params* p, int32_t n, int64_t nnz,
                                         const int32_t* h_rowptr, const int32_t* h_col,
                                         const double* h_val, const double* h_b, double* h_x,

@@ -788,6 +788,242 @@ pcamg_status solve(Ctx& c, const double* b, double* x, pcamg_stats* st) {
     return status;
 }
 
+// ---------------------------------------------------------------- several right-hand sides
+// The batched V-cycle: the single-vector cycle's steps (gamma = 1:
+// pre-smoothing, residual, restriction with the child's fresh start, the
+// child, prolongation, post-smoothing; the tail as its dense operator, the
+// coarsest level by its pseudo-inverse) on K row-interleaved vectors per
+// level. The finest level's vectors belong to the context and a cycle
+// continues from its x (x <- x + B_h (b - A x)), so the factors of Alg. 2's
+// composite follow one another in place, as in the single-vector composite.
+template <class T>
+static T* mvb(DBuf<unsigned char>& d) { return reinterpret_cast<T*>(d.p); }
+
+template <class T>
+static void mv_ensure(Ctx& c, Hier& h, int K) {
+    if (c.mv0_K != K) {
+        const size_t bytes = sizeof(T) * (size_t)c.n * K;
+        c.mv0_x.alloc(c.mem, bytes);
+        c.mv0_b.alloc(c.mem, bytes);
+        c.mv0_r.alloc(c.mem, bytes);
+        c.mv0_K = K;
+    }
+    if (h.mv_K == K) return;
+    for (int32_t l = 1; l < h.nlev; ++l) {
+        Level& L = h.lev[l];
+        const size_t bytes = sizeof(T) * (size_t)L.n * K;
+        h.mv_x[l].alloc(c.mem, bytes);
+        h.mv_b[l].alloc(c.mem, bytes);
+        h.mv_r[l].alloc(c.mem, bytes);
+        if (L.jac) h.mv_x2[l].alloc(c.mem, bytes); else h.mv_x2[l].free();
+    }
+    h.mv_K = K;
+}
+
+// the level vectors of one batched cycle of h (level 0: the context's)
+template <class T>
+struct MvVecs {
+    T* x[kMaxLevels];
+    T* x2[kMaxLevels];
+    T* b[kMaxLevels];
+    T* r[kMaxLevels];
+};
+
+template <class T>
+static MvVecs<T> mv_vecs(Ctx& c, Hier& h) {
+    MvVecs<T> v;
+    for (int32_t l = 0; l < h.nlev; ++l) {
+        v.x[l] = l == 0 ? mvb<T>(c.mv0_x) : mvb<T>(h.mv_x[l]);
+        v.x2[l] = l == 0 ? nullptr : mvb<T>(h.mv_x2[l]);
+        v.b[l] = l == 0 ? mvb<T>(c.mv0_b) : mvb<T>(h.mv_b[l]);
+        v.r[l] = l == 0 ? mvb<T>(c.mv0_r) : mvb<T>(h.mv_r[l]);
+    }
+    return v;
+}
+
+template <class T>
+static void mv_smooth(Ctx& c, Hier& h, int K, int32_t l, MvVecs<T>& v, bool forward) {
+    Level& L = h.lev[l];
+    const Csr& A = (l == 0 && L.perm) ? L.Ap : L.A;
+    if (L.jac && v.x2[l]) {
+        const T* d;
+        if constexpr (sizeof(T) == 8) d = L.dl1_64.p; else d = L.dl1_32.p;
+        mv_rows<T>(c.stream, 1, K, L.n, nullptr, 0, A, v.x[l], v.b[l], d, v.x2[l]);
+        std::swap(v.x[l], v.x2[l]);
+        return;
+    }
+    for (int32_t t = 0; t < L.ncolour; ++t) {
+        const int32_t k = forward ? t : L.ncolour - 1 - t;
+        const int32_t beg = L.h_colour_ptr[k], end = L.h_colour_ptr[k + 1];
+        if (L.perm)   // colour order: the colour's rows are positions beg..end
+            mv_rows<T>(c.stream, 2, K, end - beg, nullptr, beg, A, v.x[l], v.b[l], nullptr, v.x[l]);
+        else
+            mv_rows<T>(c.stream, 2, K, end - beg, L.colour_rows_v + beg, 0, A, v.x[l], v.b[l], nullptr, v.x[l]);
+    }
+}
+
+// One visit of level l. Level 0 continues from its x; a coarser level starts
+// from zero, or from one l1-Jacobi sweep from zero when `fresh`.
+template <class T>
+static void mv_level(Ctx& c, Hier& h, int K, int32_t l, bool fresh, MvVecs<T>& v) {
+    cudaStream_t s = c.stream;
+    Level& L = h.lev[l];
+    const bool dense = l == h.lt && h.tail_op[0].p && h.tail_visits[0] == 1;
+    if (dense || l == h.nlev - 1) {
+        const T* rhs = v.b[l];
+        if (l == 0) {   // the whole hierarchy is one operator: x += M (b - A x)
+            mv_rows<T>(s, 0, K, L.n, nullptr, 0, L.perm ? L.Ap : L.A, v.x[0], v.b[0], nullptr, v.r[0]);
+            rhs = v.r[0];
+        }
+        if (dense) mv_dense<T>(s, K, L.n, h.tail_ld, reinterpret_cast<const T*>(h.tail_op[0].p), rhs, v.x[l], l == 0);
+        else mv_coarse<T>(s, K, L.n, h.Xinv.p, rhs, v.x[l], l == 0);
+        return;
+    }
+    for (int32_t k = fresh ? 1 : 0; k < c.p.nu_pre; ++k) mv_smooth<T>(c, h, K, l, v, true);
+    const Csr& A = (l == 0 && L.perm) ? L.Ap : L.A;
+    mv_rows<T>(s, 0, K, L.n, nullptr, 0, A, v.x[l], v.b[l], nullptr, v.r[l]);
+    Level& C = h.lev[l + 1];
+    const bool child_dense = l + 1 == h.lt && h.tail_op[0].p && h.tail_visits[0] == 1;
+    const bool child_fresh = !child_dense && C.jac && c.p.nu_pre >= 1 && l + 1 < h.nlev - 1;
+    const T* dc = nullptr;
+    if (child_fresh) { if constexpr (sizeof(T) == 8) dc = C.dl1_64.p; else dc = C.dl1_32.p; }
+    const T* pv = l == 0 ? LV<T>::pv(L) : nullptr;
+    mv_restrict<T>(s, K, L.nc, L.agg_ptr.p, L.perm ? L.memp.p : L.agg_mem.p, pv, v.r[l], v.b[l + 1], v.x[l + 1], dc);
+    mv_level<T>(c, h, K, l + 1, child_fresh, v);
+    mv_prolong<T>(s, K, L.n, L.perm ? L.aggp.p : L.agg.p, pv, v.x[l + 1], v.x[l]);
+    for (int32_t k = 0; k < c.p.nu_post; ++k) mv_smooth<T>(c, h, K, l, v, false);
+}
+
+// Z = M R for the kr columns of R (column-major n x kr), M Alg. 2's symmetric
+// composite of V-cycles over every hierarchy held, z += B_j (r - A z) for
+// j = 1..re, re..1 from z = 0; the columns scaled by their fixed scales into
+// the finest level's order and back.
+template <class T>
+static void mv_precond(Ctx& c, int K, int kr, const double* R, double* Z, const double* scale, const double* inv) {
+    cudaStream_t s = c.stream;
+    const int32_t re = (int32_t)c.hist.size();
+    for (Hier* h : c.hist) mv_ensure<T>(c, *h, K);
+    Level& L0 = c.hist[0]->lev[0];
+    const int* perm = L0.perm ? c.colour_rows0.p : nullptr;
+    const int* iperm = L0.perm ? c.iperm0.p : nullptr;
+    mv_in<T>(s, K, kr, c.n, perm, R, inv, mvb<T>(c.mv0_b));
+    PC_CUDA(cudaMemsetAsync(c.mv0_x.p, 0, sizeof(T) * (size_t)c.n * K, s));
+    for (int32_t q = 0; q < 2 * re; ++q) {
+        Hier& h = *c.hist[q < re ? q : 2 * re - 1 - q];
+        MvVecs<T> v = mv_vecs<T>(c, h);
+        mv_level<T>(c, h, K, 0, false, v);
+        c.ncycles += 1;
+    }
+    mv_out<T>(s, K, kr, c.n, iperm, mvb<T>(c.mv0_x), scale, Z);
+}
+
+// Columns [c0, c0 + kb) of B and X (kb <= 8, run as one batch of K >= kb
+// vectors): the outer iteration of params.outer for each column, no re-setup,
+// preconditioned by the batched composite.
+static pcamg_status solve_multi_block(Ctx& c, int32_t kb, const double* B, double* X, int32_t* iters,
+                                      double* rel_res) {
+    cudaStream_t s = c.stream;
+    const size_t n = (size_t)c.n;
+    int K = 1;
+    while (K < kb) K <<= 1;
+    const bool f32 = c.p.precision == PCAMG_FP32_IR;
+    DBuf<double> R, Z, P, Q, Rold, Zold, sc;
+    for (DBuf<double>* v : {&R, &Z, &P, &Q, &Rold, &Zold}) v->alloc(c.mem, n * kb);
+    sc.alloc(c.mem, 16);
+    std::vector<double> bn(kb), res(kb);
+    std::vector<int32_t> it(kb, 0);
+    std::vector<char> active(kb, 1), restart(kb, 1);
+    // per column: its norm, the fixed power-of-two scale of the FP32 cycles
+    // (as in a single solve), its mean removed, its residual
+    for (int32_t j = 0; j < kb; ++j) {
+        dot(s, c.n, B + j * n, B + j * n, partials(c), slot(c, S_NORM2));
+        bn[j] = read_norm(c);
+        if (!std::isfinite(bn[j]) || !(bn[j] > 0.0)) fail(PCAMG_ERR_INVALID, "a right-hand side is zero or not finite");
+        const double rms = bn[j] / std::sqrt((double)c.n);
+        const int e = (f32 && rms > 0.0 && std::isfinite(rms)) ? std::ilogb(rms) : 0;
+        c.h_red[16 + j] = std::ldexp(1.0, e);
+        c.h_red[24 + j] = std::ldexp(1.0, -e);
+    }
+    PC_CUDA(cudaMemcpyAsync(sc.p, c.h_red + 16, sizeof(double) * 16, cudaMemcpyHostToDevice, s));
+    for (int32_t j = 0; j < kb; ++j) {
+        remove_mean(c, X + j * n);
+        fine_residual(c, X + j * n, B + j * n, R.p + j * n, slot(c, S_NORM2));
+        res[j] = read_norm(c);
+        if (!std::isfinite(res[j])) fail(PCAMG_ERR_INVALID, "an initial guess is not finite");
+        active[j] = res[j] / bn[j] > c.p.tol;
+    }
+    const bool fcg = c.p.outer == PCAMG_OUTER_FCG;
+    pcamg_status status = PCAMG_OK;
+    for (int32_t k = 0; k < c.p.max_iter; ++k) {
+        bool any = false;
+        for (int32_t j = 0; j < kb; ++j) any = any || active[j];
+        if (!any) break;
+        if (f32) mv_precond<float>(c, K, kb, R.p, Z.p, sc.p, sc.p + 8);
+        else mv_precond<double>(c, K, kb, R.p, Z.p, sc.p, sc.p + 8);
+        for (int32_t j = 0; j < kb; ++j) {
+            if (!active[j]) continue;
+            double* x = X + j * n;
+            const double* r = R.p + j * n;
+            const double* z = Z.p + j * n;
+            if (fcg) {   // the single solve's flexible CG, column j
+                double *fp = P.p + j * n, *fq = Q.p + j * n, *frold = Rold.p + j * n, *fzold = Zold.p + j * n;
+                dot(s, c.n, r, z, partials(c), slot(c, S_FRZ));
+                if (restart[j]) {
+                    copy(s, c.n, z, fp);
+                    restart[j] = 0;
+                } else {
+                    copy(s, c.n, r, c.w_t1.p);
+                    axpy(s, c.n, -1.0, frold, c.w_t1.p);
+                    dot(s, c.n, z, c.w_t1.p, partials(c), slot(c, S_FNUM));
+                    dot(s, c.n, fzold, frold, partials(c), slot(c, S_FDEN));
+                    scalar_ops(s, SOP_DIV, slot(c, 0), S_FNUM, S_FDEN, S_FBETA);
+                    xpby_dev(s, c.n, z, slot(c, S_FBETA), fp);
+                }
+                spmv_A(c, fp, fq);
+                dot(s, c.n, fp, fq, partials(c), slot(c, S_FPQ));
+                scalar_ops(s, SOP_PCG_ALPHA, slot(c, 0), S_FRZ, S_FPQ, S_FALPHA);
+                axpy_dev(s, c.n, slot(c, S_FALPHA), 1.0, fp, x);
+                copy(s, c.n, r, frold);
+                copy(s, c.n, z, fzold);
+            } else {
+                axpy(s, c.n, 1.0, z, x);
+            }
+            remove_mean(c, x);
+            fine_residual(c, x, B + j * n, R.p + j * n, slot(c, S_NORM2));
+            const double nres = read_norm(c);
+            it[j] += 1;
+            if (!std::isfinite(nres)) { status = PCAMG_ERR_DIVERGED; active[j] = 0; res[j] = nres; continue; }
+            res[j] = nres;
+            if (res[j] / bn[j] <= c.p.tol) active[j] = 0;
+        }
+    }
+    for (int32_t j = 0; j < kb; ++j) {
+        if (iters) iters[j] = it[j];
+        if (rel_res) rel_res[j] = res[j] / bn[j];
+        if (status == PCAMG_OK && !(res[j] / bn[j] <= c.p.tol)) status = PCAMG_ERR_NOT_CONVERGED;
+    }
+    sync(c);
+    return status;
+}
+
+pcamg_status solve_multi(Ctx& c, int32_t k, const double* B, double* X, int32_t* iters, double* rel_res) {
+    if (k < 1) fail(PCAMG_ERR_INVALID, "no right-hand sides");
+    if (c.hist.empty()) fail(PCAMG_ERR_INVALID, "no hierarchy built");
+    const bool f32 = c.p.precision == PCAMG_FP32_IR;
+    for (Hier* hh : c.hist) {
+        if (f32) ensure_tail_op<float>(c, *hh, 1); else ensure_tail_op<double>(c, *hh, 1);
+    }
+    pcamg_status status = PCAMG_OK;
+    const size_t n = (size_t)c.n;
+    for (int32_t c0 = 0; c0 < k; c0 += 8) {
+        const int32_t kb = std::min<int32_t>(8, k - c0);
+        const pcamg_status sb = solve_multi_block(c, kb, B + c0 * n, X + c0 * n, iters ? iters + c0 : nullptr,
+                                                  rel_res ? rel_res + c0 : nullptr);
+        if (sb == PCAMG_ERR_DIVERGED || (sb != PCAMG_OK && status == PCAMG_OK)) status = sb;
+    }
+    return status;
+}
+
 pcamg_status solve_zero_rhs(Ctx& c, double* x, pcamg_stats* st) {
     cudaStream_t s = c.stream;
     double t0 = now_ms(), t_setup = 0.0;

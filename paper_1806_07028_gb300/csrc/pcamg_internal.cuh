@@ -258,6 +258,11 @@ struct Hier {
     // params.tail_dense selects it; row-major m x tail_ld, m = lev[lt].n
     DBuf<unsigned char> tail_op[2];
     bool tail_op_tried[2] = {false, false};
+    // buffers of the batched cycle (pcamg_solve_multi): per level K
+    // row-interleaved vectors x, a second x (l1-Jacobi levels), b and r, in
+    // the cycle precision; mv_K = the K they were sized for
+    int mv_K = 0;
+    DBuf<unsigned char> mv_x[kMaxLevels], mv_x2[kMaxLevels], mv_b[kMaxLevels], mv_r[kMaxLevels];
     // visits of the tail's first level that one product with tail_op[k] stands
     // for: gamma when the parent (level lt - 1) applies it, 1 when lt = 0
     int tail_visits[2] = {1, 1};
@@ -306,6 +311,11 @@ struct Ctx {
     DBuf<int32_t> gs_ptr0, gs_col0;   // row-permuted copy of A by colour
     DBuf<double> gs_val0_64;
     DBuf<float> gs_val0_32;
+    // finest-level vectors of the batched cycles (K row-interleaved x, b, r;
+    // shared by every hierarchy, so each factor of the composite continues
+    // from the last), sized for mv0_K vectors in the cycle precision
+    int mv0_K = 0;
+    DBuf<unsigned char> mv0_x, mv0_b, mv0_r;
     // perm0: the cycles keep the finest level in colour order; gs_col0 then
     // holds positions (iperm0[column]) and iperm0[row] = position of the row
     bool perm0 = false;
@@ -479,6 +489,27 @@ void d2h(Ctx& c, T* host, const T* dev, size_t count);
 void sync(Ctx& c);
 int64_t read_i64(Ctx& c, const int64_t* dev);
 int32_t read_i32(Ctx& c, const int32_t* dev);
+// batched kernels (k_multi.cu): K = 1, 2, 4 or 8 row-interleaved vectors.
+// mv_rows mode 0: out = b - A x; 1: out = x + (b - A x) / d; 2: Gauss-Seidel on
+// rows (rows ? rows[t] : beg + t), out == x
+template <class T>
+void mv_rows(cudaStream_t s, int mode, int K, int nrows, const int* rows, int beg, const Csr& A, const T* x,
+             const T* b, const T* d, T* out);
+template <class T>
+void mv_restrict(cudaStream_t s, int K, int nc, const int* agg_ptr, const int* mem, const T* pval, const T* r,
+                 T* bc, T* xc, const T* dc);
+template <class T>
+void mv_prolong(cudaStream_t s, int K, int n, const int* agg, const T* pval, const T* xc, T* x);
+template <class T>
+void mv_dense(cudaStream_t s, int K, int m, int ld, const T* N, const T* v, T* x, bool accum);
+template <class T>
+void mv_coarse(cudaStream_t s, int K, int m, const double* X, const T* b, T* x, bool accum);
+template <class T>
+void mv_in(cudaStream_t s, int K, int kr, int n, const int* perm, const double* r, const double* inv, T* v);
+template <class T>
+void mv_out(cudaStream_t s, int K, int kr, int n, const int* iperm, const T* v, const double* scale, double* z);
+// k right-hand sides, column-major n x k (driver.cu)
+pcamg_status solve_multi(Ctx& c, int32_t k, const double* B, double* X, int32_t* iters, double* rel_res);
 double read_f64(Ctx& c, const double* dev);
 // exclusive scan of int32 counts into int32 offsets (out has n+1 entries); returns total
 int64_t scan_i32(Ctx& c, const int32_t* in, int32_t* out, int64_t n);

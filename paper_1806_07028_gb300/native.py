@@ -32,7 +32,7 @@ EXPORTS = [
     "pcamg_mpnn_num_params", "pcamg_mpnn_create", "pcamg_mpnn_destroy", "pcamg_mpnn_get_params",
     "pcamg_mpnn_set_params", "pcamg_mpnn_get_grad", "pcamg_mpnn_forward", "pcamg_mpnn_loss_grad",
     "pcamg_mpnn_adam_step", "pcamg_mpnn_save", "pcamg_mpnn_load", "pcamg_set_allocator",
-    "pcamg_trim_memory",
+    "pcamg_trim_memory", "pcamg_solve_multi",
 ]
 
 
@@ -88,6 +88,7 @@ def lib():
                 "pcamg_adapt": ([vp, vp], i32),
                 "pcamg_solve": ([vp, vp, vp, P(Stats)], i32),
                 "pcamg_solve_zero_rhs": ([vp, vp, P(Stats)], i32),
+                "pcamg_solve_multi": ([vp, i32, vp, vp, vp, vp], i32),
                 "pcamg_solve_host": ([P(Params), i32, i64, vp, vp, vp, vp, vp, P(Stats), vp], i32),
                 "pcamg_cycle": ([vp, i32, i32, vp, vp], i32),
                 "pcamg_smooth_error": ([vp, vp, vp], i32),

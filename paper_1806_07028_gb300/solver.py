@@ -197,6 +197,32 @@ class Solver:
                 N.check(status, self._h)
             return xt, _stats_dict(st, hist, reb)
 
+    def solve_multi(self, B, X0=None, raise_on_error=True):
+        """Several right-hand sides at once (the columns of B, shape n x k):
+        each column's outer iteration (params.outer) without re-setup,
+        preconditioned by the newest hierarchy's V-cycle, up to 8 columns per
+        batched cycle. Returns (X, n x k torch tensor on the device, and a
+        dict with per-column "iters", "rel_res" and the "status")."""
+        torch = _torch()
+        with torch.cuda.device(self.device):
+            Bt = torch.as_tensor(B, dtype=torch.float64)
+            if Bt.dim() == 1:
+                Bt = Bt[:, None]
+            if Bt.dim() != 2 or Bt.shape[0] != self.n:
+                raise ValueError("B must be n x k")
+            k = int(Bt.shape[1])
+            # column-major n x k: column c at offset c * n
+            Bc = Bt.t().contiguous().to(self.device)
+            Xc = (torch.zeros((k, self.n), dtype=torch.float64, device=self.device) if X0 is None else
+                  torch.as_tensor(X0, dtype=torch.float64).reshape(self.n, k).t().contiguous().to(self.device))
+            iters = np.zeros(k, np.int32)
+            rel = np.zeros(k)
+            status = N.lib().pcamg_solve_multi(self._h, k, _ptr(Bc), _ptr(Xc),
+                                               iters.ctypes.data_as(C.c_void_p), rel.ctypes.data_as(C.c_void_p))
+            if raise_on_error and status not in (N.OK, N.ERR_NOT_CONVERGED):
+                N.check(status, self._h)
+            return Xc.t(), {"iters": iters, "rel_res": rel, "status": N.status_name(status)}
+
     def cycle(self, r, hist=-1, gamma=1):
         """One V- (gamma=1) or W-cycle (gamma=2) correction of hierarchy `hist`."""
         torch = _torch()

@@ -1,0 +1,158 @@
+"""Several right-hand sides at once (pcamg_solve_multi): every column runs the
+outer iteration of Alg. 5 without re-setup, preconditioned by Alg. 2's
+composite of V-cycles over every hierarchy held, and the cycles of up to 8
+columns run as one batched cycle. Checked column by column against the oracle
+(orc_solve_multi) on the same hierarchies -- both sides build them from the
+same error vectors, bit for bit -- and against the library's own batches of
+one column."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1806_07028_gb300 import inputs as I
+from tests.helpers import random_graph
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1806_07028_gb300.build import build
+    build()
+    import paper_1806_07028_gb300 as pkg
+    return pkg
+
+
+GRAPHS = {
+    "C1": I.workload("C1"),
+    "C2-small": I.workload("C2-small"),
+    "er": random_graph(3000, 0.002, 7),
+    "ring": I.ring(2000, 4),
+}
+
+
+def _rhs(n, k, seed):
+    return np.stack([I.rhs_normal(n, seed + c) for c in range(k)], axis=1)
+
+
+def _errors(g, m):
+    # m smooth error vectors: the relaxed random start and m - 1 more seeds
+    return [O.start_vector(g, O.default_params(seed=12345 + 31 * j)) for j in range(m)]
+
+
+def _both(P, g, errs, precision, **kw):
+    """The library with one hierarchy per error vector, and the oracle's."""
+    s = P.Solver(g, params=P.default_params(precision=precision, **kw), e0=errs[0])
+    for e in errs[1:]:
+        s.adapt(e)
+    return s, [O.Hierarchy(g, e) for e in errs]
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("precision", [0, 1])
+def test_first_iterate_is_the_oracle_composite(P, name, precision):
+    # stationary outer iteration, one step from x = 0: column c of X is the
+    # composite of V-cycles over both hierarchies applied to b_c, mean removed
+    g = GRAPHS[name]
+    s, hs = _both(P, g, _errors(g, 2), precision, outer=0, max_iter=1)
+    B = _rhs(g.n, 3, 40)
+    X, st = s.solve_multi(B)
+    s.close()
+    assert st["status"] == "NOT_CONVERGED" and list(st["iters"]) == [1, 1, 1]
+    X = X.cpu().numpy()
+    Xo, ito, relo, sto = O.solve_multi(g, B, hs, params=O.default_params(outer=0, max_iter=1))
+    tol = 1e-9 if precision == 0 else 2e-4
+    for c in range(3):
+        z = O.precond(g, B[:, c], hs, O.default_params(numW=0))
+        z = z - z.mean()
+        assert np.allclose(Xo[:, c], z, rtol=0, atol=1e-12 * np.abs(z).max())
+        assert np.linalg.norm(X[:, c] - z) <= tol * np.linalg.norm(z), c
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("precision", [0, 1])
+def test_columns_follow_the_oracle(P, name, precision):
+    # flexible CG per column on three hierarchies (built from smooth random
+    # vectors, not from adapted errors: on C2-small they do not reach 1e-8 in
+    # 60 steps, and the two sides are compared step 60 to step 60)
+    g = GRAPHS[name]
+    s, hs = _both(P, g, _errors(g, 3), precision, outer=1, max_iter=60)
+    k = 3
+    B = _rhs(g.n, k, 20)
+    X, st = s.solve_multi(B)
+    s.close()
+    Xo, ito, relo, sto = O.solve_multi(g, B, hs, params=O.default_params(outer=1, max_iter=60))
+    assert st["status"] == sto
+    X = X.cpu().numpy()
+    A = g.to_scipy()
+    for c in range(k):
+        rel = np.linalg.norm(B[:, c] - A @ X[:, c]) / np.linalg.norm(B[:, c])
+        assert abs(rel - st["rel_res"][c]) <= 1e-3 * rel
+        assert abs(X[:, c].sum()) <= 1e-8 * np.abs(X[:, c]).sum()
+        if relo[c] <= 1e-8:
+            assert rel <= 1e-8
+            assert abs(int(st["iters"][c]) - int(ito[c])) <= (0 if precision == 0 else 1), (c, st["iters"][c], ito[c])
+            assert np.linalg.norm(X[:, c] - Xo[:, c]) <= 1e-4 * np.linalg.norm(Xo[:, c])
+        else:   # the same number of steps, the same residual to rounding
+            assert int(st["iters"][c]) == int(ito[c]) == 60
+            assert abs(rel - relo[c]) <= (1e-6 if precision == 0 else 0.05) * relo[c], (rel, relo[c])
+
+
+@pytest.mark.parametrize("k", [1, 5, 9])
+def test_padding_and_blocks(P, k):
+    # k = 5 runs as a batch of 8 with 3 empty columns; k = 9 as 8 + 1: every
+    # column agrees with its own batch of one
+    g = GRAPHS["C2-small"]
+    s, _ = _both(P, g, _errors(g, 2), 1, outer=1, max_iter=40)
+    B = _rhs(g.n, k, 60)
+    X, st = s.solve_multi(B)
+    X = X.cpu().numpy()
+    for c in range(k):
+        x1, s1 = s.solve_multi(B[:, c:c + 1])
+        x1 = x1.cpu().numpy()[:, 0]
+        assert abs(int(st["iters"][c]) - int(s1["iters"][0])) <= 1
+        assert abs(st["rel_res"][c] - s1["rel_res"][0]) <= 1e-3 * s1["rel_res"][0] + 1e-12
+        assert np.linalg.norm(X[:, c] - x1) <= 1e-4 * np.linalg.norm(x1), c
+    s.close()
+
+
+def test_fullsize_batch(P):
+    # C2 (the finest level in colour order, its diagonal marked): a batch of
+    # four columns against the same columns one at a time, and its first
+    # column against the oracle, 8 flexible-CG steps on two hierarchies
+    g = I.workload("C2")
+    errs = _errors(g, 2)
+    s, hs = _both(P, g, errs, 1, outer=1, max_iter=8)
+    k = 4
+    B = _rhs(g.n, k, 80)
+    X, st = s.solve_multi(B)
+    X = X.cpu().numpy()
+    for c in range(k):
+        x1, s1 = s.solve_multi(B[:, c:c + 1])
+        assert int(st["iters"][c]) == int(s1["iters"][0]) == 8
+        assert abs(st["rel_res"][c] - s1["rel_res"][0]) <= 1e-3 * s1["rel_res"][0]
+        x1 = x1.cpu().numpy()[:, 0]
+        assert np.linalg.norm(X[:, c] - x1) <= 1e-4 * np.linalg.norm(x1)
+    s.close()
+    Xo, ito, relo, sto = O.solve_multi(g, B[:, :1], hs, params=O.default_params(outer=1, max_iter=8))
+    assert int(ito[0]) == 8
+    assert abs(st["rel_res"][0] - relo[0]) <= 0.05 * relo[0]
+
+
+def test_invalid_inputs(P):
+    from paper_1806_07028_gb300 import native as N
+    g = GRAPHS["C1"]
+    s = P.Solver(g)
+    B = _rhs(g.n, 2, 1)
+    B[:, 1] = 0.0
+    with pytest.raises(N.PCAMGError) as ei:
+        s.solve_multi(B)
+    assert ei.value.status == N.ERR_INVALID
+    B[:, 1] = np.nan
+    with pytest.raises(N.PCAMGError) as ei:
+        s.solve_multi(B)
+    assert ei.value.status == N.ERR_INVALID
+    s.close()
