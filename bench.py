@@ -381,6 +381,7 @@ def run_ours(a):
                                                                np.linalg.norm(b_host))}
         if "fp64" in out["forms"] and a.form != "fp64":
             out["speedup_vs_fp64"] = out["forms"]["fp64"]["ms"] / ms
+        out["multi_rhs"] = multi_rhs_leg(dg, g, b_host, params_for(a.form), net_for(a.form), dev)
         # errors: to the oracle's recorded solution of this workload where one
         # exists, between the forms here, and to the oracle's full solve of C1
         err = {}
@@ -561,6 +562,46 @@ def run_reference(a):
                             "extrapolated": True, "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def multi_rhs_leg(dg, g, b_host, params, net, dev, k=4):
+    """Several right-hand sides of the workload's operator (pcamg_solve_multi):
+    an adaptive solve builds the hierarchies, then k new columns are solved in
+    one batch (flexible CG per column, Alg. 2's composite over every hierarchy)
+    and the same columns one at a time (batches of one), timed with CUDA events."""
+    import numpy as np
+    import torch
+    from paper_1806_07028_gb300 import Solver, inputs as I
+    params.outer = 1
+    s = Solver(dg, params=params, device=dev, mpnn=net)
+    s.solve(torch.as_tensor(b_host, device=dev))
+    B = torch.stack([torch.as_tensor(I.rhs_normal(g.n, 500 + c), device=dev) for c in range(k)], 1)
+    s.solve_multi(B[:, :1])   # warm-up: batched buffers and kernels
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    X, sm = s.solve_multi(B)
+    ev[1].record()
+    torch.cuda.synchronize()
+    batched = ev[0].elapsed_time(ev[1])
+    one, iters_one = 0.0, []
+    for c in range(k):
+        ev[0].record()
+        x1, s1 = s.solve_multi(B[:, c:c + 1])
+        ev[1].record()
+        torch.cuda.synchronize()
+        one += ev[0].elapsed_time(ev[1])
+        iters_one.append(int(s1["iters"][0]))
+    A = g.to_scipy()
+    Xh = X.cpu().numpy()
+    rel = [float(np.linalg.norm(B[:, c].cpu().numpy() - A @ Xh[:, c]) / np.linalg.norm(B[:, c].cpu().numpy()))
+           for c in range(k)]
+    out = {"k": k, "hierarchies": s.num_hierarchies, "status": sm["status"],
+           "iters": [int(v) for v in sm["iters"]], "rel_res_host_check": rel,
+           "batched_ms": batched, "one_at_a_time_ms": one, "iters_one_at_a_time": iters_one,
+           "speedup_batched": one / batched, "unknowns_per_s_batched": k * g.n / (batched / 1e3)}
+    s.close()
+    return out
 
 
 def run_kernel(a):
