@@ -206,7 +206,7 @@ template <class T>
 static T* X(Level& L) { return L.xcur ? xalt<T>(L) : LV<T>::x(L); }
 
 template <class T>
-static void smooth(Ctx& c, Level& L, const T* b, T* x, bool forward) {
+static void smooth(Ctx& c, Level& L, const T* b, T* x, bool forward, bool skip_first = false) {
     if (L.jac && xalt<T>(L)) {   // l1-Jacobi in one pass: x' = x + (b - A x) / d
         const T* d;
         if constexpr (sizeof(T) == 8) d = L.dl1_64.p; else d = L.dl1_32.p;
@@ -226,7 +226,7 @@ static void smooth(Ctx& c, Level& L, const T* b, T* x, bool forward) {
     }
     const T* pv;
     if constexpr (sizeof(T) == 8) pv = L.gs_val64_v; else pv = L.gs_val32_v;
-    for (int32_t t = 0; t < L.ncolour; ++t) {
+    for (int32_t t = skip_first ? 1 : 0; t < L.ncolour; ++t) {
         int32_t k = forward ? t : L.ncolour - 1 - t;
         int32_t beg = L.h_colour_ptr[k], end = L.h_colour_ptr[k + 1];
         if (pv) gs_colour_perm<T>(c.stream, beg, end, L.perm ? nullptr : L.colour_rows_v, L.gs_ptr_v, L.gs_col_v, pv, b, x);
@@ -316,9 +316,12 @@ static void cycle_level(Ctx& c, Hier& h, int32_t l, int gamma, bool fresh, bool 
         return;
     }
     T* b = LV<T>::b(L);
-    const bool prof = l == 0 && gamma == 1 && (c.p.profile & 2);
+    const bool prof = l == 0 && gamma == 1 && (c.p.profile & 2) && c.cur_kind != 3;
+    // kind 3: the finest level's first colour was the last one updated, from
+    // the same b and the same other colours
+    const bool skip = l == 0 && c.cur_kind == 3 && !L.jac;
     if (prof) prof_mark(c, h, 0);
-    for (int32_t k = fresh ? 1 : 0; k < c.p.nu_pre; ++k) smooth<T>(c, L, b, X<T>(L), true);
+    for (int32_t k = fresh ? 1 : 0; k < c.p.nu_pre; ++k) smooth<T>(c, L, b, X<T>(L), true, skip && k == 0);
     if (prof) prof_mark(c, h, 1);
     T* x = X<T>(L);
     Level& C = h.lev[l + 1];
@@ -354,11 +357,12 @@ template <class T>
 static void cycle_body(Ctx& c, Hier& h, int kind) {
     for (int32_t l = 0; l < h.nlev; ++l) h.lev[l].xcur = 0;
     Level& L0 = h.lev[0];
-    if (kind != 2) {
+    const bool cont = kind == 2 || kind == 3;
+    if (!cont) {
         PC_CUDA(cudaMemsetAsync(LV<T>::x(L0), 0, sizeof(T) * L0.n, c.stream));
         pdl_after_copy();
     }
-    cycle_level<T>(c, h, 0, kind == 1 ? 2 : 1, false, kind != 2);
+    cycle_level<T>(c, h, 0, kind == 1 ? 2 : 1, false, !cont);
 }
 
 // Forms the tail levels' dense operator for this cycle kind once per
@@ -511,10 +515,15 @@ static void composite(Ctx& c, const double* r, double* z) {
         to_cycle_f64(c, L0, r, L0.b64v);
         PC_CUDA(cudaMemsetAsync(L0.x64v, 0, sizeof(double) * c.n, s));
     }
+    // after the first factor, each one follows the previous factor's
+    // post-sweep on the same finest level (kind 3) when that level is smoothed
+    // by Gauss-Seidel above the coarse tail
+    Level& F = c.hist[0]->lev[0];
+    const bool follow = !F.jac && F.ncolour >= 1 && c.hist[0]->lt >= 1;
     for (int32_t k = 0; k < 2 * re; ++k) {
         const int32_t j = (k < re) ? k : 2 * re - 1 - k;
         c.ncycles += 1;
-        run_body(c, *c.hist[j], 2);
+        run_body(c, *c.hist[j], (k > 0 && follow) ? 3 : 2);
     }
     if (f32) from_cycle_f32(c, L0, L0.x32v, z);
     else from_cycle_f64(c, L0, L0.x64v, z);
@@ -842,7 +851,7 @@ static MvVecs<T> mv_vecs(Ctx& c, Hier& h) {
 }
 
 template <class T>
-static void mv_smooth(Ctx& c, Hier& h, int K, int32_t l, MvVecs<T>& v, bool forward) {
+static void mv_smooth(Ctx& c, Hier& h, int K, int32_t l, MvVecs<T>& v, bool forward, bool skip_first = false) {
     Level& L = h.lev[l];
     const Csr& A = (l == 0 && L.perm) ? L.Ap : L.A;
     if (L.jac && v.x2[l]) {
@@ -852,7 +861,7 @@ static void mv_smooth(Ctx& c, Hier& h, int K, int32_t l, MvVecs<T>& v, bool forw
         std::swap(v.x[l], v.x2[l]);
         return;
     }
-    for (int32_t t = 0; t < L.ncolour; ++t) {
+    for (int32_t t = skip_first ? 1 : 0; t < L.ncolour; ++t) {
         const int32_t k = forward ? t : L.ncolour - 1 - t;
         const int32_t beg = L.h_colour_ptr[k], end = L.h_colour_ptr[k + 1];
         if (L.perm)   // colour order: the colour's rows are positions beg..end
@@ -865,7 +874,7 @@ static void mv_smooth(Ctx& c, Hier& h, int K, int32_t l, MvVecs<T>& v, bool forw
 // One visit of level l. Level 0 continues from its x; a coarser level starts
 // from zero, or from one l1-Jacobi sweep from zero when `fresh`.
 template <class T>
-static void mv_level(Ctx& c, Hier& h, int K, int32_t l, bool fresh, MvVecs<T>& v) {
+static void mv_level(Ctx& c, Hier& h, int K, int32_t l, bool fresh, MvVecs<T>& v, bool follows = false) {
     cudaStream_t s = c.stream;
     Level& L = h.lev[l];
     const bool dense = l == h.lt && h.tail_op[0].p && h.tail_visits[0] == 1;
@@ -879,7 +888,10 @@ static void mv_level(Ctx& c, Hier& h, int K, int32_t l, bool fresh, MvVecs<T>& v
         else mv_coarse<T>(s, K, L.n, h.Xinv.p, rhs, v.x[l], l == 0);
         return;
     }
-    for (int32_t k = fresh ? 1 : 0; k < c.p.nu_pre; ++k) mv_smooth<T>(c, h, K, l, v, true);
+    // `follows` (level 0): a post-sweep of this level just ended with the
+    // first colour, from the same b and other colours, so it is not repeated
+    for (int32_t k = fresh ? 1 : 0; k < c.p.nu_pre; ++k)
+        mv_smooth<T>(c, h, K, l, v, true, follows && l == 0 && k == 0 && !L.jac);
     const Csr& A = (l == 0 && L.perm) ? L.Ap : L.A;
     mv_rows<T>(s, 0, K, L.n, nullptr, 0, A, v.x[l], v.b[l], nullptr, v.r[l]);
     Level& C = h.lev[l + 1];
@@ -908,10 +920,11 @@ static void mv_precond(Ctx& c, int K, int kr, const double* R, double* Z, const 
     const int* iperm = L0.perm ? c.iperm0.p : nullptr;
     mv_in<T>(s, K, kr, c.n, perm, R, inv, mvb<T>(c.mv0_b));
     PC_CUDA(cudaMemsetAsync(c.mv0_x.p, 0, sizeof(T) * (size_t)c.n * K, s));
+    const bool follow = !L0.jac && L0.ncolour >= 1 && c.hist[0]->lt >= 1 && c.hist[0]->nlev >= 2;
     for (int32_t q = 0; q < 2 * re; ++q) {
         Hier& h = *c.hist[q < re ? q : 2 * re - 1 - q];
         MvVecs<T> v = mv_vecs<T>(c, h);
-        mv_level<T>(c, h, K, 0, false, v);
+        mv_level<T>(c, h, K, 0, false, v, follow && q > 0);
         c.ncycles += 1;
     }
     mv_out<T>(s, K, kr, c.n, iperm, mvb<T>(c.mv0_x), scale, Z);

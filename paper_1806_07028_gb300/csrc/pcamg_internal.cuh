@@ -268,13 +268,17 @@ struct Hier {
     int tail_visits[2] = {1, 1};
     int32_t tail_ld = 0;
     // CUDA graphs of the cycle: 0 V-cycle from zero, 1 W-cycle from zero,
-    // 2 V-cycle continuing from the finest level's current x
-    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
-    int64_t graph_kernels[3] = {0, 0, 0};
-    // event-record nodes around the finest-level residual of the V-cycle graphs
-    // (params.profile bit 1), retargeted to fresh events before each replay
-    cudaGraphNode_t prof_node[3][4] = {};   // finest-level pre-sweep start/end, residual start/end
-    cudaGraph_t graph_tmpl[3] = {nullptr, nullptr, nullptr};   // graphs those nodes belong to
+    // 2 V-cycle continuing from the finest level's current x, 3 the same right
+    // after another such cycle's post-sweep (its pre-sweep starts at the
+    // second colour: the first colour's update would repeat, bit for bit, the
+    // last one of that post-sweep)
+    cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
+    int64_t graph_kernels[4] = {0, 0, 0, 0};
+    // event-record nodes around the finest-level pre-sweep and residual of the
+    // V-cycle graphs of kinds 0 and 2 (params.profile bit 1), retargeted to
+    // fresh events before each replay
+    cudaGraphNode_t prof_node[4][4] = {};   // finest-level pre-sweep start/end, residual start/end
+    cudaGraph_t graph_tmpl[4] = {nullptr, nullptr, nullptr, nullptr};   // graphs those nodes belong to
     ~Hier();
 };
 
