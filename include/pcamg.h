@@ -245,7 +245,8 @@ PCAMG_API pcamg_status pcamg_solve_zero_rhs(pcamg_handle h, double* d_x, pcamg_s
  * pcamg_adapt and earlier solves built; z += B_j (r - A z) for j = 1..Re,
  * Re..1 from z = 0). The cycles of up to 8 columns run together: every pass
  * over a level's matrix serves all of them (the level's vectors
- * row-interleaved, K = 1, 2, 4 or 8 per pass). A column agrees with the same
+ * row-interleaved, K = 2, 4 or 8 per pass); a batch of one column runs the
+ * single-vector cycles of pcamg_solve. A column agrees with the same
  * iteration on that column alone to rounding (the batched row sums take the
  * sub-warp order).
  * d_B, d_X: device, column-major n x k (column c at offset c*n); d_X holds the

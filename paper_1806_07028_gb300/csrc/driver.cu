@@ -971,8 +971,15 @@ static pcamg_status solve_multi_block(Ctx& c, int32_t kb, const double* B, doubl
         bool any = false;
         for (int32_t j = 0; j < kb; ++j) any = any || active[j];
         if (!any) break;
-        if (f32) mv_precond<float>(c, K, kb, R.p, Z.p, sc.p, sc.p + 8);
-        else mv_precond<double>(c, K, kb, R.p, Z.p, sc.p, sc.p + 8);
+        if (kb == 1) {   // one column: the single-vector composite (graph-captured cycles)
+            ScaleGuard sg{c};
+            fix_scale(c, bn[0]);
+            composite(c, R.p, Z.p);
+        } else if (f32) {
+            mv_precond<float>(c, K, kb, R.p, Z.p, sc.p, sc.p + 8);
+        } else {
+            mv_precond<double>(c, K, kb, R.p, Z.p, sc.p, sc.p + 8);
+        }
         for (int32_t j = 0; j < kb; ++j) {
             if (!active[j]) continue;
             double* x = X + j * n;

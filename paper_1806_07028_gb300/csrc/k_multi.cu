@@ -22,6 +22,48 @@ __device__ __forceinline__ T group_sum_rt(T v, int lpr) {
     return v;
 }
 
+// a row's K values as wide loads and stores (row i starts at i * K, so a row
+// of 2, 4 or 8 floats, or 2, 4 or 8 doubles, is 8- or 16-byte aligned)
+template <class T, int K>
+__device__ __forceinline__ void ldk(const T* p, T (&v)[K]) {
+    if constexpr (sizeof(T) == 4 && K % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < K / 4; ++q) {
+            const float4 w = reinterpret_cast<const float4*>(p)[q];
+            v[4 * q] = w.x; v[4 * q + 1] = w.y; v[4 * q + 2] = w.z; v[4 * q + 3] = w.w;
+        }
+    } else if constexpr (sizeof(T) == 4 && K == 2) {
+        const float2 w = *reinterpret_cast<const float2*>(p);
+        v[0] = w.x; v[1] = w.y;
+    } else if constexpr (sizeof(T) == 8 && K % 2 == 0) {
+#pragma unroll
+        for (int q = 0; q < K / 2; ++q) {
+            const double2 w = reinterpret_cast<const double2*>(p)[q];
+            v[2 * q] = w.x; v[2 * q + 1] = w.y;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < K; ++c) v[c] = p[c];
+    }
+}
+
+template <class T, int K>
+__device__ __forceinline__ void stk(T* p, const T (&v)[K]) {
+    if constexpr (sizeof(T) == 4 && K % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < K / 4; ++q)
+            reinterpret_cast<float4*>(p)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else if constexpr (sizeof(T) == 4 && K == 2) {
+        *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+    } else if constexpr (sizeof(T) == 8 && K % 2 == 0) {
+#pragma unroll
+        for (int q = 0; q < K / 2; ++q) reinterpret_cast<double2*>(p)[q] = make_double2(v[2 * q], v[2 * q + 1]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < K; ++c) p[c] = v[c];
+    }
+}
+
 enum { MV_RES = 0, MV_JAC = 1, MV_GS = 2 };
 
 // Rows t of [0, nrows): row = rows ? rows[t] : beg + t. A row's entries are
@@ -59,7 +101,8 @@ __global__ void __launch_bounds__(256) k_mv_rows(int nrows, const int* __restric
                     continue;
                 }
                 if (j < 0) j = ~j;
-                const T* xj = x + (size_t)j * K;
+                T xj[K];
+                ldk<T, K>(x + (size_t)j * K, xj);
 #pragma unroll
                 for (int c = 0; c < K; ++c) s[c] = mfma(a, xj[c], s[c]);
             }
@@ -69,17 +112,22 @@ __global__ void __launch_bounds__(256) k_mv_rows(int nrows, const int* __restric
         if (MODE == MV_GS) dg = group_sum_rt(dg, lpr);
         if (t < nrows && sub == 0) {
             const size_t o = (size_t)row * K;
+            T bv[K], ov[K];
+            ldk<T, K>(b + o, bv);
             if (MODE == MV_RES) {
 #pragma unroll
-                for (int c = 0; c < K; ++c) out[o + c] = b[o + c] - s[c];
+                for (int c = 0; c < K; ++c) ov[c] = bv[c] - s[c];
             } else if (MODE == MV_JAC) {
                 const T dr = __ldg(d + row);
+                T xv[K];
+                ldk<T, K>(x + o, xv);
 #pragma unroll
-                for (int c = 0; c < K; ++c) out[o + c] = x[o + c] + (b[o + c] - s[c]) / dr;
+                for (int c = 0; c < K; ++c) ov[c] = xv[c] + (bv[c] - s[c]) / dr;
             } else {
 #pragma unroll
-                for (int c = 0; c < K; ++c) out[o + c] = (b[o + c] - s[c]) / dg;
+                for (int c = 0; c < K; ++c) ov[c] = (bv[c] - s[c]) / dg;
             }
+            stk<T, K>(out + o, ov);
         }
     }
 }
@@ -98,14 +146,18 @@ __global__ void k_mv_restrict(int nc, const int* __restrict__ agg_ptr, const int
         for (int t = __ldg(agg_ptr + I); t < e; ++t) {
             const int u = __ldg(mem + t);
             const T p = pval ? __ldg(pval + u) : T(1);
+            T ru[K];
+            ldk<T, K>(r + (size_t)u * K, ru);
 #pragma unroll
-            for (int c = 0; c < K; ++c) s[c] += pval ? p * r[(size_t)u * K + c] : r[(size_t)u * K + c];
+            for (int c = 0; c < K; ++c) s[c] += pval ? p * ru[c] : ru[c];
         }
         const T dI = dc ? __ldg(dc + I) : T(1);
+        stk<T, K>(bc + (size_t)I * K, s);
+        if (xc) {
+            T xv[K];
 #pragma unroll
-        for (int c = 0; c < K; ++c) {
-            bc[(size_t)I * K + c] = s[c];
-            if (xc) xc[(size_t)I * K + c] = dc ? s[c] / dI : T(0);
+            for (int c = 0; c < K; ++c) xv[c] = dc ? s[c] / dI : T(0);
+            stk<T, K>(xc + (size_t)I * K, xv);
         }
     }
 }
@@ -115,10 +167,13 @@ template <class T, int K>
 __global__ void k_mv_prolong(int n, const int* __restrict__ agg, const T* __restrict__ pval,
                              const T* __restrict__ xc, T* __restrict__ x) {
     for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x) {
-        const T* cu = xc + (size_t)__ldg(agg + u) * K;
+        T cu[K], xu[K];
+        ldk<T, K>(xc + (size_t)__ldg(agg + u) * K, cu);
+        ldk<T, K>(x + (size_t)u * K, xu);
         const T p = pval ? __ldg(pval + u) : T(1);
 #pragma unroll
-        for (int c = 0; c < K; ++c) x[(size_t)u * K + c] += pval ? p * cu[c] : cu[c];
+        for (int c = 0; c < K; ++c) xu[c] += pval ? p * cu[c] : cu[c];
+        stk<T, K>(x + (size_t)u * K, xu);
     }
 }
 
