@@ -564,7 +564,7 @@ def run_reference(a):
     print(json.dumps(out), flush=True)
 
 
-def multi_rhs_leg(dg, g, b_host, params, net, dev, k=4):
+def multi_rhs_leg(dg, g, b_host, params, net, dev, k=8):
     """Several right-hand sides of the workload's operator (pcamg_solve_multi):
     an adaptive solve builds the hierarchies, then k new columns are solved in
     one batch (flexible CG per column, Alg. 2's composite over every hierarchy)

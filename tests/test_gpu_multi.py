@@ -142,6 +142,24 @@ def test_fullsize_batch(P):
     assert abs(st["rel_res"][0] - relo[0]) <= 0.05 * relo[0]
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_single_level_hierarchies(P, precision):
+    # n <= n_min: every hierarchy is one level, its coarsest solve; each factor
+    # of the composite is then x += X (b - A x)
+    g = I.grid2d(12, 12)
+    s, hs = _both(P, g, _errors(g, 2), precision, outer=1)
+    assert s.num_levels(0) == 1
+    B = _rhs(g.n, 3, 7)
+    X, st = s.solve_multi(B)
+    s.close()
+    Xo, ito, relo, sto = O.solve_multi(g, B, hs, params=O.default_params(outer=1))
+    assert st["status"] == sto == "OK"
+    X = X.cpu().numpy()
+    for c in range(3):
+        assert abs(int(st["iters"][c]) - int(ito[c])) <= 1
+        assert np.linalg.norm(X[:, c] - Xo[:, c]) <= 1e-6 * np.linalg.norm(Xo[:, c])
+
+
 def test_invalid_inputs(P):
     from paper_1806_07028_gb300 import native as N
     g = GRAPHS["C1"]
