@@ -234,6 +234,16 @@ static void smooth(Ctx& c, Level& L, const T* b, T* x, bool forward, bool skip_f
     }
 }
 
+// Rows the prolongation must update: on a level kept in colour order and
+// smoothed by Gauss-Seidel after the coarse correction, the backward post-sweep
+// begins with the last colour, whose new values do not read their own old x:
+// the prolongation of those rows (the last range of the order) would be
+// overwritten unread.
+static int32_t prolong_rows(const Level& L, int32_t nu_post) {
+    if (L.perm && !L.jac && nu_post >= 1 && L.ncolour >= 2) return L.h_colour_ptr[L.ncolour - 1];
+    return L.n;
+}
+
 // ---------------------------------------------------------------- live timing
 // params.profile bit 1: CUDA events around the finest-level residual of every
 // V-cycle. Inside a captured graph they are event-record nodes, retargeted to a
@@ -346,7 +356,8 @@ static void cycle_level(Ctx& c, Hier& h, int32_t l, int gamma, bool fresh, bool 
                      LV<T>::x(C), false);
     else
         for (int g = 0; g < gamma; ++g) cycle_level<T>(c, h, l + 1, gamma, child_fresh && g == 0, g == 0);
-    prolong_add<T>(s, L.n, L.perm ? L.aggp.p : L.agg.p, l == 0 ? LV<T>::pv(L) : nullptr, X<T>(C), x);
+    prolong_add<T>(s, prolong_rows(L, c.p.nu_post), L.perm ? L.aggp.p : L.agg.p, l == 0 ? LV<T>::pv(L) : nullptr,
+                   X<T>(C), x);
     for (int32_t k = 0; k < c.p.nu_post; ++k) smooth<T>(c, L, b, X<T>(L), false);
 }
 
@@ -902,7 +913,7 @@ static void mv_level(Ctx& c, Hier& h, int K, int32_t l, bool fresh, MvVecs<T>& v
     const T* pv = l == 0 ? LV<T>::pv(L) : nullptr;
     mv_restrict<T>(s, K, L.nc, L.agg_ptr.p, L.perm ? L.memp.p : L.agg_mem.p, pv, v.r[l], v.b[l + 1], v.x[l + 1], dc);
     mv_level<T>(c, h, K, l + 1, child_fresh, v);
-    mv_prolong<T>(s, K, L.n, L.perm ? L.aggp.p : L.agg.p, pv, v.x[l + 1], v.x[l]);
+    mv_prolong<T>(s, K, prolong_rows(L, c.p.nu_post), L.perm ? L.aggp.p : L.agg.p, pv, v.x[l + 1], v.x[l]);
     for (int32_t k = 0; k < c.p.nu_post; ++k) mv_smooth<T>(c, h, K, l, v, false);
 }
 
