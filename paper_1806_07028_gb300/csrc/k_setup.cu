@@ -82,24 +82,48 @@ struct GalSrc {
     }
 };
 
-// Warp per row. The row's contributions are numbered in their fixed order
-// (member rows one after another); lanes stage them as 64-bit keys
-// (column << 32 | number) with their values in shared memory, the warp sorts
-// the keys (bitonic, padded to a power of two), and the first lane of each run
-// of equal columns adds the run's values in contribution order. Rows with more
-// than kWarpMembers member rows or kWarpCap contributions are flagged for the
-// block kernels. (128 keeps a warp's scratch at 2.8 KB, so the block's eight
-// warps fit eight times per SM; the rare longer rows take the block kernels.)
+// Warp per row. The row's contributions are numbered e = 0..total-1 in their
+// fixed order (member rows one after another), and every output entry is the
+// sum of one column's contributions taken in that order. A row of more than
+// 32 contributions whose columns all fit 24 bits is merged through a per-warp
+// hash table keyed by column (twice as many slots as the padded contribution
+// count): each round of 32 contributions groups equal columns (a warp match),
+// the group's first lane adds the column with the group's size, the distinct
+// columns are then sorted, each column's contributions are given consecutive
+// positions in contribution order, and one lane per column adds them up.
+// Shorter or wider rows sort (column, e) keys of all contributions instead
+// (bitonic, padded to a power of two) and the first lane of each run of equal
+// columns adds the run. Rows with more than kWarpMembers member rows or
+// kWarpCap contributions are flagged for the block kernels. (A warp's scratch
+// is 3.2 KB, so the block's eight warps fit eight times per SM; the rare
+// longer rows take the block kernels.)
 constexpr int kWarpCap = 128;
 constexpr int kWarpMembers = 64;
 constexpr int kWarpsPerBlock = 8;
+constexpr int kHashSlots = 256;              // at most twice kWarpCap: never more than half full
+constexpr uint32_t kHashEmpty = 0xffffffffu;
+constexpr uint16_t kNoSlot = 0xffffu;
+static_assert(kHashSlots == 2 * kWarpCap && kHashSlots == 256, "slot numbers are 8 bits");
 
-struct WarpScratch {
-    uint64_t key[kWarpCap];
-    double val[kWarpCap];
-    int mpre[kWarpMembers + 1];
-    int mrow[kWarpMembers];
-    int mbeg[kWarpMembers];   // first input entry of each member row
+struct MemberInfo {
+    int pre[kWarpMembers + 1];   // prefix of the member rows' lengths
+    int row[kWarpMembers];
+    int beg[kWarpMembers];       // first input entry of each member row
+};
+
+struct alignas(16) WarpScratch {
+    union {
+        uint64_t key[kWarpCap];        // wide rows: the sorted keys
+        uint32_t hash[kHashSlots];     // narrow rows: column << 8 | count, later a column's next position
+    };
+    double val[kWarpCap];              // value of contribution e
+    union {
+        MemberInfo m;                  // while the contributions are staged
+        uint32_t dist[kWarpCap + 1];   // narrow rows, afterwards: distinct columns (column << 8 | slot),
+                                       // then the columns' first merged positions
+    };
+    uint16_t slot[kWarpCap];           // narrow rows: table slot of contribution e (kNoSlot: skipped)
+    uint8_t ord[kWarpCap];             // narrow rows: the contribution at each merged position
 };
 
 // Ascending bitonic sort of 32*R 64-bit keys held in registers: key i lives in
@@ -166,12 +190,26 @@ __device__ __forceinline__ void sort_keys_regs32(uint32_t (&key)[R], int lane) {
     }
 }
 
-// Stage the row's contributions (numbered e = 0..total-1 in their fixed order)
-// as keys (column, e) in registers and values in W.val[e], sort the keys and
-// store them in W.key as (column << 32 | e) in sorted order. Keys of skipped
-// contributions and of the padding are ~0 and sort last. NARROW packs a key
-// into 32 bits, column << 8 | e, when every column is below 2^24 and e below
-// 255 (so no real key equals the padding); the order is the same.
+// Contribution e of the row (e < total): its column key (kSkip when dropped)
+// and value, from the member row t with pre[t] <= e < pre[t + 1].
+template <class Src>
+__device__ __forceinline__ void contribution(int r, int nm, int e, const Src& src, const WarpScratch& W,
+                                             uint32_t& kk, double& v) {
+    int lo = 0, hi = nm - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (W.m.pre[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    const int j = W.m.row[lo];
+    const int k = W.m.beg[lo] + (e - W.m.pre[lo]);
+    src.kv(r, j, k, kk, v);
+}
+
+// Stage the contributions as keys (column, e) in registers and values in
+// W.val[e], sort the keys and store them in W.key as (column << 32 | e) in
+// sorted order. Keys of skipped contributions and of the padding are ~0 and
+// sort last. NARROW (every column below 2^24, at most 32 contributions) packs
+// a key into 32 bits, column << 8 | e; the order is the same.
 template <int R, bool NARROW, class Src>
 __device__ __forceinline__ void stage_sort_keys(int lane, int r, int nm, int total, const Src& src,
                                                 WarpScratch& W) {
@@ -184,15 +222,8 @@ __device__ __forceinline__ void stage_sort_keys(int lane, int r, int nm, int tot
         key[q] = kPad;
         double v = 0.0;
         if (e < total) {
-            int lo = 0, hi = nm - 1;          // member t with mpre[t] <= e < mpre[t+1]
-            while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (W.mpre[mid] <= e) lo = mid; else hi = mid - 1;
-            }
-            const int j = W.mrow[lo];
-            const int k = W.mbeg[lo] + (e - W.mpre[lo]);
             uint32_t kk;
-            src.kv(r, j, k, kk, v);
+            contribution(r, nm, e, src, W, kk, v);
             if (kk != kSkip) key[q] = NARROW ? (K)((kk << 8) | (uint32_t)e) : (K)(((uint64_t)kk << 32) | (uint64_t)e);
         }
         W.val[e] = v;
@@ -210,13 +241,127 @@ __device__ __forceinline__ void stage_sort_keys(int lane, int r, int nm, int tot
     }
 }
 
+// Narrow rows (every column below 2^24), first half: stage the contributions
+// (values in W.val[e]) and count each column's contributions in the hash
+// table, W.hash[slot] = column << 8 | count (a count is at most kWarpCap, so it
+// never reaches the column bits). Lanes of one round with the same column form
+// one group; the group's first lane adds the column with the group's size, so
+// the table takes one atomic per distinct column and round. Returns the number
+// of distinct columns D, listed unsorted in W.dist[0..D) as column << 8 | slot,
+// and leaves each contribution's slot in W.slot[e].
+template <class Src>
+__device__ __forceinline__ int hash_stage(int lane, int r, int nm, int total, int hbits, const Src& src,
+                                          WarpScratch& W) {
+    const int nslots = 1 << hbits;   // twice the padded contribution count, 128 or 256
+    uint4* h4 = reinterpret_cast<uint4*>(W.hash);
+    const uint4 empty = make_uint4(kHashEmpty, kHashEmpty, kHashEmpty, kHashEmpty);
+    for (int t = lane; t < nslots / 4; t += 32) h4[t] = empty;
+    __syncwarp();
+    for (int e0 = 0; e0 < total; e0 += 32) {
+        const int e = e0 + lane;
+        uint32_t kk = kSkip;
+        if (e < total) {
+            double v;
+            contribution(r, nm, e, src, W, kk, v);
+            W.val[e] = v;
+        }
+        const unsigned grp = __match_any_sync(0xffffffffu, kk);
+        const int lead = __ffs(grp) - 1;
+        int sl = kNoSlot;
+        if (kk != kSkip && lane == lead) {
+            const uint32_t n = (uint32_t)__popc(grp);
+            uint32_t h = (kk * 2654435761u) >> (32 - hbits);   // multiplicative hash
+            // at most nslots / 2 columns: a free or matching slot is always
+            // found within the bound
+            for (int probe = 0; probe < nslots; ++probe, h = (h + 1) & (uint32_t)(nslots - 1)) {
+                const uint32_t old = atomicCAS(&W.hash[h], kHashEmpty, (kk << 8) | n);
+                if (old == kHashEmpty) { sl = (int)h; break; }
+                if ((old >> 8) == kk) { atomicAdd(&W.hash[h], n); sl = (int)h; break; }
+            }
+        }
+        sl = __shfl_sync(0xffffffffu, sl, lead);
+        if (e < total) W.slot[e] = (kk != kSkip) ? (uint16_t)sl : kNoSlot;
+        __syncwarp();
+    }
+    // the member lists are no longer read: W.dist takes their place
+    int D = 0;
+    for (int h = lane; h < nslots; h += 32) {
+        const uint32_t w = W.hash[h];
+        const bool used = w != kHashEmpty;
+        const unsigned b = __ballot_sync(0xffffffffu, used);
+        if (used) W.dist[D + __popc(b & ((1u << lane) - 1u))] = (w & 0xffffff00u) | (uint32_t)h;
+        D += __popc(b);
+    }
+    __syncwarp();
+    return D;
+}
+
+// Narrow rows, second half (D distinct columns, D <= 32 * R): sort the
+// distinct columns, give column i the merged positions W.dist[i] ..
+// W.dist[i + 1] - 1 (in column order), place each contribution at its
+// column's next position, round by round and lane by lane, i.e. in
+// contribution order, and let lane i add column i's values in that order.
+// Writes the row's D entries at ocol/oval[o ..].
+template <int R>
+__device__ __forceinline__ void hash_emit(int lane, int total, int D, WarpScratch& W, int64_t o,
+                                          int* __restrict__ ocol, double* __restrict__ oval) {
+    uint32_t key[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) key[q] = (lane + 32 * q < D) ? W.dist[lane + 32 * q] : 0xffffffffu;
+    sort_keys_regs32<R>(key, lane);
+    __syncwarp();   // every lane has read W.dist: it now takes the columns' first positions
+    int carry = 0;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int i = lane + 32 * q;
+        const uint32_t sl = key[q] & 255u;
+        const int c = (i < D) ? (int)(W.hash[sl] & 255u) : 0;
+        int inc = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, d);
+            if (lane >= d) inc += y;
+        }
+        __syncwarp();
+        if (i < D) { W.hash[sl] = (uint32_t)(carry + inc - c); W.dist[i] = (uint32_t)(carry + inc - c); }
+        carry += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    if (lane == 0) W.dist[D] = (uint32_t)carry;
+    __syncwarp();
+    for (int e0 = 0; e0 < total; e0 += 32) {
+        const int e = e0 + lane;
+        const uint32_t sl = (e < total) ? W.slot[e] : kNoSlot;
+        const unsigned grp = __match_any_sync(0xffffffffu, sl);
+        uint32_t base = 0;
+        if (sl != kNoSlot) {
+            base = W.hash[sl];
+            W.ord[base + __popc(grp & ((1u << lane) - 1u))] = (uint8_t)e;
+        }
+        __syncwarp();
+        if (sl != kNoSlot && lane == __ffs(grp) - 1) W.hash[sl] = base + (uint32_t)__popc(grp);
+        __syncwarp();
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+        const int i = lane + 32 * q;
+        if (i < D) {
+            const int b = (int)W.dist[i], en = (int)W.dist[i + 1];
+            double sum = W.val[W.ord[b]];
+            for (int t = b + 1; t < en; ++t) sum = __dadd_rn(sum, W.val[W.ord[t]]);
+            ocol[o + i] = (int)(key[q] >> 8);
+            if (oval) oval[o + i] = sum;
+        }
+    }
+}
+
 // MODE 0: count the row's distinct columns (cnt) and flag long rows;
 // MODE 1: write the row at optr[r] (counts known);
 // MODE 2: both at once -- count, flag, and write the row at tptr[r] of a
 //         temporary layout sized by each row's contribution count (compacted
 //         afterwards), so the sort-reduce runs once.
-// (eight blocks of eight warps per SM: the row's sort-reduce is a long chain
-// of dependent shuffles and compares, so resident warps are what hides it)
+// (eight blocks of eight warps per SM: a row's merge is a long chain of
+// dependent shuffles, shared-memory atomics and compares, so resident warps
+// are what hides it)
 template <class Src, int MODE>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 8) k_rowprod_warp(
         int nrows, Src src, int* __restrict__ cnt, unsigned char* __restrict__ is_long,
@@ -270,7 +415,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 8) k_rowprod_warp(
                 if (lane >= o) inc += y;
             }
             total = __shfl_sync(0xffffffffu, inc, 31);
-            if (lane < nm) { W.mpre[lane + 1] = inc; W.mrow[lane] = mr; W.mbeg[lane] = mb; }
+            if (lane < nm) { W.m.pre[lane + 1] = inc; W.m.row[lane] = mr; W.m.beg[lane] = mb; }
             if (nm > 32) {
                 int len2 = 0, mr2 = 0, mb2 = 0;
                 if (lane + 32 < nm) { mr2 = src.mem_at(cur.base, lane + 32); mb2 = src.in_beg(mr2); len2 = src.in_end(mr2) - mb2; }
@@ -280,20 +425,28 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 8) k_rowprod_warp(
                     int y = __shfl_up_sync(0xffffffffu, inc2, o);
                     if (lane >= o) inc2 += y;
                 }
-                if (lane + 32 < nm) { W.mpre[lane + 33] = total + inc2; W.mrow[lane + 32] = mr2; W.mbeg[lane + 32] = mb2; }
+                if (lane + 32 < nm) { W.m.pre[lane + 33] = total + inc2; W.m.row[lane + 32] = mr2; W.m.beg[lane + 32] = mb2; }
                 total += __shfl_sync(0xffffffffu, inc2, 31);
             }
-            if (lane == 0) W.mpre[0] = 0;
+            if (lane == 0) W.m.pre[0] = 0;
             over = total > kWarpCap;
         }
-        if (!over) {
+        if (!over && narrow && total > 32) {
+            // columns of a square product are row numbers, below nrows
+            __syncwarp();
+            const int64_t o = (MODE == 1) ? (int64_t)optr[r] : (MODE == 2 ? tptr[r] : 0);
+            const int D = hash_stage(lane, r, nm, total, total > 64 ? 8 : 7, src, W);
+            if (FILL && D > 0) {
+                if (D <= 32) hash_emit<1>(lane, total, D, W, o, ocol, oval);
+                else if (D <= 64) hash_emit<2>(lane, total, D, W, o, ocol, oval);
+                else hash_emit<4>(lane, total, D, W, o, ocol, oval);
+            }
+            if (COUNT && lane == 0) { cnt[r] = D; is_long[r] = 0; }
+        } else if (!over) {
             __syncwarp();
             int P = 32;
             while (P < total) P <<= 1;
-            // columns of a square product are row numbers, below nrows
             if (narrow && P == 32) stage_sort_keys<1, true>(lane, r, nm, total, src, W);
-            else if (narrow && P == 64) stage_sort_keys<2, true>(lane, r, nm, total, src, W);
-            else if (narrow && P == 128) stage_sort_keys<4, true>(lane, r, nm, total, src, W);
             else if (P == 32) stage_sort_keys<1, false>(lane, r, nm, total, src, W);
             else if (P == 64) stage_sort_keys<2, false>(lane, r, nm, total, src, W);
             else stage_sort_keys<4, false>(lane, r, nm, total, src, W);
