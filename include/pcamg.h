@@ -49,7 +49,10 @@ typedef enum {
     PCAMG_ERR_OOM = 3,            /* device allocation failed */
     PCAMG_ERR_CUDA = 4,           /* a CUDA runtime call or launch failed */
     PCAMG_ERR_ROUND_CAP = 5,      /* an iterative setup round hit its cap */
-    PCAMG_ERR_SINGULAR = 6,       /* coarsest factorisation broke down */
+    PCAMG_ERR_SINGULAR = 6,       /* reserved, not returned: a coarsest-level pivot at or
+                                     below 1e-12 of the largest diagonal entry is pinned
+                                     (its row and column replaced by the identity), so the
+                                     dense factorisation does not break down */
     PCAMG_ERR_NOT_CONVERGED = 7,  /* max_iter reached before tol (stats are filled) */
     PCAMG_ERR_DIVERGED = 8,       /* NaN/Inf residual */
     PCAMG_ERR_COARSE_TOO_BIG = 9, /* coarsening stalled above dense_max */

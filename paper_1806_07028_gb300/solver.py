@@ -200,8 +200,8 @@ class Solver:
     def solve_multi(self, B, X0=None, raise_on_error=True):
         """Several right-hand sides at once (the columns of B, shape n x k):
         each column's outer iteration (params.outer) without re-setup,
-        preconditioned by the newest hierarchy's V-cycle, up to 8 columns per
-        batched cycle. Returns (X, n x k torch tensor on the device, and a
+        preconditioned by Alg. 2's symmetric composite of V-cycles over every
+        hierarchy the handle holds, up to 8 columns per batched cycle. Returns (X, n x k torch tensor on the device, and a
         dict with per-column "iters", "rel_res" and the "status")."""
         torch = _torch()
         with torch.cuda.device(self.device):

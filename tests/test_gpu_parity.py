@@ -323,6 +323,28 @@ def test_invalid_inputs_return_status(P):
         assert ei.value.status == N.ERR_INVALID
 
 
+def test_fp64_is_scale_equivariant_and_fp32_range_gives_diverged(P):
+    # A scaled by 2^-200 stays exact in FP64 (every entry is still a normal
+    # number) and every step of Alg. 5 is then scaled exactly: the same
+    # iterations and re-setups, x scaled by 2^200. In FP32 every entry of that
+    # matrix underflows to zero, the first cycle divides by a zero diagonal and
+    # the residual is no longer finite: DIVERGED, returned with the statistics.
+    g = GRAPHS["C1"]
+    s = 2.0 ** -200
+    gs = I.Graph(g.rowptr, g.col, g.val * s)
+    b = I.rhs_normal(g.n, 3)
+    x0, st0 = P.Solver(g, params=P.default_params(precision=0)).solve(b)
+    x1, st1 = P.Solver(gs, params=P.default_params(precision=0)).solve(b)
+    assert st0["status"] == "OK" and st1["status"] == "OK"
+    assert (st1["iters"], st1["resetups"]) == (st0["iters"], st0["resetups"])
+    x0h, x1h = x0.cpu().numpy(), x1.cpu().numpy() * s
+    assert np.linalg.norm(x1h - x0h) <= 1e-10 * np.linalg.norm(x0h)
+    s2 = P.Solver(gs, params=P.default_params(precision=1))
+    x2, st2 = s2.solve(b, raise_on_error=False)
+    assert st2["status"] == "DIVERGED" and st2["iters"] == 0
+    assert not np.isfinite(st2["rel_res"])
+
+
 @pytest.mark.parametrize("name", ["C1", "C2-small", "C4-small"])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_coarse_tail_block_matches_per_level_kernels(P, name, precision):
