@@ -7,6 +7,7 @@
 //  * list ranking of the paths, matching along them and leftover handling
 //    (Alg. 3), aggregate numbering, members, P values and path shortening.
 // Every integer result is deterministic and independent of thread scheduling.
+#include <utility>
 #include <algorithm>
 #include <climits>
 #include <type_traits>
@@ -771,15 +772,18 @@ __device__ __forceinline__ bool edge_before(double w1, int a1, int b1, double w2
 }
 
 // Each row re-ordered by (w desc, column asc): the order in which a vertex
-// proposes its edges. Thread per row for short rows.
-// Class of every row for the proposal ordering: 1 = up to kOrderWarpCap
-// candidates, sorted by a warp; 2 = longer, listed for a block each.
+// proposes its edges.
+// Class of every row for the proposal ordering: 0 = up to kOrderThreadCap
+// candidates, sorted by one thread; 1 = up to kOrderWarpCap, sorted by a warp;
+// 2 = longer, listed for a block each.
+constexpr int kOrderThreadCap = 24;   // every interior row of a 3D 7-point grid's A^2 pattern
 __global__ void k_order_rows_classify(int n, const int* __restrict__ ptr, unsigned char* __restrict__ cls,
                                       int* __restrict__ long_list, int* __restrict__ long_count) {
     FOR_EACH(u64, n) {
         const int u = (int)u64;
-        const bool big = ptr[u + 1] - ptr[u] > kOrderWarpCap;
-        cls[u] = big ? 2 : 1;
+        const int len = ptr[u + 1] - ptr[u];
+        const bool big = len > kOrderWarpCap;
+        cls[u] = big ? 2 : (len <= kOrderThreadCap ? 0 : 1);
         if (big) long_list[atomicAdd(long_count, 1)] = u;
     }
 }
@@ -796,6 +800,80 @@ __global__ void k_order_rows_classify(int n, const int* __restrict__ ptr, unsign
 // result unique.
 __device__ __forceinline__ bool order_before(uint64_t w1, int c1, uint64_t w2, int c2) {
     return (w1 > w2) || (w1 == w2 && c1 < c2);
+}
+
+// Thread per row for rows of up to kOrderThreadCap entries (class 0): Batcher's
+// odd-even merge sort on 32 positions held in the thread's registers (every
+// index is a compile-time constant once the loops are unrolled). Every
+// comparator puts the element that comes first (order_before) at its lower
+// position, so the padding entries, which come last, never move down, and the
+// comparators that reach a position at or beyond kOrderThreadCap are left out:
+// 132 comparators. A row's loads are all issued before the network starts;
+// neighbouring threads hold neighbouring rows, so a warp's loads and stores
+// cover one contiguous stretch of the arrays.
+template <int a, int c>
+__device__ __forceinline__ void order_cswap(uint64_t (&kw)[kOrderThreadCap], int (&kc)[kOrderThreadCap]) {
+    const bool sw = order_before(kw[c], kc[c], kw[a], kc[a]);
+    const uint64_t wa = kw[a], wc = kw[c];
+    const int ca = kc[a], cc = kc[c];
+    kw[a] = sw ? wc : wa; kw[c] = sw ? wa : wc;
+    kc[a] = sw ? cc : ca; kc[c] = sw ? ca : cc;
+}
+
+// Comparator q of the odd-even merge network on 32 positions with every
+// comparator reaching kOrderThreadCap or beyond left out: its lower (first =
+// true) or upper position, and the number of comparators (q < 0).
+__host__ __device__ constexpr int order_net(int q, bool first) {
+    int m = 0;
+    for (int p = 1; p < 32; p <<= 1)
+        for (int k = p; k >= 1; k >>= 1)
+            for (int j = k % p; j + k < 32; j += 2 * k)
+                for (int i = 0; i < k; ++i) {
+                    const int a = i + j, c = i + j + k;
+                    if (c < kOrderThreadCap && a / (2 * p) == c / (2 * p)) {
+                        if (m == q) return first ? a : c;
+                        ++m;
+                    }
+                }
+    return m;
+}
+constexpr int kOrderNet = order_net(-1, true);
+static_assert(kOrderNet == 132, "odd-even merge network on 24 of 32 positions");
+
+template <int... Q>
+__device__ __forceinline__ void order_network(uint64_t (&kw)[kOrderThreadCap], int (&kc)[kOrderThreadCap],
+                                              std::integer_sequence<int, Q...>) {
+    (order_cswap<order_net(Q, true), order_net(Q, false)>(kw, kc), ...);
+}
+
+__global__ void __launch_bounds__(kBlock)
+    k_order_rows_thread(int n, const unsigned char* __restrict__ cls, const int* __restrict__ ptr,
+                        const int* __restrict__ col, const double* __restrict__ w, int* __restrict__ scol,
+                        double* __restrict__ sw) {
+    FOR_EACH(u64, n) {
+        const int u = (int)u64;
+        if (cls[u] != 0) continue;
+        const int b = ptr[u], len = ptr[u + 1] - b;
+        uint64_t kw[kOrderThreadCap];
+        int kc[kOrderThreadCap];
+#pragma unroll
+        for (int i = 0; i < kOrderThreadCap; ++i) {
+            kw[i] = 0ull;
+            kc[i] = INT_MAX;
+            if (i < len) {
+                kw[i] = (uint64_t)__double_as_longlong(__ldg(w + b + i));
+                kc[i] = __ldg(col + b + i);
+            }
+        }
+        order_network(kw, kc, std::make_integer_sequence<int, kOrderNet>{});
+#pragma unroll
+        for (int i = 0; i < kOrderThreadCap; ++i) {
+            if (i < len) {
+                scol[b + i] = kc[i];
+                sw[b + i] = __longlong_as_double((long long)kw[i]);
+            }
+        }
+    }
 }
 
 template <int R>
@@ -1487,6 +1565,9 @@ int32_t path_cover(Ctx& c, int32_t n, const Reweighted& t, int32_t* nbr0, int32_
     k_order_rows_classify<<<grid1(n), kBlock, 0, s>>>(n, t.ptr.p, is_long.p, long_list.p, long_count.p);
     ::pc::count_launches(1);
     PC_LAUNCH("order_rows");
+    k_order_rows_thread<<<grid1(n), kBlock, 0, s>>>(n, is_long.p, t.ptr.p, t.col.p, t.w.p, scol.p, sw.p);
+    ::pc::count_launches(1);
+    PC_LAUNCH("order_rows_thread");
     k_order_rows_warp<<<grid_warps(n), kWarpsPerBlock * 32, 0, s>>>(n, is_long.p, t.ptr.p, t.col.p, t.w.p,
                                                                      scol.p, sw.p);
     ::pc::count_launches(1);
