@@ -39,6 +39,62 @@ inline int grid_warps(int64_t rows) {
 
 #define FOR_EACH(i, n) for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
+// ---------------------------------------------------------------- small sorting network
+// Batcher's odd-even merge sort on 32 positions, every comparator putting the
+// element that comes first at its lower position. Padding that comes after
+// every element never moves down, so with the positions from kNet24 on holding
+// padding no comparator reaching them ever swaps, and they are left out: 132
+// comparators sort 24 positions (the pruned network sorts every 0-1 input of
+// length 24, checked exhaustively, hence every input). Held in a thread's
+// registers: once the comparators are template arguments every index is a
+// compile-time constant.
+constexpr int kNet24 = 24;
+// comparator q's lower (first = true) or upper position; for q < 0 the number
+// of comparators
+__host__ __device__ constexpr int net24(int q, bool first) {
+    int m = 0;
+    for (int p = 1; p < 32; p <<= 1)
+        for (int k = p; k >= 1; k >>= 1)
+            for (int j = k % p; j + k < 32; j += 2 * k)
+                for (int i = 0; i < k; ++i) {
+                    const int a = i + j, c = i + j + k;
+                    if (c < kNet24 && a / (2 * p) == c / (2 * p)) {
+                        if (m == q) return first ? a : c;
+                        ++m;
+                    }
+                }
+    return m;
+}
+constexpr int kNet24Size = net24(-1, true);
+static_assert(kNet24Size == 132, "odd-even merge network on 24 of 32 positions");
+
+// (w descending, column ascending): the proposal order of a row's candidates
+__device__ __forceinline__ bool order_before(uint64_t w1, int c1, uint64_t w2, int c2) {
+    return (w1 > w2) || (w1 == w2 && c1 < c2);
+}
+// proposal order: weight bits and column move together
+template <int a, int c>
+__device__ __forceinline__ void net_cswap(uint64_t (&kw)[kNet24], int (&kc)[kNet24]) {
+    const bool sw = order_before(kw[c], kc[c], kw[a], kc[a]);
+    const uint64_t wa = kw[a], wc = kw[c];
+    const int ca = kc[a], cc = kc[c];
+    kw[a] = sw ? wc : wa; kw[c] = sw ? wa : wc;
+    kc[a] = sw ? cc : ca; kc[c] = sw ? ca : cc;
+}
+// row products: ascending 32-bit keys, each with its value
+template <int a, int c>
+__device__ __forceinline__ void net_cswap(uint32_t (&key)[kNet24], double (&val)[kNet24]) {
+    const bool sw = key[c] < key[a];
+    const uint32_t ka = key[a], kc = key[c];
+    const double va = val[a], vc = val[c];
+    key[a] = sw ? kc : ka; key[c] = sw ? ka : kc;
+    val[a] = sw ? vc : va; val[c] = sw ? va : vc;
+}
+template <class K, class V, int... Q>
+__device__ __forceinline__ void net24_apply(K (&k)[kNet24], V (&v)[kNet24], std::integer_sequence<int, Q...>) {
+    (net_cswap<net24(Q, true), net24(Q, false)>(k, v), ...);
+}
+
 // ---------------------------------------------------------------- row products
 // Row u of the A^2 pattern: for j in row u of A (A holds its diagonal), for v in
 // row j: key v, skipping v == u.
@@ -355,6 +411,104 @@ __device__ __forceinline__ void hash_emit(int lane, int total, int D, WarpScratc
     }
 }
 
+// Rows of at most kThreadProdCap contributions from at most kThreadProdCap
+// member rows (every coarse row of P^T A P at a 3D 7-point grid's finest level:
+// two or three members of seven entries), a thread per row, into the one-pass
+// layout at tptr[r] (count in cnt, long flag cleared); every other row is
+// listed in wrows for the warp kernel. Columns must fit 24 bits (nrows <= 2^24). The contributions are numbered in their
+// fixed order (member rows one after another, each in CSR order) and keyed
+// column << 8 | e (columns below 2^24), sorted with their values by the
+// 24-position network, and each run of equal columns is added up in order:
+// the warp kernel's sums, bit for bit.
+constexpr int kThreadProdCap = kNet24;
+constexpr int64_t kThreadProdMean = 20;   // largest mean contributions per row for the thread kernel
+template <class Src>
+__global__ void __launch_bounds__(kBlock) k_rowprod_thread(int nrows, Src src, int* __restrict__ cnt,
+                                                           unsigned char* __restrict__ is_long,
+                                                           int* __restrict__ ocol, double* __restrict__ oval,
+                                                           const int64_t* __restrict__ tptr,
+                                                           int* __restrict__ wrows, int* __restrict__ wcount) {
+    constexpr uint32_t kPad = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;   // a multiple of 32: w0 is warp-uniform
+    for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; w0 < nrows; w0 += stride) {
+        const int64_t r64 = w0 + lane;
+        bool mine = false;
+        int r = 0, base = 0, nm = 0, total = 0;
+        if (r64 < nrows) {
+            r = (int)r64;
+            base = src.mbase(r);
+            nm = src.nmem(r);
+            if (nm <= kThreadProdCap) {
+                for (int t = 0; t < nm && total <= kThreadProdCap; ++t) {
+                    const int j = src.mem_at(base, t);
+                    total += src.in_end(j) - src.in_beg(j);
+                }
+                mine = total <= kThreadProdCap;
+            }
+        }
+        // the other rows are listed for the warp kernel (one atomic per warp)
+        const unsigned other = __ballot_sync(0xffffffffu, r64 < nrows && !mine);
+        if (other) {
+            int b = 0;
+            if (lane == 0) b = atomicAdd(wcount, __popc(other));
+            b = __shfl_sync(0xffffffffu, b, 0);
+            if ((other >> lane) & 1u) wrows[b + __popc(other & ((1u << lane) - 1u))] = r;
+        }
+        if (!mine) continue;
+        uint32_t key[kNet24];
+        double val[kNet24];
+        int t = -1, k = 0, kend = 0, j = 0;
+#pragma unroll
+        for (int e = 0; e < kNet24; ++e) {
+            key[e] = kPad;
+            val[e] = 0.0;
+            if (e < total) {
+                while (k == kend) {   // the next member row with entries left (e < total: one exists)
+                    ++t;
+                    j = src.mem_at(base, t);
+                    k = src.in_beg(j);
+                    kend = src.in_end(j);
+                }
+                uint32_t kk;
+                double v;
+                src.kv(r, j, k, kk, v);
+                ++k;
+                if (kk != kSkip) { key[e] = (kk << 8) | (uint32_t)e; val[e] = v; }
+            }
+        }
+        net24_apply(key, val, std::make_integer_sequence<int, kNet24Size>{});
+        const int64_t o = tptr[r];
+        int D = 0;
+        uint32_t cur = kPad;
+        double sum = 0.0;
+#pragma unroll
+        for (int e = 0; e < kNet24; ++e) {
+            if (key[e] != kPad) {
+                const uint32_t c = key[e] >> 8;
+                if (c != cur) {
+                    if (cur != kPad) {
+                        ocol[o + D] = (int)cur;
+                        if (oval) oval[o + D] = sum;
+                        ++D;
+                    }
+                    cur = c;
+                    sum = val[e];
+                } else {
+                    sum = __dadd_rn(sum, val[e]);
+                }
+            }
+        }
+        if (cur != kPad) {
+            ocol[o + D] = (int)cur;
+            if (oval) oval[o + D] = sum;
+            ++D;
+        }
+        cnt[r] = D;
+        is_long[r] = 0;
+    }
+}
+
 // MODE 0: count the row's distinct columns (cnt) and flag long rows;
 // MODE 1: write the row at optr[r] (counts known);
 // MODE 2: both at once -- count, flag, and write the row at tptr[r] of a
@@ -367,7 +521,8 @@ template <class Src, int MODE>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, 8) k_rowprod_warp(
         int nrows, Src src, int* __restrict__ cnt, unsigned char* __restrict__ is_long,
         int* __restrict__ long_list, int* __restrict__ long_count, const int* __restrict__ optr,
-        int* __restrict__ ocol, double* __restrict__ oval, const int64_t* __restrict__ tptr) {
+        int* __restrict__ ocol, double* __restrict__ oval, const int64_t* __restrict__ tptr,
+        const int* __restrict__ rows = nullptr, const int* __restrict__ rcount = nullptr) {
     constexpr bool FILL = MODE != 0;
     constexpr bool COUNT = MODE != 1;
     __shared__ WarpScratch ws_all[kWarpsPerBlock];
@@ -392,16 +547,19 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, 8) k_rowprod_warp(
     auto s3 = [&](Stage& q) {
         if (lane < q.nm && lane < 32) { q.mb = src.in_beg(q.mr); q.len = src.in_end(q.mr) - q.mb; }
     };
+    // the rows: all of them, or those listed (rows[0 .. *rcount))
+    const int64_t m = rows ? (int64_t)*rcount : (int64_t)nrows;
+    auto row_at = [&](int64_t q) -> int64_t { return q < m ? (rows ? (int64_t)rows[q] : q) : (int64_t)nrows; };
     Stage p1, p2, p3;
-    s1(gw, p3); s2(p3); s3(p3);
-    s1(gw + nw, p2); s2(p2);
-    s1(gw + 2 * nw, p1);
-    for (int64_t r64 = gw; r64 < nrows; r64 += nw) {
-        const int r = (int)r64;
+    s1(row_at(gw), p3); s2(p3); s3(p3);
+    s1(row_at(gw + nw), p2); s2(p2);
+    s1(row_at(gw + 2 * nw), p1);
+    for (int64_t q64 = gw; q64 < m; q64 += nw) {
+        const int r = (int)row_at(q64);
         const Stage cur = p3;
         p3 = p2; s3(p3);
         p2 = p1; s2(p2);
-        s1(r64 + 3 * nw, p1);
+        s1(row_at(q64 + 3 * nw), p1);
         if (MODE == 1 && is_long[r]) continue;
         const int nm = cur.nm;
         bool over = nm > kWarpMembers;
@@ -776,15 +934,32 @@ __device__ __forceinline__ bool edge_before(double w1, int a1, int b1, double w2
 // Class of every row for the proposal ordering: 0 = up to kOrderThreadCap
 // candidates, sorted by one thread; 1 = up to kOrderWarpCap, sorted by a warp;
 // 2 = longer, listed for a block each.
-constexpr int kOrderThreadCap = 24;   // every interior row of a 3D 7-point grid's A^2 pattern
+constexpr int kOrderThreadCap = kNet24;   // every interior row of a 3D 7-point grid's A^2 pattern
+// Class-1 rows are listed (in no particular order: each is sorted on its own)
+// for the warp kernel, one atomic per warp; class-2 rows for the block kernel.
 __global__ void k_order_rows_classify(int n, const int* __restrict__ ptr, unsigned char* __restrict__ cls,
+                                      int* __restrict__ mid_list, int* __restrict__ mid_count,
                                       int* __restrict__ long_list, int* __restrict__ long_count) {
-    FOR_EACH(u64, n) {
-        const int u = (int)u64;
-        const int len = ptr[u + 1] - ptr[u];
-        const bool big = len > kOrderWarpCap;
-        cls[u] = big ? 2 : (len <= kOrderThreadCap ? 0 : 1);
-        if (big) long_list[atomicAdd(long_count, 1)] = u;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;   // a multiple of 32: w0 is warp-uniform
+    for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; w0 < n; w0 += stride) {
+        const int64_t u64 = w0 + lane;
+        bool mid = false;
+        if (u64 < n) {
+            const int u = (int)u64;
+            const int len = ptr[u + 1] - ptr[u];
+            const bool big = len > kOrderWarpCap;
+            mid = !big && len > kOrderThreadCap;
+            cls[u] = big ? 2 : (mid ? 1 : 0);
+            if (big) long_list[atomicAdd(long_count, 1)] = u;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, mid);
+        if (m) {
+            int b = 0;
+            if (lane == 0) b = atomicAdd(mid_count, __popc(m));
+            b = __shfl_sync(0xffffffffu, b, 0);
+            if (mid) mid_list[b + __popc(m & ((1u << lane) - 1u))] = (int)u64;
+        }
     }
 }
 
@@ -797,55 +972,14 @@ __global__ void k_order_rows_classify(int n, const int* __restrict__ ptr, unsign
 // bits on the integer pipe (GB300's FP64 pipe issues a comparison at a small
 // fraction of the integer rate). Padding entries (bits 0, column INT_MAX) sort
 // last. Columns are distinct within a row, so the order is strict and the
-// result unique.
-__device__ __forceinline__ bool order_before(uint64_t w1, int c1, uint64_t w2, int c2) {
-    return (w1 > w2) || (w1 == w2 && c1 < c2);
-}
+// result unique (order_before).
 
-// Thread per row for rows of up to kOrderThreadCap entries (class 0): Batcher's
-// odd-even merge sort on 32 positions held in the thread's registers (every
-// index is a compile-time constant once the loops are unrolled). Every
-// comparator puts the element that comes first (order_before) at its lower
-// position, so the padding entries, which come last, never move down, and the
-// comparators that reach a position at or beyond kOrderThreadCap are left out:
-// 132 comparators. A row's loads are all issued before the network starts;
-// neighbouring threads hold neighbouring rows, so a warp's loads and stores
-// cover one contiguous stretch of the arrays.
-template <int a, int c>
-__device__ __forceinline__ void order_cswap(uint64_t (&kw)[kOrderThreadCap], int (&kc)[kOrderThreadCap]) {
-    const bool sw = order_before(kw[c], kc[c], kw[a], kc[a]);
-    const uint64_t wa = kw[a], wc = kw[c];
-    const int ca = kc[a], cc = kc[c];
-    kw[a] = sw ? wc : wa; kw[c] = sw ? wa : wc;
-    kc[a] = sw ? cc : ca; kc[c] = sw ? ca : cc;
-}
-
-// Comparator q of the odd-even merge network on 32 positions with every
-// comparator reaching kOrderThreadCap or beyond left out: its lower (first =
-// true) or upper position, and the number of comparators (q < 0).
-__host__ __device__ constexpr int order_net(int q, bool first) {
-    int m = 0;
-    for (int p = 1; p < 32; p <<= 1)
-        for (int k = p; k >= 1; k >>= 1)
-            for (int j = k % p; j + k < 32; j += 2 * k)
-                for (int i = 0; i < k; ++i) {
-                    const int a = i + j, c = i + j + k;
-                    if (c < kOrderThreadCap && a / (2 * p) == c / (2 * p)) {
-                        if (m == q) return first ? a : c;
-                        ++m;
-                    }
-                }
-    return m;
-}
-constexpr int kOrderNet = order_net(-1, true);
-static_assert(kOrderNet == 132, "odd-even merge network on 24 of 32 positions");
-
-template <int... Q>
-__device__ __forceinline__ void order_network(uint64_t (&kw)[kOrderThreadCap], int (&kc)[kOrderThreadCap],
-                                              std::integer_sequence<int, Q...>) {
-    (order_cswap<order_net(Q, true), order_net(Q, false)>(kw, kc), ...);
-}
-
+// Thread per row for rows of up to kOrderThreadCap entries (class 0), sorted
+// by the 24-position network in registers (every comparator puts the element
+// that comes first, order_before, at its lower position; padding entries come
+// last). A row's loads are all issued before the network starts; neighbouring
+// threads hold neighbouring rows, so a warp's loads and stores cover one
+// contiguous stretch of the arrays.
 __global__ void __launch_bounds__(kBlock)
     k_order_rows_thread(int n, const unsigned char* __restrict__ cls, const int* __restrict__ ptr,
                         const int* __restrict__ col, const double* __restrict__ w, int* __restrict__ scol,
@@ -865,7 +999,7 @@ __global__ void __launch_bounds__(kBlock)
                 kc[i] = __ldg(col + b + i);
             }
         }
-        order_network(kw, kc, std::make_integer_sequence<int, kOrderNet>{});
+        net24_apply(kw, kc, std::make_integer_sequence<int, kNet24Size>{});
 #pragma unroll
         for (int i = 0; i < kOrderThreadCap; ++i) {
             if (i < len) {
@@ -933,13 +1067,13 @@ __device__ __forceinline__ void order_row_regs(int lane, int b, int len, const i
 }
 
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-    k_order_rows_warp(int n, const unsigned char* __restrict__ cls, const int* __restrict__ ptr,
+    k_order_rows_warp(const int* __restrict__ rows, const int* __restrict__ count, const int* __restrict__ ptr,
                       const int* __restrict__ col, const double* __restrict__ w, int* __restrict__ scol,
                       double* __restrict__ sw) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    for (int64_t i = (int64_t)blockIdx.x * kWarpsPerBlock + wib; i < n; i += (int64_t)gridDim.x * kWarpsPerBlock) {
-        if (cls[i] != 1) continue;
-        const int u = (int)i;
+    const int m = *count;
+    for (int64_t i = (int64_t)blockIdx.x * kWarpsPerBlock + wib; i < m; i += (int64_t)gridDim.x * kWarpsPerBlock) {
+        const int u = rows[i];
         const int b = ptr[u], len = ptr[u + 1] - b;
         if (len <= 1) {
             if (len == 1 && lane == 0) { scol[b] = col[b]; sw[b] = w[b]; }
@@ -1453,8 +1587,27 @@ static void row_product(Ctx& c, int32_t nrows, const Src& src, DBuf<int32_t>& op
     const int64_t tot_ub = scan_i64(c, ubr.p, tptr.p, nrows);
     tcol.alloc(c.mem, std::max<int64_t>(tot_ub, 1));
     if (oval) tval.alloc(c.mem, std::max<int64_t>(tot_ub, 1));
+    // Short rows a thread each (columns in 24 bits), the others listed for the
+    // warp kernel, where the rows are short on average: the thread kernel is
+    // faster where nearly every row qualifies (the 256^3 grid's finest two
+    // levels, 13.8 and 18.9 contributions per row on average) and slower where
+    // half or fewer do (24.8 at the next level: the listing and the warp
+    // kernel's scattered row order cost more than the thread rows save).
+    // Either way the rows get the same entries, bit for bit.
+    const bool use_thread = nrows <= (1 << 24) && tot_ub <= kThreadProdMean * (int64_t)nrows;
+    DBuf<int32_t> wrows, wcount;
+    if (use_thread) {
+        wrows.alloc(c.mem, nrows);
+        wcount.alloc(c.mem, 1);
+        PC_CUDA(cudaMemsetAsync(wcount.p, 0, sizeof(int32_t), s));
+        k_rowprod_thread<Src><<<grid1(nrows), kBlock, 0, s>>>(nrows, src, cnt.p, is_long.p, tcol.p,
+                                                              oval ? tval.p : nullptr, tptr.p, wrows.p, wcount.p);
+        ::pc::count_launches(1);
+        PC_LAUNCH("rowprod_thread(once)");
+    }
     k_rowprod_warp<Src, 2><<<grid_warps(nrows), kWarpsPerBlock * 32, 0, s>>>(
-        nrows, src, cnt.p, is_long.p, long_list.p, long_count.p, nullptr, tcol.p, oval ? tval.p : nullptr, tptr.p);
+        nrows, src, cnt.p, is_long.p, long_list.p, long_count.p, nullptr, tcol.p, oval ? tval.p : nullptr, tptr.p,
+        use_thread ? wrows.p : nullptr, use_thread ? wcount.p : nullptr);
     ::pc::count_launches(1);
     PC_LAUNCH("rowprod_warp(once)");
     int32_t nlong = read_i32(c, long_count.p);
@@ -1553,23 +1706,25 @@ void build_candidates(Ctx& c, const double* e, Reweighted& out) {
 int32_t path_cover(Ctx& c, int32_t n, const Reweighted& t, int32_t* nbr0, int32_t* nbr1) {
     cudaStream_t s = c.stream;
     // rows in proposal order
-    DBuf<int32_t> scol, long_list, long_count;
+    DBuf<int32_t> scol, long_list, long_count, mid_list;
     DBuf<double> sw;
     DBuf<unsigned char> is_long;
     scol.alloc(c.mem, t.nnz);
     sw.alloc(c.mem, t.nnz);
     long_list.alloc(c.mem, n);
-    long_count.alloc(c.mem, 1);
+    mid_list.alloc(c.mem, n);
+    long_count.alloc(c.mem, 2);   // [0] class-2 rows, [1] class-1 rows
     is_long.alloc(c.mem, n);
-    PC_CUDA(cudaMemsetAsync(long_count.p, 0, sizeof(int32_t), s));
-    k_order_rows_classify<<<grid1(n), kBlock, 0, s>>>(n, t.ptr.p, is_long.p, long_list.p, long_count.p);
+    PC_CUDA(cudaMemsetAsync(long_count.p, 0, 2 * sizeof(int32_t), s));
+    k_order_rows_classify<<<grid1(n), kBlock, 0, s>>>(n, t.ptr.p, is_long.p, mid_list.p, long_count.p + 1,
+                                                      long_list.p, long_count.p);
     ::pc::count_launches(1);
     PC_LAUNCH("order_rows");
     k_order_rows_thread<<<grid1(n), kBlock, 0, s>>>(n, is_long.p, t.ptr.p, t.col.p, t.w.p, scol.p, sw.p);
     ::pc::count_launches(1);
     PC_LAUNCH("order_rows_thread");
-    k_order_rows_warp<<<grid_warps(n), kWarpsPerBlock * 32, 0, s>>>(n, is_long.p, t.ptr.p, t.col.p, t.w.p,
-                                                                     scol.p, sw.p);
+    k_order_rows_warp<<<grid_warps(n), kWarpsPerBlock * 32, 0, s>>>(mid_list.p, long_count.p + 1, t.ptr.p,
+                                                                     t.col.p, t.w.p, scol.p, sw.p);
     ::pc::count_launches(1);
     PC_LAUNCH("order_rows_warp");
     const int32_t nbig = read_i32(c, long_count.p);
