@@ -13,6 +13,7 @@
 #include <type_traits>
 #include <cstring>
 
+#include "net24.cuh"
 #include "pcamg_internal.cuh"
 
 namespace pc {
@@ -40,33 +41,8 @@ inline int grid_warps(int64_t rows) {
 #define FOR_EACH(i, n) for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
 // ---------------------------------------------------------------- small sorting network
-// Batcher's odd-even merge sort on 32 positions, every comparator putting the
-// element that comes first at its lower position. Padding that comes after
-// every element never moves down, so with the positions from kNet24 on holding
-// padding no comparator reaching them ever swaps, and they are left out: 132
-// comparators sort 24 positions (the pruned network sorts every 0-1 input of
-// length 24, checked exhaustively, hence every input). Held in a thread's
-// registers: once the comparators are template arguments every index is a
-// compile-time constant.
-constexpr int kNet24 = 24;
-// comparator q's lower (first = true) or upper position; for q < 0 the number
-// of comparators
-__host__ __device__ constexpr int net24(int q, bool first) {
-    int m = 0;
-    for (int p = 1; p < 32; p <<= 1)
-        for (int k = p; k >= 1; k >>= 1)
-            for (int j = k % p; j + k < 32; j += 2 * k)
-                for (int i = 0; i < k; ++i) {
-                    const int a = i + j, c = i + j + k;
-                    if (c < kNet24 && a / (2 * p) == c / (2 * p)) {
-                        if (m == q) return first ? a : c;
-                        ++m;
-                    }
-                }
-    return m;
-}
-constexpr int kNet24Size = net24(-1, true);
-static_assert(kNet24Size == 132, "odd-even merge network on 24 of 32 positions");
+// The comparators of the 24-position network (net24.cuh) applied to two
+// register arrays: the keys and what moves with them.
 
 // (w descending, column ascending): the proposal order of a row's candidates
 __device__ __forceinline__ bool order_before(uint64_t w1, int c1, uint64_t w2, int c2) {
