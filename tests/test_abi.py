@@ -57,3 +57,15 @@ def test_struct_layout_matches_header(built):
     fields = re.findall(r"\b(?:double|int32_t|uint64_t|pcamg_mpnn)\s+([\w\s,]+);", body)
     names = [f.strip() for grp in fields for f in grp.split(",")]
     assert names == [f for f, _ in N.Params._fields_]
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # no CPU fallback: without the built library the first call raises
+    from paper_1806_07028_gb300 import native as N
+    monkeypatch.setattr(N, "LIB_PATH", str(tmp_path / "libpcamg.so"))
+    monkeypatch.setattr(N, "_lib", None)
+    with pytest.raises(N.NativeLibraryMissing):
+        N.lib()
+    from paper_1806_07028_gb300 import solver
+    with pytest.raises(N.NativeLibraryMissing):
+        solver.default_params()
